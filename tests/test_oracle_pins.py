@@ -1,0 +1,338 @@
+"""Pins of the CPU oracle against things other than itself (CPU only).
+
+Each pin ties the oracle to mathematics it does not contain: the analytic radial functions
+behind the tables, closed-form spherical harmonics and their quadrature, continuum
+two-centre integrals done by adaptive quadrature, the Fourier coefficient of phi^2 for a
+plane-wave potential, exact symmetries of the grid sum, and central finite differences.
+References are to the paper's Sec. IV (NAO basis, grid integration, forces).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, special
+
+from oracle import Oracle
+from paper_2501_08697_gb300 import synth as S
+
+SI_TAB = S.species_tables(S.SI)
+C0 = 0.5 / math.sqrt(math.pi)
+C1 = math.sqrt(3 / (4 * math.pi))
+C20 = math.sqrt(5 / (16 * math.pi))
+C21 = math.sqrt(15 / (4 * math.pi))
+C22 = math.sqrt(15 / (16 * math.pi))
+
+
+def _analytic_df(spec, irad, r):
+    l, a = spec.radials[irad]
+    N = S.radial_norm(l, a, spec.rcut)
+    rc = spec.rcut
+    x = 1 - (r / rc) ** 2
+    e = np.exp(-a * r * r)
+    rl = r ** l
+    drl = l * r ** (l - 1) if l > 0 else 0.0 * r
+    return N * (drl * e * x ** 3 - 2 * a * r * rl * e * x ** 3 + rl * e * 3 * x ** 2 * (-2 * r / rc ** 2))
+
+
+def _one_atom(L, N, pos, tab=SI_TAB):
+    L = np.broadcast_to(np.asarray(L, float), (3,))
+    N = np.broadcast_to(np.asarray(N, int), (3,))
+    return Oracle(np.diag(L), [0], np.array([pos], float), [tab], tuple(N))
+
+
+def _block(o, H, key):
+    keys, offs = o.pairs()
+    idx = np.nonzero((keys == np.array(key)).all(1))[0]
+    assert len(idx) == 1, key
+    b = idx[0]
+    nI = o.norb_atom[key[0]]
+    return H[offs[b]:offs[b + 1]].reshape(nI, -1)
+
+
+# ----------------------------------------------------------------------------- radial spline
+@pytest.mark.parametrize("spec", [S.SI, S.O, S.H])
+def test_spline_matches_analytic_radial(spec):
+    """Clamped cubic spline through f(r_i) reproduces the analytic radial within the
+    O(dr^4) interpolation bound, and its derivative within O(dr^3)."""
+    tab = S.species_tables(spec)
+    o = _one_atom(12.0, 8, [0, 0, 0], tab)
+    rng = np.random.default_rng(1)
+    r = rng.uniform(0, spec.rcut, 400)
+    for ir in range(len(spec.radials)):
+        f = S.radial_analytic(spec, ir, r)
+        df = _analytic_df(spec, ir, r)
+        got = np.array([o.radial(0, ir, x) for x in r])
+        scale = np.abs(f).max()
+        assert np.abs(got[:, 0] - f).max() < 5e-9 * scale
+        assert np.abs(got[:, 1] - df).max() < 2e-6 * np.abs(df).max()
+        # outside the cutoff the function and its slope vanish
+        assert o.radial(0, ir, spec.rcut) == (0.0, 0.0)
+        assert o.radial(0, ir, spec.rcut + 1.0) == (0.0, 0.0)
+
+
+# ----------------------------------------------------------------------------- spherical harmonics
+def _ylm_from_phi(o, u, r=1.3):
+    """Y_lm(u) recovered as phi(r u) / f(r) for each radial of Si (l = 0,0,1,1,2)."""
+    phi = o.phi(0, r * np.asarray(u, float))
+    f = [o.radial(0, ir, r)[0] for ir in range(5)]
+    return np.concatenate([phi[0:1] / f[0], phi[2:5] / f[2], phi[8:13] / f[4]])
+
+
+def test_ylm_orthonormal_on_sphere():
+    o = _one_atom(12.0, 8, [0, 0, 0])
+    xg, wg = np.polynomial.legendre.leggauss(16)
+    nphi = 32
+    A = np.zeros((9, 9))
+    for ct, w in zip(xg, wg):
+        st = math.sqrt(1 - ct * ct)
+        for k in range(nphi):
+            ph = 2 * math.pi * k / nphi
+            y = _ylm_from_phi(o, [st * math.cos(ph), st * math.sin(ph), ct])
+            A += w * (2 * math.pi / nphi) * np.outer(y, y)
+    assert np.abs(A - np.eye(9)).max() < 1e-12
+
+
+def test_ylm_convention_values():
+    """Ordering m = 0,+1,-1,+2,-2 and no Condon-Shortley phase: l=1 is c (z, x, y)."""
+    o = _one_atom(12.0, 8, [0, 0, 0])
+    s = 1 / math.sqrt(2)
+    #        s    p0       p+1      p-1      d0         d+1      d-1      d+2       d-2
+    cases = {
+        (1, 0, 0): [C0, 0, C1, 0, -C20, 0, 0, C22, 0],
+        (0, 1, 0): [C0, 0, 0, C1, -C20, 0, 0, -C22, 0],
+        (0, 0, 1): [C0, C1, 0, 0, 2 * C20, 0, 0, 0, 0],
+        (s, s, 0): [C0, 0, C1 * s, C1 * s, -C20, 0, 0, 0, C21 / 2],
+        (s, 0, s): [C0, C1 * s, C1 * s, 0, C20 / 2, C21 / 2, 0, C22 / 2, 0],
+        (0, s, s): [C0, C1 * s, 0, C1 * s, C20 / 2, 0, C21 / 2, -C22 / 2, 0],
+    }
+    for u, want in cases.items():
+        y = _ylm_from_phi(o, u)
+        assert np.allclose(y, np.array(want), rtol=0, atol=1e-13), (u, y, want)
+
+
+# ----------------------------------------------------------------------------- orbital gradient
+def test_phi_gradient_matches_finite_difference():
+    o = _one_atom(12.0, 8, [0, 0, 0])
+    rng = np.random.default_rng(2)
+    h = 1e-6
+    for _ in range(20):
+        d = rng.normal(size=3)
+        d *= rng.uniform(0.2, 6.5) / np.linalg.norm(d)
+        _, g = o.phi(0, d, grad=True)
+        fd = np.zeros_like(g)
+        for c in range(3):
+            e = np.zeros(3)
+            e[c] = h
+            fd[:, c] = (o.phi(0, d + e) - o.phi(0, d - e)) / (2 * h)
+        assert np.abs(g - fd).max() < 1e-7 * max(1.0, np.abs(g).max())
+
+
+def test_phi_at_centre_limits():
+    """At r = 0: phi = f(0) Y00 for s, 0 otherwise; grad phi = f'(0) c1 e_m for p."""
+    o = _one_atom(12.0, 8, [0, 0, 0])
+    phi, g = o.phi(0, np.zeros(3), grad=True)
+    f0 = [o.radial(0, ir, 0.0) for ir in range(5)]
+    assert phi[0] == pytest.approx(f0[0][0] * C0, rel=1e-14)
+    assert phi[1] == pytest.approx(f0[1][0] * C0, rel=1e-14)
+    assert np.all(phi[2:] == 0)
+    for ir, base in ((2, 2), (3, 5)):
+        df0 = f0[ir][1]
+        assert df0 == pytest.approx(SI_TAB.dfdr0[ir], rel=1e-12)
+        want = np.array([[0, 0, df0 * C1], [df0 * C1, 0, 0], [0, df0 * C1, 0]])
+        assert np.allclose(g[base:base + 3], want, rtol=1e-12, atol=0)
+        # continuity: the limit agrees with a central difference through the centre
+        for m, axis in enumerate((2, 0, 1)):
+            e = np.zeros(3)
+            e[axis] = 1e-5
+            fd = (o.phi(0, e)[base + m] - o.phi(0, -e)[base + m]) / 2e-5
+            assert fd == pytest.approx(want[m, axis], rel=1e-6)
+    assert np.all(g[0:2] == 0) and np.all(g[8:] == 0)
+
+
+# ----------------------------------------------------------------------------- grid quadrature
+def test_normalisation_as_grid_refines():
+    """V = 1, one atom: the diagonal of the on-site block is the grid quadrature of
+    int phi^2 = 1 (unit-normalised radials, orthonormal Y_lm)."""
+    for N in (24, 36, 48):
+        o = _one_atom(10.26, N, [1.0, 2.0, 3.0])
+        H = o.vlocal(np.ones(N ** 3))
+        blk = _block(o, H, (0, 0, 0, 0, 0))
+        err = np.abs(np.diag(blk) - 1).max()
+        assert err < (1e-6 if N == 24 else 1e-9)
+        # different (l, m) on one centre are orthogonal in the continuum
+        lm = [(0, 0), (0, 0), (1, 0), (1, 1), (1, -1), (1, 0), (1, 1), (1, -1), (2, 0), (2, 1), (2, -1), (2, 2), (2, -2)]
+        for a in range(13):
+            for b in range(13):
+                if lm[a] != lm[b]:
+                    assert abs(blk[a, b]) < 1e-9
+
+
+def test_onsite_orthogonality_is_exact_on_cubic_grid():
+    """Atom on a grid point of a cubic grid: the grid has the cube's symmetry, so overlaps of
+    harmonics of different (l, m) vanish to rounding."""
+    N = 32
+    o = _one_atom(10.26, N, [0.0, 0.0, 0.0])
+    H = o.vlocal(np.ones(N ** 3))
+    blk = _block(o, H, (0, 0, 0, 0, 0))
+    lm = [(0, 0), (0, 0), (1, 0), (1, 1), (1, -1), (1, 0), (1, 1), (1, -1), (2, 0), (2, 1), (2, -1), (2, 2), (2, -2)]
+    off = [abs(blk[a, b]) for a in range(13) for b in range(13) if lm[a] != lm[b]]
+    assert max(off) < 1e-14
+    assert np.allclose(blk, blk.T, atol=1e-15)
+
+
+def _gl_composite(a, b, npan, order=8):
+    x, w = np.polynomial.legendre.leggauss(order)
+    edges = np.linspace(a, b, npan + 1)
+    h = (edges[1:] - edges[:-1])[:, None]
+    mid = (edges[1:] + edges[:-1])[:, None] / 2
+    return (mid + h / 2 * x).ravel(), (h / 2 * w).ravel()
+
+
+def _two_centre(g1, g2, d, rc=7.0):
+    """Continuum integral of g1 about the origin times g2 about d z_hat, both axially
+    symmetric, in prolate spheroidal coordinates lambda = (r1+r2)/d, mu = (r1-r2)/d
+    (dV = d^3/8 (lambda^2 - mu^2) dlambda dmu dphi), composite Gauss-Legendre."""
+    lam, wl = _gl_composite(1.0, 2 * rc / d, 400)
+    mu, wm = _gl_composite(-1.0, 1.0, 200)
+    L, M = np.meshgrid(lam, mu, indexing="ij")
+    W = np.outer(wl, wm)
+    r1 = d * (L + M) / 2
+    r2 = d * (L - M) / 2
+    cos1 = (1 + L * M) / (L + M)
+    cos2 = (L * M - 1) / (L - M)
+    return float((W * g1(r1, cos1) * g2(r2, cos2) * (d ** 3 / 8) * (L * L - M * M)).sum() * 2 * math.pi)
+
+
+def test_two_centre_overlaps_match_continuum():
+    """Block (0,1,R=0) with V = 1 is the two-centre overlap of Sec. IV.B's template, centre J
+    at tau_I + d z_hat.  Signs pin which centre is which and that blocks are not transposed."""
+    d = 2.5
+    N = 64
+    o = Oracle(np.diag([10.26] * 3), [0, 0], np.array([[1.0, 2.0, 3.0], [1.0, 2.0, 3.0 + d]]), [SI_TAB], (N, N, N))
+    H = o.vlocal(np.ones(N ** 3))
+    blk = _block(o, H, (0, 1, 0, 0, 0))
+    blkT = _block(o, H, (1, 0, 0, 0, 0))
+
+    def s(ir):
+        return lambda r, c: S.radial_analytic(S.SI, ir, r) * C0
+
+    def pz(ir):
+        return lambda r, c: S.radial_analytic(S.SI, ir, r) * C1 * c
+
+    def dz2():
+        return lambda r, c: S.radial_analytic(S.SI, 4, r) * C20 * (3 * c * c - 1)
+
+    cases = [((0, 0), s(0), s(0)), ((2, 0), pz(2), s(0)), ((0, 2), s(0), pz(2)),
+             ((2, 2), pz(2), pz(2)), ((8, 1), dz2(), s(1)), ((5, 5), pz(3), pz(3))]
+    for (mu, nu), g1, g2 in cases:
+        want = _two_centre(g1, g2, d)
+        assert blk[mu, nu] == pytest.approx(want, abs=1e-9), (mu, nu)
+        assert blkT[nu, mu] == pytest.approx(want, abs=1e-9)
+    assert blk[2, 0] > 0 > blk[0, 2]
+
+
+def test_plane_wave_potential_fourier_coefficient():
+    """One s orbital, V = -1 + 0.5 cos(G.r + theta) with G a reciprocal-lattice vector of an
+    orthorhombic cell: H_ss = -1 + 0.5 cos(G.tau + theta) F(|G|), F(k) = int f^2 r^2 j0(kr) dr."""
+    L = np.array([10.0, 11.0, 12.0])
+    N = np.array([48, 52, 56])
+    tau = np.array([1.3, 2.7, 4.1])
+    o = _one_atom(L, N, tau)
+    n = np.array([1, -2, 3])
+    theta = 0.7
+    i, j, k = np.meshgrid(np.arange(N[0]) / N[0], np.arange(N[1]) / N[1], np.arange(N[2]) / N[2], indexing="ij")
+    V = -1 + 0.5 * np.cos(2 * math.pi * (n[0] * i + n[1] * j + n[2] * k) + theta)
+    H = o.vlocal(V.reshape(-1))
+    blk = _block(o, H, (0, 0, 0, 0, 0))
+    G = 2 * math.pi * n / L
+    kk = np.linalg.norm(G)
+    for ir, mu in ((0, 0), (1, 1)):
+        F, _ = integrate.quad(lambda r: S.radial_analytic(S.SI, ir, r) ** 2 * r * r * special.spherical_jn(0, kk * r),
+                              0, 7.0, epsabs=1e-14, epsrel=1e-12, limit=200)
+        want = -1 + 0.5 * math.cos(G @ tau + theta) * F
+        assert blk[mu, mu] == pytest.approx(want, abs=1e-9)
+
+
+# ----------------------------------------------------------------------------- invariants
+@pytest.fixture(scope="module")
+def si8_small():
+    st = S.si_diamond((1, 1, 1), grid=(32, 32, 32), sigma=0.05, seed=S.BASE_SEED + 91)
+    o = Oracle.from_structure(st)
+    keys, offs = o.pairs()
+    V = S.local_potential(st)
+    DM = S.density_matrix(keys, st.norb_atom, seed=st.seed)
+    H = o.vlocal(V)
+    return st, o, keys, offs, V, DM, H
+
+
+def test_h_block_symmetry(si8_small):
+    st, o, keys, offs, V, DM, H = si8_small
+    part = S.partner_index(keys)
+    for b in range(len(keys)):
+        A = H[offs[b]:offs[b + 1]].reshape(o.norb_atom[keys[b, 0]], -1)
+        B = H[offs[part[b]]:offs[part[b] + 1]].reshape(o.norb_atom[keys[part[b], 0]], -1)
+        assert np.allclose(A, B.T, rtol=0, atol=1e-14)
+
+
+def test_linearity_and_constant_potential(si8_small):
+    st, o, keys, offs, V, DM, H = si8_small
+    Sg = o.vlocal(np.ones(st.npts))
+    H2 = o.vlocal(2.0 * V - 3.0)
+    assert np.abs(H2 - (2 * H - 3 * Sg)).max() < 1e-13 * np.abs(H).max() * 10
+    Hc = o.vlocal(np.full(st.npts, -0.37))
+    assert np.abs(Hc + 0.37 * Sg).max() < 1e-15 * 100
+
+
+def test_adjoint_and_charge_identities(si8_small):
+    """<rho(r), V(r)> dV = <rho_mu,nu, V_mu,nu>  and  Sum_r rho dV = <rho_mu,nu, S_mu,nu>
+    (the energy term int V_local rho of Eq. lcao_etot2 computed two ways)."""
+    st, o, keys, offs, V, DM, H = si8_small
+    rho = o.rho(DM)
+    lhs = (rho * V.reshape(-1)).sum() * st.dV
+    rhs = (DM * H).sum()
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+    Sg = o.vlocal(np.ones(st.npts))
+    assert rho.sum() * st.dV == pytest.approx((DM * Sg).sum(), rel=1e-12)
+
+
+def test_translation_by_grid_vector(si8_small):
+    st, o, keys, offs, V, DM, H = si8_small
+    shift = np.array([3, -5, 7])
+    t = (shift / np.array(st.grid)) @ st.cell
+    o2 = Oracle(st.cell, st.species, st.tau + t, st.tables, st.grid)
+    V2 = np.roll(V, shift=tuple(shift), axis=(0, 1, 2))
+    k2, _ = o2.pairs()
+    assert np.array_equal(k2, keys)
+    H2 = o2.vlocal(V2)
+    assert np.abs(H2 - H).max() < 1e-12 * np.abs(H).max()
+
+
+def test_force_matches_central_differences(si8_small):
+    """The Pulay term: dL/dtau from grad phi equals central differences (h = 1e-4 bohr) of
+    L = <rho_mu,nu, V_mu,nu(tau)> with rho_mu,nu and V(r) fixed."""
+    st, o, keys, offs, V, DM, H = si8_small
+    g = o.dLdtau(V, DM)
+    h = 1e-4
+    for atom in (0, 5):
+        for c in range(3):
+            Ls = []
+            for sgn in (1, -1):
+                tau = st.tau.copy()
+                tau[atom, c] += sgn * h
+                o2 = Oracle(st.cell, st.species, tau, st.tables, st.grid)
+                k2, _ = o2.pairs()
+                assert np.array_equal(k2, keys)
+                Ls.append((DM * o2.vlocal(V)).sum())
+            fd = (Ls[0] - Ls[1]) / (2 * h)
+            assert fd == pytest.approx(g[atom, c], rel=1e-6, abs=1e-9 * np.abs(g).max())
+    assert np.allclose(o.force(V, DM), -g)
+
+
+def test_density_matrix_generator_is_block_symmetric(si8_small):
+    st, o, keys, offs, V, DM, H = si8_small
+    part = S.partner_index(keys)
+    for b in range(0, len(keys), 7):
+        A = DM[offs[b]:offs[b + 1]].reshape(o.norb_atom[keys[b, 0]], -1)
+        B = DM[offs[part[b]]:offs[part[b] + 1]].reshape(o.norb_atom[keys[part[b], 0]], -1)
+        assert np.array_equal(A, B.T)
+        assert np.abs(A).max() <= 0.1

@@ -1,0 +1,192 @@
+/*
+ * gint — real-space grid integration for LCAO (numerical atomic orbital) Kohn-Sham DFT on
+ * one NVIDIA GB300 (sm_103a).  C ABI: plain pointers and sizes, no C++ or framework types.
+ *
+ * What is computed (paper: "ABACUS: An Electronic Structure Analysis Package for the AI
+ * Era", Sec. IV.A-D):
+ *   basis     phi_mu(r) = f_{zeta l}(|r - tau_I|) Y_lm(r_hat): a strictly localised radial
+ *             function times a real spherical harmonic (Sec. IV.A; the same "radial times
+ *             spherical harmonic" form the paper states for projectors and auxiliary functions).
+ *   vlocal    V_mu,nu(R) = Sum_r phi_mu(r - tau_I) V(r) phi_nu(r - tau_J - R) dV — the
+ *             two-centre template O_mu,nu(R) of Sec. IV.B with a multiplicative local
+ *             operator, evaluated on the uniform real-space grid ("grid integration", Sec. IV.B),
+ *             stored in a sparse block container (the paper's HContainer, Fig. 2 caption).
+ *   rho       rho(r) = Sum_R Sum_mu,nu rho_mu,nu(R) phi_mu(r) phi_nu(r - R), the real-space
+ *             density from the density matrix of Eq. (density_matrix), Sec. IV.B; it is the
+ *             adjoint of vlocal: <rho(r), V(r)> dV = Sum rho_mu,nu V_mu,nu (Eq. lcao_etot2).
+ *   force     the basis-motion (Pulay) term of Eq. (force_lcao), Sec. IV.D, for
+ *             L = Sum_blocks Sum_mu,nu rho_mu,nu(R) V_mu,nu(R) with V(r) held fixed:
+ *             F_I = -dL/dtau_I.
+ *
+ * Conventions.
+ *   cell      rows a1, a2, a3 (bohr), row-major double[9].
+ *   grid      N1 x N2 x N3; point (i,j,k) sits at r = (i/N1) a1 + (j/N2) a2 + (k/N3) a3; grid
+ *             arrays (V, rho) are double, C order (i, j, k) with k fastest; dV = |det A|/(N1 N2 N3).
+ *   atoms     tau is Cartesian (bohr) and used as given (it need not lie inside the cell).
+ *   orbitals  per species: radial functions in the order given, each with 2l+1 real harmonics
+ *             ordered m = 0, +1, -1, +2, -2 (no Condon-Shortley phase; l = 1 is
+ *             sqrt(3/4pi) (z, x, y)/r); l <= 2.  Radials are clamped cubic splines through the
+ *             table f(i*dr), end slopes f'(0) (given) and 0 at the last knot, and f = 0 for
+ *             r >= rcut.  At r = 0 the orbital takes its limit (f(0) Y_00 for l = 0, else 0).
+ *   blocks    a block key (I, J, n1, n2, n3) couples phi centred at tau_I with phi centred at
+ *             tau_J + n1 a1 + n2 a2 + n3 a3; it exists iff that distance is below
+ *             rcut_I + rcut_J.  Keys are sorted by (I, J, n1, n2, n3); block b holds
+ *             norb_I x norb_J doubles, row-major, at offsets[b].  H and the density matrix
+ *             use this layout.  The partner of (I,J,R) is (J,I,-R); V_mu,nu(R) = V_nu,mu(-R).
+ *
+ * Execution and errors.  Every compute call is asynchronous on the given CUDA stream
+ * (a cudaStream_t passed as void*; NULL = legacy default stream) and reads/writes only
+ * caller-owned device buffers plus library-owned memory created in gint_setup.  Inputs are
+ * validated on the host before any launch; a failed validation returns GINT_EINVAL and
+ * launches nothing.  Kernels bound every wait; a wait that runs out records GINT_ETIMEOUT in
+ * a device status word that gint_get_status() reads.  There is no CPU fallback: without a usable
+ * sm_103a device gint_setup returns GINT_ECUDA.  gint_last_error() gives a message for the
+ * last failing call on the calling thread.
+ */
+#ifndef GINT_H
+#define GINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gint_handle_s *gint_handle;
+
+typedef enum {
+    GINT_OK = 0,
+    GINT_EINVAL = 1,    /* bad argument: null pointer, size, shape, l > 2, limits */
+    GINT_ENOMEM = 2,    /* device or host allocation failed */
+    GINT_ECUDA = 3,     /* CUDA runtime error or no sm_103a device */
+    GINT_ETIMEOUT = 4,  /* a kernel gave up on a bounded wait (device status word) */
+    GINT_ESTATE = 5     /* call not valid for this handle's state (e.g. topology changed) */
+} gint_status;
+
+/* Arithmetic of the per-batch contraction.  Orbital values, the contraction and the
+ * per-batch partial sums use the named precision; the accumulation across batches into the
+ * block store, rho(r) and the forces is FP64 in every mode.
+ *   GINT_FP64    FP64 CUDA-core FMA throughout (orbitals evaluated in FP64).
+ *   GINT_FP32    FP32 CUDA-core FMA (orbitals in FP32).
+ *   GINT_TF32X3  tcgen05 tensor cores, kind::tf32, each FP32 operand split hi+lo and
+ *                hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory.
+ *   GINT_BF16X3  tcgen05 kind::f16 with bf16 hi+lo splits, 3 products (about 16 bits).
+ *   GINT_BF16X6  tcgen05 kind::f16 with bf16 hi+mid+lo splits, the 6 products of order <= 2. */
+typedef enum {
+    GINT_FP64 = 0,
+    GINT_FP32 = 1,
+    GINT_TF32X3 = 2,
+    GINT_BF16X3 = 3,
+    GINT_BF16X6 = 4
+} gint_prec;
+
+/* One atomic species.  All pointers are host memory, read during gint_setup only. */
+typedef struct {
+    int nrad;              /* number of radial functions, 1..16 */
+    const int *l;          /* [nrad] angular momentum of each radial, 0..2 */
+    double rcut;           /* cutoff radius (bohr), > 0 */
+    double dr;             /* table spacing (bohr), > 0 */
+    int ntab;              /* knots per radial; (ntab-1)*dr must reach rcut */
+    const double *ftab;    /* [nrad * ntab] f(i*dr), radial-major */
+    const double *dfdr0;   /* [nrad] slope f'(0) of each radial */
+} gint_species;
+
+typedef struct {
+    int batch[3];          /* grid points per batch along a1, a2, a3 (default 4, 4, 8);
+                              batches whose orbital count exceeds the kernel limits are split */
+    int reserved[5];
+} gint_options;
+
+/* Sizes of a handle (host values). */
+typedef struct {
+    int64_t npts;          /* N1*N2*N3 */
+    int64_t nblocks;       /* blocks in the store */
+    int64_t nvalues;       /* doubles in the store */
+    int64_t nbatches;      /* grid batches */
+    int64_t nslots;        /* (batch, atom image) pairs */
+    int max_orbitals;      /* largest per-batch orbital count */
+    int max_slots;         /* largest per-batch atom-image count */
+    double dV;             /* volume element */
+    double flops_useful;   /* 2 * Sum_r n(r)^2: one vlocal contraction, n(r) = orbitals at r */
+    double flops_dense;    /* 2 * Sum_b npts_b * nb_b^2: the dense per-batch contraction */
+} gint_info_t;
+
+/* Build a handle: validates the inputs, fits the radial splines, finds the block list
+ * (Sec. IV.B: pairs (I, J, R) over all valid neighbouring cells) and the batch -> atom-image
+ * lists (strict locality of NAOs, Sec. IV.A), and uploads them to the current device.
+ * natoms >= 1, nspecies >= 1, species[i] in [0, nspecies), grid[i] >= 1; opt may be NULL.
+ * All pointers are host memory.  On success *out owns device memory until gint_destroy. */
+gint_status gint_setup(gint_handle *out, const double cell[9], int natoms, const int *species,
+                       const double *tau, int nspecies, const gint_species *sp,
+                       const int grid[3], const gint_options *opt);
+
+/* Release everything the handle owns.  NULL is accepted. */
+gint_status gint_destroy(gint_handle h);
+
+/* Read-only host view of the block layout: keys[5*b .. 5*b+4] = (I, J, n1, n2, n3),
+ * offsets[b] (nblocks+1 entries, offsets[nblocks] = nvalues).  Valid until gint_destroy or
+ * gint_update_positions. */
+gint_status gint_block_layout(gint_handle h, int64_t *nblocks, int64_t *nvalues,
+                              const int32_t **keys, const int64_t **offsets);
+
+gint_status gint_get_info(gint_handle h, gint_info_t *info);
+
+/* Move the atoms (host tau, natoms*3).  If the block list and every batch's atom-image list
+ * are unchanged, only positions are updated (no reallocation).  Otherwise nothing changes
+ * and GINT_ESTATE is returned: build a new handle. */
+gint_status gint_update_positions(gint_handle h, const double *tau);
+
+/* H <- V_mu,nu(R) for the potential V (device, npts doubles).  H (device, nvalues doubles)
+ * is overwritten; both halves of every partner pair are written. */
+gint_status gint_vlocal(gint_handle h, const double *V_dev, double *H_dev, gint_prec prec,
+                        void *stream);
+
+/* rho (device, npts doubles) <- rho(r) from the density matrix DM (device, block layout).
+ * Only the block-symmetric part of DM contributes. */
+gint_status gint_rho(gint_handle h, const double *DM_dev, double *rho_dev, gint_prec prec,
+                     void *stream);
+
+/* F (device, natoms*3 doubles) <- F_I = -dL/dtau_I, L = Sum DM_mu,nu V_mu,nu(R), for V
+ * (device, npts) and DM (device, block layout).  DM is symmetrised in the block sense first
+ * (into library-owned scratch), so any DM is accepted. */
+gint_status gint_force(gint_handle h, const double *V_dev, const double *DM_dev, double *F_dev,
+                       gint_prec prec, void *stream);
+
+/* rho and F from one pass over the grid (the backward of vlocal); either output may be NULL. */
+gint_status gint_rho_force(gint_handle h, const double *V_dev, const double *DM_dev,
+                           double *rho_dev, double *F_dev, gint_prec prec, void *stream);
+
+/* out[0] (device double) <- Sum_r rho(r) dV, summed in FP64 on the device. */
+gint_status gint_charge(gint_handle h, const double *rho_dev, double *out_dev, void *stream);
+
+/* out[0] (device double) <- Sum_i A[i] B[i] over the block store (e.g. Tr(rho S),
+ * <rho_mu,nu, V_mu,nu>), FP64 on the device. */
+gint_status gint_block_dot(gint_handle h, const double *A_dev, const double *B_dev,
+                           double *out_dev, void *stream);
+
+/* End-to-end call from host buffers: copies V and DM (pinned or pageable host memory) to
+ * library-owned device buffers, runs vlocal and rho_force, and copies H, rho and F back.
+ * Synchronous: returns after the results are in host memory.  Outputs may be NULL. */
+gint_status gint_run_host(gint_handle h, const double *V_host, const double *DM_host,
+                          double *H_host, double *rho_host, double *F_host, gint_prec prec,
+                          void *stream);
+
+/* Many structures in one persistent launch: for each s, H[s] <- vlocal(V[s]) and, if DM and
+ * rho are non-NULL, rho[s] <- rho(DM[s]).  All handles must be on the current device.
+ * Pointer arrays are host memory; the buffers they point to are device memory. */
+gint_status gint_batched(int nstruct, const gint_handle *hs, const double *const *V,
+                         double *const *H, const double *const *DM, double *const *rho,
+                         gint_prec prec, void *stream);
+
+/* Status word of the handle's kernels (GINT_OK or GINT_ETIMEOUT); synchronises the stream
+ * the handle last used.  Clears the word. */
+gint_status gint_get_status(gint_handle h);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *gint_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

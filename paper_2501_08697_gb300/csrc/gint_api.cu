@@ -1,0 +1,279 @@
+// Compute entry points of libgint (C ABI), small helper kernels (block symmetrisation,
+// FP64 reductions) and precision dispatch.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "gint_device.cuh"
+
+using namespace gint;
+
+namespace gint {
+cudaError_t launch_mirror(const Plan &P, double *H, cudaStream_t s);
+}
+
+namespace {
+
+// DMs <- (DM + DM^T_block) / 2, DM^T_block(I,J,R) = DM(J,I,-R)^T
+__global__ void k_symmetrise(Plan P, const double *__restrict__ DM, double *out)
+{
+    for (int64_t b = blockIdx.x; b < P.nblocks; b += gridDim.x) {
+        const int pb = P.partner[b];
+        const int64_t off = P.blk_off[b], poff = P.blk_off[pb];
+        const int rows = P.blk_rows[b];
+        const int cols = (int)((P.blk_off[b + 1] - off) / rows);
+        for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+            const int mu = e / cols, nu = e - mu * cols;
+            out[off + e] = 0.5 * (DM[off + e] + DM[poff + nu * rows + mu]);
+        }
+    }
+}
+
+constexpr int kRedBlocks = 1024;
+constexpr int kRedThreads = 256;
+
+// Deterministic two-pass FP64 reduction: block partials into scratch, then one block sums
+// them in a fixed order.
+__global__ void k_dot_partial(const double *__restrict__ a, const double *__restrict__ b, int64_t n, double *part)
+{
+    __shared__ double sh[kRedThreads];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += b ? a[i] * b[i] : a[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_dot_final(const double *part, int n, double scale, double *out)
+{
+    __shared__ double sh[kRedThreads];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0] * scale;
+}
+
+gint_status check_handle(gint_handle h, const char *who)
+{
+    if (!h) {
+        set_error("%s: null handle", who);
+        return GINT_EINVAL;
+    }
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    if (dev != h->device) {
+        set_error("%s: current device %d differs from the handle's device %d", who, dev, h->device);
+        return GINT_EINVAL;
+    }
+    return GINT_OK;
+}
+
+bool valid_prec(gint_prec p) { return p >= GINT_FP64 && p <= GINT_BF16X6; }
+
+gint_status do_dot(gint_handle h, const double *a, const double *b, int64_t n, double scale, double *out,
+                   cudaStream_t s, const char *who)
+{
+    int nblk = (int)std::min<int64_t>(kRedBlocks, std::max<int64_t>(1, (n + kRedThreads - 1) / kRedThreads));
+    k_dot_partial<<<nblk, kRedThreads, 0, s>>>(a, b, n, h->d_red);
+    k_dot_final<<<1, kRedThreads, 0, s>>>(h->d_red, nblk, scale, out);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GINT_OK : cuda_fail(e, who);
+}
+
+gint_status run_vlocal(gint_handle h, const double *V, double *H, gint_prec prec, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(H, 0, sizeof(double) * h->info.nvalues, s);
+    if (e != cudaSuccess) return cuda_fail(e, "gint_vlocal: memset");
+    if (prec == GINT_FP64 || prec == GINT_FP32)
+        e = launch_vlocal_simt(h->plan, prec == GINT_FP64, V, H, s, h->nsm);
+    else
+        e = launch_vlocal_tc(h->plan, prec, V, H, s, h->nsm);
+    if (e != cudaSuccess) return cuda_fail(e, "gint_vlocal: launch");
+    e = launch_mirror(h->plan, H, s);
+    if (e != cudaSuccess) return cuda_fail(e, "gint_vlocal: mirror");
+    h->last_stream = s;
+    return GINT_OK;
+}
+
+gint_status run_rho_force(gint_handle h, const double *V, const double *DM, double *rho, double *F, gint_prec prec,
+                          cudaStream_t s)
+{
+    cudaError_t e;
+    const double *D = DM;
+    if (F) {
+        if (h->info.nblocks > 0) {
+            k_symmetrise<<<(int)std::min<int64_t>(h->info.nblocks, 8192), 128, 0, s>>>(h->plan, DM, h->d_dmsym);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gint_force: symmetrise");
+        }
+        D = h->d_dmsym;
+        if ((e = cudaMemsetAsync(F, 0, sizeof(double) * 3 * h->natoms, s)) != cudaSuccess)
+            return cuda_fail(e, "gint_force: memset");
+    }
+    if (prec == GINT_FP64 || prec == GINT_FP32)
+        e = launch_rho_force_simt(h->plan, prec == GINT_FP64, V, D, rho, F, s, h->nsm);
+    else
+        e = launch_rho_force_tc(h->plan, prec, V, D, rho, F, s, h->nsm);
+    if (e != cudaSuccess) return cuda_fail(e, "gint_rho_force: launch");
+    h->last_stream = s;
+    return GINT_OK;
+}
+
+}  // namespace
+
+extern "C" gint_status gint_vlocal(gint_handle h, const double *V_dev, double *H_dev, gint_prec prec, void *stream)
+{
+    gint_status st = check_handle(h, "gint_vlocal");
+    if (st != GINT_OK) return st;
+    if (!V_dev || !H_dev || !valid_prec(prec)) {
+        set_error("gint_vlocal: null buffer or invalid precision");
+        return GINT_EINVAL;
+    }
+    return run_vlocal(h, V_dev, H_dev, prec, (cudaStream_t)stream);
+}
+
+extern "C" gint_status gint_rho(gint_handle h, const double *DM_dev, double *rho_dev, gint_prec prec, void *stream)
+{
+    gint_status st = check_handle(h, "gint_rho");
+    if (st != GINT_OK) return st;
+    if (!DM_dev || !rho_dev || !valid_prec(prec)) {
+        set_error("gint_rho: null buffer or invalid precision");
+        return GINT_EINVAL;
+    }
+    return run_rho_force(h, nullptr, DM_dev, rho_dev, nullptr, prec, (cudaStream_t)stream);
+}
+
+extern "C" gint_status gint_force(gint_handle h, const double *V_dev, const double *DM_dev, double *F_dev,
+                                  gint_prec prec, void *stream)
+{
+    gint_status st = check_handle(h, "gint_force");
+    if (st != GINT_OK) return st;
+    if (!V_dev || !DM_dev || !F_dev || !valid_prec(prec)) {
+        set_error("gint_force: null buffer or invalid precision");
+        return GINT_EINVAL;
+    }
+    return run_rho_force(h, V_dev, DM_dev, nullptr, F_dev, prec, (cudaStream_t)stream);
+}
+
+extern "C" gint_status gint_rho_force(gint_handle h, const double *V_dev, const double *DM_dev, double *rho_dev,
+                                      double *F_dev, gint_prec prec, void *stream)
+{
+    gint_status st = check_handle(h, "gint_rho_force");
+    if (st != GINT_OK) return st;
+    if (!DM_dev || (!rho_dev && !F_dev) || (F_dev && !V_dev) || !valid_prec(prec)) {
+        set_error("gint_rho_force: null buffer or invalid precision");
+        return GINT_EINVAL;
+    }
+    return run_rho_force(h, V_dev, DM_dev, rho_dev, F_dev, prec, (cudaStream_t)stream);
+}
+
+extern "C" gint_status gint_charge(gint_handle h, const double *rho_dev, double *out_dev, void *stream)
+{
+    gint_status st = check_handle(h, "gint_charge");
+    if (st != GINT_OK) return st;
+    if (!rho_dev || !out_dev) {
+        set_error("gint_charge: null buffer");
+        return GINT_EINVAL;
+    }
+    return do_dot(h, rho_dev, nullptr, h->info.npts, h->info.dV, out_dev, (cudaStream_t)stream, "gint_charge");
+}
+
+extern "C" gint_status gint_block_dot(gint_handle h, const double *A_dev, const double *B_dev, double *out_dev,
+                                      void *stream)
+{
+    gint_status st = check_handle(h, "gint_block_dot");
+    if (st != GINT_OK) return st;
+    if (!A_dev || !B_dev || !out_dev) {
+        set_error("gint_block_dot: null buffer");
+        return GINT_EINVAL;
+    }
+    return do_dot(h, A_dev, B_dev, h->info.nvalues, 1.0, out_dev, (cudaStream_t)stream, "gint_block_dot");
+}
+
+extern "C" gint_status gint_run_host(gint_handle h, const double *V_host, const double *DM_host, double *H_host,
+                                     double *rho_host, double *F_host, gint_prec prec, void *stream)
+{
+    gint_status st = check_handle(h, "gint_run_host");
+    if (st != GINT_OK) return st;
+    if (!V_host || !DM_host || !valid_prec(prec)) {
+        set_error("gint_run_host: null input or invalid precision");
+        return GINT_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nv = (size_t)h->info.nvalues, np = (size_t)h->info.npts, na = (size_t)h->natoms;
+    const size_t need = sizeof(double) * (2 * np + 2 * nv + 3 * na);
+    cudaError_t e;
+    if (h->hostio_bytes < need) {
+        if (h->d_hostio) cudaFree(h->d_hostio);
+        h->d_hostio = nullptr;
+        h->hostio_bytes = 0;
+        if ((e = cudaMalloc((void **)&h->d_hostio, need)) != cudaSuccess) return cuda_fail(e, "gint_run_host: allocate");
+        h->hostio_bytes = need;
+    }
+    double *dV = h->d_hostio, *drho = dV + np, *dDM = drho + np, *dH = dDM + nv, *dF = dH + nv;
+    if ((e = cudaMemcpyAsync(dV, V_host, sizeof(double) * np, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dDM, DM_host, sizeof(double) * nv, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "gint_run_host: copy in");
+    if ((st = run_vlocal(h, dV, dH, prec, s)) != GINT_OK) return st;
+    if ((st = run_rho_force(h, dV, dDM, drho, dF, prec, s)) != GINT_OK) return st;
+    if ((H_host && (e = cudaMemcpyAsync(H_host, dH, sizeof(double) * nv, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
+        (rho_host && (e = cudaMemcpyAsync(rho_host, drho, sizeof(double) * np, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
+        (F_host && (e = cudaMemcpyAsync(F_host, dF, sizeof(double) * 3 * na, cudaMemcpyDeviceToHost, s)) != cudaSuccess))
+        return cuda_fail(e, "gint_run_host: copy out");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "gint_run_host: synchronise");
+    return GINT_OK;
+}
+
+extern "C" gint_status gint_get_status(gint_handle h)
+{
+    gint_status st = check_handle(h, "gint_get_status");
+    if (st != GINT_OK) return st;
+    cudaError_t e = cudaStreamSynchronize(h->last_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "gint_get_status: synchronise");
+    int w = 0;
+    if ((e = cudaMemcpy(&w, h->d_status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "gint_get_status: read");
+    if (w != 0) {
+        cudaMemset(h->d_status, 0, sizeof(int));
+        set_error("a kernel gave up on a bounded wait (status %d)", w);
+        return (gint_status)w;
+    }
+    return GINT_OK;
+}
+
+extern "C" gint_status gint_batched(int nstruct, const gint_handle *hs, const double *const *V, double *const *H,
+                                   const double *const *DM, double *const *rho, gint_prec prec, void *stream)
+{
+    if (nstruct < 0 || (nstruct > 0 && (!hs || !V || !H)) || !valid_prec(prec)) {
+        set_error("gint_batched: invalid arguments");
+        return GINT_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < nstruct; ++i) {
+        gint_status st = check_handle(hs[i], "gint_batched");
+        if (st != GINT_OK) return st;
+        if (!V[i] || !H[i] || (DM && rho && (!DM[i] || !rho[i]))) {
+            set_error("gint_batched: null buffer for structure %d", i);
+            return GINT_EINVAL;
+        }
+    }
+    for (int i = 0; i < nstruct; ++i) {
+        gint_status st = run_vlocal(hs[i], V[i], H[i], prec, s);
+        if (st != GINT_OK) return st;
+        if (DM && rho) {
+            st = run_rho_force(hs[i], nullptr, DM[i], rho[i], nullptr, prec, s);
+            if (st != GINT_OK) return st;
+        }
+    }
+    return GINT_OK;
+}

@@ -1,0 +1,237 @@
+// Device helpers of libgint: orbital evaluation (spline radial x real solid harmonic),
+// bounded waits and the status word.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "gint_internal.h"
+
+namespace gint {
+
+// Real harmonics (no Condon-Shortley phase), per l ordered m = 0, +1, -1, +2, -2, written as
+// Y_lm(r_hat) = S_lm(d) / r^l with the solid harmonics
+//   S_00 = c0
+//   S_1m = c1 (z, x, y)
+//   S_2m = (c20 (2z^2 - x^2 - y^2), c21 xz, c21 yz, c22 (x^2 - y^2), c21 xy)
+// c0 = 1/(2 sqrt(pi)), c1 = sqrt(3/(4 pi)), c20 = sqrt(5/(16 pi)), c21 = sqrt(15/(4 pi)),
+// c22 = sqrt(15/(16 pi)) (orthonormal on the unit sphere).
+template <typename T>
+struct YC {
+    static constexpr T c0 = T(0.28209479177387814347);
+    static constexpr T c1 = T(0.48860251190291992159);
+    static constexpr T c20 = T(0.31539156525252000603);
+    static constexpr T c21 = T(1.09254843059207907054);
+    static constexpr T c22 = T(0.54627421529603953527);
+};
+
+template <typename T>
+__device__ __forceinline__ T dsqrt(T x);
+template <>
+__device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+
+// spline record of radial ir at interval i (coefficients of c0 + c1 t + c2 t^2 + c3 t^3)
+template <typename T>
+struct Coef;
+template <>
+struct Coef<double> {
+    double c0, c1, c2, c3;
+    __device__ __forceinline__ void load(const Plan &P, int rec)
+    {
+        const double2 *p = reinterpret_cast<const double2 *>(P.coef64) + 2 * rec;
+        double2 a = __ldg(p), b = __ldg(p + 1);
+        c0 = a.x; c1 = a.y; c2 = b.x; c3 = b.y;
+    }
+};
+template <>
+struct Coef<float> {
+    float c0, c1, c2, c3;
+    __device__ __forceinline__ void load(const Plan &P, int rec)
+    {
+        float4 a = __ldg(P.coef32 + rec);
+        c0 = a.x; c1 = a.y; c2 = a.z; c3 = a.w;
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ T rcut_of(const DevSpecies &S);
+template <>
+__device__ __forceinline__ double rcut_of<double>(const DevSpecies &S) { return S.rcut; }
+template <>
+__device__ __forceinline__ float rcut_of<float>(const DevSpecies &S) { return S.rcut_f; }
+template <typename T>
+__device__ __forceinline__ T invdr_of(const DevSpecies &S);
+template <>
+__device__ __forceinline__ double invdr_of<double>(const DevSpecies &S) { return S.inv_dr; }
+template <>
+__device__ __forceinline__ float invdr_of<float>(const DevSpecies &S) { return S.inv_dr_f; }
+
+// Evaluate every orbital of species `sp` at displacement d = r - centre.  emit(o, phi) is
+// called for o = 0 .. norb-1 in order; with GRAD, emit(o, phi, gx, gy, gz) with the
+// gradient with respect to r.  Outside the cutoff all values are 0.
+template <typename T, bool GRAD, typename Emit>
+__device__ __forceinline__ void eval_orbitals(const Plan &P, int sp, T dx, T dy, T dz, Emit &&emit)
+{
+    const DevSpecies &S = P.sp[sp];
+    const T rc = rcut_of<T>(S);
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    const int nrad = S.nrad;
+    if (!(r2 < rc * rc)) {
+        int o = 0;
+        for (int ir = 0; ir < nrad; ++ir) {
+            int nm = 2 * S.l[ir] + 1;
+            for (int m = 0; m < nm; ++m, ++o) {
+                if constexpr (GRAD) emit(o, T(0), T(0), T(0), T(0));
+                else emit(o, T(0));
+            }
+        }
+        return;
+    }
+    const T inv_dr = invdr_of<T>(S);
+    const T r = dsqrt<T>(r2);
+    if (r < T(1e-12)) {
+        // limits at the centre: phi = f(0) c0 for l = 0, grad phi = f'(0) c1 e_m for l = 1
+        int o = 0;
+        for (int ir = 0; ir < nrad; ++ir) {
+            Coef<T> c;
+            c.load(P, S.coef_off + ir);
+            int l = S.l[ir];
+            if (l == 0) {
+                if constexpr (GRAD) emit(o, c.c0 * YC<T>::c0, T(0), T(0), T(0));
+                else emit(o, c.c0 * YC<T>::c0);
+                ++o;
+            } else if (l == 1) {
+                T g = c.c1 * inv_dr * YC<T>::c1;
+                if constexpr (GRAD) {
+                    emit(o, T(0), T(0), T(0), g);
+                    emit(o + 1, T(0), g, T(0), T(0));
+                    emit(o + 2, T(0), T(0), g, T(0));
+                } else {
+                    emit(o, T(0)); emit(o + 1, T(0)); emit(o + 2, T(0));
+                }
+                o += 3;
+            } else {
+                for (int m = 0; m < 5; ++m, ++o) {
+                    if constexpr (GRAD) emit(o, T(0), T(0), T(0), T(0));
+                    else emit(o, T(0));
+                }
+            }
+        }
+        return;
+    }
+    T x = r * inv_dr;
+    int i = (int)x;
+    if (i > S.nint - 1) i = S.nint - 1;
+    const T t = x - T(i);
+    const int rec0 = S.coef_off + i * nrad;
+    const T ir1 = T(1) / r;
+    const T ux = dx * ir1, uy = dy * ir1, uz = dz * ir1;
+    int o = 0;
+    for (int ir = 0; ir < nrad; ++ir) {
+        Coef<T> c;
+        c.load(P, rec0 + ir);
+        const T f = c.c0 + t * (c.c1 + t * (c.c2 + t * c.c3));
+        const int l = S.l[ir];
+        if constexpr (!GRAD) {
+            if (l == 0) {
+                emit(o, f * YC<T>::c0);
+                o += 1;
+            } else if (l == 1) {
+                const T a = f * YC<T>::c1;
+                emit(o, a * uz); emit(o + 1, a * ux); emit(o + 2, a * uy);
+                o += 3;
+            } else {
+                emit(o, f * YC<T>::c20 * (T(2) * uz * uz - ux * ux - uy * uy));
+                emit(o + 1, f * YC<T>::c21 * ux * uz);
+                emit(o + 2, f * YC<T>::c21 * uy * uz);
+                emit(o + 3, f * YC<T>::c22 * (ux * ux - uy * uy));
+                emit(o + 4, f * YC<T>::c21 * ux * uy);
+                o += 5;
+            }
+        } else {
+            const T df = (c.c1 + t * (T(2) * c.c2 + T(3) * t * c.c3)) * inv_dr;
+            if (l == 0) {
+                const T a = df * YC<T>::c0;
+                emit(o, f * YC<T>::c0, a * ux, a * uy, a * uz);
+                o += 1;
+            } else if (l == 1) {
+                // phi = g S, g = f/r, grad = g' u S + g grad S, g' = (f' - f/r)/r
+                const T g = f * ir1;
+                const T gp = (df - g) * ir1;
+                const T c1 = YC<T>::c1;
+                const T Sz = c1 * dz, Sx = c1 * dx, Sy = c1 * dy;
+                const T gc = g * c1;
+                emit(o, g * Sz, gp * ux * Sz, gp * uy * Sz, gp * uz * Sz + gc);
+                emit(o + 1, g * Sx, gp * ux * Sx + gc, gp * uy * Sx, gp * uz * Sx);
+                emit(o + 2, g * Sy, gp * ux * Sy, gp * uy * Sy + gc, gp * uz * Sy);
+                o += 3;
+            } else {
+                // g = f/r^2, g' = f'/r^2 - 2 f/r^3
+                const T g = f * ir1 * ir1;
+                const T gp = (df - T(2) * f * ir1) * ir1 * ir1;
+                const T c20 = YC<T>::c20, c21 = YC<T>::c21, c22 = YC<T>::c22;
+                T Sv, gxs, gys, gzs;
+                Sv = c20 * (T(2) * dz * dz - dx * dx - dy * dy);
+                gxs = -T(2) * c20 * dx; gys = -T(2) * c20 * dy; gzs = T(4) * c20 * dz;
+                emit(o, g * Sv, gp * ux * Sv + g * gxs, gp * uy * Sv + g * gys, gp * uz * Sv + g * gzs);
+                Sv = c21 * dx * dz;
+                emit(o + 1, g * Sv, gp * ux * Sv + g * c21 * dz, gp * uy * Sv, gp * uz * Sv + g * c21 * dx);
+                Sv = c21 * dy * dz;
+                emit(o + 2, g * Sv, gp * ux * Sv, gp * uy * Sv + g * c21 * dz, gp * uz * Sv + g * c21 * dy);
+                Sv = c22 * (dx * dx - dy * dy);
+                emit(o + 3, g * Sv, gp * ux * Sv + T(2) * g * c22 * dx, gp * uy * Sv - T(2) * g * c22 * dy, gp * uz * Sv);
+                Sv = c21 * dx * dy;
+                emit(o + 4, g * Sv, gp * ux * Sv + g * c21 * dy, gp * uy * Sv + g * c21 * dx, gp * uz * Sv);
+                o += 5;
+            }
+        }
+    }
+}
+
+// Displacement of local point (a, b, c) of a batch from a slot's centre.  FP64 directly;
+// FP32 as (d0_hi + off_hi) + (d0_lo + off_lo) so that the rounding error is relative to |d|
+// rather than to |d0| (d0 can be ~8 bohr while |d| ~ 1 bohr dominates the integrals).
+__device__ __forceinline__ void point_offset64(const Plan &P, int a, int b, int c, double *off)
+{
+    for (int q = 0; q < 3; ++q) off[q] = a * P.h[q] + b * P.h[3 + q] + c * P.h[6 + q];
+}
+
+__device__ __forceinline__ void split_f32(double x, float &hi, float &lo)
+{
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+// One scatter of a contraction element (mu in slot a, nu in slot b) with the canonical
+// rule.  `both` = the element (nu, mu) was also computed by this batch.
+__device__ __forceinline__ void scatter_elem(double *H, const int *tbl, int ns, int a, int oa, int na, int b, int ob,
+                                             int nbo, double val, bool both)
+{
+    int e = tbl[a * ns + b];
+    if (e < 0) return;
+    int off = e >> 1;
+    bool canon = e & 1;
+    if (both) {
+        // self-partner blocks (a == b) keep only their upper triangle; the mirror fills the rest
+        if (canon && (a != b || oa <= ob)) atomicAdd(H + off + oa * nbo + ob, val);
+        return;
+    }
+    if (a == b) {
+        atomicAdd(H + off + min(oa, ob) * na + max(oa, ob), val);
+    } else if (canon) {
+        atomicAdd(H + off + oa * nbo + ob, val);
+    } else {
+        int e2 = tbl[b * ns + a];
+        atomicAdd(H + (e2 >> 1) + ob * na + oa, val);
+    }
+}
+
+// ----------------------------------------------------------------------- status and waits
+__device__ __forceinline__ void report_timeout(const Plan &P) { atomicCAS(P.status, 0, (int)GINT_ETIMEOUT); }
+
+__device__ __forceinline__ bool aborted(const Plan &P)
+{
+    return *(volatile int *)P.status != 0;
+}
+
+}  // namespace gint

@@ -1,0 +1,113 @@
+// Internal data structures shared by the host set-up and the CUDA kernels of libgint.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gint.h"
+
+namespace gint {
+
+constexpr int kMaxRad = 16;        // radial functions per species
+constexpr int kMaxSpecies = 8;
+constexpr int kMaxOrbSpecies = 48; // orbitals per species (l <= 2)
+constexpr int kMaxNb = 256;        // orbitals per batch (tensor-memory columns of one tile pair)
+constexpr int kMaxSlots = 64;      // atom images per batch
+constexpr int kMaxBatchPts = 128;  // grid points per batch
+constexpr int kMaxBatchDim = 16;   // points per batch along one axis
+
+// One species as the kernels see it.  Orbital o of the species belongs to radial rad_of[o]
+// with harmonic index m_of[o] in 0..2l (order m = 0, +1, -1, +2, -2).
+struct DevSpecies {
+    int nrad, norb, nint;          // nint = ntab - 1 spline intervals
+    int coef_off;                  // first interval record of this species (see Plan::coef*)
+    double rcut, inv_dr;
+    float rcut_f, inv_dr_f;
+    int l[kMaxRad];
+};
+
+// A grid batch: points (i0 + a, j0 + b, k0 + c) for a < n1, b < n2, c < n3 (k fastest inside
+// the batch), its atom images slot0 .. slot0+nslots-1 and orbital count nb.
+struct Batch {
+    int i0, j0, k0;
+    int dims;                      // n1 | n2 << 8 | n3 << 16
+    int slot0, nslots, nb;
+    int tbl;                       // first entry of this batch's nslots x nslots pair table
+};
+
+// An atom image seen by a batch.  d0 = (grid point (i0,j0,k0)) - (tau_I + R_a), Cartesian.
+struct Slot {
+    int atom, species, orb_off, norb;
+    double d0[3];
+};
+
+// Everything a kernel needs, passed by value.
+struct Plan {
+    int natoms, nspecies;
+    int grid[3];
+    int64_t npts;
+    int nbatches;
+    double dV;
+    double h[9];                   // h[3*i + c] = component c of a_i / N_i
+    DevSpecies sp[kMaxSpecies];
+    const double *coef64;          // [interval record][4]: per species, interval-major, radial-minor
+    const float4 *coef32;
+    const Batch *batches;
+    const Slot *slots;
+    const int *tbl;                // (block offset << 1 | canonical) or -1 if no block
+    const int *partner;            // [nblocks] partner block index
+    const int64_t *blk_off;        // [nblocks + 1]
+    const int *blk_rows;           // [nblocks] rows of each block
+    int64_t nblocks, nvalues;
+    int *status;                   // device status word
+    long long spin_limit;          // clock64 cycles a kernel may wait on one barrier
+};
+
+}  // namespace gint
+
+struct gint_handle_s {
+    gint::Plan plan{};
+    int device = 0;
+    int nsm = 0;
+    // host copies
+    double cell[9];
+    int grid[3];
+    int natoms = 0, nspecies = 0;
+    std::vector<int> species;
+    std::vector<double> tau;
+    std::vector<int> norb_atom;
+    std::vector<int32_t> keys;       // 5 per block
+    std::vector<int64_t> offsets;    // nblocks + 1
+    std::vector<int> partner;
+    std::vector<gint::Batch> batches;
+    std::vector<gint::Slot> slots;
+    std::vector<int> slot_img;       // 3 per slot: image n of the slot's atom
+    std::vector<int> tbl;
+    gint_options opt{};
+    gint_info_t info{};
+    // device memory (owned)
+    void *d_coef64 = nullptr, *d_coef32 = nullptr, *d_batches = nullptr, *d_slots = nullptr;
+    void *d_tbl = nullptr, *d_partner = nullptr, *d_blkoff = nullptr, *d_blkrows = nullptr;
+    int *d_status = nullptr;
+    double *d_dmsym = nullptr;       // scratch: block-symmetrised density matrix
+    double *d_red = nullptr;         // scratch: partial sums of reductions
+    double *d_hostio = nullptr;      // buffers of gint_run_host (allocated on first use)
+    size_t hostio_bytes = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace gint {
+void set_error(const char *fmt, ...);
+gint_status cuda_fail(cudaError_t e, const char *where);
+// set-up helpers (gint_setup.cpp)
+gint_status build_geometry(gint_handle h, const double *tau, bool update_only);
+// kernel launchers (gint_simt.cu, gint_tc.cu, gint_api.cu)
+cudaError_t launch_vlocal_simt(const Plan &p, bool fp64, const double *V, double *H, cudaStream_t s, int nsm);
+cudaError_t launch_rho_force_simt(const Plan &p, bool fp64, const double *V, const double *DM,
+                                  double *rho, double *F, cudaStream_t s, int nsm);
+cudaError_t launch_vlocal_tc(const Plan &p, gint_prec prec, const double *V, double *H, cudaStream_t s, int nsm);
+cudaError_t launch_rho_force_tc(const Plan &p, gint_prec prec, const double *V, const double *DM,
+                                double *rho, double *F, cudaStream_t s, int nsm);
+}  // namespace gint

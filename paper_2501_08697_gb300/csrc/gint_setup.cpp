@@ -1,0 +1,746 @@
+// Host-side set-up of libgint: validation, radial splines, the block list (HContainer
+// layout), grid batches and their atom-image lists, per-batch block tables, device upload.
+//
+// Paper references: NAO basis and strict locality (Sec. IV.A); block list over "all valid
+// neighbouring cells" R and the HContainer store of H(R)/DM(R) (Sec. IV.B, Fig. 2 caption);
+// grid partitioned into pieces that are integrated independently (Sec. IV.B).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <thread>
+
+#include "gint_internal.h"
+
+namespace gint {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+const char *last_error() { return g_err.c_str(); }
+
+gint_status cuda_fail(cudaError_t e, const char *where)
+{
+    set_error("%s: CUDA error %d (%s)", where, (int)e, cudaGetErrorString(e));
+    return GINT_ECUDA;
+}
+
+// ---------------------------------------------------------------------------------------
+// Clamped cubic spline in slope form: knot slopes k_i from
+//   k_{i-1} + 4 k_i + k_{i+1} = 3 (y_{i+1} - y_{i-1}) / h,   k_0 = d0, k_{n-1} = dn,
+// then each interval as a cubic in t = (r - r_i)/h in [0, 1).
+static void spline_slopes(const double *y, int n, double h, double d0, double dn, std::vector<double> &k)
+{
+    k.assign(n, 0.0);
+    k[0] = d0;
+    k[n - 1] = dn;
+    if (n <= 2) return;
+    int m = n - 2;  // unknowns k_1 .. k_{n-2}
+    std::vector<double> cp(m), dp(m);
+    for (int j = 0; j < m; ++j) {
+        int i = j + 1;
+        double rhs = 3.0 * (y[i + 1] - y[i - 1]) / h;
+        if (j == 0) rhs -= d0;
+        if (j == m - 1) rhs -= dn;
+        double diag = 4.0, lower = (j > 0) ? 1.0 : 0.0, upper = (j < m - 1) ? 1.0 : 0.0;
+        double den = diag - (j > 0 ? lower * cp[j - 1] : 0.0);
+        cp[j] = upper / den;
+        dp[j] = (rhs - (j > 0 ? lower * dp[j - 1] : 0.0)) / den;
+    }
+    for (int j = m - 1; j >= 0; --j) k[j + 1] = dp[j] - (j < m - 1 ? cp[j] * k[j + 2] : 0.0);
+}
+
+static inline int64_t pack_key(int I, int J, int n1, int n2, int n3)
+{
+    return ((int64_t)I << 41) | ((int64_t)J << 21) | ((int64_t)(n1 + 64) << 14) | ((int64_t)(n2 + 64) << 7) |
+           (int64_t)(n3 + 64);
+}
+
+struct Geo {
+    double A[9];     // rows a_i
+    double g[9];     // g[3*c + i]: component c of reciprocal vector g_i
+    double gn[3];
+    double det;
+};
+
+static Geo make_geo(const double *cell)
+{
+    Geo G;
+    memcpy(G.A, cell, sizeof(G.A));
+    const double *A = cell;
+    G.det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) + A[2] * (A[3] * A[7] - A[4] * A[6]);
+    for (int i = 0; i < 3; ++i) {
+        const double *aj = A + 3 * ((i + 1) % 3), *ak = A + 3 * ((i + 2) % 3);
+        double v[3] = {aj[1] * ak[2] - aj[2] * ak[1], aj[2] * ak[0] - aj[0] * ak[2], aj[0] * ak[1] - aj[1] * ak[0]};
+        for (int c = 0; c < 3; ++c) G.g[3 * c + i] = v[c] / G.det;
+        G.gn[i] = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / std::fabs(G.det);
+    }
+    return G;
+}
+
+static inline double frac_of(const Geo &G, const double *x, int i)
+{
+    return x[0] * G.g[0 + i] + x[1] * G.g[3 + i] + x[2] * G.g[6 + i];
+}
+
+// distance^2 from point c to the axis-aligned box [lo, hi] (orthogonal cells)
+static inline double box_dist2(const double *c, const double *lo, const double *hi)
+{
+    double s = 0.0;
+    for (int x = 0; x < 3; ++x) {
+        double d = 0.0;
+        if (c[x] < lo[x]) d = lo[x] - c[x];
+        else if (c[x] > hi[x]) d = c[x] - hi[x];
+        s += d * d;
+    }
+    return s;
+}
+
+struct RawSlot {
+    int atom, n[3];
+};
+
+// Does the sphere (centre c, radius rc) touch any point of the batch box?  For orthogonal
+// cells the exact box distance; otherwise a conservative centre-distance test.
+struct BatchGeom {
+    bool ortho;
+    double h[9];  // a_i / N_i
+};
+
+static void batch_box(const BatchGeom &bg, int i0, int j0, int k0, int n1, int n2, int n3, double *lo, double *hi,
+                      double *ctr, double *rad)
+{
+    // corners of the point parallelepiped
+    double o[3], e[3][3];
+    for (int c = 0; c < 3; ++c) {
+        o[c] = i0 * bg.h[c] + j0 * bg.h[3 + c] + k0 * bg.h[6 + c];
+        e[0][c] = (n1 - 1) * bg.h[c];
+        e[1][c] = (n2 - 1) * bg.h[3 + c];
+        e[2][c] = (n3 - 1) * bg.h[6 + c];
+    }
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = o[c] + std::min(0.0, e[0][c]) + std::min(0.0, e[1][c]) + std::min(0.0, e[2][c]);
+        hi[c] = o[c] + std::max(0.0, e[0][c]) + std::max(0.0, e[1][c]) + std::max(0.0, e[2][c]);
+        ctr[c] = o[c] + 0.5 * (e[0][c] + e[1][c] + e[2][c]);
+    }
+    double r2 = 0.0;
+    for (int s1 = -1; s1 <= 1; s1 += 2)
+        for (int s2 = -1; s2 <= 1; s2 += 2)
+            for (int s3 = -1; s3 <= 1; s3 += 2) {
+                double v[3];
+                for (int c = 0; c < 3; ++c) v[c] = 0.5 * (s1 * e[0][c] + s2 * e[1][c] + s3 * e[2][c]);
+                r2 = std::max(r2, v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            }
+    *rad = std::sqrt(r2);
+}
+
+static bool sphere_meets_batch(const BatchGeom &bg, const double *c, double rc, const double *lo, const double *hi,
+                               const double *ctr, double rad)
+{
+    if (bg.ortho) return box_dist2(c, lo, hi) < rc * rc;
+    double d[3] = {c[0] - ctr[0], c[1] - ctr[1], c[2] - ctr[2]};
+    double dist = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    return dist < rc + rad;
+}
+
+// ---------------------------------------------------------------------------------------
+gint_status build_geometry(gint_handle h, const double *tau, bool update_only)
+{
+    const int natoms = h->natoms;
+    Geo G = make_geo(h->cell);
+    Plan &P = h->plan;
+    const int N1 = h->grid[0], N2 = h->grid[1], N3 = h->grid[2];
+    std::vector<double> rc(natoms);
+    for (int I = 0; I < natoms; ++I) rc[I] = P.sp[h->species[I]].rcut;
+
+    // ---- block list: all (I, J, n) with |tau_J + n.A - tau_I| < rc_I + rc_J
+    std::vector<int32_t> keys;
+    std::vector<int64_t> packed;
+    for (int I = 0; I < natoms; ++I) {
+        for (int J = 0; J < natoms; ++J) {
+            double rs = rc[I] + rc[J];
+            double dt[3] = {tau[3 * J] - tau[3 * I], tau[3 * J + 1] - tau[3 * I + 1], tau[3 * J + 2] - tau[3 * I + 2]};
+            int lo[3], hi[3];
+            for (int i = 0; i < 3; ++i) {
+                double s = frac_of(G, dt, i);
+                lo[i] = (int)std::floor(-s - rs * G.gn[i]) - 1;
+                hi[i] = (int)std::ceil(-s + rs * G.gn[i]) + 1;
+            }
+            for (int n1 = lo[0]; n1 <= hi[0]; ++n1)
+                for (int n2 = lo[1]; n2 <= hi[1]; ++n2)
+                    for (int n3 = lo[2]; n3 <= hi[2]; ++n3) {
+                        double v[3];
+                        for (int x = 0; x < 3; ++x) v[x] = dt[x] + n1 * G.A[x] + n2 * G.A[3 + x] + n3 * G.A[6 + x];
+                        if (v[0] * v[0] + v[1] * v[1] + v[2] * v[2] < rs * rs) {
+                            if (std::abs(n1) > 63 || std::abs(n2) > 63 || std::abs(n3) > 63) {
+                                set_error("gint_setup: periodic image index beyond 63 (cell too small for rcut)");
+                                return GINT_EINVAL;
+                            }
+                            keys.insert(keys.end(), {I, J, n1, n2, n3});
+                            packed.push_back(pack_key(I, J, n1, n2, n3));
+                        }
+                    }
+        }
+    }
+    const int64_t nblocks = (int64_t)packed.size();
+    if (update_only) {
+        if (keys != h->keys) {
+            set_error("gint_update_positions: block list changed; build a new handle");
+            return GINT_ESTATE;
+        }
+    }
+    std::vector<int64_t> offsets(nblocks + 1, 0);
+    std::vector<int> rows(nblocks);
+    for (int64_t b = 0; b < nblocks; ++b) {
+        rows[b] = h->norb_atom[keys[5 * b]];
+        offsets[b + 1] = offsets[b] + (int64_t)h->norb_atom[keys[5 * b]] * h->norb_atom[keys[5 * b + 1]];
+    }
+    if (offsets[nblocks] >= ((int64_t)1 << 30)) {
+        set_error("gint_setup: block store of %lld values exceeds 2^30", (long long)offsets[nblocks]);
+        return GINT_EINVAL;
+    }
+    std::vector<int> partner(nblocks);
+    std::vector<uint8_t> canon(nblocks);
+    for (int64_t b = 0; b < nblocks; ++b) {
+        const int32_t *k = &keys[5 * b];
+        int64_t pk = pack_key(k[1], k[0], -k[2], -k[3], -k[4]);
+        auto it = std::lower_bound(packed.begin(), packed.end(), pk);
+        if (it == packed.end() || *it != pk) {
+            set_error("gint_setup: internal error, partner block missing");
+            return GINT_EINVAL;
+        }
+        partner[b] = (int)(it - packed.begin());
+        canon[b] = packed[b] <= pk;
+    }
+
+    // ---- batches and their atom-image slots
+    BatchGeom bg;
+    bg.ortho = true;
+    for (int i = 0; i < 3; ++i)
+        for (int c = 0; c < 3; ++c)
+            if (i != c && h->cell[3 * i + c] != 0.0) bg.ortho = false;
+    for (int i = 0; i < 3; ++i)
+        for (int c = 0; c < 3; ++c) bg.h[3 * i + c] = h->cell[3 * i + c] / h->grid[i];
+
+    const int B1 = h->opt.batch[0], B2 = h->opt.batch[1], B3 = h->opt.batch[2];
+    const int nb1 = (N1 + B1 - 1) / B1, nb2 = (N2 + B2 - 1) / B2, nb3 = (N3 + B3 - 1) / B3;
+    const int64_t nbase = (int64_t)nb1 * nb2 * nb3;
+    std::vector<std::vector<RawSlot>> lists(nbase);
+
+    // atom images that reach the cell
+    for (int I = 0; I < natoms; ++I) {
+        const double *t = tau + 3 * I;
+        int lo[3], hi[3];
+        for (int i = 0; i < 3; ++i) {
+            double s = frac_of(G, t, i);
+            lo[i] = (int)std::floor(-s - rc[I] * G.gn[i]) - 1;
+            hi[i] = (int)std::ceil(1.0 - s + rc[I] * G.gn[i]) + 1;
+        }
+        for (int n1 = lo[0]; n1 <= hi[0]; ++n1)
+            for (int n2 = lo[1]; n2 <= hi[1]; ++n2)
+                for (int n3 = lo[2]; n3 <= hi[2]; ++n3) {
+                    double c[3];
+                    for (int x = 0; x < 3; ++x) c[x] = t[x] + n1 * G.A[x] + n2 * G.A[3 + x] + n3 * G.A[6 + x];
+                    // grid-index range along each axis that the sphere can reach
+                    int ilo[3], ihi[3];
+                    bool empty = false;
+                    for (int i = 0; i < 3; ++i) {
+                        double s = frac_of(G, c, i) * h->grid[i];
+                        double ext = rc[I] * G.gn[i] * h->grid[i];
+                        ilo[i] = std::max(0, (int)std::floor(s - ext) - 1);
+                        ihi[i] = std::min(h->grid[i] - 1, (int)std::ceil(s + ext) + 1);
+                        if (ilo[i] > ihi[i]) empty = true;
+                    }
+                    if (empty) continue;
+                    int Bs[3] = {B1, B2, B3};
+                    for (int b1 = ilo[0] / Bs[0]; b1 <= ihi[0] / Bs[0]; ++b1)
+                        for (int b2 = ilo[1] / Bs[1]; b2 <= ihi[1] / Bs[1]; ++b2)
+                            for (int b3 = ilo[2] / Bs[2]; b3 <= ihi[2] / Bs[2]; ++b3) {
+                                int i0 = b1 * B1, j0 = b2 * B2, k0 = b3 * B3;
+                                int n1p = std::min(B1, N1 - i0), n2p = std::min(B2, N2 - j0), n3p = std::min(B3, N3 - k0);
+                                double lo3[3], hi3[3], ctr[3], rad;
+                                batch_box(bg, i0, j0, k0, n1p, n2p, n3p, lo3, hi3, ctr, &rad);
+                                if (sphere_meets_batch(bg, c, rc[I], lo3, hi3, ctr, rad))
+                                    lists[((int64_t)b1 * nb2 + b2) * nb3 + b3].push_back({I, {n1, n2, n3}});
+                            }
+                }
+    }
+
+    // split batches whose orbital or slot count exceeds the kernel limits
+    struct Work {
+        int i0, j0, k0, n1, n2, n3;
+        std::vector<RawSlot> s;
+    };
+    std::vector<Batch> batches;
+    std::vector<Slot> slots;
+    std::vector<int> slot_img;
+    std::vector<int> tbl;
+    int max_nb = 0, max_slots = 0;
+    double flops_useful = 0.0, flops_dense = 0.0;
+    auto orb_count = [&](const std::vector<RawSlot> &s) {
+        int n = 0;
+        for (auto &x : s) n += h->norb_atom[x.atom];
+        return n;
+    };
+    auto slot_less = [](const RawSlot &a, const RawSlot &b) {
+        if (a.atom != b.atom) return a.atom < b.atom;
+        if (a.n[0] != b.n[0]) return a.n[0] < b.n[0];
+        if (a.n[1] != b.n[1]) return a.n[1] < b.n[1];
+        return a.n[2] < b.n[2];
+    };
+    for (int b1 = 0; b1 < nb1; ++b1)
+        for (int b2 = 0; b2 < nb2; ++b2)
+            for (int b3 = 0; b3 < nb3; ++b3) {
+                std::vector<Work> stack;
+                Work w0{b1 * B1, b2 * B2, b3 * B3, std::min(B1, N1 - b1 * B1), std::min(B2, N2 - b2 * B2),
+                        std::min(B3, N3 - b3 * B3), std::move(lists[((int64_t)b1 * nb2 + b2) * nb3 + b3])};
+                stack.push_back(std::move(w0));
+                while (!stack.empty()) {
+                    Work w = std::move(stack.back());
+                    stack.pop_back();
+                    std::sort(w.s.begin(), w.s.end(), slot_less);
+                    int nb = orb_count(w.s);
+                    if (nb > kMaxNb || (int)w.s.size() > kMaxSlots) {
+                        // halve the longest axis (keep k halves even so k0 stays even)
+                        int dims[3] = {w.n1, w.n2, w.n3};
+                        int ax = 0;
+                        for (int a = 1; a < 3; ++a)
+                            if (dims[a] > dims[ax]) ax = a;
+                        if (dims[ax] <= 1) {
+                            set_error("gint_setup: a single grid point sees %d orbitals / %d atom images (limits %d / %d)",
+                                      nb, (int)w.s.size(), kMaxNb, kMaxSlots);
+                            return GINT_EINVAL;
+                        }
+                        int cut = dims[ax] / 2;
+                        if (ax == 2 && (cut % 2) && dims[ax] > 2) cut += 1;
+                        Work a = w, b = w;
+                        if (ax == 0) { a.n1 = cut; b.i0 += cut; b.n1 -= cut; }
+                        if (ax == 1) { a.n2 = cut; b.j0 += cut; b.n2 -= cut; }
+                        if (ax == 2) { a.n3 = cut; b.k0 += cut; b.n3 -= cut; }
+                        for (Work *x : {&b, &a}) {
+                            double lo3[3], hi3[3], ctr[3], rad;
+                            batch_box(bg, x->i0, x->j0, x->k0, x->n1, x->n2, x->n3, lo3, hi3, ctr, &rad);
+                            std::vector<RawSlot> keep;
+                            for (auto &s : w.s) {
+                                double c[3];
+                                for (int q = 0; q < 3; ++q)
+                                    c[q] = tau[3 * s.atom + q] + s.n[0] * G.A[q] + s.n[1] * G.A[3 + q] + s.n[2] * G.A[6 + q];
+                                if (sphere_meets_batch(bg, c, rc[s.atom], lo3, hi3, ctr, rad)) keep.push_back(s);
+                            }
+                            x->s = std::move(keep);
+                            stack.push_back(std::move(*x));
+                        }
+                        continue;
+                    }
+                    Batch B{};
+                    B.i0 = w.i0; B.j0 = w.j0; B.k0 = w.k0;
+                    B.dims = w.n1 | (w.n2 << 8) | (w.n3 << 16);
+                    B.slot0 = (int)slots.size();
+                    B.nslots = (int)w.s.size();
+                    B.nb = nb;
+                    B.tbl = (int)tbl.size();
+                    int npb = w.n1 * w.n2 * w.n3;
+                    flops_dense += 2.0 * npb * (double)nb * nb;
+                    max_nb = std::max(max_nb, nb);
+                    max_slots = std::max(max_slots, (int)w.s.size());
+                    int off = 0;
+                    double o[3];
+                    for (int c = 0; c < 3; ++c) o[c] = w.i0 * bg.h[c] + w.j0 * bg.h[3 + c] + w.k0 * bg.h[6 + c];
+                    for (auto &s : w.s) {
+                        Slot S{};
+                        S.atom = s.atom;
+                        S.species = h->species[s.atom];
+                        S.orb_off = off;
+                        S.norb = h->norb_atom[s.atom];
+                        for (int q = 0; q < 3; ++q)
+                            S.d0[q] = o[q] - (tau[3 * s.atom + q] + s.n[0] * G.A[q] + s.n[1] * G.A[3 + q] + s.n[2] * G.A[6 + q]);
+                        off += S.norb;
+                        slots.push_back(S);
+                        slot_img.insert(slot_img.end(), {s.n[0], s.n[1], s.n[2]});
+                    }
+                    // pair table: block of (I_a, I_b, n_b - n_a)
+                    for (auto &sa : w.s)
+                        for (auto &sb : w.s) {
+                            int64_t pk = pack_key(sa.atom, sb.atom, sb.n[0] - sa.n[0], sb.n[1] - sa.n[1], sb.n[2] - sa.n[2]);
+                            auto it = std::lower_bound(packed.begin(), packed.end(), pk);
+                            if (it == packed.end() || *it != pk) {
+                                tbl.push_back(-1);
+                            } else {
+                                int64_t bi = it - packed.begin();
+                                tbl.push_back((int)((offsets[bi] << 1) | canon[bi]));
+                            }
+                        }
+                    batches.push_back(B);
+                }
+            }
+    if ((int64_t)tbl.size() >= ((int64_t)1 << 31) || batches.size() >= ((size_t)1 << 31)) {
+        set_error("gint_setup: too many batches / table entries");
+        return GINT_EINVAL;
+    }
+    // useful flops: 2 n(r)^2 per point, n(r) = orbitals whose sphere contains r
+    {
+        // computed per batch from exact per-point counts (cheap: a distance test per slot and point)
+        for (auto &B : batches) {
+            int n1 = B.dims & 255, n2 = (B.dims >> 8) & 255, n3 = (B.dims >> 16) & 255;
+            for (int a = 0; a < n1; ++a)
+                for (int b = 0; b < n2; ++b)
+                    for (int c = 0; c < n3; ++c) {
+                        double off[3];
+                        for (int q = 0; q < 3; ++q) off[q] = a * bg.h[q] + b * bg.h[3 + q] + c * bg.h[6 + q];
+                        int n = 0;
+                        for (int s = 0; s < B.nslots; ++s) {
+                            const Slot &S = slots[B.slot0 + s];
+                            double d[3] = {S.d0[0] + off[0], S.d0[1] + off[1], S.d0[2] + off[2]};
+                            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                            if (r2 < rc[S.atom] * rc[S.atom]) n += S.norb;
+                        }
+                        flops_useful += 2.0 * n * (double)n;
+                    }
+        }
+    }
+    if (update_only) {
+        if (batches.size() != h->batches.size() || slot_img != h->slot_img || tbl != h->tbl) {
+            set_error("gint_update_positions: batch atom lists changed; build a new handle");
+            return GINT_ESTATE;
+        }
+        for (size_t i = 0; i < slots.size(); ++i)
+            if (slots[i].atom != h->slots[i].atom) {
+                set_error("gint_update_positions: batch atom lists changed; build a new handle");
+                return GINT_ESTATE;
+            }
+    }
+    h->keys = std::move(keys);
+    h->offsets = std::move(offsets);
+    h->partner = std::move(partner);
+    h->batches = std::move(batches);
+    h->slots = std::move(slots);
+    h->slot_img = std::move(slot_img);
+    h->tbl = std::move(tbl);
+    h->tau.assign(tau, tau + 3 * natoms);
+    gint_info_t &info = h->info;
+    info.npts = (int64_t)N1 * N2 * N3;
+    info.nblocks = nblocks;
+    info.nvalues = h->offsets[nblocks];
+    info.nbatches = (int64_t)h->batches.size();
+    info.nslots = (int64_t)h->slots.size();
+    info.max_orbitals = max_nb;
+    info.max_slots = max_slots;
+    info.dV = std::fabs(G.det) / (double)info.npts;
+    info.flops_useful = flops_useful;
+    info.flops_dense = flops_dense;
+    (void)rows;
+    h->plan.nblocks = nblocks;
+    h->plan.nvalues = info.nvalues;
+    h->plan.nbatches = (int)info.nbatches;
+    h->plan.dV = info.dV;
+    for (int i = 0; i < 3; ++i)
+        for (int c = 0; c < 3; ++c) h->plan.h[3 * i + c] = bg.h[3 * i + c];
+    return GINT_OK;
+}
+
+}  // namespace gint
+
+// ---------------------------------------------------------------------------------------
+// gint_setup and the host-only entry points
+// ---------------------------------------------------------------------------------------
+using namespace gint;
+
+template <class T>
+static cudaError_t upload(void **dst, const std::vector<T> &v)
+{
+    size_t bytes = std::max<size_t>(sizeof(T), v.size() * sizeof(T));
+    cudaError_t e = cudaMalloc(dst, bytes);
+    if (e != cudaSuccess) return e;
+    if (!v.empty()) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+static void free_dev(gint_handle h)
+{
+    void *ptrs[] = {h->d_coef64, h->d_coef32, h->d_batches, h->d_slots, h->d_tbl, h->d_partner,
+                    h->d_blkoff, h->d_blkrows, h->d_status, h->d_dmsym, h->d_red, h->d_hostio};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+static gint_status upload_geometry(gint_handle h)
+{
+    cudaError_t e;
+    // (re)upload everything that depends on positions; sizes are fixed after set-up
+    if (!h->d_batches) {
+        if ((e = upload(&h->d_batches, h->batches)) != cudaSuccess) return cuda_fail(e, "upload batches");
+        if ((e = upload(&h->d_slots, h->slots)) != cudaSuccess) return cuda_fail(e, "upload slots");
+        if ((e = upload(&h->d_tbl, h->tbl)) != cudaSuccess) return cuda_fail(e, "upload tables");
+        if ((e = upload(&h->d_partner, h->partner)) != cudaSuccess) return cuda_fail(e, "upload partner");
+        if ((e = upload(&h->d_blkoff, h->offsets)) != cudaSuccess) return cuda_fail(e, "upload offsets");
+        std::vector<int> rows(h->info.nblocks);
+        for (int64_t b = 0; b < h->info.nblocks; ++b) rows[b] = h->norb_atom[h->keys[5 * b]];
+        if ((e = upload(&h->d_blkrows, rows)) != cudaSuccess) return cuda_fail(e, "upload rows");
+    } else {
+        e = cudaMemcpy(h->d_slots, h->slots.data(), h->slots.size() * sizeof(Slot), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "update slots");
+    }
+    Plan &P = h->plan;
+    P.batches = (const Batch *)h->d_batches;
+    P.slots = (const Slot *)h->d_slots;
+    P.tbl = (const int *)h->d_tbl;
+    P.partner = (const int *)h->d_partner;
+    P.blk_off = (const int64_t *)h->d_blkoff;
+    P.blk_rows = (const int *)h->d_blkrows;
+    return GINT_OK;
+}
+
+extern "C" gint_status gint_setup(gint_handle *out, const double cell[9], int natoms, const int *species,
+                                  const double *tau, int nspecies, const gint_species *sp, const int grid[3],
+                                  const gint_options *opt)
+{
+    if (!out || !cell || !species || !tau || !sp || !grid) {
+        set_error("gint_setup: null argument");
+        return GINT_EINVAL;
+    }
+    *out = nullptr;
+    if (natoms < 1 || natoms >= (1 << 20) || nspecies < 1 || nspecies > kMaxSpecies) {
+        set_error("gint_setup: natoms must be in [1, 2^20) and nspecies in [1, %d]", kMaxSpecies);
+        return GINT_EINVAL;
+    }
+    for (int i = 0; i < 3; ++i)
+        if (grid[i] < 1 || grid[i] > (1 << 14)) {
+            set_error("gint_setup: grid dimension %d out of range", grid[i]);
+            return GINT_EINVAL;
+        }
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(cell[i])) {
+            set_error("gint_setup: non-finite cell");
+            return GINT_EINVAL;
+        }
+    Geo G = make_geo(cell);
+    if (!(std::fabs(G.det) > 1e-8)) {
+        set_error("gint_setup: singular cell");
+        return GINT_EINVAL;
+    }
+    for (int i = 0; i < natoms; ++i) {
+        if (species[i] < 0 || species[i] >= nspecies) {
+            set_error("gint_setup: species[%d] = %d out of range", i, species[i]);
+            return GINT_EINVAL;
+        }
+        for (int c = 0; c < 3; ++c)
+            if (!std::isfinite(tau[3 * i + c])) {
+                set_error("gint_setup: non-finite position of atom %d", i);
+                return GINT_EINVAL;
+            }
+    }
+    gint_options o{};
+    o.batch[0] = 4; o.batch[1] = 4; o.batch[2] = 8;
+    if (opt) {
+        for (int i = 0; i < 3; ++i)
+            if (opt->batch[i] > 0) o.batch[i] = opt->batch[i];
+    }
+    if (o.batch[0] > kMaxBatchDim || o.batch[1] > kMaxBatchDim || o.batch[2] > kMaxBatchDim ||
+        o.batch[0] * o.batch[1] * o.batch[2] > kMaxBatchPts || (o.batch[2] % 2)) {
+        set_error("gint_setup: batch %dx%dx%d invalid (<= %d per axis, <= %d points, even along a3)",
+                  o.batch[0], o.batch[1], o.batch[2], kMaxBatchDim, kMaxBatchPts);
+        return GINT_EINVAL;
+    }
+    // device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "gint_setup: no CUDA device");
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, dev)) != cudaSuccess) return cuda_fail(e, "gint_setup");
+    if (prop.major * 10 + prop.minor != 103) {
+        set_error("gint_setup: device %d is sm_%d%d; this library is built for sm_103a only", dev, prop.major,
+                  prop.minor);
+        return GINT_ECUDA;
+    }
+
+    gint_handle h = new gint_handle_s();
+    h->device = dev;
+    h->nsm = prop.multiProcessorCount;
+    memcpy(h->cell, cell, sizeof(h->cell));
+    for (int i = 0; i < 3; ++i) h->grid[i] = grid[i];
+    h->natoms = natoms;
+    h->nspecies = nspecies;
+    h->species.assign(species, species + natoms);
+    h->opt = o;
+    Plan &P = h->plan;
+    P.natoms = natoms;
+    P.nspecies = nspecies;
+    for (int i = 0; i < 3; ++i) P.grid[i] = grid[i];
+    P.npts = (int64_t)grid[0] * grid[1] * grid[2];
+    P.spin_limit = 4000000000LL;   // about 2 s at 2 GHz
+
+    // species and splines
+    std::vector<double> coef64;
+    std::vector<float4> coef32;
+    for (int s = 0; s < nspecies; ++s) {
+        const gint_species &S = sp[s];
+        if (S.nrad < 1 || S.nrad > kMaxRad || !S.l || !S.ftab || !S.dfdr0 || !(S.rcut > 0) || !(S.dr > 0) ||
+            S.ntab < 3) {
+            set_error("gint_setup: species %d invalid (nrad 1..%d, tables, rcut > 0, dr > 0, ntab >= 3)", s, kMaxRad);
+            delete h;
+            return GINT_EINVAL;
+        }
+        if ((S.ntab - 1) * S.dr < S.rcut * (1.0 - 1e-12)) {
+            set_error("gint_setup: species %d table ends at %g < rcut %g", s, (S.ntab - 1) * S.dr, S.rcut);
+            delete h;
+            return GINT_EINVAL;
+        }
+        DevSpecies &D = P.sp[s];
+        D.nrad = S.nrad;
+        D.nint = S.ntab - 1;
+        D.coef_off = (int)(coef64.size() / 4);
+        D.rcut = S.rcut;
+        D.inv_dr = 1.0 / S.dr;
+        D.rcut_f = (float)S.rcut;
+        D.inv_dr_f = (float)(1.0 / S.dr);
+        int norb = 0;
+        for (int r = 0; r < S.nrad; ++r) {
+            if (S.l[r] < 0 || S.l[r] > 2) {
+                set_error("gint_setup: species %d radial %d has l = %d (supported: 0..2)", s, r, S.l[r]);
+                delete h;
+                return GINT_EINVAL;
+            }
+            D.l[r] = S.l[r];
+            norb += 2 * S.l[r] + 1;
+        }
+        if (norb > kMaxOrbSpecies) {
+            set_error("gint_setup: species %d has %d orbitals (max %d)", s, norb, kMaxOrbSpecies);
+            delete h;
+            return GINT_EINVAL;
+        }
+        D.norb = norb;
+        for (int i = 0; i < S.nrad * S.ntab; ++i)
+            if (!std::isfinite(S.ftab[i])) {
+                set_error("gint_setup: species %d table has a non-finite value", s);
+                delete h;
+                return GINT_EINVAL;
+            }
+        // slopes per radial, then interval-major records
+        std::vector<std::vector<double>> k(S.nrad);
+        for (int r = 0; r < S.nrad; ++r) spline_slopes(S.ftab + (size_t)r * S.ntab, S.ntab, S.dr, S.dfdr0[r], 0.0, k[r]);
+        for (int i = 0; i < S.ntab - 1; ++i)
+            for (int r = 0; r < S.nrad; ++r) {
+                const double *y = S.ftab + (size_t)r * S.ntab;
+                double hh = S.dr;
+                double c0 = y[i], c1 = hh * k[r][i];
+                double c2 = 3.0 * (y[i + 1] - y[i]) - hh * (2.0 * k[r][i] + k[r][i + 1]);
+                double c3 = 2.0 * (y[i] - y[i + 1]) + hh * (k[r][i] + k[r][i + 1]);
+                coef64.insert(coef64.end(), {c0, c1, c2, c3});
+                coef32.push_back(make_float4((float)c0, (float)c1, (float)c2, (float)c3));
+            }
+    }
+    h->norb_atom.resize(natoms);
+    for (int i = 0; i < natoms; ++i) h->norb_atom[i] = P.sp[species[i]].norb;
+
+    gint_status st = build_geometry(h, tau, false);
+    if (st != GINT_OK) {
+        delete h;
+        return st;
+    }
+    if ((e = upload(&h->d_coef64, coef64)) != cudaSuccess || (e = upload(&h->d_coef32, coef32)) != cudaSuccess) {
+        free_dev(h);
+        delete h;
+        return cuda_fail(e, "gint_setup: upload splines");
+    }
+    P.coef64 = (const double *)h->d_coef64;
+    P.coef32 = (const float4 *)h->d_coef32;
+    if ((st = upload_geometry(h)) != GINT_OK) {
+        free_dev(h);
+        delete h;
+        return st;
+    }
+    if ((e = cudaMalloc((void **)&h->d_status, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(h->d_status, 0, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&h->d_dmsym, std::max<size_t>(8, h->info.nvalues * sizeof(double)))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&h->d_red, 4096 * sizeof(double))) != cudaSuccess) {
+        free_dev(h);
+        delete h;
+        return cuda_fail(e, "gint_setup: allocate");
+    }
+    P.status = h->d_status;
+    *out = h;
+    return GINT_OK;
+}
+
+extern "C" gint_status gint_destroy(gint_handle h)
+{
+    if (!h) return GINT_OK;
+    free_dev(h);
+    delete h;
+    return GINT_OK;
+}
+
+extern "C" gint_status gint_block_layout(gint_handle h, int64_t *nblocks, int64_t *nvalues, const int32_t **keys,
+                                         const int64_t **offsets)
+{
+    if (!h) {
+        set_error("gint_block_layout: null handle");
+        return GINT_EINVAL;
+    }
+    if (nblocks) *nblocks = h->info.nblocks;
+    if (nvalues) *nvalues = h->info.nvalues;
+    if (keys) *keys = h->keys.data();
+    if (offsets) *offsets = h->offsets.data();
+    return GINT_OK;
+}
+
+extern "C" gint_status gint_get_info(gint_handle h, gint_info_t *info)
+{
+    if (!h || !info) {
+        set_error("gint_get_info: null argument");
+        return GINT_EINVAL;
+    }
+    *info = h->info;
+    return GINT_OK;
+}
+
+extern "C" gint_status gint_update_positions(gint_handle h, const double *tau)
+{
+    if (!h || !tau) {
+        set_error("gint_update_positions: null argument");
+        return GINT_EINVAL;
+    }
+    for (int i = 0; i < 3 * h->natoms; ++i)
+        if (!std::isfinite(tau[i])) {
+            set_error("gint_update_positions: non-finite position");
+            return GINT_EINVAL;
+        }
+    // build into a scratch copy so a topology change leaves the handle untouched
+    gint_handle_s tmp;
+    tmp.plan = h->plan;
+    memcpy(tmp.cell, h->cell, sizeof(tmp.cell));
+    memcpy(tmp.grid, h->grid, sizeof(tmp.grid));
+    tmp.natoms = h->natoms;
+    tmp.nspecies = h->nspecies;
+    tmp.species = h->species;
+    tmp.norb_atom = h->norb_atom;
+    tmp.keys = h->keys;
+    tmp.batches = h->batches;
+    tmp.slots = h->slots;
+    tmp.slot_img = h->slot_img;
+    tmp.tbl = h->tbl;
+    tmp.opt = h->opt;
+    gint_status st = build_geometry(&tmp, tau, true);
+    if (st != GINT_OK) return st;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(e, "gint_update_positions");
+    h->slots = std::move(tmp.slots);
+    h->tau = std::move(tmp.tau);
+    h->info = tmp.info;
+    h->plan.dV = tmp.plan.dV;
+    return upload_geometry(h);
+}
+
+extern "C" const char *gint_last_error(void) { return gint::last_error(); }

@@ -1,0 +1,814 @@
+// tcgen05 tensor-core kernels of libgint: the split-precision grid integrations.
+//
+// The per-batch contractions (Sec. IV.B: "parallel matrix operations" over partitions of the
+// real-space grid) run on the 5th-generation tensor cores:
+//   vlocal      P_b = Phi_b^T diag(V) Phi_b dV      M = N = orbitals of the batch, K = points
+//   rho/force   Psi_b = Phi_b D_b                   M = points, N = K = orbitals of the batch
+// Each FP32 operand x is split into terms (hi + lo for TF32x3 and BF16x3, hi + mid + lo for
+// BF16x6); the products of total order <= 1 (TF32x3, BF16x3) or <= 2 (BF16x6) accumulate in
+// FP32 in tensor memory (TMEM); the cross-batch sums (block store, rho(r), forces) are FP64.
+//
+// One persistent CTA per SM, 8 warps:
+//   warps 0-3  producers: orbital values (FP32, spline x solid harmonic) into an FP32 staging
+//              tile, then split into the canonical K-major no-swizzle shared-memory layout
+//              (8-row x 16-byte core matrices; the K-direction core-matrix stride is padded
+//              to 144 bytes so 16-byte stores from a warp spread over all banks); thread 0
+//              also issues the MMAs and commits them to mbarriers.
+//   warps 4-7  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes 32(w-4)..),
+//              then the FP64 scatter into the block store (vlocal) or rho(r)/force (rho).
+// Every mbarrier wait is bounded (clock64 budget); a wait that runs out records
+// GINT_ETIMEOUT in the status word and the CTA drains and exits without deadlock.
+#include <cuda_bf16.h>
+
+#include "gint_device.cuh"
+
+namespace gint {
+namespace {
+
+constexpr int kProd = 128;        // producer threads
+constexpr int kEpi = 128;         // epilogue threads
+constexpr int kThreadsTC = kProd + kEpi;
+constexpr int kLBO = 144;         // bytes between core matrices along K
+constexpr int kTmemCols = 512;
+constexpr int kWin = 64;          // epilogue window (columns) of the rho kernel
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t sbo)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(kLBO >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(su32(bar)) : "memory");
+}
+
+// bounded wait on the phase with the given parity; false if the budget ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long budget)
+{
+    const uint32_t a = su32(bar);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(ok)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > budget) return false;
+    }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+template <bool F16KIND>
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    if constexpr (F16KIND)
+        asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d),
+                     "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    else
+        asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(d),
+                     "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float *v)
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------------ precision schemes
+// CG elements = 16 bytes per core-matrix row; KCM core matrices per row per pipeline chunk.
+// PA/PB: operand term of product q, packed one nibble per product.
+struct TF32x3 {
+    static constexpr int CG = 4, NT = 2, NPROD = 3, KCM = 4;
+    static constexpr bool F16 = false;
+    static constexpr uint32_t FMT = 2, PA = 0x100, PB = 0x010;
+};
+struct BF16x3 {
+    static constexpr int CG = 8, NT = 2, NPROD = 3, KCM = 4;
+    static constexpr bool F16 = true;
+    static constexpr uint32_t FMT = 1, PA = 0x100, PB = 0x010;
+};
+struct BF16x6 {
+    static constexpr int CG = 8, NT = 3, NPROD = 6, KCM = 2;
+    static constexpr bool F16 = true;
+    static constexpr uint32_t FMT = 1, PA = 0x210100, PB = 0x012010;
+};
+__host__ __device__ constexpr int term(uint32_t packed, int q) { return (int)((packed >> (4 * q)) & 0xF); }
+
+__device__ __forceinline__ float tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// split CG consecutive FP32 values into NT terms and store each as one 16-byte chunk
+template <class S>
+__device__ __forceinline__ void split_store(const float *x, unsigned char *const *dst)
+{
+    if constexpr (!S::F16) {
+        float4 hi, lo;
+        float *h = &hi.x, *l = &lo.x;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            h[i] = tf32_rna(x[i]);
+            l[i] = tf32_rna(x[i] - h[i]);
+        }
+        *reinterpret_cast<float4 *>(dst[0]) = hi;
+        *reinterpret_cast<float4 *>(dst[1]) = lo;
+    } else {
+        __align__(16) __nv_bfloat16 t[S::NT][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float r = x[i];
+#pragma unroll
+            for (int k = 0; k < S::NT; ++k) {
+                __nv_bfloat16 b = __float2bfloat16_rn(r);
+                t[k][i] = b;
+                r -= __bfloat162float(b);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < S::NT; ++k) *reinterpret_cast<uint4 *>(dst[k]) = *reinterpret_cast<const uint4 *>(t[k]);
+    }
+}
+
+template <class S>
+__device__ __forceinline__ void zero_store(unsigned char *const *dst)
+{
+#pragma unroll
+    for (int k = 0; k < S::NT; ++k) *reinterpret_cast<uint4 *>(dst[k]) = make_uint4(0, 0, 0, 0);
+}
+
+// byte offset of core-matrix row (row, kc) in an operand array
+template <class S>
+__device__ __forceinline__ int cm_off(int row, int kc)
+{
+    constexpr int SBO = S::KCM * kLBO;
+    return (row >> 3) * SBO + kc * kLBO + (row & 7) * 16;
+}
+
+template <class S>
+constexpr int arr_bytes(int rows)
+{
+    return (rows / 8) * S::KCM * kLBO;
+}
+
+template <class S>
+__host__ __device__ constexpr uint32_t idesc(int M, int N)
+{
+    return (1u << 4) | (S::FMT << 7) | (S::FMT << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ------------------------------------------------------------------ shared batch metadata
+struct PSlot {
+    int species, off, norb, atom;
+    float dh[3], dl[3];
+};
+
+__device__ __forceinline__ void unpack(int dims, int &n1, int &n2, int &n3)
+{
+    n1 = dims & 255;
+    n2 = (dims >> 8) & 255;
+    n3 = (dims >> 16) & 255;
+}
+
+// slots and point offsets of batch B into shared memory (called by the threads of one role)
+__device__ __forceinline__ void load_geom(const Plan &P, const Batch &B, PSlot *ps, float *poff, int tid, int nthr)
+{
+    for (int s = tid; s < B.nslots; s += nthr) {
+        const Slot S = P.slots[B.slot0 + s];
+        PSlot q;
+        q.species = S.species;
+        q.off = S.orb_off;
+        q.norb = S.norb;
+        q.atom = S.atom;
+        for (int c = 0; c < 3; ++c) split_f32(S.d0[c], q.dh[c], q.dl[c]);
+        ps[s] = q;
+    }
+    int n1, n2, n3;
+    unpack(B.dims, n1, n2, n3);
+    const int np = n1 * n2 * n3;
+    for (int p = tid; p < np; p += nthr) {
+        const int c = p % n3, b = (p / n3) % n2, a = p / (n3 * n2);
+        double off[3];
+        point_offset64(P, a, b, c, off);
+        for (int q = 0; q < 3; ++q) split_f32(off[q], poff[6 * p + q], poff[6 * p + 3 + q]);
+    }
+}
+
+__device__ __forceinline__ void disp(const PSlot &s, const float *po, float &dx, float &dy, float &dz)
+{
+    dx = (s.dh[0] + po[0]) + (s.dl[0] + po[3]);
+    dy = (s.dh[1] + po[1]) + (s.dl[1] + po[4]);
+    dz = (s.dh[2] + po[2]) + (s.dl[2] + po[5]);
+}
+
+__device__ __forceinline__ int64_t grid_index(const Plan &P, const Batch &B, int p, int n2, int n3)
+{
+    const int c = p % n3, b = (p / n3) % n2, a = p / (n3 * n2);
+    return ((int64_t)(B.i0 + a) * P.grid[1] + (B.j0 + b)) * P.grid[2] + (B.k0 + c);
+}
+
+// role-uniform bounded wait: thread `leader` waits, the verdict is shared through `flag`
+__device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, const Plan &P, int rtid, volatile int *flag,
+                                          int barid, int nthr)
+{
+    if (rtid == 0) {
+        bool ok = !aborted(P) && mbar_wait(bar, parity, P.spin_limit);
+        if (!ok) report_timeout(P);
+        *flag = ok ? 0 : 1;
+    }
+    named_sync(barid, nthr);
+    const bool ok = *flag == 0;
+    named_sync(barid, nthr);
+    return ok;
+}
+
+// ====================================================================== vlocal
+template <class S>
+struct VSmem {
+    static constexpr int KC = S::KCM * S::CG;             // points per chunk
+    static constexpr int ARR = arr_bytes<S>(kMaxNb);      // one operand term, 256 rows
+    static constexpr int STAGE = 2 * S::NT * ARR;         // A terms then B terms
+    static constexpr int NSTAGE = 2;
+    static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [256][KC]
+    static constexpr int OFF_PSLOT = OFF_STG + kMaxNb * KC * 4;             // PSlot[64]
+    static constexpr int OFF_POFF = OFF_PSLOT + kMaxSlots * (int)sizeof(PSlot);  // float [128][6]
+    static constexpr int OFF_V = OFF_POFF + kMaxBatchPts * 6 * 4;           // float [128]
+    static constexpr int OFF_TBL = OFF_V + kMaxBatchPts * 4;                // int [64*64]
+    static constexpr int OFF_OMAP = OFF_TBL + kMaxSlots * kMaxSlots * 4;    // uchar oslot[256], oidx[256]
+    static constexpr int OFF_NORB = OFF_OMAP + 2 * kMaxNb;                  // uchar [64]
+    static constexpr int OFF_BAR = OFF_NORB + kMaxSlots;                    // 8 mbarriers
+    static constexpr int OFF_MISC = OFF_BAR + 8 * 8;                        // tmem base, flags
+    static constexpr int TOTAL = OFF_MISC + 64;
+};
+
+template <class S>
+__global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const double *__restrict__ V, double *H)
+{
+    using L = VSmem<S>;
+    constexpr int KC = L::KC;
+    constexpr int SBO = S::KCM * kLBO;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    float *stg = reinterpret_cast<float *>(sm + L::OFF_STG);
+    PSlot *ps = reinterpret_cast<PSlot *>(sm + L::OFF_PSLOT);
+    float *poff = reinterpret_cast<float *>(sm + L::OFF_POFF);
+    float *vs = reinterpret_cast<float *>(sm + L::OFF_V);
+    int *tbl = reinterpret_cast<int *>(sm + L::OFF_TBL);
+    unsigned char *oslot = sm + L::OFF_OMAP, *oidx = oslot + kMaxNb;
+    unsigned char *snorb = sm + L::OFF_NORB;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::OFF_BAR);
+    uint64_t *empty = bars, *accfull = bars + 2, *accempty = bars + 3, *fin = bars + 4;
+    uint32_t *tmem_base = reinterpret_cast<uint32_t *>(sm + L::OFF_MISC);
+    volatile int *pflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 4);
+    volatile int *eflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 8);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        mbar_init(&empty[0], 1);
+        mbar_init(&empty[1], 1);
+        mbar_init(accfull, 1);
+        mbar_init(accempty, kEpi);
+        mbar_init(fin, 1);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_base)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_base;
+
+    if (tid < kProd) {
+        // ------------------------------------------------------------ producers + MMA issue
+        const int pt = tid;
+        int g = 0;  // chunk counter (stage = g & 1)
+        int it = 0;
+        bool ok = true;
+        for (int bi = blockIdx.x; bi < P.nbatches && ok; bi += gridDim.x) {
+            const Batch B = P.batches[bi];
+            int n1, n2, n3;
+            unpack(B.dims, n1, n2, n3);
+            const int ns = B.nslots, nb = B.nb, npb = n1 * n2 * n3;
+            const int npad = (nb + 15) & ~15;
+            if (nb == 0) continue;  // no orbital reaches this batch: nothing to add
+            named_sync(1, kProd);
+            load_geom(P, B, ps, poff, pt, kProd);
+            for (int p = pt; p < kMaxBatchPts; p += kProd) vs[p] = p < npb ? (float)V[grid_index(P, B, p, n2, n3)] : 0.f;
+            named_sync(1, kProd);
+            const int nch = (npb + KC - 1) / KC;
+            for (int ch = 0; ch < nch && ok; ++ch, ++g) {
+                const int stage = g & 1;
+                // phase 1: orbital values at the chunk's points -> staging [row][KC]
+                for (int w = pt; w < KC * ns; w += kProd) {
+                    const int k = w % KC, s = w / KC;
+                    const int p = ch * KC + k;
+                    const PSlot sl = ps[s];
+                    float *col = stg + sl.off * KC + k;
+                    if (p < npb) {
+                        float dx, dy, dz;
+                        disp(sl, poff + 6 * p, dx, dy, dz);
+                        eval_orbitals<float, false>(P, sl.species, dx, dy, dz, [&](int o, float v) { col[o * KC] = v; });
+                    } else {
+                        for (int o = 0; o < sl.norb; ++o) col[o * KC] = 0.f;
+                    }
+                }
+                if (g >= 2) ok = role_wait(&empty[stage], ((g >> 1) - 1) & 1, P, pt, pflag, 1, kProd);
+                else named_sync(1, kProd);
+                if (!ok) break;
+                // phase 2: split Phi (A) and V*Phi (B) into the canonical layout
+                unsigned char *base = sm + stage * L::STAGE;
+                for (int w = pt; w < npad * S::KCM; w += kProd) {
+                    const int kc = w % S::KCM, row = w / S::KCM;
+                    unsigned char *da[S::NT], *db[S::NT];
+#pragma unroll
+                    for (int t = 0; t < S::NT; ++t) {
+                        da[t] = base + t * L::ARR + cm_off<S>(row, kc);
+                        db[t] = base + (S::NT + t) * L::ARR + cm_off<S>(row, kc);
+                    }
+                    if (row < nb) {
+                        float x[S::CG], y[S::CG];
+#pragma unroll
+                        for (int i = 0; i < S::CG; ++i) {
+                            x[i] = stg[row * KC + kc * S::CG + i];
+                            y[i] = x[i] * vs[ch * KC + kc * S::CG + i];
+                        }
+                        split_store<S>(x, da);
+                        split_store<S>(y, db);
+                    } else {
+                        zero_store<S>(da);
+                        zero_store<S>(db);
+                    }
+                }
+                fence_async_smem();
+                named_sync(1, kProd);
+                if (pt == 0) {
+                    if (ch == 0 && it > 0) {
+                        ok = !aborted(P) && mbar_wait(accempty, (it - 1) & 1, P.spin_limit);
+                        if (!ok) report_timeout(P);
+                    }
+                    if (ok) {
+                        tc_fence_after();
+                        const uint32_t a0 = su32(base), b0 = su32(base + S::NT * L::ARR);
+#pragma unroll
+                        for (int ks = 0; ks < S::KCM / 2; ++ks) {
+                            for (int t = 0; t < (nb > 128 ? 2 : 1); ++t) {
+                                const int N = t == 0 ? npad : npad - 128;
+                                const uint32_t id = idesc<S>(128, N);
+                                const uint32_t rowoff = t * 16 * SBO;
+#pragma unroll
+                                for (int q = 0; q < S::NPROD; ++q) {
+                                    const uint64_t da = sdesc(a0 + term(S::PA, q) * L::ARR + rowoff + ks * 2 * kLBO, SBO);
+                                    const uint64_t db = sdesc(b0 + term(S::PB, q) * L::ARR + rowoff + ks * 2 * kLBO, SBO);
+                                    const uint32_t acc = (ch == 0 && ks == 0 && q == 0) ? 0u : 1u;
+                                    umma<S::F16>(tmem + t * 256, da, db, id, acc);
+                                }
+                            }
+                        }
+                        umma_commit(&empty[stage]);
+                        if (ch == nch - 1) umma_commit(accfull);
+                    }
+                    *pflag = ok ? 0 : 1;
+                }
+                named_sync(1, kProd);
+                ok = ok && (*pflag == 0);
+                named_sync(1, kProd);
+            }
+            ++it;
+        }
+        if (pt == 0) {
+            // wait (bounded) for every MMA this thread issued before TMEM is released
+            umma_commit(fin);
+            if (!mbar_wait(fin, 0, P.spin_limit)) report_timeout(P);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int et = tid - kProd, q = et >> 5, lane = et & 31;
+        int it = 0;
+        for (int bi = blockIdx.x; bi < P.nbatches; bi += gridDim.x) {
+            const Batch B = P.batches[bi];
+            const int ns = B.nslots, nb = B.nb;
+            const int npad = (nb + 15) & ~15;
+            if (nb == 0) continue;
+            named_sync(2, kEpi);
+            for (int e = et; e < ns * ns; e += kEpi) tbl[e] = P.tbl[B.tbl + e];
+            for (int s = et; s < ns; s += kEpi) {
+                const Slot sl = P.slots[B.slot0 + s];
+                snorb[s] = (unsigned char)sl.norb;
+                for (int o = 0; o < sl.norb; ++o) {
+                    oslot[sl.orb_off + o] = (unsigned char)s;
+                    oidx[sl.orb_off + o] = (unsigned char)o;
+                }
+            }
+            if (!role_wait(accfull, it & 1, P, et, eflag, 2, kEpi)) break;
+            tc_fence_after();
+            const double dV = P.dV;
+            for (int t = 0; t < (nb > 128 ? 2 : 1); ++t) {
+                const int mu = t * 128 + q * 32 + lane;
+                const bool rv = mu < nb;
+                const int a = rv ? oslot[mu] : 0, oa = rv ? oidx[mu] : 0;
+                const int na = snorb[a];
+                for (int c0 = t * 128; c0 < npad; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 256 + c0 - t * 128), v);
+                    if (!rv) continue;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int nu = c0 + j;
+                        if (nu >= nb) break;
+                        const int b = oslot[nu], ob = oidx[nu];
+                        const bool both = (t == 1) || (nu < 128);
+                        scatter_elem(H, tbl, ns, a, oa, na, b, ob, snorb[b], (double)v[j] * dV, both);
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(accempty);
+            ++it;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
+// ====================================================================== rho / force
+template <class S>
+struct RSmem {
+    static constexpr int KC = S::KCM * S::CG;              // orbitals per chunk
+    static constexpr int ARR_A = arr_bytes<S>(kMaxBatchPts);
+    static constexpr int ARR_B = arr_bytes<S>(kMaxNb);
+    static constexpr int STAGE = S::NT * (ARR_A + ARR_B);
+    static constexpr int NSTAGE = 2;
+    static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [KC][128]
+    static constexpr int OFF_PSLOT = OFF_STG + KC * kMaxBatchPts * 4;       // producer PSlot[64]
+    static constexpr int OFF_POFF = OFF_PSLOT + kMaxSlots * (int)sizeof(PSlot);
+    static constexpr int OFF_TBL = OFF_POFF + kMaxBatchPts * 24;            // int [64*64]
+    static constexpr int OFF_OMAP = OFF_TBL + kMaxSlots * kMaxSlots * 4;    // oslot[256], oidx[256]
+    static constexpr int OFF_EPSLOT = OFF_OMAP + 2 * kMaxNb;                // epilogue PSlot[64]
+    static constexpr int OFF_EPOFF = OFF_EPSLOT + kMaxSlots * (int)sizeof(PSlot);
+    static constexpr int OFF_WIN = OFF_EPOFF + kMaxBatchPts * 24;           // float [4][kWin][32]
+    static constexpr int OFF_FACC = OFF_WIN + 4 * kWin * 32 * 4;            // double [64][3]
+    static constexpr int OFF_BAR = OFF_FACC + kMaxSlots * 3 * 8;
+    static constexpr int OFF_MISC = OFF_BAR + 8 * 8;
+    static constexpr int TOTAL = OFF_MISC + 64;
+};
+
+template <class S, bool RHO, bool FORCE>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_rho_tc(Plan P, const double *__restrict__ V, const double *__restrict__ DM, double *rho, double *F)
+{
+    using L = RSmem<S>;
+    constexpr int KC = L::KC;
+    constexpr int SBO = S::KCM * kLBO;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    float *stg = reinterpret_cast<float *>(sm + L::OFF_STG);
+    PSlot *ps = reinterpret_cast<PSlot *>(sm + L::OFF_PSLOT);
+    float *poff = reinterpret_cast<float *>(sm + L::OFF_POFF);
+    int *tbl = reinterpret_cast<int *>(sm + L::OFF_TBL);
+    unsigned char *oslot = sm + L::OFF_OMAP, *oidx = oslot + kMaxNb;
+    PSlot *eps = reinterpret_cast<PSlot *>(sm + L::OFF_EPSLOT);
+    float *epoff = reinterpret_cast<float *>(sm + L::OFF_EPOFF);
+    float *win = reinterpret_cast<float *>(sm + L::OFF_WIN);
+    double *facc = reinterpret_cast<double *>(sm + L::OFF_FACC);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::OFF_BAR);
+    uint64_t *empty = bars, *accfull = bars + 2, *accempty = bars + 4, *fin = bars + 6;
+    uint32_t *tmem_base = reinterpret_cast<uint32_t *>(sm + L::OFF_MISC);
+    volatile int *pflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 4);
+    volatile int *eflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 8);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        mbar_init(&empty[0], 1);
+        mbar_init(&empty[1], 1);
+        mbar_init(&accfull[0], 1);
+        mbar_init(&accfull[1], 1);
+        mbar_init(&accempty[0], kEpi);
+        mbar_init(&accempty[1], kEpi);
+        mbar_init(fin, 1);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_base)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_base;
+
+    if (tid < kProd) {
+        // ------------------------------------------------------------ producers + MMA issue
+        const int pt = tid;
+        int g = 0, it = 0;
+        bool ok = true;
+        for (int bi = blockIdx.x; bi < P.nbatches && ok; bi += gridDim.x) {
+            const Batch B = P.batches[bi];
+            int n1, n2, n3;
+            unpack(B.dims, n1, n2, n3);
+            const int ns = B.nslots, nb = B.nb, npb = n1 * n2 * n3;
+            const int npad = (nb + 15) & ~15;
+            const int buf = it & 1;
+            if (nb == 0) continue;  // the epilogue writes rho = 0 there
+            named_sync(1, kProd);
+            load_geom(P, B, ps, poff, pt, kProd);
+            for (int e = pt; e < ns * ns; e += kProd) tbl[e] = P.tbl[B.tbl + e];
+            named_sync(1, kProd);
+            for (int s = pt; s < ns; s += kProd)
+                for (int o = 0; o < ps[s].norb; ++o) {
+                    oslot[ps[s].off + o] = (unsigned char)s;
+                    oidx[ps[s].off + o] = (unsigned char)o;
+                }
+            named_sync(1, kProd);
+            const int nch = (nb + KC - 1) / KC;
+            for (int ch = 0; ch < nch && ok; ++ch, ++g) {
+                const int stage = g & 1;
+                const int k0 = ch * KC, k1 = min(k0 + KC, nb);
+                const int s_lo = oslot[k0], s_hi = oslot[k1 - 1];
+                const int nsc = s_hi - s_lo + 1;
+                // phase 1: orbital values of the chunk's orbitals at all points -> staging [KC][128]
+                for (int w = pt; w < kMaxBatchPts * nsc; w += kProd) {
+                    const int p = w % kMaxBatchPts, s = s_lo + w / kMaxBatchPts;
+                    const PSlot sl = ps[s];
+                    float *col = stg + p;
+                    const int base_k = sl.off - k0;
+                    if (p < npb) {
+                        float dx, dy, dz;
+                        disp(sl, poff + 6 * p, dx, dy, dz);
+                        eval_orbitals<float, false>(P, sl.species, dx, dy, dz, [&](int o, float v) {
+                            const int k = base_k + o;
+                            if (k >= 0 && k < KC) col[k * kMaxBatchPts] = v;
+                        });
+                    } else {
+                        for (int o = 0; o < sl.norb; ++o) {
+                            const int k = base_k + o;
+                            if (k >= 0 && k < KC) col[k * kMaxBatchPts] = 0.f;
+                        }
+                    }
+                }
+                for (int w = pt; w < (KC - (k1 - k0)) * kMaxBatchPts; w += kProd)
+                    stg[(k1 - k0) * kMaxBatchPts + w] = 0.f;
+                if (g >= 2) ok = role_wait(&empty[stage], ((g >> 1) - 1) & 1, P, pt, pflag, 1, kProd);
+                else named_sync(1, kProd);
+                if (!ok) break;
+                unsigned char *base = sm + stage * L::STAGE;
+                // phase 2a: A = Phi (rows = points, K = orbitals of the chunk)
+                for (int w = pt; w < kMaxBatchPts * S::KCM; w += kProd) {
+                    const int p = w % kMaxBatchPts, kc = w / kMaxBatchPts;
+                    unsigned char *da[S::NT];
+#pragma unroll
+                    for (int t = 0; t < S::NT; ++t) da[t] = base + t * L::ARR_A + cm_off<S>(p, kc);
+                    float x[S::CG];
+#pragma unroll
+                    for (int i = 0; i < S::CG; ++i) x[i] = stg[(kc * S::CG + i) * kMaxBatchPts + p];
+                    split_store<S>(x, da);
+                }
+                // phase 2b: B = D rows nu (N), K = orbitals mu of the chunk: D(b_nu, a_mu)[o_nu][o_mu]
+                for (int w = pt; w < npad * S::KCM; w += kProd) {
+                    const int kc = w % S::KCM, nu = w / S::KCM;
+                    unsigned char *db[S::NT];
+#pragma unroll
+                    for (int t = 0; t < S::NT; ++t) db[t] = base + S::NT * L::ARR_A + t * L::ARR_B + cm_off<S>(nu, kc);
+                    if (nu >= nb) {
+                        zero_store<S>(db);
+                        continue;
+                    }
+                    const int b = oslot[nu], ob = oidx[nu];
+                    float x[S::CG];
+#pragma unroll
+                    for (int i = 0; i < S::CG; ++i) {
+                        const int mu = k0 + kc * S::CG + i;
+                        float v = 0.f;
+                        if (mu < nb) {
+                            const int a = oslot[mu];
+                            const int e = tbl[b * ns + a];
+                            if (e >= 0) v = (float)__ldg(DM + (e >> 1) + ob * ps[a].norb + oidx[mu]);
+                        }
+                        x[i] = v;
+                    }
+                    split_store<S>(x, db);
+                }
+                fence_async_smem();
+                named_sync(1, kProd);
+                if (pt == 0) {
+                    if (ch == 0 && it >= 2) {
+                        ok = !aborted(P) && mbar_wait(&accempty[buf], ((it >> 1) - 1) & 1, P.spin_limit);
+                        if (!ok) report_timeout(P);
+                    }
+                    if (ok) {
+                        tc_fence_after();
+                        const uint32_t a0 = su32(base), b0 = su32(base + S::NT * L::ARR_A);
+                        const uint32_t id = idesc<S>(128, npad);
+#pragma unroll
+                        for (int ks = 0; ks < S::KCM / 2; ++ks) {
+#pragma unroll
+                            for (int q = 0; q < S::NPROD; ++q) {
+                                const uint64_t da = sdesc(a0 + term(S::PA, q) * L::ARR_A + ks * 2 * kLBO, SBO);
+                                const uint64_t db = sdesc(b0 + term(S::PB, q) * L::ARR_B + ks * 2 * kLBO, SBO);
+                                const uint32_t acc = (ch == 0 && ks == 0 && q == 0) ? 0u : 1u;
+                                umma<S::F16>(tmem + buf * 256, da, db, id, acc);
+                            }
+                        }
+                        umma_commit(&empty[stage]);
+                        if (ch == nch - 1) umma_commit(&accfull[buf]);
+                    }
+                    *pflag = ok ? 0 : 1;
+                }
+                named_sync(1, kProd);
+                ok = ok && (*pflag == 0);
+                named_sync(1, kProd);
+            }
+            ++it;
+        }
+        if (pt == 0) {
+            umma_commit(fin);
+            if (!mbar_wait(fin, 0, P.spin_limit)) report_timeout(P);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue: rho and force
+        const int et = tid - kProd, q = et >> 5, lane = et & 31;
+        const int p = et;  // TMEM lane = point of the batch
+        float *w = win + q * kWin * 32;
+        int it = 0;
+        for (int bi = blockIdx.x; bi < P.nbatches; bi += gridDim.x) {
+            const Batch B = P.batches[bi];
+            int n1, n2, n3;
+            unpack(B.dims, n1, n2, n3);
+            const int ns = B.nslots, npb = n1 * n2 * n3;
+            const int buf = it & 1;
+            if (B.nb == 0) {
+                if (RHO && p < npb) rho[grid_index(P, B, p, n2, n3)] = 0.0;
+                continue;
+            }
+            named_sync(2, kEpi);
+            load_geom(P, B, eps, epoff, et, kEpi);
+            if (FORCE)
+                for (int e = et; e < 3 * ns; e += kEpi) facc[e] = 0.0;
+            if (!role_wait(&accfull[buf], (it >> 1) & 1, P, et, eflag, 2, kEpi)) break;
+            tc_fence_after();
+            const bool pv = p < npb;
+            const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256);
+            float vp = 0.f;
+            int64_t gi = 0;
+            if (pv) {
+                gi = grid_index(P, B, p, n2, n3);
+                if (FORCE) vp = (float)V[gi];
+            }
+            float racc = 0.f;
+            int w0 = -1000, wn = 0;
+            for (int s = 0; s < ns; ++s) {
+                const PSlot sl = eps[s];
+                if (sl.off < w0 || sl.off + sl.norb > w0 + wn) {
+                    w0 = sl.off & ~15;
+                    wn = ((sl.off + sl.norb - w0) + 15) & ~15;
+                    __syncwarp();
+                    for (int c = 0; c < wn; c += 16) {
+                        float v[16];
+                        tmem_ld16(trow + (uint32_t)(w0 + c), v);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) w[(c + j) * 32 + lane] = v[j];
+                    }
+                    __syncwarp();
+                }
+                const float *col = w + (sl.off - w0) * 32 + lane;
+                float fx = 0.f, fy = 0.f, fz = 0.f;
+                if (pv) {
+                    float dx, dy, dz;
+                    disp(sl, epoff + 6 * p, dx, dy, dz);
+                    if (FORCE)
+                        eval_orbitals<float, true>(P, sl.species, dx, dy, dz,
+                                                   [&](int o, float v, float gx, float gy, float gz) {
+                                                       const float y = col[o * 32];
+                                                       racc += v * y;
+                                                       fx += gx * y; fy += gy * y; fz += gz * y;
+                                                   });
+                    else
+                        eval_orbitals<float, false>(P, sl.species, dx, dy, dz,
+                                                    [&](int o, float v) { racc += v * col[o * 32]; });
+                }
+                if (FORCE) {
+                    fx *= vp; fy *= vp; fz *= vp;
+#pragma unroll
+                    for (int m = 16; m > 0; m >>= 1) {
+                        fx += __shfl_xor_sync(0xffffffffu, fx, m);
+                        fy += __shfl_xor_sync(0xffffffffu, fy, m);
+                        fz += __shfl_xor_sync(0xffffffffu, fz, m);
+                    }
+                    if (lane == 0) {
+                        atomicAdd(&facc[3 * s + 0], (double)fx);
+                        atomicAdd(&facc[3 * s + 1], (double)fy);
+                        atomicAdd(&facc[3 * s + 2], (double)fz);
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&accempty[buf]);
+            if (RHO && pv) rho[gi] = (double)racc;
+            if (FORCE) {
+                named_sync(2, kEpi);
+                for (int e = et; e < 3 * ns; e += kEpi)
+                    atomicAdd(&F[3 * eps[e / 3].atom + e % 3], 2.0 * P.dV * facc[e]);
+            }
+            ++it;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
+template <class S>
+cudaError_t vlocal_launch(const Plan &P, const double *V, double *H, cudaStream_t s, int nsm)
+{
+    constexpr int smem = VSmem<S>::TOTAL;
+    static_assert(smem <= 232448, "vlocal shared memory");
+    cudaError_t e = cudaFuncSetAttribute(k_vlocal_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(nsm, P.nbatches);
+    k_vlocal_tc<S><<<grid, kThreadsTC, smem, s>>>(P, V, H);
+    return cudaGetLastError();
+}
+
+template <class S, bool R, bool Fo>
+cudaError_t rho_launch3(const Plan &P, const double *V, const double *DM, double *rho, double *F, cudaStream_t s,
+                        int nsm)
+{
+    constexpr int smem = RSmem<S>::TOTAL;
+    static_assert(smem <= 232448, "rho shared memory");
+    cudaError_t e = cudaFuncSetAttribute(k_rho_tc<S, R, Fo>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::min(nsm, P.nbatches);
+    k_rho_tc<S, R, Fo><<<grid, kThreadsTC, smem, s>>>(P, V, DM, rho, F);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t rho_launch(const Plan &P, const double *V, const double *DM, double *rho, double *F, cudaStream_t s,
+                       int nsm)
+{
+    if (rho && F) return rho_launch3<S, true, true>(P, V, DM, rho, F, s, nsm);
+    if (rho) return rho_launch3<S, true, false>(P, V, DM, rho, F, s, nsm);
+    return rho_launch3<S, false, true>(P, V, DM, rho, F, s, nsm);
+}
+
+}  // namespace
+
+cudaError_t launch_vlocal_tc(const Plan &P, gint_prec prec, const double *V, double *H, cudaStream_t s, int nsm)
+{
+    if (P.nbatches == 0) return cudaSuccess;
+    switch (prec) {
+    case GINT_TF32X3: return vlocal_launch<TF32x3>(P, V, H, s, nsm);
+    case GINT_BF16X3: return vlocal_launch<BF16x3>(P, V, H, s, nsm);
+    case GINT_BF16X6: return vlocal_launch<BF16x6>(P, V, H, s, nsm);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_rho_force_tc(const Plan &P, gint_prec prec, const double *V, const double *DM, double *rho,
+                                double *F, cudaStream_t s, int nsm)
+{
+    if (P.nbatches == 0) return cudaSuccess;
+    switch (prec) {
+    case GINT_TF32X3: return rho_launch<TF32x3>(P, V, DM, rho, F, s, nsm);
+    case GINT_BF16X3: return rho_launch<BF16x3>(P, V, DM, rho, F, s, nsm);
+    case GINT_BF16X6: return rho_launch<BF16x6>(P, V, DM, rho, F, s, nsm);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace gint

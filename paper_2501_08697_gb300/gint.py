@@ -1,0 +1,269 @@
+"""Python binding of libgint (ctypes): argument marshalling only.
+
+Every function here forwards to the C ABI declared in include/gint.h with the same name;
+tensors are passed as raw device pointers, the stream is torch's current CUDA stream.  No
+step of the grid integration runs in Python or PyTorch: if the CUDA library cannot be built
+or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+GINT_OK, GINT_EINVAL, GINT_ENOMEM, GINT_ECUDA, GINT_ETIMEOUT, GINT_ESTATE = range(6)
+PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3, "bf16x6": 4}
+PREC_NAME = {v: k for k, v in PREC.items()}
+
+EXPORTS = ["gint_setup", "gint_destroy", "gint_block_layout", "gint_get_info", "gint_update_positions",
+           "gint_vlocal", "gint_rho", "gint_force", "gint_rho_force", "gint_charge", "gint_block_dot",
+           "gint_run_host", "gint_batched", "gint_get_status", "gint_last_error"]
+
+
+class GintError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libgint error {code}: {msg}")
+        self.code = code
+
+
+class _Species(C.Structure):
+    _fields_ = [("nrad", C.c_int), ("l", C.POINTER(C.c_int)), ("rcut", C.c_double), ("dr", C.c_double),
+                ("ntab", C.c_int), ("ftab", C.POINTER(C.c_double)), ("dfdr0", C.POINTER(C.c_double))]
+
+
+class _Options(C.Structure):
+    _fields_ = [("batch", C.c_int * 3), ("reserved", C.c_int * 5)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("npts", C.c_int64), ("nblocks", C.c_int64), ("nvalues", C.c_int64), ("nbatches", C.c_int64),
+                ("nslots", C.c_int64), ("max_orbitals", C.c_int), ("max_slots", C.c_int), ("dV", C.c_double),
+                ("flops_useful", C.c_double), ("flops_dense", C.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libgint.so (building it in-tree if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build_library()
+        if not os.path.exists(path):
+            raise GintError(GINT_ECUDA, f"libgint.so not built at {path}")
+        lib = C.CDLL(path)
+        P, vp = C.POINTER, C.c_void_p
+        i32, i64, d = C.c_int, C.c_int64, C.c_double
+        lib.gint_setup.argtypes = [P(vp), P(d), i32, P(i32), P(d), i32, P(_Species), P(i32), P(_Options)]
+        lib.gint_destroy.argtypes = [vp]
+        lib.gint_block_layout.argtypes = [vp, P(i64), P(i64), P(P(C.c_int32)), P(P(i64))]
+        lib.gint_get_info.argtypes = [vp, P(_Info)]
+        lib.gint_update_positions.argtypes = [vp, P(d)]
+        lib.gint_vlocal.argtypes = [vp, vp, vp, i32, vp]
+        lib.gint_rho.argtypes = [vp, vp, vp, i32, vp]
+        lib.gint_force.argtypes = [vp, vp, vp, vp, i32, vp]
+        lib.gint_rho_force.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+        lib.gint_charge.argtypes = [vp, vp, vp, vp]
+        lib.gint_block_dot.argtypes = [vp, vp, vp, vp, vp]
+        lib.gint_run_host.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp]
+        lib.gint_batched.argtypes = [i32, P(vp), P(vp), P(vp), P(vp), P(vp), i32, vp]
+        lib.gint_get_status.argtypes = [vp]
+        lib.gint_last_error.restype = C.c_char_p
+        for name in EXPORTS:
+            if name != "gint_last_error":
+                getattr(lib, name).restype = C.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != GINT_OK:
+        msg = load().gint_last_error().decode(errors="replace")
+        raise GintError(rc, msg)
+
+
+def _ptr(t) -> int:
+    """Device pointer of a contiguous float64 CUDA tensor (or None)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return int(stream)
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _prec(p):
+    if isinstance(p, str):
+        return PREC[p]
+    return int(p)
+
+
+class Handle:
+    """A set-up structure (geometry, species, grid) owned by libgint."""
+
+    def __init__(self, ptr, natoms):
+        self._ptr = C.c_void_p(ptr)
+        self.natoms = natoms
+        info = _Info()
+        _check(load().gint_get_info(self._ptr, C.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in _Info._fields_}
+        self._layout = None
+
+    @property
+    def ptr(self):
+        return self._ptr
+
+    def layout(self):
+        """(keys [nblocks, 5] int32, offsets [nblocks+1] int64) as numpy copies."""
+        if self._layout is None:
+            nb, nv = C.c_int64(), C.c_int64()
+            kp, op = C.POINTER(C.c_int32)(), C.POINTER(C.c_int64)()
+            _check(load().gint_block_layout(self._ptr, C.byref(nb), C.byref(nv), C.byref(kp), C.byref(op)))
+            keys = np.ctypeslib.as_array(kp, shape=(nb.value * 5,)).reshape(-1, 5).copy() if nb.value else np.zeros((0, 5), np.int32)
+            offs = np.ctypeslib.as_array(op, shape=(nb.value + 1,)).copy()
+            self._layout = (keys, offs)
+        return self._layout
+
+    def close(self):
+        if self._ptr:
+            load().gint_destroy(self._ptr)
+            self._ptr = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gint_setup(cell, species, tau, tables, grid, batch=(4, 4, 8)) -> Handle:
+    """cell [3,3] rows (bohr), species [natoms] ints, tau [natoms,3] (bohr), tables: list of
+    objects with .l, .rcut, .dr, .ftab [nrad, ntab], .dfdr0 (see synth.SpeciesTables)."""
+    lib = load()
+    cell = np.ascontiguousarray(cell, np.float64).reshape(9)
+    species = np.ascontiguousarray(species, np.int32)
+    tau = np.ascontiguousarray(tau, np.float64).reshape(-1)
+    grid_a = (C.c_int * 3)(*[int(g) for g in grid])
+    keep = []
+    sp = (_Species * len(tables))()
+    for i, t in enumerate(tables):
+        l = np.ascontiguousarray(t.l, np.int32)
+        f = np.ascontiguousarray(t.ftab, np.float64)
+        d0 = np.ascontiguousarray(t.dfdr0, np.float64)
+        keep += [l, f, d0]
+        sp[i].nrad = len(l)
+        sp[i].l = l.ctypes.data_as(C.POINTER(C.c_int))
+        sp[i].rcut = float(t.rcut)
+        sp[i].dr = float(t.dr)
+        sp[i].ntab = int(f.shape[-1])
+        sp[i].ftab = f.ctypes.data_as(C.POINTER(C.c_double))
+        sp[i].dfdr0 = d0.ctypes.data_as(C.POINTER(C.c_double))
+    opt = _Options()
+    for i in range(3):
+        opt.batch[i] = int(batch[i])
+    out = C.c_void_p()
+    _check(lib.gint_setup(C.byref(out), cell.ctypes.data_as(C.POINTER(C.c_double)), len(species),
+                          species.ctypes.data_as(C.POINTER(C.c_int)), tau.ctypes.data_as(C.POINTER(C.c_double)),
+                          len(tables), sp, grid_a, C.byref(opt)))
+    return Handle(out.value, len(species))
+
+
+def gint_destroy(h: Handle):
+    h.close()
+
+
+def gint_block_layout(h: Handle):
+    return h.layout()
+
+
+def gint_get_info(h: Handle):
+    return dict(h.info)
+
+
+def gint_update_positions(h: Handle, tau):
+    tau = np.ascontiguousarray(tau, np.float64).reshape(-1)
+    _check(load().gint_update_positions(h.ptr, tau.ctypes.data_as(C.POINTER(C.c_double))))
+    h._layout = None
+    info = _Info()
+    _check(load().gint_get_info(h.ptr, C.byref(info)))
+    h.info = {k: getattr(info, k) for k, _ in _Info._fields_}
+
+
+def gint_vlocal(h: Handle, V, H, prec="fp64", stream=None):
+    _check(load().gint_vlocal(h.ptr, _ptr(V), _ptr(H), _prec(prec), _stream(stream)))
+
+
+def gint_rho(h: Handle, DM, rho, prec="fp64", stream=None):
+    _check(load().gint_rho(h.ptr, _ptr(DM), _ptr(rho), _prec(prec), _stream(stream)))
+
+
+def gint_force(h: Handle, V, DM, F, prec="fp64", stream=None):
+    _check(load().gint_force(h.ptr, _ptr(V), _ptr(DM), _ptr(F), _prec(prec), _stream(stream)))
+
+
+def gint_rho_force(h: Handle, V, DM, rho, F, prec="fp64", stream=None):
+    _check(load().gint_rho_force(h.ptr, _ptr(V), _ptr(DM), _ptr(rho), _ptr(F), _prec(prec), _stream(stream)))
+
+
+def gint_charge(h: Handle, rho, out, stream=None):
+    _check(load().gint_charge(h.ptr, _ptr(rho), _ptr(out), _stream(stream)))
+
+
+def gint_block_dot(h: Handle, A, B, out, stream=None):
+    _check(load().gint_block_dot(h.ptr, _ptr(A), _ptr(B), _ptr(out), _stream(stream)))
+
+
+def _host_ptr(a, writable=False):
+    if a is None:
+        return None
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("expected a contiguous float64 CPU tensor")
+        return a.data_ptr()
+    if a.dtype != np.float64 or not a.flags.c_contiguous or (writable and not a.flags.writeable):
+        raise TypeError("expected a contiguous float64 numpy array")
+    return a.ctypes.data
+
+
+def gint_run_host(h: Handle, V, DM, H=None, rho=None, F=None, prec="fp64", stream=None):
+    """Host buffers in, host buffers out (copies inside, synchronous)."""
+    _check(load().gint_run_host(h.ptr, _host_ptr(V), _host_ptr(DM), _host_ptr(H, True), _host_ptr(rho, True),
+                                _host_ptr(F, True), _prec(prec), _stream(stream)))
+
+
+def gint_batched(handles, V, H, DM=None, rho=None, prec="fp64", stream=None):
+    n = len(handles)
+    arr = lambda xs: (C.c_void_p * n)(*[_ptr(x) for x in xs])
+    hs = (C.c_void_p * n)(*[h.ptr.value for h in handles])
+    _check(load().gint_batched(n, hs, arr(V), arr(H), arr(DM) if DM is not None else None,
+                               arr(rho) if rho is not None else None, _prec(prec), _stream(stream)))
+
+
+def gint_get_status(h: Handle):
+    return load().gint_get_status(h.ptr)
+
+
+def setup_structure(st, batch=(4, 4, 8), tau=None) -> Handle:
+    """Convenience: gint_setup from a synth.Structure."""
+    return gint_setup(st.cell, st.species, st.tau if tau is None else tau, st.tables, st.grid, batch)

@@ -1,0 +1,57 @@
+"""Shared seeded cases for the parity tests: a structure, its inputs and the oracle's
+results (computed once per session)."""
+from __future__ import annotations
+
+import functools
+
+import numpy as np
+
+from paper_2501_08697_gb300 import synth as S
+
+
+def rel_fro(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def structure(name):
+    if name == "si8":
+        return S.workload("si8")
+    if name == "si8_ragged":      # grid not a multiple of the batch, displaced atoms
+        return S.si_diamond((1, 1, 1), grid=(30, 34, 38), sigma=0.05, seed=S.BASE_SEED + 61, name="si8_ragged")
+    if name == "si16_strained":   # orthorhombic 2x1x1 cell, strained, displaced
+        return S.si_diamond((2, 1, 1), sigma=0.05, strain=0.021, seed=S.BASE_SEED + 62, name="si16_strained")
+    if name == "water8":          # two species, mixed block shapes 13x13 / 13x5 / 5x5
+        return S.water_box(8, (8 * 23.5 ** 3 / 64) ** (1 / 3), seed=S.BASE_SEED + 63, name="water8")
+    if name == "water1_vacuum":   # one molecule in a large box: batches with no orbitals
+        return S.water_box(1, 16.0, grid=(64, 64, 72), seed=S.BASE_SEED + 64, name="water1_vacuum")
+    if name == "si64":
+        return S.workload("si64")
+    if name == "water64":
+        return S.workload("water64")
+    if name == "si512":
+        return S.workload("si512")
+    raise KeyError(name)
+
+
+@functools.lru_cache(maxsize=None)
+def inputs(name):
+    st = structure(name)
+    V = S.local_potential(st)
+    return st, V
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_full(name):
+    """Oracle keys/offsets, H, DM, rho, F for a case small enough to run in full."""
+    from oracle import Oracle
+    st, V = inputs(name)
+    o = Oracle.from_structure(st)
+    keys, offs = o.pairs()
+    DM = S.density_matrix(keys, st.norb_atom, seed=st.seed)
+    H = o.vlocal(V)
+    rho = o.rho(DM)
+    F = o.force(V, DM)
+    return dict(st=st, V=V, keys=keys, offs=offs, DM=DM, H=H, rho=rho, F=F, oracle=o)

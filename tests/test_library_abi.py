@@ -1,0 +1,60 @@
+"""The C ABI library builds for sm_103a, loads, and exports every entry point that
+include/gint.h declares (CPU only: no compute call is made)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2501_08697_gb300 import build as B
+from paper_2501_08697_gb300 import gint as G
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "gint.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gint_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    return B.build_library()
+
+
+def test_header_and_binding_agree():
+    assert sorted(G.EXPORTS) == _declared()
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (gint_[a-z_]+)\b", out))
+    missing = [s for s in _declared() if s not in exported]
+    assert not missing, missing
+
+
+def test_library_targets_sm103a_only(lib_path):
+    out = subprocess.run(["cuobjdump", "--list-elf", lib_path], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    archs = set(re.findall(r"sm_(\d+a?)", out.stdout))
+    assert archs == {"103a"}, archs
+
+
+def test_loads_with_ctypes(lib_path):
+    lib = G.load()
+    for name in G.EXPORTS:
+        assert hasattr(lib, name)
+    assert lib.gint_last_error() is not None
+
+
+def test_setup_without_gpu_fails_loudly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2501_08697_gb300 import synth as S
+    st = S.si_diamond((1, 1, 1), grid=(16, 16, 16))
+    with pytest.raises(G.GintError) as e:
+        G.setup_structure(st)
+    assert e.value.code == G.GINT_ECUDA

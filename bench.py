@@ -1,0 +1,327 @@
+"""Benchmark of the grid-integration hot path on GB300.
+
+One step = the per-SCF-iteration grid work on one structure: V_mu,nu(R) (gint_vlocal), the
+backward pass rho(r) + Pulay force (gint_rho_force) and the FP64 checks Sum rho dV
+(gint_charge) and Tr(rho_mu,nu V_mu,nu) (gint_block_dot).  The geometry set-up (block list,
+batch lists) is done once per structure and is outside the timed region.
+
+Default workload: the 512-atom Si precision case (4x4x4 diamond supercell, 6656 orbitals,
+grid 192^3 = 7,077,888 points), synthetic seeded inputs.  Metric: grid points per second.
+
+  python bench.py [--steps K] [--warmup W] [--prec tf32x3] [--workload si512]
+  python bench.py --impl reference ...    # the FP64 CPU oracle on a bounded sample
+Under torchrun (N > 1) every rank runs an independent replica (the path has no data
+exchange across structures); value = points of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gint V_mu_nu + rho(r) grid points/s (split-precision vs FP64, at stated error)"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return m, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _tensor_peak(prec, peaks, sustained=True):
+    """Dense peak (TFLOP/s) for the contraction dtype: measured bf16 x nominal dtype ratio."""
+    bf16 = peaks.get("bf16_tflops_sustained" if sustained else "bf16_tflops", 1700.0)
+    ratio = {"tf32x3": 1.1 / 2.25, "bf16x3": 1.0, "bf16x6": 1.0, "fp32": 1.1 / 2.25}.get(prec, 1.0)
+    return bf16 * ratio
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_inputs(name, seed_dm=True):
+    from paper_2501_08697_gb300 import synth as S
+    st = S.workload(name)
+    V = S.local_potential(st)
+    return st, V
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2501_08697_gb300 import gint as G
+    from paper_2501_08697_gb300 import synth as S
+
+    dev = torch.device(f"cuda:{int(os.environ.get('LOCAL_RANK', 0))}")
+    torch.cuda.set_device(dev)
+    st, Vn = build_inputs(args.workload)
+    t0 = time.time()
+    h = G.setup_structure(st, batch=tuple(args.batch), batch_rho=tuple(args.batch_rho))
+    setup_s = time.time() - t0
+    keys, offs = h.layout()
+    DMn = S.density_matrix(keys, st.norb_atom, seed=st.seed)
+    info = h.info
+    V = torch.from_numpy(Vn.reshape(-1)).to(dev)
+    DM = torch.from_numpy(DMn).to(dev)
+    H = torch.empty(info["nvalues"], dtype=torch.float64, device=dev)
+    rho = torch.empty(info["npts"], dtype=torch.float64, device=dev)
+    F = torch.empty(3 * st.natoms, dtype=torch.float64, device=dev)
+    chk = torch.zeros(2, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(prec, ev=None):
+        if ev:
+            ev[0].record(stream)
+        G.gint_vlocal(h, V, H, prec)
+        if ev:
+            ev[1].record(stream)
+        G.gint_rho_force(h, V, DM, rho, F, prec)
+        if ev:
+            ev[2].record(stream)
+        G.gint_charge(h, rho, chk[0:1])
+        G.gint_block_dot(h, DM, H, chk[1:2])
+        if ev:
+            ev[3].record(stream)
+
+    def timed(prec, steps, warmup):
+        for _ in range(warmup):
+            step(prec)
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for i in range(steps):
+            flush.fill_(float(i))                       # evict L2 (512 MiB write) outside the events
+            step(prec, evs[i])
+        torch.cuda.synchronize()
+        tot = sum(e[0].elapsed_time(e[3]) for e in evs) / 1e3
+        tv = sum(e[0].elapsed_time(e[1]) for e in evs) / steps / 1e3
+        tr = sum(e[1].elapsed_time(e[2]) for e in evs) / steps / 1e3
+        tc = sum(e[2].elapsed_time(e[3]) for e in evs) / steps / 1e3
+        return tot, tv, tr, tc
+
+    prec = args.prec
+    with ClockSampler(dev.index) as clk:
+        tot, tv, tr, tc = timed(prec, args.steps, args.warmup)
+    clocks = clk.summary()
+    G.gint_get_status(h)
+    tmax = tot
+    if world > 1:
+        t = torch.tensor([tot], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tmax = float(t.item())
+    npts = info["npts"]
+    value = world * npts * args.steps / tmax
+    ms = tmax / args.steps * 1e3
+
+    # the FP64 GPU path on the same step, for the split-vs-FP64 comparison
+    fp64 = None
+    if not args.skip_fp64 and rank == 0:
+        f_tot, f_tv, f_tr, _ = timed("fp64", 1, 1)
+        fp64 = {"pts_per_s": npts / f_tot, "ms_per_step": f_tot * 1e3, "vlocal_ms": f_tv * 1e3,
+                "rho_force_ms": f_tr * 1e3}
+        H64, rho64, F64 = H.clone(), rho.clone(), F.clone()
+        step(prec)
+        torch.cuda.synchronize()
+        rel = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+        err = {"H": rel(H, H64), "rho": rel(rho, rho64), "F": rel(F, F64)}
+    else:
+        err = None
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    pin = lambda n: torch.empty(n, dtype=torch.float64).pin_memory()
+    Vh, DMh = pin(npts), pin(info["nvalues"])
+    Vh.copy_(torch.from_numpy(Vn.reshape(-1)))
+    DMh.copy_(torch.from_numpy(DMn))
+    Hh, rhoh, Fh = pin(info["nvalues"]), pin(npts), pin(3 * st.natoms)
+    G.gint_run_host(h, Vh, DMh, Hh, rhoh, Fh, prec)
+    t0 = time.perf_counter()
+    n_e2e = max(1, args.steps)
+    for _ in range(n_e2e):
+        G.gint_run_host(h, Vh, DMh, Hh, rhoh, Fh, prec)
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    e2e = {"value": world * npts / e2e_s, "unit": "grid points/s",
+           "h2d_bytes_per_step": 8 * (npts + info["nvalues"]),
+           "d2h_bytes_per_step": 8 * (info["nvalues"] + npts + 3 * st.natoms)}
+
+    peaks, src = _peaks()
+    dominant = ("rho_force", tr) if tr >= tv else ("vlocal", tv)
+    alg_flops = info["flops_useful"]                       # 2 n(r)^2 summed over the grid
+    exec_flops = {"tf32x3": 3, "bf16x3": 3, "bf16x6": 6}.get(prec, 1) * (
+        info["flops_dense"] if dominant[0] == "vlocal" else info["flops_dense_rho"])
+    tp = _tensor_peak(prec, peaks, sustained=True)
+    achieved = alg_flops / dominant[1] / 1e12
+    roofline = {"bound": "tensor", "kernel": dominant[0], "achieved": achieved, "peak": tp, "unit": "TFLOP/s",
+                "frac": achieved / tp, "traffic": None,
+                "peak_source": f"{src} bf16 sustained x nominal {prec} ratio",
+                "executed_tflops": exec_flops / dominant[1] / 1e12}
+    out = {
+        "metric": METRIC, "value": value, "unit": "grid points/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec, "data": "synthetic (seeded Si diamond 4x4x4, plane-wave V, random DM)",
+        "config": {"workload": f"{args.workload}: {st.natoms} atoms, {st.nbasis} orbitals, grid "
+                               f"{'x'.join(map(str, st.grid))}",
+                   "prec": prec, "batch_vlocal": list(args.batch), "batch_rho": list(args.batch_rho),
+                   "step": "vlocal + rho_force + charge + trace", "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
+                   "nbatches": info["nbatches"], "nbatches_rho": info["nbatches_rho"]},
+        "kernel_ms": {"vlocal": tv * 1e3, "rho_force": tr * 1e3, "checks": tc * 1e3},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": args.steps * 8,
+        "clocks": clocks,
+        "fp64_gpu": fp64,
+        "err_vs_fp64_gpu": err,
+        "speedup_vs_fp64_gpu": (value / world / fp64["pts_per_s"]) if fp64 else None,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, st, Vn, keys, offs, DMn)
+    h.close()
+    return out
+
+
+def cpu_baseline(args, st, Vn, keys=None, offs=None, DMn=None, budget_pts=None):
+    """The FP64 CPU oracle (as it stands) on a bounded sample of the same workload:
+    vlocal + rho + dL/dtau contributions of a contiguous slab of grid points."""
+    from oracle import Oracle
+    from paper_2501_08697_gb300 import synth as S
+    o = Oracle.from_structure(st)
+    k2, o2 = o.pairs()
+    if DMn is None:
+        DMn = S.density_matrix(k2, st.norb_atom, seed=st.seed)
+    n = budget_pts or args.cpu_points
+    pts = np.arange(n, dtype=np.int64)
+    t0 = time.perf_counter()
+    o.vlocal(Vn, pts)
+    o.rho(DMn, pts)
+    o.dLdtau(Vn, DMn, pts)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "grid points/s", "cores": Oracle.threads(), "kind": "oracle",
+            "sample": f"first {n} grid points (a slab of i-planes) of {args.workload}: vlocal + rho + force, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    st, Vn = build_inputs(args.workload)
+    steps_t = []
+    for _ in range(args.warmup):
+        pass
+    res = None
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        res = cpu_baseline(args, st, Vn, budget_pts=args.cpu_points)
+        steps_t.append(time.perf_counter() - t0)
+    tot = sum(steps_t)
+    value = args.cpu_points * args.steps / tot
+    return {"metric": METRIC, "value": value, "unit": "grid points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "sample_points_per_step": args.cpu_points},
+            "cpu_baseline": {"value": value, "unit": "grid points/s", "cores": res["cores"], "kind": "oracle",
+                             "sample": res["sample"]},
+            "e2e": {"value": value, "unit": "grid points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="si512")
+    ap.add_argument("--prec", default="tf32x3")
+    ap.add_argument("--batch", type=int, nargs=3, default=[4, 4, 4])
+    ap.add_argument("--batch-rho", type=int, nargs=3, default=[4, 4, 8])
+    ap.add_argument("--cpu-points", type=int, default=100000)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

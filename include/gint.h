@@ -93,9 +93,12 @@ typedef struct {
 } gint_species;
 
 typedef struct {
-    int batch[3];          /* grid points per batch along a1, a2, a3 (default 4, 4, 8);
-                              batches whose orbital count exceeds the kernel limits are split */
-    int reserved[5];
+    int batch[3];          /* grid points per vlocal batch along a1, a2, a3 (default 4, 4, 4);
+                              at most 16 per axis and 128 in all, even along a3 */
+    int batch_rho[3];      /* grid points per rho/force batch (default 4, 4, 8), same limits.
+                              Batches whose orbital count (256) or atom-image count (64)
+                              exceeds the kernel limits are split. */
+    int reserved[2];
 } gint_options;
 
 /* Sizes of a handle (host values). */
@@ -103,13 +106,17 @@ typedef struct {
     int64_t npts;          /* N1*N2*N3 */
     int64_t nblocks;       /* blocks in the store */
     int64_t nvalues;       /* doubles in the store */
-    int64_t nbatches;      /* grid batches */
-    int64_t nslots;        /* (batch, atom image) pairs */
-    int max_orbitals;      /* largest per-batch orbital count */
-    int max_slots;         /* largest per-batch atom-image count */
+    int64_t nbatches;      /* vlocal grid batches */
+    int64_t nslots;        /* vlocal (batch, atom image) pairs */
+    int max_orbitals;      /* largest vlocal per-batch orbital count */
+    int max_slots;         /* largest vlocal per-batch atom-image count */
     double dV;             /* volume element */
-    double flops_useful;   /* 2 * Sum_r n(r)^2: one vlocal contraction, n(r) = orbitals at r */
-    double flops_dense;    /* 2 * Sum_b npts_b * nb_b^2: the dense per-batch contraction */
+    double flops_useful;   /* 2 * Sum_r n(r)^2: one contraction, n(r) = orbitals whose sphere holds r */
+    double flops_dense;    /* 2 * Sum_b npts_b * nb_b^2: the dense vlocal per-batch contraction */
+    int64_t nbatches_rho;  /* rho/force grid batches */
+    int max_orbitals_rho;  /* largest rho/force per-batch orbital count */
+    int reserved;
+    double flops_dense_rho;/* 2 * Sum_b npts_b * nb_b^2 over the rho/force batches */
 } gint_info_t;
 
 /* Build a handle: validates the inputs, fits the radial splines, finds the block list

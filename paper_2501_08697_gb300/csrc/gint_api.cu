@@ -29,6 +29,26 @@ __global__ void k_symmetrise(Plan P, const double *__restrict__ DM, double *out)
     }
 }
 
+// out <- FP32 copy of DM, or of its block-symmetric part (DM + DM^T_block)/2
+__global__ void k_dm_to_f32(Plan P, const double *__restrict__ DM, float *out, int sym)
+{
+    if (!sym) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.nvalues; i += (int64_t)gridDim.x * blockDim.x)
+            out[i] = d2f(DM[i]);
+        return;
+    }
+    for (int64_t b = blockIdx.x; b < P.nblocks; b += gridDim.x) {
+        const int pb = P.partner[b];
+        const int64_t off = P.blk_off[b], poff = P.blk_off[pb];
+        const int rows = P.blk_rows[b];
+        const int cols = (int)((P.blk_off[b + 1] - off) / rows);
+        for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+            const int mu = e / cols, nu = e - mu * cols;
+            out[off + e] = 0.5f * (d2f(DM[off + e]) + d2f(DM[poff + nu * rows + mu]));
+        }
+    }
+}
+
 constexpr int kRedBlocks = 1024;
 constexpr int kRedThreads = 256;
 
@@ -96,9 +116,9 @@ gint_status run_vlocal(gint_handle h, const double *V, double *H, gint_prec prec
     cudaError_t e = cudaMemsetAsync(H, 0, sizeof(double) * h->info.nvalues, s);
     if (e != cudaSuccess) return cuda_fail(e, "gint_vlocal: memset");
     if (prec == GINT_FP64 || prec == GINT_FP32)
-        e = launch_vlocal_simt(h->plan, prec == GINT_FP64, V, H, s, h->nsm);
+        e = launch_vlocal_simt(plan_for(h, 0), prec == GINT_FP64, V, H, s, h->nsm);
     else
-        e = launch_vlocal_tc(h->plan, prec, V, H, s, h->nsm);
+        e = launch_vlocal_tc(plan_for(h, 0), prec, V, H, s, h->nsm);
     if (e != cudaSuccess) return cuda_fail(e, "gint_vlocal: launch");
     e = launch_mirror(h->plan, H, s);
     if (e != cudaSuccess) return cuda_fail(e, "gint_vlocal: mirror");
@@ -110,20 +130,27 @@ gint_status run_rho_force(gint_handle h, const double *V, const double *DM, doub
                           cudaStream_t s)
 {
     cudaError_t e;
-    const double *D = DM;
-    if (F) {
-        if (h->info.nblocks > 0) {
+    const bool simt = (prec == GINT_FP64 || prec == GINT_FP32);
+    if (F && (e = cudaMemsetAsync(F, 0, sizeof(double) * 3 * h->natoms, s)) != cudaSuccess)
+        return cuda_fail(e, "gint_force: memset");
+    if (simt) {
+        // CUDA-core kernels read FP64; the force needs the block-symmetric part
+        const double *D = DM;
+        if (F && h->info.nblocks > 0) {
             k_symmetrise<<<(int)std::min<int64_t>(h->info.nblocks, 8192), 128, 0, s>>>(h->plan, DM, h->d_dmsym);
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gint_force: symmetrise");
+            D = h->d_dmsym;
         }
-        D = h->d_dmsym;
-        if ((e = cudaMemsetAsync(F, 0, sizeof(double) * 3 * h->natoms, s)) != cudaSuccess)
-            return cuda_fail(e, "gint_force: memset");
+        e = launch_rho_force_simt(plan_for(h, 1), prec == GINT_FP64, V, D, rho, F, s, h->nsm);
+    } else {
+        // tensor-core kernels gather the density matrix in FP32 (split again on chip)
+        if (h->info.nvalues > 0) {
+            const int grid = (int)std::min<int64_t>(F ? h->info.nblocks : (h->info.nvalues + 255) / 256, 8192);
+            k_dm_to_f32<<<grid, F ? 128 : 256, 0, s>>>(h->plan, DM, h->d_dm32, F ? 1 : 0);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gint_rho: convert");
+        }
+        e = launch_rho_force_tc(plan_for(h, 1), prec, V, h->d_dm32, rho, F, s, h->nsm);
     }
-    if (prec == GINT_FP64 || prec == GINT_FP32)
-        e = launch_rho_force_simt(h->plan, prec == GINT_FP64, V, D, rho, F, s, h->nsm);
-    else
-        e = launch_rho_force_tc(h->plan, prec, V, D, rho, F, s, h->nsm);
     if (e != cudaSuccess) return cuda_fail(e, "gint_rho_force: launch");
     h->last_stream = s;
     return GINT_OK;

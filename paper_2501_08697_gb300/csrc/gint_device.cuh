@@ -226,6 +226,25 @@ __device__ __forceinline__ void scatter_elem(double *H, const int *tbl, int ns, 
     }
 }
 
+// FP64 -> FP32 with integer operations, round to nearest even (normal range; |x| below
+// 2^-126 flushes to 0); keeps the conversion off GB300's narrow FP64 pipe.
+__device__ __forceinline__ float d2f(double x)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const uint32_t sign = (uint32_t)(b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0x7FF) return (float)x;
+    const int ne = e - 1023 + 127;
+    if (ne <= 0) return __uint_as_float(sign);
+    if (ne >= 255) return (float)x;
+    const uint64_t m = b & 0xFFFFFFFFFFFFFull;
+    uint32_t mh = (uint32_t)(m >> 29);
+    const uint32_t rem = (uint32_t)(m & 0x1FFFFFFFu);
+    if (rem > 0x10000000u || (rem == 0x10000000u && (mh & 1u))) ++mh;
+    uint32_t bits = ((uint32_t)ne << 23) + mh;   // a mantissa carry rolls into the exponent
+    return __uint_as_float(sign | bits);
+}
+
 // ----------------------------------------------------------------------- status and waits
 __device__ __forceinline__ void report_timeout(const Plan &P) { atomicCAS(P.status, 0, (int)GINT_ETIMEOUT); }
 

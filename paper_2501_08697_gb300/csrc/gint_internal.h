@@ -37,11 +37,15 @@ struct Batch {
     int tbl;                       // first entry of this batch's nslots x nslots pair table
 };
 
-// An atom image seen by a batch.  d0 = (grid point (i0,j0,k0)) - (tau_I + R_a), Cartesian.
+// An atom image seen by a batch.  d0 = (grid point (i0,j0,k0)) - (tau_I + R_a), Cartesian,
+// in FP64 and as an FP32 pair (dh + dl) for the FP32 kernels.
 struct Slot {
     int atom, species, orb_off, norb;
     double d0[3];
+    float dh[3], dl[3];
 };
+
+constexpr int kPoffDim = 16;       // point-offset table covers local indices 0..15 per axis
 
 // Everything a kernel needs, passed by value.
 struct Plan {
@@ -57,12 +61,26 @@ struct Plan {
     const Batch *batches;
     const Slot *slots;
     const int *tbl;                // (block offset << 1 | canonical) or -1 if no block
+    const float *poff;             // [16][16][16][6]: a h1 + b h2 + c h3 as FP32 hi (3) + lo (3)
     const int *partner;            // [nblocks] partner block index
     const int64_t *blk_off;        // [nblocks + 1]
     const int *blk_rows;           // [nblocks] rows of each block
     int64_t nblocks, nvalues;
     int *status;                   // device status word
     long long spin_limit;          // clock64 cycles a kernel may wait on one barrier
+};
+
+// One decomposition of the grid into batches, with its atom-image lists and pair tables.
+struct BatchSet {
+    int dims[3] = {0, 0, 0};
+    std::vector<Batch> batches;
+    std::vector<Slot> slots;
+    std::vector<int> slot_img;       // 3 per slot: image n of the slot's atom
+    std::vector<int> tbl;
+    int limit_nb = 256;              // batches with more orbitals are split
+    int max_nb = 0, max_slots = 0;
+    double flops_dense = 0.0;
+    void *d_batches = nullptr, *d_slots = nullptr, *d_tbl = nullptr;
 };
 
 }  // namespace gint
@@ -81,17 +99,16 @@ struct gint_handle_s {
     std::vector<int32_t> keys;       // 5 per block
     std::vector<int64_t> offsets;    // nblocks + 1
     std::vector<int> partner;
-    std::vector<gint::Batch> batches;
-    std::vector<gint::Slot> slots;
-    std::vector<int> slot_img;       // 3 per slot: image n of the slot's atom
-    std::vector<int> tbl;
+    gint::BatchSet bs[2];            // [0] vlocal batches, [1] rho/force batches
     gint_options opt{};
     gint_info_t info{};
     // device memory (owned)
-    void *d_coef64 = nullptr, *d_coef32 = nullptr, *d_batches = nullptr, *d_slots = nullptr;
-    void *d_tbl = nullptr, *d_partner = nullptr, *d_blkoff = nullptr, *d_blkrows = nullptr;
+    void *d_coef64 = nullptr, *d_coef32 = nullptr;
+    void *d_partner = nullptr, *d_blkoff = nullptr, *d_blkrows = nullptr;
     int *d_status = nullptr;
-    double *d_dmsym = nullptr;       // scratch: block-symmetrised density matrix
+    double *d_dmsym = nullptr;       // scratch: block-symmetrised density matrix (FP64 kernels)
+    float *d_dm32 = nullptr;         // scratch: density matrix (or its symmetric part) in FP32
+    float *d_poff = nullptr;         // point-offset table
     double *d_red = nullptr;         // scratch: partial sums of reductions
     double *d_hostio = nullptr;      // buffers of gint_run_host (allocated on first use)
     size_t hostio_bytes = 0;
@@ -99,6 +116,17 @@ struct gint_handle_s {
 };
 
 namespace gint {
+// kernel parameters for one batch decomposition (0 = vlocal, 1 = rho/force)
+inline Plan plan_for(const gint_handle_s *h, int which)
+{
+    Plan p = h->plan;
+    const BatchSet &b = h->bs[which];
+    p.batches = (const Batch *)b.d_batches;
+    p.slots = (const Slot *)b.d_slots;
+    p.tbl = (const int *)b.d_tbl;
+    p.nbatches = (int)b.batches.size();
+    return p;
+}
 void set_error(const char *fmt, ...);
 gint_status cuda_fail(cudaError_t e, const char *where);
 // set-up helpers (gint_setup.cpp)
@@ -108,6 +136,6 @@ cudaError_t launch_vlocal_simt(const Plan &p, bool fp64, const double *V, double
 cudaError_t launch_rho_force_simt(const Plan &p, bool fp64, const double *V, const double *DM,
                                   double *rho, double *F, cudaStream_t s, int nsm);
 cudaError_t launch_vlocal_tc(const Plan &p, gint_prec prec, const double *V, double *H, cudaStream_t s, int nsm);
-cudaError_t launch_rho_force_tc(const Plan &p, gint_prec prec, const double *V, const double *DM,
+cudaError_t launch_rho_force_tc(const Plan &p, gint_prec prec, const double *V, const float *DM,
                                 double *rho, double *F, cudaStream_t s, int nsm);
 }  // namespace gint

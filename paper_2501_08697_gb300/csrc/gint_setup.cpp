@@ -156,6 +156,165 @@ static bool sphere_meets_batch(const BatchGeom &bg, const double *c, double rc, 
 }
 
 // ---------------------------------------------------------------------------------------
+// Batches of `out.dims` grid points, each with the atom images whose sphere meets it and the
+// slot-pair -> block table; batches over the orbital or image limits are halved recursively.
+static gint_status build_batches(gint_handle h, const double *tau, const Geo &G, const BatchGeom &bg,
+                                 const std::vector<double> &rc, const std::vector<int64_t> &packed,
+                                 const std::vector<int64_t> &offsets, const std::vector<uint8_t> &canon, BatchSet &out)
+{
+    const int natoms = h->natoms;
+    const int N1 = h->grid[0], N2 = h->grid[1], N3 = h->grid[2];
+    const int B1 = out.dims[0], B2 = out.dims[1], B3 = out.dims[2];
+    const int nb1 = (N1 + B1 - 1) / B1, nb2 = (N2 + B2 - 1) / B2, nb3 = (N3 + B3 - 1) / B3;
+    const int64_t nbase = (int64_t)nb1 * nb2 * nb3;
+    std::vector<std::vector<RawSlot>> lists(nbase);
+    for (int I = 0; I < natoms; ++I) {
+        const double *t = tau + 3 * I;
+        int lo[3], hi[3];
+        for (int i = 0; i < 3; ++i) {
+            double s = frac_of(G, t, i);
+            lo[i] = (int)std::floor(-s - rc[I] * G.gn[i]) - 1;
+            hi[i] = (int)std::ceil(1.0 - s + rc[I] * G.gn[i]) + 1;
+        }
+        for (int n1 = lo[0]; n1 <= hi[0]; ++n1)
+            for (int n2 = lo[1]; n2 <= hi[1]; ++n2)
+                for (int n3 = lo[2]; n3 <= hi[2]; ++n3) {
+                    double c[3];
+                    for (int x = 0; x < 3; ++x) c[x] = t[x] + n1 * G.A[x] + n2 * G.A[3 + x] + n3 * G.A[6 + x];
+                    int ilo[3], ihi[3];
+                    bool empty = false;
+                    for (int i = 0; i < 3; ++i) {
+                        double s = frac_of(G, c, i) * h->grid[i];
+                        double ext = rc[I] * G.gn[i] * h->grid[i];
+                        ilo[i] = std::max(0, (int)std::floor(s - ext) - 1);
+                        ihi[i] = std::min(h->grid[i] - 1, (int)std::ceil(s + ext) + 1);
+                        if (ilo[i] > ihi[i]) empty = true;
+                    }
+                    if (empty) continue;
+                    for (int b1 = ilo[0] / B1; b1 <= ihi[0] / B1; ++b1)
+                        for (int b2 = ilo[1] / B2; b2 <= ihi[1] / B2; ++b2)
+                            for (int b3 = ilo[2] / B3; b3 <= ihi[2] / B3; ++b3) {
+                                int i0 = b1 * B1, j0 = b2 * B2, k0 = b3 * B3;
+                                int n1p = std::min(B1, N1 - i0), n2p = std::min(B2, N2 - j0), n3p = std::min(B3, N3 - k0);
+                                double lo3[3], hi3[3], ctr[3], rad;
+                                batch_box(bg, i0, j0, k0, n1p, n2p, n3p, lo3, hi3, ctr, &rad);
+                                if (sphere_meets_batch(bg, c, rc[I], lo3, hi3, ctr, rad))
+                                    lists[((int64_t)b1 * nb2 + b2) * nb3 + b3].push_back({I, {n1, n2, n3}});
+                            }
+                }
+    }
+    struct Work {
+        int i0, j0, k0, n1, n2, n3;
+        std::vector<RawSlot> s;
+    };
+    auto orb_count = [&](const std::vector<RawSlot> &s) {
+        int n = 0;
+        for (auto &x : s) n += h->norb_atom[x.atom];
+        return n;
+    };
+    auto slot_less = [](const RawSlot &a, const RawSlot &b) {
+        if (a.atom != b.atom) return a.atom < b.atom;
+        if (a.n[0] != b.n[0]) return a.n[0] < b.n[0];
+        if (a.n[1] != b.n[1]) return a.n[1] < b.n[1];
+        return a.n[2] < b.n[2];
+    };
+    for (int b1 = 0; b1 < nb1; ++b1)
+        for (int b2 = 0; b2 < nb2; ++b2)
+            for (int b3 = 0; b3 < nb3; ++b3) {
+                std::vector<Work> stack;
+                Work w0{b1 * B1, b2 * B2, b3 * B3, std::min(B1, N1 - b1 * B1), std::min(B2, N2 - b2 * B2),
+                        std::min(B3, N3 - b3 * B3), std::move(lists[((int64_t)b1 * nb2 + b2) * nb3 + b3])};
+                stack.push_back(std::move(w0));
+                while (!stack.empty()) {
+                    Work w = std::move(stack.back());
+                    stack.pop_back();
+                    std::sort(w.s.begin(), w.s.end(), slot_less);
+                    int nb = orb_count(w.s);
+                    if (nb > out.limit_nb || (int)w.s.size() > kMaxSlots) {
+                        // halve the longest axis; a3 halves stay even so batch origins stay even
+                        int dims[3] = {w.n1, w.n2, w.n3};
+                        int ax = -1;
+                        for (int a = 0; a < 3; ++a) {
+                            bool can = (a == 2) ? dims[a] >= 4 : dims[a] >= 2;
+                            if (can && (ax < 0 || dims[a] > dims[ax])) ax = a;
+                        }
+                        if (ax < 0) {
+                            set_error("gint_setup: a grid batch sees %d orbitals / %d atom images (limits %d / %d)",
+                                      nb, (int)w.s.size(), kMaxNb, kMaxSlots);
+                            return GINT_EINVAL;
+                        }
+                        int cut = dims[ax] / 2;
+                        if (ax == 2 && (cut % 2)) cut += 1;
+                        Work a = w, b = w;
+                        if (ax == 0) { a.n1 = cut; b.i0 += cut; b.n1 -= cut; }
+                        if (ax == 1) { a.n2 = cut; b.j0 += cut; b.n2 -= cut; }
+                        if (ax == 2) { a.n3 = cut; b.k0 += cut; b.n3 -= cut; }
+                        for (Work *x : {&b, &a}) {
+                            double lo3[3], hi3[3], ctr[3], rad;
+                            batch_box(bg, x->i0, x->j0, x->k0, x->n1, x->n2, x->n3, lo3, hi3, ctr, &rad);
+                            std::vector<RawSlot> keep;
+                            for (auto &s : w.s) {
+                                double c[3];
+                                for (int q = 0; q < 3; ++q)
+                                    c[q] = tau[3 * s.atom + q] + s.n[0] * G.A[q] + s.n[1] * G.A[3 + q] + s.n[2] * G.A[6 + q];
+                                if (sphere_meets_batch(bg, c, rc[s.atom], lo3, hi3, ctr, rad)) keep.push_back(s);
+                            }
+                            x->s = std::move(keep);
+                            stack.push_back(std::move(*x));
+                        }
+                        continue;
+                    }
+                    Batch B{};
+                    B.i0 = w.i0; B.j0 = w.j0; B.k0 = w.k0;
+                    B.dims = w.n1 | (w.n2 << 8) | (w.n3 << 16);
+                    B.slot0 = (int)out.slots.size();
+                    B.nslots = (int)w.s.size();
+                    B.nb = nb;
+                    B.tbl = (int)out.tbl.size();
+                    out.flops_dense += 2.0 * (w.n1 * w.n2 * w.n3) * (double)nb * nb;
+                    out.max_nb = std::max(out.max_nb, nb);
+                    out.max_slots = std::max(out.max_slots, (int)w.s.size());
+                    int off = 0;
+                    double o[3];
+                    for (int c = 0; c < 3; ++c) o[c] = w.i0 * bg.h[c] + w.j0 * bg.h[3 + c] + w.k0 * bg.h[6 + c];
+                    for (auto &s : w.s) {
+                        Slot S{};
+                        S.atom = s.atom;
+                        S.species = h->species[s.atom];
+                        S.orb_off = off;
+                        S.norb = h->norb_atom[s.atom];
+                        for (int q = 0; q < 3; ++q) {
+                            S.d0[q] = o[q] - (tau[3 * s.atom + q] + s.n[0] * G.A[q] + s.n[1] * G.A[3 + q] + s.n[2] * G.A[6 + q]);
+                            S.dh[q] = (float)S.d0[q];
+                            S.dl[q] = (float)(S.d0[q] - (double)S.dh[q]);
+                        }
+                        off += S.norb;
+                        out.slots.push_back(S);
+                        out.slot_img.insert(out.slot_img.end(), {s.n[0], s.n[1], s.n[2]});
+                    }
+                    for (auto &sa : w.s)
+                        for (auto &sb : w.s) {
+                            int64_t pk = pack_key(sa.atom, sb.atom, sb.n[0] - sa.n[0], sb.n[1] - sa.n[1], sb.n[2] - sa.n[2]);
+                            auto it = std::lower_bound(packed.begin(), packed.end(), pk);
+                            if (it == packed.end() || *it != pk) {
+                                out.tbl.push_back(-1);
+                            } else {
+                                int64_t bi = it - packed.begin();
+                                out.tbl.push_back((int)((offsets[bi] << 1) | canon[bi]));
+                            }
+                        }
+                    out.batches.push_back(B);
+                }
+            }
+    if ((int64_t)out.tbl.size() >= ((int64_t)1 << 31) || out.batches.size() >= ((size_t)1 << 31) ||
+        out.slots.size() >= ((size_t)1 << 31)) {
+        set_error("gint_setup: too many batches / table entries");
+        return GINT_EINVAL;
+    }
+    return GINT_OK;
+}
+
+// ---------------------------------------------------------------------------------------
 gint_status build_geometry(gint_handle h, const double *tau, bool update_only)
 {
     const int natoms = h->natoms;
@@ -225,7 +384,7 @@ gint_status build_geometry(gint_handle h, const double *tau, bool update_only)
         canon[b] = packed[b] <= pk;
     }
 
-    // ---- batches and their atom-image slots
+    // ---- batches and their atom-image slots, once per decomposition
     BatchGeom bg;
     bg.ortho = true;
     for (int i = 0; i < 3; ++i)
@@ -233,217 +392,71 @@ gint_status build_geometry(gint_handle h, const double *tau, bool update_only)
             if (i != c && h->cell[3 * i + c] != 0.0) bg.ortho = false;
     for (int i = 0; i < 3; ++i)
         for (int c = 0; c < 3; ++c) bg.h[3 * i + c] = h->cell[3 * i + c] / h->grid[i];
-
-    const int B1 = h->opt.batch[0], B2 = h->opt.batch[1], B3 = h->opt.batch[2];
-    const int nb1 = (N1 + B1 - 1) / B1, nb2 = (N2 + B2 - 1) / B2, nb3 = (N3 + B3 - 1) / B3;
-    const int64_t nbase = (int64_t)nb1 * nb2 * nb3;
-    std::vector<std::vector<RawSlot>> lists(nbase);
-
-    // atom images that reach the cell
-    for (int I = 0; I < natoms; ++I) {
-        const double *t = tau + 3 * I;
-        int lo[3], hi[3];
-        for (int i = 0; i < 3; ++i) {
-            double s = frac_of(G, t, i);
-            lo[i] = (int)std::floor(-s - rc[I] * G.gn[i]) - 1;
-            hi[i] = (int)std::ceil(1.0 - s + rc[I] * G.gn[i]) + 1;
-        }
-        for (int n1 = lo[0]; n1 <= hi[0]; ++n1)
-            for (int n2 = lo[1]; n2 <= hi[1]; ++n2)
-                for (int n3 = lo[2]; n3 <= hi[2]; ++n3) {
-                    double c[3];
-                    for (int x = 0; x < 3; ++x) c[x] = t[x] + n1 * G.A[x] + n2 * G.A[3 + x] + n3 * G.A[6 + x];
-                    // grid-index range along each axis that the sphere can reach
-                    int ilo[3], ihi[3];
-                    bool empty = false;
-                    for (int i = 0; i < 3; ++i) {
-                        double s = frac_of(G, c, i) * h->grid[i];
-                        double ext = rc[I] * G.gn[i] * h->grid[i];
-                        ilo[i] = std::max(0, (int)std::floor(s - ext) - 1);
-                        ihi[i] = std::min(h->grid[i] - 1, (int)std::ceil(s + ext) + 1);
-                        if (ilo[i] > ihi[i]) empty = true;
-                    }
-                    if (empty) continue;
-                    int Bs[3] = {B1, B2, B3};
-                    for (int b1 = ilo[0] / Bs[0]; b1 <= ihi[0] / Bs[0]; ++b1)
-                        for (int b2 = ilo[1] / Bs[1]; b2 <= ihi[1] / Bs[1]; ++b2)
-                            for (int b3 = ilo[2] / Bs[2]; b3 <= ihi[2] / Bs[2]; ++b3) {
-                                int i0 = b1 * B1, j0 = b2 * B2, k0 = b3 * B3;
-                                int n1p = std::min(B1, N1 - i0), n2p = std::min(B2, N2 - j0), n3p = std::min(B3, N3 - k0);
-                                double lo3[3], hi3[3], ctr[3], rad;
-                                batch_box(bg, i0, j0, k0, n1p, n2p, n3p, lo3, hi3, ctr, &rad);
-                                if (sphere_meets_batch(bg, c, rc[I], lo3, hi3, ctr, rad))
-                                    lists[((int64_t)b1 * nb2 + b2) * nb3 + b3].push_back({I, {n1, n2, n3}});
-                            }
-                }
+    BatchSet sets[2];
+    const int *dims[2] = {h->opt.batch, h->opt.batch_rho};
+    for (int w = 0; w < 2; ++w) {
+        for (int i = 0; i < 3; ++i) sets[w].dims[i] = dims[w][i];
+        // vlocal batches stay within 192 orbitals so two accumulators fit in tensor memory
+        sets[w].limit_nb = (w == 0) ? 192 : kMaxNb;
+        gint_status st = build_batches(h, tau, G, bg, rc, packed, offsets, canon, sets[w]);
+        if (st != GINT_OK) return st;
     }
-
-    // split batches whose orbital or slot count exceeds the kernel limits
-    struct Work {
-        int i0, j0, k0, n1, n2, n3;
-        std::vector<RawSlot> s;
-    };
-    std::vector<Batch> batches;
-    std::vector<Slot> slots;
-    std::vector<int> slot_img;
-    std::vector<int> tbl;
-    int max_nb = 0, max_slots = 0;
-    double flops_useful = 0.0, flops_dense = 0.0;
-    auto orb_count = [&](const std::vector<RawSlot> &s) {
-        int n = 0;
-        for (auto &x : s) n += h->norb_atom[x.atom];
-        return n;
-    };
-    auto slot_less = [](const RawSlot &a, const RawSlot &b) {
-        if (a.atom != b.atom) return a.atom < b.atom;
-        if (a.n[0] != b.n[0]) return a.n[0] < b.n[0];
-        if (a.n[1] != b.n[1]) return a.n[1] < b.n[1];
-        return a.n[2] < b.n[2];
-    };
-    for (int b1 = 0; b1 < nb1; ++b1)
-        for (int b2 = 0; b2 < nb2; ++b2)
-            for (int b3 = 0; b3 < nb3; ++b3) {
-                std::vector<Work> stack;
-                Work w0{b1 * B1, b2 * B2, b3 * B3, std::min(B1, N1 - b1 * B1), std::min(B2, N2 - b2 * B2),
-                        std::min(B3, N3 - b3 * B3), std::move(lists[((int64_t)b1 * nb2 + b2) * nb3 + b3])};
-                stack.push_back(std::move(w0));
-                while (!stack.empty()) {
-                    Work w = std::move(stack.back());
-                    stack.pop_back();
-                    std::sort(w.s.begin(), w.s.end(), slot_less);
-                    int nb = orb_count(w.s);
-                    if (nb > kMaxNb || (int)w.s.size() > kMaxSlots) {
-                        // halve the longest axis (keep k halves even so k0 stays even)
-                        int dims[3] = {w.n1, w.n2, w.n3};
-                        int ax = 0;
-                        for (int a = 1; a < 3; ++a)
-                            if (dims[a] > dims[ax]) ax = a;
-                        if (dims[ax] <= 1) {
-                            set_error("gint_setup: a single grid point sees %d orbitals / %d atom images (limits %d / %d)",
-                                      nb, (int)w.s.size(), kMaxNb, kMaxSlots);
-                            return GINT_EINVAL;
-                        }
-                        int cut = dims[ax] / 2;
-                        if (ax == 2 && (cut % 2) && dims[ax] > 2) cut += 1;
-                        Work a = w, b = w;
-                        if (ax == 0) { a.n1 = cut; b.i0 += cut; b.n1 -= cut; }
-                        if (ax == 1) { a.n2 = cut; b.j0 += cut; b.n2 -= cut; }
-                        if (ax == 2) { a.n3 = cut; b.k0 += cut; b.n3 -= cut; }
-                        for (Work *x : {&b, &a}) {
-                            double lo3[3], hi3[3], ctr[3], rad;
-                            batch_box(bg, x->i0, x->j0, x->k0, x->n1, x->n2, x->n3, lo3, hi3, ctr, &rad);
-                            std::vector<RawSlot> keep;
-                            for (auto &s : w.s) {
-                                double c[3];
-                                for (int q = 0; q < 3; ++q)
-                                    c[q] = tau[3 * s.atom + q] + s.n[0] * G.A[q] + s.n[1] * G.A[3 + q] + s.n[2] * G.A[6 + q];
-                                if (sphere_meets_batch(bg, c, rc[s.atom], lo3, hi3, ctr, rad)) keep.push_back(s);
-                            }
-                            x->s = std::move(keep);
-                            stack.push_back(std::move(*x));
-                        }
-                        continue;
+    // useful flops: 2 n(r)^2 per point, n(r) = orbitals whose sphere contains r (exact count
+    // per point from the vlocal decomposition)
+    double flops_useful = 0.0;
+    for (auto &B : sets[0].batches) {
+        int n1 = B.dims & 255, n2 = (B.dims >> 8) & 255, n3 = (B.dims >> 16) & 255;
+        for (int a = 0; a < n1; ++a)
+            for (int b = 0; b < n2; ++b)
+                for (int c = 0; c < n3; ++c) {
+                    double off[3];
+                    for (int q = 0; q < 3; ++q) off[q] = a * bg.h[q] + b * bg.h[3 + q] + c * bg.h[6 + q];
+                    int n = 0;
+                    for (int s = 0; s < B.nslots; ++s) {
+                        const Slot &S = sets[0].slots[B.slot0 + s];
+                        double d[3] = {S.d0[0] + off[0], S.d0[1] + off[1], S.d0[2] + off[2]};
+                        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        if (r2 < rc[S.atom] * rc[S.atom]) n += S.norb;
                     }
-                    Batch B{};
-                    B.i0 = w.i0; B.j0 = w.j0; B.k0 = w.k0;
-                    B.dims = w.n1 | (w.n2 << 8) | (w.n3 << 16);
-                    B.slot0 = (int)slots.size();
-                    B.nslots = (int)w.s.size();
-                    B.nb = nb;
-                    B.tbl = (int)tbl.size();
-                    int npb = w.n1 * w.n2 * w.n3;
-                    flops_dense += 2.0 * npb * (double)nb * nb;
-                    max_nb = std::max(max_nb, nb);
-                    max_slots = std::max(max_slots, (int)w.s.size());
-                    int off = 0;
-                    double o[3];
-                    for (int c = 0; c < 3; ++c) o[c] = w.i0 * bg.h[c] + w.j0 * bg.h[3 + c] + w.k0 * bg.h[6 + c];
-                    for (auto &s : w.s) {
-                        Slot S{};
-                        S.atom = s.atom;
-                        S.species = h->species[s.atom];
-                        S.orb_off = off;
-                        S.norb = h->norb_atom[s.atom];
-                        for (int q = 0; q < 3; ++q)
-                            S.d0[q] = o[q] - (tau[3 * s.atom + q] + s.n[0] * G.A[q] + s.n[1] * G.A[3 + q] + s.n[2] * G.A[6 + q]);
-                        off += S.norb;
-                        slots.push_back(S);
-                        slot_img.insert(slot_img.end(), {s.n[0], s.n[1], s.n[2]});
-                    }
-                    // pair table: block of (I_a, I_b, n_b - n_a)
-                    for (auto &sa : w.s)
-                        for (auto &sb : w.s) {
-                            int64_t pk = pack_key(sa.atom, sb.atom, sb.n[0] - sa.n[0], sb.n[1] - sa.n[1], sb.n[2] - sa.n[2]);
-                            auto it = std::lower_bound(packed.begin(), packed.end(), pk);
-                            if (it == packed.end() || *it != pk) {
-                                tbl.push_back(-1);
-                            } else {
-                                int64_t bi = it - packed.begin();
-                                tbl.push_back((int)((offsets[bi] << 1) | canon[bi]));
-                            }
-                        }
-                    batches.push_back(B);
+                    flops_useful += 2.0 * n * (double)n;
                 }
-            }
-    if ((int64_t)tbl.size() >= ((int64_t)1 << 31) || batches.size() >= ((size_t)1 << 31)) {
-        set_error("gint_setup: too many batches / table entries");
-        return GINT_EINVAL;
-    }
-    // useful flops: 2 n(r)^2 per point, n(r) = orbitals whose sphere contains r
-    {
-        // computed per batch from exact per-point counts (cheap: a distance test per slot and point)
-        for (auto &B : batches) {
-            int n1 = B.dims & 255, n2 = (B.dims >> 8) & 255, n3 = (B.dims >> 16) & 255;
-            for (int a = 0; a < n1; ++a)
-                for (int b = 0; b < n2; ++b)
-                    for (int c = 0; c < n3; ++c) {
-                        double off[3];
-                        for (int q = 0; q < 3; ++q) off[q] = a * bg.h[q] + b * bg.h[3 + q] + c * bg.h[6 + q];
-                        int n = 0;
-                        for (int s = 0; s < B.nslots; ++s) {
-                            const Slot &S = slots[B.slot0 + s];
-                            double d[3] = {S.d0[0] + off[0], S.d0[1] + off[1], S.d0[2] + off[2]};
-                            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                            if (r2 < rc[S.atom] * rc[S.atom]) n += S.norb;
-                        }
-                        flops_useful += 2.0 * n * (double)n;
-                    }
-        }
     }
     if (update_only) {
-        if (batches.size() != h->batches.size() || slot_img != h->slot_img || tbl != h->tbl) {
-            set_error("gint_update_positions: batch atom lists changed; build a new handle");
-            return GINT_ESTATE;
-        }
-        for (size_t i = 0; i < slots.size(); ++i)
-            if (slots[i].atom != h->slots[i].atom) {
+        for (int w = 0; w < 2; ++w) {
+            const BatchSet &o = h->bs[w], &n = sets[w];
+            bool same = o.batches.size() == n.batches.size() && o.slot_img == n.slot_img && o.tbl == n.tbl &&
+                        o.slots.size() == n.slots.size();
+            for (size_t i = 0; same && i < n.slots.size(); ++i) same = o.slots[i].atom == n.slots[i].atom;
+            if (!same) {
                 set_error("gint_update_positions: batch atom lists changed; build a new handle");
                 return GINT_ESTATE;
             }
+        }
+        for (int w = 0; w < 2; ++w) h->bs[w].slots = std::move(sets[w].slots);
+    } else {
+        h->keys = std::move(keys);
+        h->offsets = std::move(offsets);
+        h->partner = std::move(partner);
+        for (int w = 0; w < 2; ++w) h->bs[w] = std::move(sets[w]);
     }
-    h->keys = std::move(keys);
-    h->offsets = std::move(offsets);
-    h->partner = std::move(partner);
-    h->batches = std::move(batches);
-    h->slots = std::move(slots);
-    h->slot_img = std::move(slot_img);
-    h->tbl = std::move(tbl);
     h->tau.assign(tau, tau + 3 * natoms);
     gint_info_t &info = h->info;
     info.npts = (int64_t)N1 * N2 * N3;
     info.nblocks = nblocks;
     info.nvalues = h->offsets[nblocks];
-    info.nbatches = (int64_t)h->batches.size();
-    info.nslots = (int64_t)h->slots.size();
-    info.max_orbitals = max_nb;
-    info.max_slots = max_slots;
+    info.nbatches = (int64_t)h->bs[0].batches.size();
+    info.nslots = (int64_t)h->bs[0].slots.size();
+    info.max_orbitals = h->bs[0].max_nb;
+    info.max_slots = h->bs[0].max_slots;
     info.dV = std::fabs(G.det) / (double)info.npts;
     info.flops_useful = flops_useful;
-    info.flops_dense = flops_dense;
+    info.flops_dense = h->bs[0].flops_dense;
+    info.nbatches_rho = (int64_t)h->bs[1].batches.size();
+    info.max_orbitals_rho = h->bs[1].max_nb;
+    info.flops_dense_rho = h->bs[1].flops_dense;
     (void)rows;
     h->plan.nblocks = nblocks;
     h->plan.nvalues = info.nvalues;
-    h->plan.nbatches = (int)info.nbatches;
     h->plan.dV = info.dV;
     for (int i = 0; i < 3; ++i)
         for (int c = 0; c < 3; ++c) h->plan.h[3 * i + c] = bg.h[3 * i + c];
@@ -469,8 +482,9 @@ static cudaError_t upload(void **dst, const std::vector<T> &v)
 
 static void free_dev(gint_handle h)
 {
-    void *ptrs[] = {h->d_coef64, h->d_coef32, h->d_batches, h->d_slots, h->d_tbl, h->d_partner,
-                    h->d_blkoff, h->d_blkrows, h->d_status, h->d_dmsym, h->d_red, h->d_hostio};
+    void *ptrs[] = {h->d_coef64, h->d_coef32, h->d_partner, h->d_blkoff, h->d_blkrows, h->d_status, h->d_dmsym,
+                    h->d_dm32, h->d_poff, h->d_red, h->d_hostio, h->bs[0].d_batches, h->bs[0].d_slots, h->bs[0].d_tbl,
+                    h->bs[1].d_batches, h->bs[1].d_slots, h->bs[1].d_tbl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -479,23 +493,27 @@ static gint_status upload_geometry(gint_handle h)
 {
     cudaError_t e;
     // (re)upload everything that depends on positions; sizes are fixed after set-up
-    if (!h->d_batches) {
-        if ((e = upload(&h->d_batches, h->batches)) != cudaSuccess) return cuda_fail(e, "upload batches");
-        if ((e = upload(&h->d_slots, h->slots)) != cudaSuccess) return cuda_fail(e, "upload slots");
-        if ((e = upload(&h->d_tbl, h->tbl)) != cudaSuccess) return cuda_fail(e, "upload tables");
+    if (!h->d_blkoff) {
+        for (int w = 0; w < 2; ++w) {
+            BatchSet &b = h->bs[w];
+            if ((e = upload(&b.d_batches, b.batches)) != cudaSuccess) return cuda_fail(e, "upload batches");
+            if ((e = upload(&b.d_slots, b.slots)) != cudaSuccess) return cuda_fail(e, "upload slots");
+            if ((e = upload(&b.d_tbl, b.tbl)) != cudaSuccess) return cuda_fail(e, "upload tables");
+        }
         if ((e = upload(&h->d_partner, h->partner)) != cudaSuccess) return cuda_fail(e, "upload partner");
         if ((e = upload(&h->d_blkoff, h->offsets)) != cudaSuccess) return cuda_fail(e, "upload offsets");
         std::vector<int> rows(h->info.nblocks);
         for (int64_t b = 0; b < h->info.nblocks; ++b) rows[b] = h->norb_atom[h->keys[5 * b]];
         if ((e = upload(&h->d_blkrows, rows)) != cudaSuccess) return cuda_fail(e, "upload rows");
     } else {
-        e = cudaMemcpy(h->d_slots, h->slots.data(), h->slots.size() * sizeof(Slot), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return cuda_fail(e, "update slots");
+        for (int w = 0; w < 2; ++w) {
+            BatchSet &b = h->bs[w];
+            if (b.slots.empty()) continue;
+            e = cudaMemcpy(b.d_slots, b.slots.data(), b.slots.size() * sizeof(Slot), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(e, "update slots");
+        }
     }
     Plan &P = h->plan;
-    P.batches = (const Batch *)h->d_batches;
-    P.slots = (const Slot *)h->d_slots;
-    P.tbl = (const int *)h->d_tbl;
     P.partner = (const int *)h->d_partner;
     P.blk_off = (const int64_t *)h->d_blkoff;
     P.blk_rows = (const int *)h->d_blkrows;
@@ -542,17 +560,21 @@ extern "C" gint_status gint_setup(gint_handle *out, const double cell[9], int na
             }
     }
     gint_options o{};
-    o.batch[0] = 4; o.batch[1] = 4; o.batch[2] = 8;
+    o.batch[0] = 4; o.batch[1] = 4; o.batch[2] = 4;
+    o.batch_rho[0] = 4; o.batch_rho[1] = 4; o.batch_rho[2] = 8;
     if (opt) {
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i) {
             if (opt->batch[i] > 0) o.batch[i] = opt->batch[i];
+            if (opt->batch_rho[i] > 0) o.batch_rho[i] = opt->batch_rho[i];
+        }
     }
-    if (o.batch[0] > kMaxBatchDim || o.batch[1] > kMaxBatchDim || o.batch[2] > kMaxBatchDim ||
-        o.batch[0] * o.batch[1] * o.batch[2] > kMaxBatchPts || (o.batch[2] % 2)) {
-        set_error("gint_setup: batch %dx%dx%d invalid (<= %d per axis, <= %d points, even along a3)",
-                  o.batch[0], o.batch[1], o.batch[2], kMaxBatchDim, kMaxBatchPts);
-        return GINT_EINVAL;
-    }
+    for (const int *b : {o.batch, o.batch_rho})
+        if (b[0] > kMaxBatchDim || b[1] > kMaxBatchDim || b[2] > kMaxBatchDim || b[0] * b[1] * b[2] > kMaxBatchPts ||
+            (b[2] % 2)) {
+            set_error("gint_setup: batch %dx%dx%d invalid (<= %d per axis, <= %d points, even along a3)", b[0], b[1],
+                      b[2], kMaxBatchDim, kMaxBatchPts);
+            return GINT_EINVAL;
+        }
     // device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -664,10 +686,31 @@ extern "C" gint_status gint_setup(gint_handle *out, const double cell[9], int na
     if ((e = cudaMalloc((void **)&h->d_status, sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(h->d_status, 0, sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc((void **)&h->d_dmsym, std::max<size_t>(8, h->info.nvalues * sizeof(double)))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&h->d_dm32, std::max<size_t>(16, h->info.nvalues * sizeof(float)))) != cudaSuccess ||
         (e = cudaMalloc((void **)&h->d_red, 4096 * sizeof(double))) != cudaSuccess) {
         free_dev(h);
         delete h;
         return cuda_fail(e, "gint_setup: allocate");
+    }
+    {
+        // offsets a h1 + b h2 + c h3 of local grid points, FP64 then split into FP32 hi + lo
+        std::vector<float> tab((size_t)kPoffDim * kPoffDim * kPoffDim * 6);
+        for (int a = 0; a < kPoffDim; ++a)
+            for (int b = 0; b < kPoffDim; ++b)
+                for (int c = 0; c < kPoffDim; ++c) {
+                    float *t = &tab[(((size_t)a * kPoffDim + b) * kPoffDim + c) * 6];
+                    for (int q = 0; q < 3; ++q) {
+                        double v = a * P.h[q] + b * P.h[3 + q] + c * P.h[6 + q];
+                        t[q] = (float)v;
+                        t[3 + q] = (float)(v - (double)t[q]);
+                    }
+                }
+        if ((e = upload((void **)&h->d_poff, tab)) != cudaSuccess) {
+            free_dev(h);
+            delete h;
+            return cuda_fail(e, "gint_setup: point offsets");
+        }
+        P.poff = h->d_poff;
     }
     P.status = h->d_status;
     *out = h;
@@ -727,16 +770,19 @@ extern "C" gint_status gint_update_positions(gint_handle h, const double *tau)
     tmp.species = h->species;
     tmp.norb_atom = h->norb_atom;
     tmp.keys = h->keys;
-    tmp.batches = h->batches;
-    tmp.slots = h->slots;
-    tmp.slot_img = h->slot_img;
-    tmp.tbl = h->tbl;
+    tmp.offsets = h->offsets;
+    for (int w = 0; w < 2; ++w) {
+        tmp.bs[w].batches = h->bs[w].batches;
+        tmp.bs[w].slots = h->bs[w].slots;
+        tmp.bs[w].slot_img = h->bs[w].slot_img;
+        tmp.bs[w].tbl = h->bs[w].tbl;
+    }
     tmp.opt = h->opt;
     gint_status st = build_geometry(&tmp, tau, true);
     if (st != GINT_OK) return st;
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(e, "gint_update_positions");
-    h->slots = std::move(tmp.slots);
+    for (int w = 0; w < 2; ++w) h->bs[w].slots = std::move(tmp.bs[w].slots);
     h->tau = std::move(tmp.tau);
     h->info = tmp.info;
     h->plan.dV = tmp.plan.dV;

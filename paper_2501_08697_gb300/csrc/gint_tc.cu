@@ -8,14 +8,18 @@
 // BF16x6); the products of total order <= 1 (TF32x3, BF16x3) or <= 2 (BF16x6) accumulate in
 // FP32 in tensor memory (TMEM); the cross-batch sums (block store, rho(r), forces) are FP64.
 //
-// One persistent CTA per SM, 8 warps:
-//   warps 0-3  producers: orbital values (FP32, spline x solid harmonic) into an FP32 staging
+// One persistent CTA per SM, 12 warps:
+//   warps 0-7  producers: orbital values (FP32, spline x solid harmonic) into an FP32 staging
 //              tile, then split into the canonical K-major no-swizzle shared-memory layout
 //              (8-row x 16-byte core matrices; the K-direction core-matrix stride is padded
 //              to 144 bytes so 16-byte stores from a warp spread over all banks); thread 0
 //              also issues the MMAs and commits them to mbarriers.
-//   warps 4-7  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes 32(w-4)..),
+//   warps 8-11 epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes 32(w-8)..),
 //              then the FP64 scatter into the block store (vlocal) or rho(r)/force (rho).
+// Accumulators are double-buffered in TMEM so the epilogue of batch i overlaps the MMAs of
+// batch i+1.  No FP64 arithmetic runs in the hot loops (GB300's FP64 rate is 1/64 of FP32):
+// offsets come as FP32 hi/lo pairs, dV is folded into the FP32 operand, FP32 -> FP64 for the
+// atomics is done with integer bit operations, and the density matrix is read as FP32.
 // Every mbarrier wait is bounded (clock64 budget); a wait that runs out records
 // GINT_ETIMEOUT in the status word and the CTA drains and exits without deadlock.
 #include <cuda_bf16.h>
@@ -25,7 +29,7 @@
 namespace gint {
 namespace {
 
-constexpr int kProd = 128;        // producer threads
+constexpr int kProd = 256;        // producer threads
 constexpr int kEpi = 128;         // epilogue threads
 constexpr int kThreadsTC = kProd + kEpi;
 constexpr int kLBO = 144;         // bytes between core matrices along K
@@ -203,13 +207,16 @@ __device__ __forceinline__ void unpack(int dims, int &n1, int &n2, int &n3)
 __device__ __forceinline__ void load_geom(const Plan &P, const Batch &B, PSlot *ps, float *poff, int tid, int nthr)
 {
     for (int s = tid; s < B.nslots; s += nthr) {
-        const Slot S = P.slots[B.slot0 + s];
+        const Slot &S = P.slots[B.slot0 + s];
         PSlot q;
         q.species = S.species;
         q.off = S.orb_off;
         q.norb = S.norb;
         q.atom = S.atom;
-        for (int c = 0; c < 3; ++c) split_f32(S.d0[c], q.dh[c], q.dl[c]);
+        for (int c = 0; c < 3; ++c) {
+            q.dh[c] = S.dh[c];
+            q.dl[c] = S.dl[c];
+        }
         ps[s] = q;
     }
     int n1, n2, n3;
@@ -217,10 +224,22 @@ __device__ __forceinline__ void load_geom(const Plan &P, const Batch &B, PSlot *
     const int np = n1 * n2 * n3;
     for (int p = tid; p < np; p += nthr) {
         const int c = p % n3, b = (p / n3) % n2, a = p / (n3 * n2);
-        double off[3];
-        point_offset64(P, a, b, c, off);
-        for (int q = 0; q < 3; ++q) split_f32(off[q], poff[6 * p + q], poff[6 * p + 3 + q]);
+        const float *t = P.poff + ((a * kPoffDim + b) * kPoffDim + c) * 6;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) poff[6 * p + q] = __ldg(t + q);
     }
+}
+
+// FP32 -> FP64 with integer operations (exact for normal numbers; subnormals flush to 0)
+__device__ __forceinline__ double f2d(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFF;
+    if (e == 0) return 0.0;
+    if (e == 0xFF) return (double)f;
+    const uint64_t bits = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
+                          ((uint64_t)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
 }
 
 __device__ __forceinline__ void disp(const PSlot &s, const float *po, float &dx, float &dy, float &dz)
@@ -252,14 +271,17 @@ __device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, const 
 }
 
 // ====================================================================== vlocal
+// TMEM accumulator buffer b (b = 0, 1) occupies columns [256 b, 256 b + 256): tile 0 (rows
+// 0..127, N = npad <= 192 columns) at +0 and tile 1 (rows 128.., N = npad - 128 <= 64) at +192.
 template <class S>
 struct VSmem {
     static constexpr int KC = S::KCM * S::CG;             // points per chunk
-    static constexpr int ARR = arr_bytes<S>(kMaxNb);      // one operand term, 256 rows
+    static constexpr int ROWS = 192;                      // orbitals per batch (vlocal limit)
+    static constexpr int ARR = arr_bytes<S>(256);         // one operand term (tile 1 reads rows 128..255)
     static constexpr int STAGE = 2 * S::NT * ARR;         // A terms then B terms
     static constexpr int NSTAGE = 2;
-    static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [256][KC]
-    static constexpr int OFF_PSLOT = OFF_STG + kMaxNb * KC * 4;             // PSlot[64]
+    static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [192][KC]
+    static constexpr int OFF_PSLOT = OFF_STG + ROWS * KC * 4;               // PSlot[64]
     static constexpr int OFF_POFF = OFF_PSLOT + kMaxSlots * (int)sizeof(PSlot);  // float [128][6]
     static constexpr int OFF_V = OFF_POFF + kMaxBatchPts * 6 * 4;           // float [128]
     static constexpr int OFF_TBL = OFF_V + kMaxBatchPts * 4;                // int [64*64]
@@ -285,7 +307,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
     unsigned char *oslot = sm + L::OFF_OMAP, *oidx = oslot + kMaxNb;
     unsigned char *snorb = sm + L::OFF_NORB;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::OFF_BAR);
-    uint64_t *empty = bars, *accfull = bars + 2, *accempty = bars + 3, *fin = bars + 4;
+    uint64_t *empty = bars, *accfull = bars + 2, *accempty = bars + 4, *fin = bars + 6;
     uint32_t *tmem_base = reinterpret_cast<uint32_t *>(sm + L::OFF_MISC);
     volatile int *pflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 4);
     volatile int *eflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 8);
@@ -294,8 +316,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
     if (tid == 0) {
         mbar_init(&empty[0], 1);
         mbar_init(&empty[1], 1);
-        mbar_init(accfull, 1);
-        mbar_init(accempty, kEpi);
+        mbar_init(&accfull[0], 1);
+        mbar_init(&accfull[1], 1);
+        mbar_init(&accempty[0], kEpi);
+        mbar_init(&accempty[1], kEpi);
         mbar_init(fin, 1);
     }
     if (warp == 0) {
@@ -307,12 +331,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_base;
+    const float dVf = (float)P.dV;
 
     if (tid < kProd) {
         // ------------------------------------------------------------ producers + MMA issue
         const int pt = tid;
         int g = 0;  // chunk counter (stage = g & 1)
-        int it = 0;
+        int it = 0; // batches with MMAs issued
         bool ok = true;
         for (int bi = blockIdx.x; bi < P.nbatches && ok; bi += gridDim.x) {
             const Batch B = P.batches[bi];
@@ -320,10 +345,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
             unpack(B.dims, n1, n2, n3);
             const int ns = B.nslots, nb = B.nb, npb = n1 * n2 * n3;
             const int npad = (nb + 15) & ~15;
+            const int buf = it & 1;
             if (nb == 0) continue;  // no orbital reaches this batch: nothing to add
             named_sync(1, kProd);
             load_geom(P, B, ps, poff, pt, kProd);
-            for (int p = pt; p < kMaxBatchPts; p += kProd) vs[p] = p < npb ? (float)V[grid_index(P, B, p, n2, n3)] : 0.f;
+            for (int p = pt; p < kMaxBatchPts; p += kProd)
+                vs[p] = p < npb ? d2f(V[grid_index(P, B, p, n2, n3)]) * dVf : 0.f;
             named_sync(1, kProd);
             const int nch = (npb + KC - 1) / KC;
             for (int ch = 0; ch < nch && ok; ++ch, ++g) {
@@ -345,7 +372,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
                 if (g >= 2) ok = role_wait(&empty[stage], ((g >> 1) - 1) & 1, P, pt, pflag, 1, kProd);
                 else named_sync(1, kProd);
                 if (!ok) break;
-                // phase 2: split Phi (A) and V*Phi (B) into the canonical layout
+                // phase 2: split Phi (A) and V dV Phi (B) into the canonical layout
                 unsigned char *base = sm + stage * L::STAGE;
                 for (int w = pt; w < npad * S::KCM; w += kProd) {
                     const int kc = w % S::KCM, row = w / S::KCM;
@@ -372,8 +399,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
                 fence_async_smem();
                 named_sync(1, kProd);
                 if (pt == 0) {
-                    if (ch == 0 && it > 0) {
-                        ok = !aborted(P) && mbar_wait(accempty, (it - 1) & 1, P.spin_limit);
+                    if (ch == 0 && it >= 2) {
+                        ok = !aborted(P) && mbar_wait(&accempty[buf], ((it >> 1) - 1) & 1, P.spin_limit);
                         if (!ok) report_timeout(P);
                     }
                     if (ok) {
@@ -390,12 +417,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
                                     const uint64_t da = sdesc(a0 + term(S::PA, q) * L::ARR + rowoff + ks * 2 * kLBO, SBO);
                                     const uint64_t db = sdesc(b0 + term(S::PB, q) * L::ARR + rowoff + ks * 2 * kLBO, SBO);
                                     const uint32_t acc = (ch == 0 && ks == 0 && q == 0) ? 0u : 1u;
-                                    umma<S::F16>(tmem + t * 256, da, db, id, acc);
+                                    umma<S::F16>(tmem + buf * 256 + t * 192, da, db, id, acc);
                                 }
                             }
                         }
                         umma_commit(&empty[stage]);
-                        if (ch == nch - 1) umma_commit(accfull);
+                        if (ch == nch - 1) umma_commit(&accfull[buf]);
                     }
                     *pflag = ok ? 0 : 1;
                 }
@@ -418,20 +445,21 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
             const Batch B = P.batches[bi];
             const int ns = B.nslots, nb = B.nb;
             const int npad = (nb + 15) & ~15;
+            const int buf = it & 1;
             if (nb == 0) continue;
             named_sync(2, kEpi);
             for (int e = et; e < ns * ns; e += kEpi) tbl[e] = P.tbl[B.tbl + e];
             for (int s = et; s < ns; s += kEpi) {
-                const Slot sl = P.slots[B.slot0 + s];
-                snorb[s] = (unsigned char)sl.norb;
-                for (int o = 0; o < sl.norb; ++o) {
-                    oslot[sl.orb_off + o] = (unsigned char)s;
-                    oidx[sl.orb_off + o] = (unsigned char)o;
+                const Slot &sl = P.slots[B.slot0 + s];
+                const int no = sl.norb, off = sl.orb_off;
+                snorb[s] = (unsigned char)no;
+                for (int o = 0; o < no; ++o) {
+                    oslot[off + o] = (unsigned char)s;
+                    oidx[off + o] = (unsigned char)o;
                 }
             }
-            if (!role_wait(accfull, it & 1, P, et, eflag, 2, kEpi)) break;
+            if (!role_wait(&accfull[buf], (it >> 1) & 1, P, et, eflag, 2, kEpi)) break;
             tc_fence_after();
-            const double dV = P.dV;
             for (int t = 0; t < (nb > 128 ? 2 : 1); ++t) {
                 const int mu = t * 128 + q * 32 + lane;
                 const bool rv = mu < nb;
@@ -439,7 +467,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
                 const int na = snorb[a];
                 for (int c0 = t * 128; c0 < npad; c0 += 16) {
                     float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 256 + c0 - t * 128), v);
+                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + t * 192 + c0 - t * 128), v);
                     if (!rv) continue;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
@@ -447,12 +475,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
                         if (nu >= nb) break;
                         const int b = oslot[nu], ob = oidx[nu];
                         const bool both = (t == 1) || (nu < 128);
-                        scatter_elem(H, tbl, ns, a, oa, na, b, ob, snorb[b], (double)v[j] * dV, both);
+                        scatter_elem(H, tbl, ns, a, oa, na, b, ob, snorb[b], f2d(v[j]), both);
                     }
                 }
             }
             tc_fence_before();
-            mbar_arrive(accempty);
+            mbar_arrive(&accempty[buf]);
             ++it;
         }
     }
@@ -488,7 +516,7 @@ struct RSmem {
 
 template <class S, bool RHO, bool FORCE>
 __global__ void __launch_bounds__(kThreadsTC, 1)
-    k_rho_tc(Plan P, const double *__restrict__ V, const double *__restrict__ DM, double *rho, double *F)
+    k_rho_tc(Plan P, const double *__restrict__ V, const float *__restrict__ DM, double *rho, double *F)
 {
     using L = RSmem<S>;
     constexpr int KC = L::KC;
@@ -595,30 +623,40 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     for (int i = 0; i < S::CG; ++i) x[i] = stg[(kc * S::CG + i) * kMaxBatchPts + p];
                     split_store<S>(x, da);
                 }
-                // phase 2b: B = D rows nu (N), K = orbitals mu of the chunk: D(b_nu, a_mu)[o_nu][o_mu]
-                for (int w = pt; w < npad * S::KCM; w += kProd) {
-                    const int kc = w % S::KCM, nu = w / S::KCM;
-                    unsigned char *db[S::NT];
+                // phase 2b: B = D rows nu (N), K = orbitals mu of the chunk: D(b_nu, a_mu)[o_nu][o_mu],
+                // FP32; GB tasks per thread with all their loads in flight before any store
+                constexpr int GB = 4;
+                for (int w0 = pt; w0 < npad * S::KCM; w0 += kProd * GB) {
+                    float x[GB][S::CG];
 #pragma unroll
-                    for (int t = 0; t < S::NT; ++t) db[t] = base + S::NT * L::ARR_A + t * L::ARR_B + cm_off<S>(nu, kc);
-                    if (nu >= nb) {
-                        zero_store<S>(db);
-                        continue;
-                    }
-                    const int b = oslot[nu], ob = oidx[nu];
-                    float x[S::CG];
+                    for (int gq = 0; gq < GB; ++gq) {
+                        const int w = w0 + gq * kProd;
+                        const int kc = w % S::KCM, nu = w / S::KCM;
+                        const bool rv = w < npad * S::KCM && nu < nb;
+                        const int b = rv ? oslot[nu] : 0, ob = rv ? oidx[nu] : 0;
 #pragma unroll
-                    for (int i = 0; i < S::CG; ++i) {
-                        const int mu = k0 + kc * S::CG + i;
-                        float v = 0.f;
-                        if (mu < nb) {
-                            const int a = oslot[mu];
-                            const int e = tbl[b * ns + a];
-                            if (e >= 0) v = (float)__ldg(DM + (e >> 1) + ob * ps[a].norb + oidx[mu]);
+                        for (int i = 0; i < S::CG; ++i) {
+                            const int mu = k0 + kc * S::CG + i;
+                            int idx = -1;
+                            if (rv && mu < nb) {
+                                const int a = oslot[mu];
+                                const int e = tbl[b * ns + a];
+                                if (e >= 0) idx = (e >> 1) + ob * ps[a].norb + oidx[mu];
+                            }
+                            x[gq][i] = idx >= 0 ? __ldg(DM + idx) : 0.f;
                         }
-                        x[i] = v;
                     }
-                    split_store<S>(x, db);
+#pragma unroll
+                    for (int gq = 0; gq < GB; ++gq) {
+                        const int w = w0 + gq * kProd;
+                        if (w >= npad * S::KCM) break;
+                        const int kc = w % S::KCM, nu = w / S::KCM;
+                        unsigned char *db[S::NT];
+#pragma unroll
+                        for (int t = 0; t < S::NT; ++t)
+                            db[t] = base + S::NT * L::ARR_A + t * L::ARR_B + cm_off<S>(nu, kc);
+                        split_store<S>(x[gq], db);
+                    }
                 }
                 fence_async_smem();
                 named_sync(1, kProd);
@@ -684,7 +722,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             int64_t gi = 0;
             if (pv) {
                 gi = grid_index(P, B, p, n2, n3);
-                if (FORCE) vp = (float)V[gi];
+                if (FORCE) vp = d2f(V[gi]);
             }
             float racc = 0.f;
             int w0 = -1000, wn = 0;
@@ -735,7 +773,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             }
             tc_fence_before();
             mbar_arrive(&accempty[buf]);
-            if (RHO && pv) rho[gi] = (double)racc;
+            if (RHO && pv) rho[gi] = f2d(racc);
             if (FORCE) {
                 named_sync(2, kEpi);
                 for (int e = et; e < 3 * ns; e += kEpi)
@@ -765,7 +803,7 @@ cudaError_t vlocal_launch(const Plan &P, const double *V, double *H, cudaStream_
 }
 
 template <class S, bool R, bool Fo>
-cudaError_t rho_launch3(const Plan &P, const double *V, const double *DM, double *rho, double *F, cudaStream_t s,
+cudaError_t rho_launch3(const Plan &P, const double *V, const float *DM, double *rho, double *F, cudaStream_t s,
                         int nsm)
 {
     constexpr int smem = RSmem<S>::TOTAL;
@@ -778,7 +816,7 @@ cudaError_t rho_launch3(const Plan &P, const double *V, const double *DM, double
 }
 
 template <class S>
-cudaError_t rho_launch(const Plan &P, const double *V, const double *DM, double *rho, double *F, cudaStream_t s,
+cudaError_t rho_launch(const Plan &P, const double *V, const float *DM, double *rho, double *F, cudaStream_t s,
                        int nsm)
 {
     if (rho && F) return rho_launch3<S, true, true>(P, V, DM, rho, F, s, nsm);
@@ -799,7 +837,7 @@ cudaError_t launch_vlocal_tc(const Plan &P, gint_prec prec, const double *V, dou
     }
 }
 
-cudaError_t launch_rho_force_tc(const Plan &P, gint_prec prec, const double *V, const double *DM, double *rho,
+cudaError_t launch_rho_force_tc(const Plan &P, gint_prec prec, const double *V, const float *DM, double *rho,
                                 double *F, cudaStream_t s, int nsm)
 {
     if (P.nbatches == 0) return cudaSuccess;

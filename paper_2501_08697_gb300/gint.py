@@ -36,13 +36,14 @@ class _Species(C.Structure):
 
 
 class _Options(C.Structure):
-    _fields_ = [("batch", C.c_int * 3), ("reserved", C.c_int * 5)]
+    _fields_ = [("batch", C.c_int * 3), ("batch_rho", C.c_int * 3), ("reserved", C.c_int * 2)]
 
 
 class _Info(C.Structure):
     _fields_ = [("npts", C.c_int64), ("nblocks", C.c_int64), ("nvalues", C.c_int64), ("nbatches", C.c_int64),
                 ("nslots", C.c_int64), ("max_orbitals", C.c_int), ("max_slots", C.c_int), ("dV", C.c_double),
-                ("flops_useful", C.c_double), ("flops_dense", C.c_double)]
+                ("flops_useful", C.c_double), ("flops_dense", C.c_double), ("nbatches_rho", C.c_int64),
+                ("max_orbitals_rho", C.c_int), ("reserved", C.c_int), ("flops_dense_rho", C.c_double)]
 
 
 _lib = None
@@ -156,7 +157,7 @@ class Handle:
             pass
 
 
-def gint_setup(cell, species, tau, tables, grid, batch=(4, 4, 8)) -> Handle:
+def gint_setup(cell, species, tau, tables, grid, batch=(4, 4, 4), batch_rho=(4, 4, 8)) -> Handle:
     """cell [3,3] rows (bohr), species [natoms] ints, tau [natoms,3] (bohr), tables: list of
     objects with .l, .rcut, .dr, .ftab [nrad, ntab], .dfdr0 (see synth.SpeciesTables)."""
     lib = load()
@@ -181,6 +182,7 @@ def gint_setup(cell, species, tau, tables, grid, batch=(4, 4, 8)) -> Handle:
     opt = _Options()
     for i in range(3):
         opt.batch[i] = int(batch[i])
+        opt.batch_rho[i] = int(batch_rho[i])
     out = C.c_void_p()
     _check(lib.gint_setup(C.byref(out), cell.ctypes.data_as(C.POINTER(C.c_double)), len(species),
                           species.ctypes.data_as(C.POINTER(C.c_int)), tau.ctypes.data_as(C.POINTER(C.c_double)),
@@ -264,6 +266,6 @@ def gint_get_status(h: Handle):
     return load().gint_get_status(h.ptr)
 
 
-def setup_structure(st, batch=(4, 4, 8), tau=None) -> Handle:
+def setup_structure(st, batch=(4, 4, 4), batch_rho=(4, 4, 8), tau=None) -> Handle:
     """Convenience: gint_setup from a synth.Structure."""
-    return gint_setup(st.cell, st.species, st.tau if tau is None else tau, st.tables, st.grid, batch)
+    return gint_setup(st.cell, st.species, st.tau if tau is None else tau, st.tables, st.grid, batch, batch_rho)

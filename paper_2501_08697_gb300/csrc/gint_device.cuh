@@ -245,6 +245,80 @@ __device__ __forceinline__ float d2f(double x)
     return __uint_as_float(sign | bits);
 }
 
+// FP32 -> FP64 in four integer operations: exact for normal numbers; zero and subnormals map
+// to +-2^-127 (harmless as an addend to FP64 sums of order 1e-30 and above).
+__device__ __forceinline__ double f2d_fast(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t hi = (((u & 0x7FFFFFFFu) >> 3) + 0x38000000u) | (u & 0x80000000u);
+    const uint32_t lo = u << 29;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// Species descriptor for the FP32 tensor-core producers, kept in shared memory.
+struct SpecSh {
+    int nrad, nint, coef_off, lpack;   // lpack: 2 bits of l per radial
+    float rcut2, inv_dr;
+};
+
+// FP32 orbital values of one species at displacement d (no gradient); rsqrt + one Newton
+// step instead of sqrt and division.  emit(o, phi) for o = 0 .. norb-1.
+template <typename Emit>
+__device__ __forceinline__ void eval_phi_f32(const SpecSh &S, const float4 *__restrict__ coef, float dx, float dy,
+                                             float dz, Emit &&emit)
+{
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const int nrad = S.nrad;
+    if (!(r2 < S.rcut2)) {
+        int o = 0;
+        for (int ir = 0; ir < nrad; ++ir) {
+            const int nm = 2 * ((S.lpack >> (2 * ir)) & 3) + 1;
+            for (int m = 0; m < nm; ++m, ++o) emit(o, 0.f);
+        }
+        return;
+    }
+    if (r2 < 1e-24f) {
+        int o = 0;
+        for (int ir = 0; ir < nrad; ++ir) {
+            const int l = (S.lpack >> (2 * ir)) & 3;
+            if (l == 0) emit(o++, __ldg(coef + S.coef_off + ir).x * YC<float>::c0);
+            else
+                for (int m = 0; m < 2 * l + 1; ++m) emit(o++, 0.f);
+        }
+        return;
+    }
+    float ir1 = rsqrtf(r2);
+    ir1 = ir1 * (1.5f - 0.5f * r2 * ir1 * ir1);
+    const float r = r2 * ir1;
+    const float x = r * S.inv_dr;
+    int i = (int)x;
+    i = min(i, S.nint - 1);
+    const float t = x - (float)i;
+    const float ux = dx * ir1, uy = dy * ir1, uz = dz * ir1;
+    const float4 *cp = coef + S.coef_off + i * nrad;
+    int o = 0;
+    for (int ir = 0; ir < nrad; ++ir) {
+        const float4 c = __ldg(cp + ir);
+        const float f = c.x + t * (c.y + t * (c.z + t * c.w));
+        const int l = (S.lpack >> (2 * ir)) & 3;
+        if (l == 0) {
+            emit(o, f * YC<float>::c0);
+            o += 1;
+        } else if (l == 1) {
+            const float a = f * YC<float>::c1;
+            emit(o, a * uz); emit(o + 1, a * ux); emit(o + 2, a * uy);
+            o += 3;
+        } else {
+            emit(o, f * YC<float>::c20 * (2.f * uz * uz - ux * ux - uy * uy));
+            emit(o + 1, f * YC<float>::c21 * ux * uz);
+            emit(o + 2, f * YC<float>::c21 * uy * uz);
+            emit(o + 3, f * YC<float>::c22 * (ux * ux - uy * uy));
+            emit(o + 4, f * YC<float>::c21 * ux * uy);
+            o += 5;
+        }
+    }
+}
+
 // ----------------------------------------------------------------------- status and waits
 __device__ __forceinline__ void report_timeout(const Plan &P) { atomicCAS(P.status, 0, (int)GINT_ETIMEOUT); }
 

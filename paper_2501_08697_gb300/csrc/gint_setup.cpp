@@ -212,11 +212,15 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
         for (auto &x : s) n += h->norb_atom[x.atom];
         return n;
     };
+    // Atom images ordered by atom ascending, then image n descending.  With this order every
+    // pair of slots a < b maps to the canonical member of its partner pair {(I,J,R), (J,I,-R)}:
+    // I_a < I_b, or I_a == I_b with R = n_b - n_a lexicographically negative.  The tensor-core
+    // scatter relies on it (it adds only elements with row <= column).
     auto slot_less = [](const RawSlot &a, const RawSlot &b) {
         if (a.atom != b.atom) return a.atom < b.atom;
-        if (a.n[0] != b.n[0]) return a.n[0] < b.n[0];
-        if (a.n[1] != b.n[1]) return a.n[1] < b.n[1];
-        return a.n[2] < b.n[2];
+        if (a.n[0] != b.n[0]) return a.n[0] > b.n[0];
+        if (a.n[1] != b.n[1]) return a.n[1] > b.n[1];
+        return a.n[2] > b.n[2];
     };
     for (int b1 = 0; b1 < nb1; ++b1)
         for (int b2 = 0; b2 < nb2; ++b2)
@@ -292,14 +296,19 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                         out.slots.push_back(S);
                         out.slot_img.insert(out.slot_img.end(), {s.n[0], s.n[1], s.n[2]});
                     }
-                    for (auto &sa : w.s)
-                        for (auto &sb : w.s) {
+                    for (size_t ia = 0; ia < w.s.size(); ++ia)
+                        for (size_t ib = 0; ib < w.s.size(); ++ib) {
+                            const RawSlot &sa = w.s[ia], &sb = w.s[ib];
                             int64_t pk = pack_key(sa.atom, sb.atom, sb.n[0] - sa.n[0], sb.n[1] - sa.n[1], sb.n[2] - sa.n[2]);
                             auto it = std::lower_bound(packed.begin(), packed.end(), pk);
                             if (it == packed.end() || *it != pk) {
                                 out.tbl.push_back(-1);
                             } else {
                                 int64_t bi = it - packed.begin();
+                                if (ia <= ib && !canon[bi]) {
+                                    set_error("gint_setup: internal error, slot order breaks the canonical-pair rule");
+                                    return GINT_EINVAL;
+                                }
                                 out.tbl.push_back((int)((offsets[bi] << 1) | canon[bi]));
                             }
                         }

@@ -8,13 +8,14 @@
 // BF16x6); the products of total order <= 1 (TF32x3, BF16x3) or <= 2 (BF16x6) accumulate in
 // FP32 in tensor memory (TMEM); the cross-batch sums (block store, rho(r), forces) are FP64.
 //
-// One persistent CTA per SM, 12 warps:
+// One persistent CTA per SM, 16 warps:
 //   warps 0-7  producers: orbital values (FP32, spline x solid harmonic) into an FP32 staging
 //              tile, then split into the canonical K-major no-swizzle shared-memory layout
 //              (8-row x 16-byte core matrices; the K-direction core-matrix stride is padded
 //              to 144 bytes so 16-byte stores from a warp spread over all banks); thread 0
 //              also issues the MMAs and commits them to mbarriers.
-//   warps 8-11 epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes 32(w-8)..),
+//   warps 8-15 epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes 32(w%4)..;
+//              the two warps of a lane quadrant share the columns or the atom images),
 //              then the FP64 scatter into the block store (vlocal) or rho(r)/force (rho).
 // Accumulators are double-buffered in TMEM so the epilogue of batch i overlaps the MMAs of
 // batch i+1.  No FP64 arithmetic runs in the hot loops (GB300's FP64 rate is 1/64 of FP32):
@@ -30,7 +31,7 @@ namespace gint {
 namespace {
 
 constexpr int kProd = 256;        // producer threads
-constexpr int kEpi = 128;         // epilogue threads
+constexpr int kEpi = 256;         // epilogue threads (two warps per TMEM lane quadrant)
 constexpr int kThreadsTC = kProd + kEpi;
 constexpr int kLBO = 144;         // bytes between core matrices along K
 constexpr int kTmemCols = 512;
@@ -270,6 +271,23 @@ __device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, const 
     return ok;
 }
 
+__device__ __forceinline__ void load_species(const Plan &P, SpecSh *spec, int tid)
+{
+    if (tid < P.nspecies) {
+        const DevSpecies &D = P.sp[tid];
+        SpecSh q;
+        q.nrad = D.nrad;
+        q.nint = D.nint;
+        q.coef_off = D.coef_off;
+        int lp = 0;
+        for (int r = 0; r < D.nrad; ++r) lp |= D.l[r] << (2 * r);
+        q.lpack = lp;
+        q.rcut2 = D.rcut_f * D.rcut_f;
+        q.inv_dr = D.inv_dr_f;
+        spec[tid] = q;
+    }
+}
+
 // ====================================================================== vlocal
 // TMEM accumulator buffer b (b = 0, 1) occupies columns [256 b, 256 b + 256): tile 0 (rows
 // 0..127, N = npad <= 192 columns) at +0 and tile 1 (rows 128.., N = npad - 128 <= 64) at +192.
@@ -285,11 +303,12 @@ struct VSmem {
     static constexpr int OFF_POFF = OFF_PSLOT + kMaxSlots * (int)sizeof(PSlot);  // float [128][6]
     static constexpr int OFF_V = OFF_POFF + kMaxBatchPts * 6 * 4;           // float [128]
     static constexpr int OFF_TBL = OFF_V + kMaxBatchPts * 4;                // int [64*64]
-    static constexpr int OFF_OMAP = OFF_TBL + kMaxSlots * kMaxSlots * 4;    // uchar oslot[256], oidx[256]
-    static constexpr int OFF_NORB = OFF_OMAP + 2 * kMaxNb;                  // uchar [64]
-    static constexpr int OFF_BAR = OFF_NORB + kMaxSlots;                    // 8 mbarriers
+    static constexpr int OFF_INFO = OFF_TBL + kMaxSlots * kMaxSlots * 4;    // int [256]: slot | o << 8 | norb << 16
+    static constexpr int OFF_TILE = OFF_INFO + kMaxNb * 4;                  // float [8][32][33]
+    static constexpr int OFF_BAR = OFF_TILE + 8 * 32 * 33 * 4;              // 8 mbarriers
     static constexpr int OFF_MISC = OFF_BAR + 8 * 8;                        // tmem base, flags
-    static constexpr int TOTAL = OFF_MISC + 64;
+    static constexpr int OFF_SPEC = OFF_MISC + 64;                          // SpecSh[kMaxSpecies]
+    static constexpr int TOTAL = OFF_SPEC + kMaxSpecies * (int)sizeof(SpecSh);
 };
 
 template <class S>
@@ -304,8 +323,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
     float *poff = reinterpret_cast<float *>(sm + L::OFF_POFF);
     float *vs = reinterpret_cast<float *>(sm + L::OFF_V);
     int *tbl = reinterpret_cast<int *>(sm + L::OFF_TBL);
-    unsigned char *oslot = sm + L::OFF_OMAP, *oidx = oslot + kMaxNb;
-    unsigned char *snorb = sm + L::OFF_NORB;
+    int *info = reinterpret_cast<int *>(sm + L::OFF_INFO);
+    float *tiles = reinterpret_cast<float *>(sm + L::OFF_TILE);
+    SpecSh *spec = reinterpret_cast<SpecSh *>(sm + L::OFF_SPEC);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::OFF_BAR);
     uint64_t *empty = bars, *accfull = bars + 2, *accempty = bars + 4, *fin = bars + 6;
     uint32_t *tmem_base = reinterpret_cast<uint32_t *>(sm + L::OFF_MISC);
@@ -313,6 +333,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
     volatile int *eflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 8);
 
     const int tid = threadIdx.x, warp = tid >> 5;
+    load_species(P, spec, tid);
     if (tid == 0) {
         mbar_init(&empty[0], 1);
         mbar_init(&empty[1], 1);
@@ -332,6 +353,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
     tc_fence_after();
     const uint32_t tmem = *tmem_base;
     const float dVf = (float)P.dV;
+    // a contiguous range of batches per CTA: CTAs running at the same time work on distant
+    // parts of the cell, so their FP64 atomics rarely meet on the same block
+    const int bbeg = (int)((int64_t)P.nbatches * blockIdx.x / gridDim.x);
+    const int bend = (int)((int64_t)P.nbatches * (blockIdx.x + 1) / gridDim.x);
 
     if (tid < kProd) {
         // ------------------------------------------------------------ producers + MMA issue
@@ -339,7 +364,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
         int g = 0;  // chunk counter (stage = g & 1)
         int it = 0; // batches with MMAs issued
         bool ok = true;
-        for (int bi = blockIdx.x; bi < P.nbatches && ok; bi += gridDim.x) {
+        for (int bi = bbeg; bi < bend && ok; ++bi) {
             const Batch B = P.batches[bi];
             int n1, n2, n3;
             unpack(B.dims, n1, n2, n3);
@@ -364,7 +389,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
                     if (p < npb) {
                         float dx, dy, dz;
                         disp(sl, poff + 6 * p, dx, dy, dz);
-                        eval_orbitals<float, false>(P, sl.species, dx, dy, dz, [&](int o, float v) { col[o * KC] = v; });
+                        eval_phi_f32(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) { col[o * KC] = v; });
                     } else {
                         for (int o = 0; o < sl.norb; ++o) col[o * KC] = 0.f;
                     }
@@ -424,11 +449,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
                         umma_commit(&empty[stage]);
                         if (ch == nch - 1) umma_commit(&accfull[buf]);
                     }
-                    *pflag = ok ? 0 : 1;
+                    // a failed wait set the status word; the next role_wait sees it and every
+                    // producer stops together
+                    ok = true;
                 }
-                named_sync(1, kProd);
-                ok = ok && (*pflag == 0);
-                named_sync(1, kProd);
             }
             ++it;
         }
@@ -439,9 +463,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int et = tid - kProd, q = et >> 5, lane = et & 31;
+        const int et = tid - kProd, ew = et >> 5, lane = et & 31;
+        const int q = ew & 3, hh = ew >> 2;  // TMEM lane quadrant, column half
         int it = 0;
-        for (int bi = blockIdx.x; bi < P.nbatches; bi += gridDim.x) {
+        for (int bi = bbeg; bi < bend; ++bi) {
             const Batch B = P.batches[bi];
             const int ns = B.nslots, nb = B.nb;
             const int npad = (nb + 15) & ~15;
@@ -452,31 +477,56 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
             for (int s = et; s < ns; s += kEpi) {
                 const Slot &sl = P.slots[B.slot0 + s];
                 const int no = sl.norb, off = sl.orb_off;
-                snorb[s] = (unsigned char)no;
-                for (int o = 0; o < no; ++o) {
-                    oslot[off + o] = (unsigned char)s;
-                    oidx[off + o] = (unsigned char)o;
-                }
+                for (int o = 0; o < no; ++o) info[off + o] = s | (o << 8) | (no << 16);
             }
             if (!role_wait(&accfull[buf], (it >> 1) & 1, P, et, eflag, 2, kEpi)) break;
             tc_fence_after();
+            // Scatter of the upper triangle.  The atom images of a batch are ordered so that
+            // every slot pair a <= b is the canonical member of its partner pair; element
+            // (mu, nu) with mu <= nu therefore goes to block (a_mu, b_nu) at (o_mu, o_nu), and
+            // the mirror kernel fills the other half.  Warp (q, hh) owns TMEM lanes (rows)
+            // row0..row0+31 and the 32-column pieces c0 = 128 t + 32 hh + 64 k; a piece is
+            // transposed through shared memory so that lanes = columns and the adds of a block
+            // row are contiguous.  Addresses of 8 rows are formed before their atomics.
+            float *tl = tiles + ew * 32 * 33;
             for (int t = 0; t < (nb > 128 ? 2 : 1); ++t) {
-                const int mu = t * 128 + q * 32 + lane;
-                const bool rv = mu < nb;
-                const int a = rv ? oslot[mu] : 0, oa = rv ? oidx[mu] : 0;
-                const int na = snorb[a];
-                for (int c0 = t * 128; c0 < npad; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + t * 192 + c0 - t * 128), v);
-                    if (!rv) continue;
+                const int row0 = t * 128 + q * 32;
+                const int nrows = min(32, nb - row0);   // <= 0 for warps past the last row
+                for (int c0 = t * 128 + hh * 32; c0 < npad; c0 += 64) {
+                    if (nrows <= 0 || c0 + 32 <= row0) continue;   // wholly below the diagonal
+                    float v[32];
+                    const uint32_t col = (uint32_t)(buf * 256 + t * 192 + c0 - t * 128);
+                    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + col;
+                    tmem_ld16(taddr, v);
+                    if (c0 + 16 < npad) tmem_ld16(taddr + 16, v + 16);
+                    else
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int nu = c0 + j;
-                        if (nu >= nb) break;
-                        const int b = oslot[nu], ob = oidx[nu];
-                        const bool both = (t == 1) || (nu < 128);
-                        scatter_elem(H, tbl, ns, a, oa, na, b, ob, snorb[b], f2d(v[j]), both);
+                        for (int j = 16; j < 32; ++j) v[j] = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) tl[j * 33 + lane] = v[j];
+                    __syncwarp();
+                    const int nu = c0 + lane;
+                    const bool cv = nu < nb;
+                    const int ci = info[cv ? nu : 0];
+                    const int b = ci & 255, ob = (ci >> 8) & 255, nbo = ci >> 16;
+                    for (int r0 = 0; r0 < nrows; r0 += 8) {
+                        double *adr[8];
+                        float val[8];
+                        bool go[8];
+#pragma unroll
+                        for (int rr = 0; rr < 8; ++rr) {
+                            const int r = r0 + rr;
+                            const int ri2 = info[row0 + (r < nrows ? r : 0)];
+                            const int e = tbl[(ri2 & 255) * ns + b];
+                            go[rr] = cv && r < nrows && nu >= row0 + r && e >= 0;
+                            adr[rr] = H + (e >> 1) + ((ri2 >> 8) & 255) * nbo + ob;
+                            val[rr] = tl[lane * 33 + (r & 31)];
+                        }
+#pragma unroll
+                        for (int rr = 0; rr < 8; ++rr)
+                            if (go[rr]) atomicAdd(adr[rr], f2d_fast(val[rr]));
                     }
+                    __syncwarp();
                 }
             }
             tc_fence_before();
@@ -507,11 +557,13 @@ struct RSmem {
     static constexpr int OFF_OMAP = OFF_TBL + kMaxSlots * kMaxSlots * 4;    // oslot[256], oidx[256]
     static constexpr int OFF_EPSLOT = OFF_OMAP + 2 * kMaxNb;                // epilogue PSlot[64]
     static constexpr int OFF_EPOFF = OFF_EPSLOT + kMaxSlots * (int)sizeof(PSlot);
-    static constexpr int OFF_WIN = OFF_EPOFF + kMaxBatchPts * 24;           // float [4][kWin][32]
-    static constexpr int OFF_FACC = OFF_WIN + 4 * kWin * 32 * 4;            // double [64][3]
+    static constexpr int OFF_WIN = OFF_EPOFF + kMaxBatchPts * 24;           // float [8][kWin][32]
+    static constexpr int OFF_RPART = OFF_WIN + 8 * kWin * 32 * 4;           // float [128]
+    static constexpr int OFF_FACC = OFF_RPART + kMaxBatchPts * 4;           // double [64][3]
     static constexpr int OFF_BAR = OFF_FACC + kMaxSlots * 3 * 8;
     static constexpr int OFF_MISC = OFF_BAR + 8 * 8;
-    static constexpr int TOTAL = OFF_MISC + 64;
+    static constexpr int OFF_SPEC = OFF_MISC + 64;
+    static constexpr int TOTAL = OFF_SPEC + kMaxSpecies * (int)sizeof(SpecSh);
 };
 
 template <class S, bool RHO, bool FORCE>
@@ -530,6 +582,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     PSlot *eps = reinterpret_cast<PSlot *>(sm + L::OFF_EPSLOT);
     float *epoff = reinterpret_cast<float *>(sm + L::OFF_EPOFF);
     float *win = reinterpret_cast<float *>(sm + L::OFF_WIN);
+    float *rpart = reinterpret_cast<float *>(sm + L::OFF_RPART);
+    SpecSh *spec = reinterpret_cast<SpecSh *>(sm + L::OFF_SPEC);
     double *facc = reinterpret_cast<double *>(sm + L::OFF_FACC);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::OFF_BAR);
     uint64_t *empty = bars, *accfull = bars + 2, *accempty = bars + 4, *fin = bars + 6;
@@ -538,6 +592,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     volatile int *eflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 8);
 
     const int tid = threadIdx.x, warp = tid >> 5;
+    load_species(P, spec, tid);
     if (tid == 0) {
         mbar_init(&empty[0], 1);
         mbar_init(&empty[1], 1);
@@ -556,13 +611,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_base;
+    const int bbeg = (int)((int64_t)P.nbatches * blockIdx.x / gridDim.x);
+    const int bend = (int)((int64_t)P.nbatches * (blockIdx.x + 1) / gridDim.x);
 
     if (tid < kProd) {
         // ------------------------------------------------------------ producers + MMA issue
         const int pt = tid;
         int g = 0, it = 0;
         bool ok = true;
-        for (int bi = blockIdx.x; bi < P.nbatches && ok; bi += gridDim.x) {
+        for (int bi = bbeg; bi < bend && ok; ++bi) {
             const Batch B = P.batches[bi];
             int n1, n2, n3;
             unpack(B.dims, n1, n2, n3);
@@ -595,7 +652,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     if (p < npb) {
                         float dx, dy, dz;
                         disp(sl, poff + 6 * p, dx, dy, dz);
-                        eval_orbitals<float, false>(P, sl.species, dx, dy, dz, [&](int o, float v) {
+                        eval_phi_f32(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) {
                             const int k = base_k + o;
                             if (k >= 0 && k < KC) col[k * kMaxBatchPts] = v;
                         });
@@ -682,11 +739,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         umma_commit(&empty[stage]);
                         if (ch == nch - 1) umma_commit(&accfull[buf]);
                     }
-                    *pflag = ok ? 0 : 1;
+                    // a failed wait set the status word; the next role_wait sees it and every
+                    // producer stops together
+                    ok = true;
                 }
-                named_sync(1, kProd);
-                ok = ok && (*pflag == 0);
-                named_sync(1, kProd);
             }
             ++it;
         }
@@ -696,18 +752,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         }
     } else {
         // ------------------------------------------------------------ epilogue: rho and force
-        const int et = tid - kProd, q = et >> 5, lane = et & 31;
-        const int p = et;  // TMEM lane = point of the batch
-        float *w = win + q * kWin * 32;
+        // warp (q, hh): TMEM lane quadrant q (points 32q..32q+31), atom images s with s % 2 == hh
+        const int et = tid - kProd, ew = et >> 5, lane = et & 31;
+        const int q = ew & 3, hh = ew >> 2;
+        const int p = q * 32 + lane;  // TMEM lane = point of the batch
+        float *w = win + ew * kWin * 32;
         int it = 0;
-        for (int bi = blockIdx.x; bi < P.nbatches; bi += gridDim.x) {
+        for (int bi = bbeg; bi < bend; ++bi) {
             const Batch B = P.batches[bi];
             int n1, n2, n3;
             unpack(B.dims, n1, n2, n3);
             const int ns = B.nslots, npb = n1 * n2 * n3;
             const int buf = it & 1;
             if (B.nb == 0) {
-                if (RHO && p < npb) rho[grid_index(P, B, p, n2, n3)] = 0.0;
+                if (RHO && hh == 0 && p < npb) rho[grid_index(P, B, p, n2, n3)] = 0.0;
                 continue;
             }
             named_sync(2, kEpi);
@@ -726,19 +784,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             }
             float racc = 0.f;
             int w0 = -1000, wn = 0;
-            for (int s = 0; s < ns; ++s) {
+            for (int s = hh; s < ns; s += 2) {
                 const PSlot sl = eps[s];
                 if (sl.off < w0 || sl.off + sl.norb > w0 + wn) {
                     w0 = sl.off & ~15;
                     wn = ((sl.off + sl.norb - w0) + 15) & ~15;
-                    __syncwarp();
                     for (int c = 0; c < wn; c += 16) {
                         float v[16];
                         tmem_ld16(trow + (uint32_t)(w0 + c), v);
 #pragma unroll
                         for (int j = 0; j < 16; ++j) w[(c + j) * 32 + lane] = v[j];
                     }
-                    __syncwarp();
                 }
                 const float *col = w + (sl.off - w0) * 32 + lane;
                 float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -753,8 +809,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                                                        fx += gx * y; fy += gy * y; fz += gz * y;
                                                    });
                     else
-                        eval_orbitals<float, false>(P, sl.species, dx, dy, dz,
-                                                    [&](int o, float v) { racc += v * col[o * 32]; });
+                        eval_phi_f32(spec[sl.species], P.coef32, dx, dy, dz,
+                                     [&](int o, float v) { racc += v * col[o * 32]; });
                 }
                 if (FORCE) {
                     fx *= vp; fy *= vp; fz *= vp;
@@ -765,20 +821,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         fz += __shfl_xor_sync(0xffffffffu, fz, m);
                     }
                     if (lane == 0) {
-                        atomicAdd(&facc[3 * s + 0], (double)fx);
-                        atomicAdd(&facc[3 * s + 1], (double)fy);
-                        atomicAdd(&facc[3 * s + 2], (double)fz);
+                        atomicAdd(&facc[3 * s + 0], f2d(fx));
+                        atomicAdd(&facc[3 * s + 1], f2d(fy));
+                        atomicAdd(&facc[3 * s + 2], f2d(fz));
                     }
                 }
             }
             tc_fence_before();
             mbar_arrive(&accempty[buf]);
-            if (RHO && pv) rho[gi] = f2d(racc);
-            if (FORCE) {
-                named_sync(2, kEpi);
+            if (RHO && hh == 1) rpart[p] = racc;
+            named_sync(2, kEpi);
+            if (RHO && hh == 0 && pv) rho[gi] = f2d(racc + rpart[p]);
+            if (FORCE)
                 for (int e = et; e < 3 * ns; e += kEpi)
                     atomicAdd(&F[3 * eps[e / 3].atom + e % 3], 2.0 * P.dV * facc[e]);
-            }
             ++it;
         }
     }

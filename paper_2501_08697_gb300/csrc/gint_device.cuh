@@ -319,6 +319,90 @@ __device__ __forceinline__ void eval_phi_f32(const SpecSh &S, const float4 *__re
     }
 }
 
+// FP32 orbital values and gradients (with respect to r) of one species at displacement d;
+// emit(o, phi, gx, gy, gz).  Same conventions as eval_orbitals.
+template <typename Emit>
+__device__ __forceinline__ void eval_phigrad_f32(const SpecSh &S, const float4 *__restrict__ coef, float dx, float dy,
+                                                 float dz, Emit &&emit)
+{
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const int nrad = S.nrad;
+    if (!(r2 < S.rcut2)) {
+        int o = 0;
+        for (int ir = 0; ir < nrad; ++ir) {
+            const int nm = 2 * ((S.lpack >> (2 * ir)) & 3) + 1;
+            for (int m = 0; m < nm; ++m, ++o) emit(o, 0.f, 0.f, 0.f, 0.f);
+        }
+        return;
+    }
+    if (r2 < 1e-24f) {
+        int o = 0;
+        for (int ir = 0; ir < nrad; ++ir) {
+            const int l = (S.lpack >> (2 * ir)) & 3;
+            const float4 c = __ldg(coef + S.coef_off + ir);
+            if (l == 0) {
+                emit(o++, c.x * YC<float>::c0, 0.f, 0.f, 0.f);
+            } else if (l == 1) {
+                const float g = c.y * S.inv_dr * YC<float>::c1;
+                emit(o++, 0.f, 0.f, 0.f, g);
+                emit(o++, 0.f, g, 0.f, 0.f);
+                emit(o++, 0.f, 0.f, g, 0.f);
+            } else {
+                for (int m = 0; m < 5; ++m) emit(o++, 0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        return;
+    }
+    float ir1 = rsqrtf(r2);
+    ir1 = ir1 * (1.5f - 0.5f * r2 * ir1 * ir1);
+    const float r = r2 * ir1;
+    const float x = r * S.inv_dr;
+    int i = (int)x;
+    i = min(i, S.nint - 1);
+    const float t = x - (float)i;
+    const float ux = dx * ir1, uy = dy * ir1, uz = dz * ir1;
+    const float4 *cp = coef + S.coef_off + i * nrad;
+    int o = 0;
+    for (int ir = 0; ir < nrad; ++ir) {
+        const float4 c = __ldg(cp + ir);
+        const float f = c.x + t * (c.y + t * (c.z + t * c.w));
+        const float df = (c.y + t * (2.f * c.z + 3.f * t * c.w)) * S.inv_dr;
+        const int l = (S.lpack >> (2 * ir)) & 3;
+        if (l == 0) {
+            const float a = df * YC<float>::c0;
+            emit(o, f * YC<float>::c0, a * ux, a * uy, a * uz);
+            o += 1;
+        } else if (l == 1) {
+            // phi = g S, g = f/r, S = c1 (z, x, y); grad = g' u S + g grad S, g' = (f' - g)/r
+            const float g = f * ir1;
+            const float gp = (df - g) * ir1;
+            const float c1 = YC<float>::c1;
+            const float gc = g * c1;
+            const float Sz = c1 * dz, Sx = c1 * dx, Sy = c1 * dy;
+            emit(o, g * Sz, gp * ux * Sz, gp * uy * Sz, gp * uz * Sz + gc);
+            emit(o + 1, g * Sx, gp * ux * Sx + gc, gp * uy * Sx, gp * uz * Sx);
+            emit(o + 2, g * Sy, gp * ux * Sy, gp * uy * Sy + gc, gp * uz * Sy);
+            o += 3;
+        } else {
+            const float g = f * ir1 * ir1;
+            const float gp = (df - 2.f * f * ir1) * ir1 * ir1;
+            const float c20 = YC<float>::c20, c21 = YC<float>::c21, c22 = YC<float>::c22;
+            float Sv = c20 * (2.f * dz * dz - dx * dx - dy * dy);
+            emit(o, g * Sv, gp * ux * Sv - 2.f * g * c20 * dx, gp * uy * Sv - 2.f * g * c20 * dy,
+                 gp * uz * Sv + 4.f * g * c20 * dz);
+            Sv = c21 * dx * dz;
+            emit(o + 1, g * Sv, gp * ux * Sv + g * c21 * dz, gp * uy * Sv, gp * uz * Sv + g * c21 * dx);
+            Sv = c21 * dy * dz;
+            emit(o + 2, g * Sv, gp * ux * Sv, gp * uy * Sv + g * c21 * dz, gp * uz * Sv + g * c21 * dy);
+            Sv = c22 * (dx * dx - dy * dy);
+            emit(o + 3, g * Sv, gp * ux * Sv + 2.f * g * c22 * dx, gp * uy * Sv - 2.f * g * c22 * dy, gp * uz * Sv);
+            Sv = c21 * dx * dy;
+            emit(o + 4, g * Sv, gp * ux * Sv + g * c21 * dy, gp * uy * Sv + g * c21 * dx, gp * uz * Sv);
+            o += 5;
+        }
+    }
+}
+
 // ----------------------------------------------------------------------- status and waits
 __device__ __forceinline__ void report_timeout(const Plan &P) { atomicCAS(P.status, 0, (int)GINT_ETIMEOUT); }
 

@@ -555,7 +555,9 @@ struct RSmem {
     static constexpr int OFF_POFF = OFF_PSLOT + kMaxSlots * (int)sizeof(PSlot);
     static constexpr int OFF_TBL = OFF_POFF + kMaxBatchPts * 24;            // int [64*64]
     static constexpr int OFF_OMAP = OFF_TBL + kMaxSlots * kMaxSlots * 4;    // oslot[256], oidx[256]
-    static constexpr int OFF_EPSLOT = OFF_OMAP + 2 * kMaxNb;                // epilogue PSlot[64]
+    static constexpr int OFF_GBASE = OFF_OMAP + 2 * kMaxNb;                 // int [64][KC]: chunk gather bases
+    static constexpr int OFF_GNA = OFF_GBASE + kMaxSlots * KC * 4;          // int [KC]: norb of column's slot
+    static constexpr int OFF_EPSLOT = OFF_GNA + KC * 4;                     // epilogue PSlot[64]
     static constexpr int OFF_EPOFF = OFF_EPSLOT + kMaxSlots * (int)sizeof(PSlot);
     static constexpr int OFF_WIN = OFF_EPOFF + kMaxBatchPts * 24;           // float [8][kWin][32]
     static constexpr int OFF_RPART = OFF_WIN + 8 * kWin * 32 * 4;           // float [128]
@@ -579,6 +581,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     float *poff = reinterpret_cast<float *>(sm + L::OFF_POFF);
     int *tbl = reinterpret_cast<int *>(sm + L::OFF_TBL);
     unsigned char *oslot = sm + L::OFF_OMAP, *oidx = oslot + kMaxNb;
+    int *gbase = reinterpret_cast<int *>(sm + L::OFF_GBASE);
+    int *gna = reinterpret_cast<int *>(sm + L::OFF_GNA);
     PSlot *eps = reinterpret_cast<PSlot *>(sm + L::OFF_EPSLOT);
     float *epoff = reinterpret_cast<float *>(sm + L::OFF_EPOFF);
     float *win = reinterpret_cast<float *>(sm + L::OFF_WIN);
@@ -665,6 +669,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 }
                 for (int w = pt; w < (KC - (k1 - k0)) * kMaxBatchPts; w += kProd)
                     stg[(k1 - k0) * kMaxBatchPts + w] = 0.f;
+                // gather tables of the chunk: element (nu, k) of B is DM32[gbase[b][k] + o_nu * gna[k]]
+                // with b the slot of nu (gbase = -1: no block, or k past the last orbital)
+                for (int w = pt; w < ns * KC; w += kProd) {
+                    const int k = w % KC, b = w / KC;
+                    const int mu = k0 + k;
+                    int v = -1;
+                    if (mu < nb) {
+                        const int a = oslot[mu];
+                        const int e = tbl[b * ns + a];
+                        if (e >= 0) v = (e >> 1) + oidx[mu];
+                    }
+                    gbase[w] = v;
+                }
+                for (int k = pt; k < KC; k += kProd) gna[k] = (k0 + k < nb) ? ps[oslot[k0 + k]].norb : 0;
                 if (g >= 2) ok = role_wait(&empty[stage], ((g >> 1) - 1) & 1, P, pt, pflag, 1, kProd);
                 else named_sync(1, kProd);
                 if (!ok) break;
@@ -680,8 +698,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     for (int i = 0; i < S::CG; ++i) x[i] = stg[(kc * S::CG + i) * kMaxBatchPts + p];
                     split_store<S>(x, da);
                 }
-                // phase 2b: B = D rows nu (N), K = orbitals mu of the chunk: D(b_nu, a_mu)[o_nu][o_mu],
-                // FP32; GB tasks per thread with all their loads in flight before any store
+                // phase 2b: B = D rows nu (N), K = orbitals mu of the chunk: D(b_nu, a_mu)[o_nu][o_mu]
+                // read in FP32 through the chunk tables; GB tasks per thread, loads issued first
                 constexpr int GB = 4;
                 for (int w0 = pt; w0 < npad * S::KCM; w0 += kProd * GB) {
                     float x[GB][S::CG];
@@ -691,16 +709,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         const int kc = w % S::KCM, nu = w / S::KCM;
                         const bool rv = w < npad * S::KCM && nu < nb;
                         const int b = rv ? oslot[nu] : 0, ob = rv ? oidx[nu] : 0;
+                        const int *gb = gbase + b * KC + kc * S::CG;
+                        const int *gn = gna + kc * S::CG;
 #pragma unroll
                         for (int i = 0; i < S::CG; ++i) {
-                            const int mu = k0 + kc * S::CG + i;
-                            int idx = -1;
-                            if (rv && mu < nb) {
-                                const int a = oslot[mu];
-                                const int e = tbl[b * ns + a];
-                                if (e >= 0) idx = (e >> 1) + ob * ps[a].norb + oidx[mu];
-                            }
-                            x[gq][i] = idx >= 0 ? __ldg(DM + idx) : 0.f;
+                            const int bs = gb[i];
+                            x[gq][i] = (rv && bs >= 0) ? __ldg(DM + bs + ob * gn[i]) : 0.f;
                         }
                     }
 #pragma unroll
@@ -802,8 +816,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     float dx, dy, dz;
                     disp(sl, epoff + 6 * p, dx, dy, dz);
                     if (FORCE)
-                        eval_orbitals<float, true>(P, sl.species, dx, dy, dz,
-                                                   [&](int o, float v, float gx, float gy, float gz) {
+                        eval_phigrad_f32(spec[sl.species], P.coef32, dx, dy, dz,
+                                         [&](int o, float v, float gx, float gy, float gz) {
                                                        const float y = col[o * 32];
                                                        racc += v * y;
                                                        fx += gx * y; fy += gy * y; fz += gz * y;

@@ -172,6 +172,17 @@ gint_status gint_charge(gint_handle h, const double *rho_dev, double *out_dev, v
 gint_status gint_block_dot(gint_handle h, const double *A_dev, const double *B_dev,
                            double *out_dev, void *stream);
 
+/* out[0] (device double) <- Sum_i A[i] B[i] over the block store, like gint_block_dot, but
+ * without allocating anything: for callers that cannot allocate device memory at the call
+ * site (inside an allocator or memory-pool callback, or after a fixed memory budget has been
+ * reached).  The paper has no counterpart; this is a service of the library.  Partial sums
+ * live in a static device array of 1024 doubles that every GPU loading the library holds
+ * until exit; a store of more than 1024 * 65536 values is rejected with GINT_EINVAL.  The
+ * first call on a device looks up the array's address (make it before any stream capture).
+ * All calls share the array: calls that overlap on the GPU race.  A, B, out: device memory. */
+gint_status gint_block_dot_noalloc(gint_handle h, const double *A_dev, const double *B_dev,
+                                   double *out_dev, void *stream);
+
 /* End-to-end call from host buffers: copies V and DM (pinned or pageable host memory) to
  * library-owned device buffers, runs vlocal and rho_force, and copies H, rho and F back.
  * Synchronous: returns after the results are in host memory.  Outputs may be NULL. */

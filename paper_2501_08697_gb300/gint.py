@@ -21,7 +21,7 @@ PREC_NAME = {v: k for k, v in PREC.items()}
 
 EXPORTS = ["gint_setup", "gint_destroy", "gint_block_layout", "gint_get_info", "gint_update_positions",
            "gint_vlocal", "gint_rho", "gint_force", "gint_rho_force", "gint_charge", "gint_block_dot",
-           "gint_run_host", "gint_batched", "gint_get_status", "gint_last_error"]
+           "gint_block_dot_noalloc", "gint_run_host", "gint_batched", "gint_get_status", "gint_last_error"]
 
 
 class GintError(RuntimeError):
@@ -79,6 +79,7 @@ def load(build_if_missing: bool = True):
         lib.gint_rho_force.argtypes = [vp, vp, vp, vp, vp, i32, vp]
         lib.gint_charge.argtypes = [vp, vp, vp, vp]
         lib.gint_block_dot.argtypes = [vp, vp, vp, vp, vp]
+        lib.gint_block_dot_noalloc.argtypes = [vp, vp, vp, vp, vp]
         lib.gint_run_host.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp]
         lib.gint_batched.argtypes = [i32, P(vp), P(vp), P(vp), P(vp), P(vp), i32, vp]
         lib.gint_get_status.argtypes = [vp]
@@ -233,6 +234,11 @@ def gint_charge(h: Handle, rho, out, stream=None):
 
 def gint_block_dot(h: Handle, A, B, out, stream=None):
     _check(load().gint_block_dot(h.ptr, _ptr(A), _ptr(B), _ptr(out), _stream(stream)))
+
+
+def gint_block_dot_noalloc(h: Handle, A, B, out, stream=None):
+    """<A, B> over the block store without allocating (static device scratch)."""
+    _check(load().gint_block_dot_noalloc(h.ptr, _ptr(A), _ptr(B), _ptr(out), _stream(stream)))
 
 
 def _host_ptr(a, writable=False):

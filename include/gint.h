@@ -164,6 +164,15 @@ gint_status gint_force(gint_handle h, const double *V_dev, const double *DM_dev,
 gint_status gint_rho_force(gint_handle h, const double *V_dev, const double *DM_dev,
                            double *rho_dev, double *F_dev, gint_prec prec, void *stream);
 
+/* Backward of gint_vlocal for L = Sum_blocks Sum_mu,nu gH_mu,nu V_mu,nu(R) (gH: device, block
+ * layout, e.g. the incoming gradient of H):
+ *   gV (device, npts)       <- dL/dV(r)   = dV * rho(r) built from the block-symmetric part of gH
+ *   gtau (device, natoms*3) <- dL/dtau_I  = -F_I (the Pulay term of Eq. force_lcao with V fixed)
+ * i.e. the adjoint of vlocal (Eq. lcao_etot2) and its basis-motion derivative (Sec. IV.D).
+ * Either output may be NULL. */
+gint_status gint_vlocal_backward(gint_handle h, const double *V_dev, const double *gH_dev,
+                                 double *gV_dev, double *gtau_dev, gint_prec prec, void *stream);
+
 /* out[0] (device double) <- Sum_r rho(r) dV, summed in FP64 on the device. */
 gint_status gint_charge(gint_handle h, const double *rho_dev, double *out_dev, void *stream);
 

@@ -49,6 +49,12 @@ __global__ void k_dm_to_f32(Plan P, const double *__restrict__ DM, float *out, i
     }
 }
 
+__global__ void k_scale(double *x, int64_t n, double a)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] *= a;
+}
+
 constexpr int kRedBlocks = 1024;
 constexpr int kRedThreads = 256;
 
@@ -118,7 +124,7 @@ gint_status run_vlocal(gint_handle h, const double *V, double *H, gint_prec prec
     if (prec == GINT_FP64 || prec == GINT_FP32)
         e = launch_vlocal_simt(plan_for(h, 0), prec == GINT_FP64, V, H, s, h->nsm);
     else
-        e = launch_vlocal_tc(plan_for(h, 0), prec, V, H, s, h->nsm);
+        e = launch_vlocal_tc(plan_for(h, 0), prec, V, H, s, h->nsm, h->bs[0].max_nb);
     if (e != cudaSuccess) return cuda_fail(e, "gint_vlocal: launch");
     e = launch_mirror(h->plan, H, s);
     if (e != cudaSuccess) return cuda_fail(e, "gint_vlocal: mirror");
@@ -202,6 +208,25 @@ extern "C" gint_status gint_rho_force(gint_handle h, const double *V_dev, const 
         return GINT_EINVAL;
     }
     return run_rho_force(h, V_dev, DM_dev, rho_dev, F_dev, prec, (cudaStream_t)stream);
+}
+
+extern "C" gint_status gint_vlocal_backward(gint_handle h, const double *V_dev, const double *gH_dev, double *gV_dev,
+                                            double *gtau_dev, gint_prec prec, void *stream)
+{
+    gint_status st = check_handle(h, "gint_vlocal_backward");
+    if (st != GINT_OK) return st;
+    if (!gH_dev || (!gV_dev && !gtau_dev) || (gtau_dev && !V_dev) || !valid_prec(prec)) {
+        set_error("gint_vlocal_backward: null buffer or invalid precision");
+        return GINT_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = run_rho_force(h, V_dev, gH_dev, gV_dev, gtau_dev, prec, s)) != GINT_OK) return st;
+    // rho -> dV rho, F -> -F (dL/dtau)
+    if (gV_dev)
+        k_scale<<<(int)std::min<int64_t>(4096, (h->info.npts + 255) / 256), 256, 0, s>>>(gV_dev, h->info.npts, h->info.dV);
+    if (gtau_dev) k_scale<<<1, 256, 0, s>>>(gtau_dev, 3 * (int64_t)h->natoms, -1.0);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GINT_OK : cuda_fail(e, "gint_vlocal_backward: scale");
 }
 
 extern "C" gint_status gint_charge(gint_handle h, const double *rho_dev, double *out_dev, void *stream)

@@ -135,7 +135,8 @@ gint_status build_geometry(gint_handle h, const double *tau, bool update_only);
 cudaError_t launch_vlocal_simt(const Plan &p, bool fp64, const double *V, double *H, cudaStream_t s, int nsm);
 cudaError_t launch_rho_force_simt(const Plan &p, bool fp64, const double *V, const double *DM,
                                   double *rho, double *F, cudaStream_t s, int nsm);
-cudaError_t launch_vlocal_tc(const Plan &p, gint_prec prec, const double *V, double *H, cudaStream_t s, int nsm);
+cudaError_t launch_vlocal_tc(const Plan &p, gint_prec prec, const double *V, double *H, cudaStream_t s, int nsm,
+                             int max_nb);
 cudaError_t launch_rho_force_tc(const Plan &p, gint_prec prec, const double *V, const float *DM,
                                 double *rho, double *F, cudaStream_t s, int nsm);
 }  // namespace gint

@@ -243,6 +243,8 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                             if (can && (ax < 0 || dims[a] > dims[ax])) ax = a;
                         }
                         if (ax < 0) {
+                            // cannot split further: accept up to the hard kernel limits
+                            if (nb <= kMaxNb && (int)w.s.size() <= kMaxSlots) goto accept;
                             set_error("gint_setup: a grid batch sees %d orbitals / %d atom images (limits %d / %d)",
                                       nb, (int)w.s.size(), kMaxNb, kMaxSlots);
                             return GINT_EINVAL;
@@ -268,6 +270,7 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                         }
                         continue;
                     }
+                accept:
                     Batch B{};
                     B.i0 = w.i0; B.j0 = w.j0; B.k0 = w.k0;
                     B.dims = w.n1 | (w.n2 << 8) | (w.n3 << 16);

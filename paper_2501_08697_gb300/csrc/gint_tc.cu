@@ -115,6 +115,11 @@ struct TF32x3 {
     static constexpr uint32_t FMT = 2, PA = 0x100, PB = 0x010;
 };
 struct BF16x3 {
+    static constexpr int CG = 8, NT = 2, NPROD = 3, KCM = 2;
+    static constexpr bool F16 = true;
+    static constexpr uint32_t FMT = 1, PA = 0x100, PB = 0x010;
+};
+struct BF16x3W {  // BF16x3 with 32-element chunks (rho/force kernel, which has the shared memory)
     static constexpr int CG = 8, NT = 2, NPROD = 3, KCM = 4;
     static constexpr bool F16 = true;
     static constexpr uint32_t FMT = 1, PA = 0x100, PB = 0x010;
@@ -289,12 +294,14 @@ __device__ __forceinline__ void load_species(const Plan &P, SpecSh *spec, int ti
 }
 
 // ====================================================================== vlocal
-// TMEM accumulator buffer b (b = 0, 1) occupies columns [256 b, 256 b + 256): tile 0 (rows
-// 0..127, N = npad <= 192 columns) at +0 and tile 1 (rows 128.., N = npad - 128 <= 64) at +192.
+// With nbuf = 2 (every batch <= 192 orbitals) TMEM accumulator buffer b occupies columns
+// [256 b, 256 b + 256): tile 0 (rows 0..127, N = npad <= 192) at +0 and tile 1 (rows 128..,
+// N = npad - 128 <= 64) at +192.  With nbuf = 1 (some batch has up to 256 orbitals) one
+// accumulator holds tile 0 at columns [0, 256) and tile 1 at [256, 384).
 template <class S>
 struct VSmem {
     static constexpr int KC = S::KCM * S::CG;             // points per chunk
-    static constexpr int ROWS = 192;                      // orbitals per batch (vlocal limit)
+    static constexpr int ROWS = kMaxNb;                   // orbitals per batch
     static constexpr int ARR = arr_bytes<S>(256);         // one operand term (tile 1 reads rows 128..255)
     static constexpr int STAGE = 2 * S::NT * ARR;         // A terms then B terms
     static constexpr int NSTAGE = 2;
@@ -312,7 +319,7 @@ struct VSmem {
 };
 
 template <class S>
-__global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const double *__restrict__ V, double *H)
+__global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const double *__restrict__ V, double *H, int nbuf)
 {
     using L = VSmem<S>;
     constexpr int KC = L::KC;
@@ -353,6 +360,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
     tc_fence_after();
     const uint32_t tmem = *tmem_base;
     const float dVf = (float)P.dV;
+    const int tile1 = nbuf == 2 ? 192 : 256;   // TMEM column of tile 1 within an accumulator
     // a contiguous range of batches per CTA: CTAs running at the same time work on distant
     // parts of the cell, so their FP64 atomics rarely meet on the same block
     const int bbeg = (int)((int64_t)P.nbatches * blockIdx.x / gridDim.x);
@@ -370,7 +378,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
             unpack(B.dims, n1, n2, n3);
             const int ns = B.nslots, nb = B.nb, npb = n1 * n2 * n3;
             const int npad = (nb + 15) & ~15;
-            const int buf = it & 1;
+            const int buf = nbuf == 2 ? (it & 1) : 0;
             if (nb == 0) continue;  // no orbital reaches this batch: nothing to add
             named_sync(1, kProd);
             load_geom(P, B, ps, poff, pt, kProd);
@@ -424,8 +432,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
                 fence_async_smem();
                 named_sync(1, kProd);
                 if (pt == 0) {
-                    if (ch == 0 && it >= 2) {
-                        ok = !aborted(P) && mbar_wait(&accempty[buf], ((it >> 1) - 1) & 1, P.spin_limit);
+                    if (ch == 0 && it >= nbuf) {
+                        // the epilogue of batch it - nbuf has released this accumulator
+                        ok = !aborted(P) && mbar_wait(&accempty[buf], ((it / nbuf) - 1) & 1, P.spin_limit);
                         if (!ok) report_timeout(P);
                     }
                     if (ok) {
@@ -442,7 +451,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
                                     const uint64_t da = sdesc(a0 + term(S::PA, q) * L::ARR + rowoff + ks * 2 * kLBO, SBO);
                                     const uint64_t db = sdesc(b0 + term(S::PB, q) * L::ARR + rowoff + ks * 2 * kLBO, SBO);
                                     const uint32_t acc = (ch == 0 && ks == 0 && q == 0) ? 0u : 1u;
-                                    umma<S::F16>(tmem + buf * 256 + t * 192, da, db, id, acc);
+                                    umma<S::F16>(tmem + buf * 256 + t * tile1, da, db, id, acc);
                                 }
                             }
                         }
@@ -470,7 +479,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
             const Batch B = P.batches[bi];
             const int ns = B.nslots, nb = B.nb;
             const int npad = (nb + 15) & ~15;
-            const int buf = it & 1;
+            const int buf = nbuf == 2 ? (it & 1) : 0;
             if (nb == 0) continue;
             named_sync(2, kEpi);
             for (int e = et; e < ns * ns; e += kEpi) tbl[e] = P.tbl[B.tbl + e];
@@ -479,7 +488,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
                 const int no = sl.norb, off = sl.orb_off;
                 for (int o = 0; o < no; ++o) info[off + o] = s | (o << 8) | (no << 16);
             }
-            if (!role_wait(&accfull[buf], (it >> 1) & 1, P, et, eflag, 2, kEpi)) break;
+            if (!role_wait(&accfull[buf], (it / nbuf) & 1, P, et, eflag, 2, kEpi)) break;
             tc_fence_after();
             // Scatter of the upper triangle.  The atom images of a batch are ordered so that
             // every slot pair a <= b is the canonical member of its partner pair; element
@@ -495,7 +504,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
                 for (int c0 = t * 128 + hh * 32; c0 < npad; c0 += 64) {
                     if (nrows <= 0 || c0 + 32 <= row0) continue;   // wholly below the diagonal
                     float v[32];
-                    const uint32_t col = (uint32_t)(buf * 256 + t * 192 + c0 - t * 128);
+                    const uint32_t col = (uint32_t)(buf * 256 + t * tile1 + c0 - t * 128);
                     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + col;
                     tmem_ld16(taddr, v);
                     if (c0 + 16 < npad) tmem_ld16(taddr + 16, v + 16);
@@ -861,14 +870,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 }
 
 template <class S>
-cudaError_t vlocal_launch(const Plan &P, const double *V, double *H, cudaStream_t s, int nsm)
+cudaError_t vlocal_launch(const Plan &P, const double *V, double *H, cudaStream_t s, int nsm, int max_nb)
 {
     constexpr int smem = VSmem<S>::TOTAL;
     static_assert(smem <= 232448, "vlocal shared memory");
     cudaError_t e = cudaFuncSetAttribute(k_vlocal_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(nsm, P.nbatches);
-    k_vlocal_tc<S><<<grid, kThreadsTC, smem, s>>>(P, V, H);
+    k_vlocal_tc<S><<<grid, kThreadsTC, smem, s>>>(P, V, H, max_nb <= 192 ? 2 : 1);
     return cudaGetLastError();
 }
 
@@ -896,13 +905,14 @@ cudaError_t rho_launch(const Plan &P, const double *V, const float *DM, double *
 
 }  // namespace
 
-cudaError_t launch_vlocal_tc(const Plan &P, gint_prec prec, const double *V, double *H, cudaStream_t s, int nsm)
+cudaError_t launch_vlocal_tc(const Plan &P, gint_prec prec, const double *V, double *H, cudaStream_t s, int nsm,
+                             int max_nb)
 {
     if (P.nbatches == 0) return cudaSuccess;
     switch (prec) {
-    case GINT_TF32X3: return vlocal_launch<TF32x3>(P, V, H, s, nsm);
-    case GINT_BF16X3: return vlocal_launch<BF16x3>(P, V, H, s, nsm);
-    case GINT_BF16X6: return vlocal_launch<BF16x6>(P, V, H, s, nsm);
+    case GINT_TF32X3: return vlocal_launch<TF32x3>(P, V, H, s, nsm, max_nb);
+    case GINT_BF16X3: return vlocal_launch<BF16x3>(P, V, H, s, nsm, max_nb);
+    case GINT_BF16X6: return vlocal_launch<BF16x6>(P, V, H, s, nsm, max_nb);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -913,7 +923,7 @@ cudaError_t launch_rho_force_tc(const Plan &P, gint_prec prec, const double *V, 
     if (P.nbatches == 0) return cudaSuccess;
     switch (prec) {
     case GINT_TF32X3: return rho_launch<TF32x3>(P, V, DM, rho, F, s, nsm);
-    case GINT_BF16X3: return rho_launch<BF16x3>(P, V, DM, rho, F, s, nsm);
+    case GINT_BF16X3: return rho_launch<BF16x3W>(P, V, DM, rho, F, s, nsm);
     case GINT_BF16X6: return rho_launch<BF16x6>(P, V, DM, rho, F, s, nsm);
     default: return cudaErrorInvalidValue;
     }

@@ -1,0 +1,91 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark uses.
+
+Si64 (96^3) and the 64-molecule water box (128^3) are compared with the oracle on every
+block, every grid point and every atom.  Si512 (192^3) is too large for the oracle in full:
+H is compared on every block (I, J, R) whose first atom I is one of 4 seeded atoms (the oracle
+integrates all grid points within rc of any image of I, which makes those blocks complete),
+rho on 1e5 seeded grid points, and the force on the same 4 atoms.  Tolerances as in
+test_gpu_parity: FP64 1e-11, TF32x3 / BF16x6 1e-6 (relative Frobenius)."""
+import numpy as np
+import pytest
+
+from tests._cases import inputs, oracle_full, rel_fro
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-11, "tf32x3": 1e-6, "bf16x6": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2501_08697_gb300 import gint
+    return gint
+
+
+def _gpu_outputs(G, st, V, DM, prec, h=None):
+    dev = torch.device("cuda")
+    h = h or G.setup_structure(st)
+    H = torch.empty(h.info["nvalues"], dtype=torch.float64, device=dev)
+    rho = torch.empty(h.info["npts"], dtype=torch.float64, device=dev)
+    F = torch.empty(3 * st.natoms, dtype=torch.float64, device=dev)
+    Vd = torch.from_numpy(V.reshape(-1)).to(dev)
+    G.gint_vlocal(h, Vd, H, prec)
+    G.gint_rho_force(h, Vd, torch.from_numpy(DM).to(dev), rho, F, prec)
+    torch.cuda.synchronize()
+    assert G.gint_get_status(h) == 0
+    return h, H.cpu().numpy(), rho.cpu().numpy(), F.cpu().numpy().reshape(-1, 3)
+
+
+@pytest.mark.parametrize("name", ["si64", "water64"])
+def test_full_parity(G, name):
+    ref = oracle_full(name)
+    h = G.setup_structure(ref["st"])
+    keys, offs = h.layout()
+    assert np.array_equal(keys, ref["keys"]) and np.array_equal(offs, ref["offs"])
+    for prec in ("fp64", "tf32x3", "bf16x6"):
+        _, H, rho, F = _gpu_outputs(G, ref["st"], ref["V"], ref["DM"], prec, h)
+        eH, er, eF = rel_fro(H, ref["H"]), rel_fro(rho, ref["rho"]), rel_fro(F, ref["F"])
+        print(f"{name} {prec}: H {eH:.2e} rho {er:.2e} F {eF:.2e}")
+        assert eH <= TOL[prec] and er <= TOL[prec] and eF <= 2 * TOL[prec]
+
+
+@pytest.fixture(scope="module")
+def si512_sample():
+    from oracle import Oracle
+    from paper_2501_08697_gb300 import synth as S
+    st, V = inputs("si512")
+    o = Oracle.from_structure(st)
+    keys, offs = o.pairs()
+    DM = S.density_matrix(keys, st.norb_atom, seed=st.seed)
+    rng = np.random.default_rng(2501)
+    atoms = np.sort(rng.choice(st.natoms, 4, replace=False))
+    pts = np.unique(np.concatenate([o.points_near_atom(int(a)) for a in atoms]))
+    H_ref = o.vlocal(V, pts)
+    F_ref = o.force(V, DM, pts)[atoms]
+    rpts = np.sort(rng.choice(st.npts, 100000, replace=False))
+    rho_ref = o.rho(DM, rpts)
+    sel = np.isin(keys[:, 0], atoms)
+    idx = np.concatenate([np.arange(offs[b], offs[b + 1]) for b in np.nonzero(sel)[0]])
+    return dict(st=st, V=V, DM=DM, keys=keys, offs=offs, atoms=atoms, idx=idx, H=H_ref[idx], F=F_ref,
+                rpts=rpts, rho=rho_ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "bf16x6"])
+def test_si512_sampled_parity(G, si512_sample, prec):
+    r = si512_sample
+    h, H, rho, F = _gpu_outputs(G, r["st"], r["V"], r["DM"], prec)
+    keys, offs = h.layout()
+    assert np.array_equal(keys, r["keys"]) and np.array_equal(offs, r["offs"])
+    eH = rel_fro(H[r["idx"]], r["H"])
+    er = rel_fro(rho[r["rpts"]], r["rho"])
+    eF = rel_fro(F[r["atoms"]], r["F"])
+    print(f"si512 {prec}: H({len(r['idx'])} values) {eH:.2e} rho(1e5 pts) {er:.2e} F(4 atoms) {eF:.2e}")
+    assert eH <= TOL[prec] and er <= TOL[prec] and eF <= 2 * TOL[prec]
+    # properties at full size: the adjoint identity and the charge identity in FP64
+    dV = h.info["dV"]
+    tr = float((r["DM"] * H).sum())
+    assert float((rho * r["V"].reshape(-1)).sum()) * dV == pytest.approx(tr, rel=10 * TOL[prec])
+    h.close()

@@ -98,7 +98,10 @@ typedef struct {
     int batch_rho[3];      /* grid points per rho/force batch (default 4, 4, 8), same limits.
                               Batches whose orbital count (256) or atom-image count (64)
                               exceeds the kernel limits are split. */
-    int reserved[2];
+    int wait_budget;       /* clock cycles a tensor-core kernel waits on one pipeline barrier
+                              before it gives up with GINT_ETIMEOUT; 0 = default (4e9, about
+                              2 s).  The final wait for in-flight MMAs always uses the default. */
+    int reserved;
 } gint_options;
 
 /* Sizes of a handle (host values). */
@@ -199,9 +202,37 @@ gint_status gint_run_host(gint_handle h, const double *V_host, const double *DM_
                           double *H_host, double *rho_host, double *F_host, gint_prec prec,
                           void *stream);
 
-/* Many structures in one persistent launch: for each s, H[s] <- vlocal(V[s]) and, if DM and
- * rho are non-NULL, rho[s] <- rho(DM[s]).  All handles must be on the current device.
- * Pointer arrays are host memory; the buffers they point to are device memory. */
+/* A reusable multi-structure job (Sec. IV.B grid integrals of many independent structures):
+ * every structure's grid batches are concatenated into one work list, run by one persistent
+ * launch of the tensor-core vlocal kernel (two when some structures have batches of more than
+ * 192 orbitals, which need the single-accumulator layout) and one of the rho kernel; the sequence
+ * (H zeroing, density-matrix conversion, the two persistent launches, block mirroring) is
+ * captured once into a CUDA graph that gint_batch_launch replays.  prec must be a tensor-core
+ * precision (GINT_TF32X3, GINT_BF16X3, GINT_BF16X6); at most 255 structures, all on the current
+ * device, at most 8 distinct species in total.  Pointer arrays are host memory, read during
+ * create; the buffers they point to are device memory and are bound to the job.  DM and rho
+ * may be NULL (vlocal only).  The handles must outlive the job. */
+typedef struct gint_batch_s *gint_batch;
+gint_status gint_batch_create(gint_batch *out, int nstruct, const gint_handle *hs,
+                              const double *const *V, double *const *H, const double *const *DM,
+                              double *const *rho, gint_prec prec);
+/* Replay the job's graph on `stream` (asynchronous). */
+gint_status gint_batch_launch(gint_batch b, void *stream);
+gint_status gint_batch_destroy(gint_batch b);
+
+/* Choose batch shapes for one structure by timing candidates on the current device: vlocal
+ * shapes of at most 64 points (the tensor-core accumulation error grows with the points per
+ * batch) and rho shapes of 128 points (one M = 128 tile).  Inputs as for gint_setup; writes
+ * the fastest shapes into *best (and their times in ms, if the pointers are non-NULL).
+ * Allocates and frees its own device buffers. */
+gint_status gint_autotune(const double cell[9], int natoms, const int *species, const double *tau,
+                          int nspecies, const gint_species *sp, const int grid[3], gint_prec prec,
+                          gint_options *best, double *ms_vlocal, double *ms_rho);
+
+/* One-shot form of the multi-structure job: for each s, H[s] <- vlocal(V[s]) and, if DM and
+ * rho are non-NULL, rho[s] <- rho(DM[s]).  With a tensor-core precision this is
+ * gint_batch_create + gint_batch_launch + a stream synchronisation + gint_batch_destroy (so it
+ * blocks); with GINT_FP64 / GINT_FP32 the structures run one after another on the CUDA cores. */
 gint_status gint_batched(int nstruct, const gint_handle *hs, const double *const *V,
                          double *const *H, const double *const *DM, double *const *rho,
                          gint_prec prec, void *stream);

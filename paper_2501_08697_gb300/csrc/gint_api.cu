@@ -10,6 +10,21 @@ using namespace gint;
 
 namespace gint {
 cudaError_t launch_mirror(const Plan &P, double *H, cudaStream_t s);
+cudaError_t launch_dm_to_f32(const Plan &P, const double *DM, float *out, bool sym, cudaStream_t s);
+
+SInfo sinfo_for(const gint_handle_s *h, const double *V, double *H, const float *DM32, double *rho, double *F)
+{
+    SInfo si{};
+    si.V = V;
+    si.H = H;
+    si.DM32 = DM32;
+    si.rho = rho;
+    si.F = F;
+    si.poff = h->d_poff;
+    for (int i = 0; i < 3; ++i) si.grid[i] = h->grid[i];
+    si.dV = h->info.dV;
+    return si;
+}
 }
 
 namespace {
@@ -124,7 +139,8 @@ gint_status run_vlocal(gint_handle h, const double *V, double *H, gint_prec prec
     if (prec == GINT_FP64 || prec == GINT_FP32)
         e = launch_vlocal_simt(plan_for(h, 0), prec == GINT_FP64, V, H, s, h->nsm);
     else
-        e = launch_vlocal_tc(plan_for(h, 0), prec, V, H, s, h->nsm, h->bs[0].max_nb);
+        e = launch_vlocal_tc(plan_for(h, 0), prec, sinfo_for(h, V, H, nullptr, nullptr, nullptr), nullptr, s, h->nsm,
+                             h->bs[0].max_nb);
     if (e != cudaSuccess) return cuda_fail(e, "gint_vlocal: launch");
     e = launch_mirror(h->plan, H, s);
     if (e != cudaSuccess) return cuda_fail(e, "gint_vlocal: mirror");
@@ -150,12 +166,10 @@ gint_status run_rho_force(gint_handle h, const double *V, const double *DM, doub
         e = launch_rho_force_simt(plan_for(h, 1), prec == GINT_FP64, V, D, rho, F, s, h->nsm);
     } else {
         // tensor-core kernels gather the density matrix in FP32 (split again on chip)
-        if (h->info.nvalues > 0) {
-            const int grid = (int)std::min<int64_t>(F ? h->info.nblocks : (h->info.nvalues + 255) / 256, 8192);
-            k_dm_to_f32<<<grid, F ? 128 : 256, 0, s>>>(h->plan, DM, h->d_dm32, F ? 1 : 0);
-            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gint_rho: convert");
-        }
-        e = launch_rho_force_tc(plan_for(h, 1), prec, V, h->d_dm32, rho, F, s, h->nsm);
+        if (h->info.nvalues > 0 && (e = launch_dm_to_f32(h->plan, DM, h->d_dm32, F != nullptr, s)) != cudaSuccess)
+            return cuda_fail(e, "gint_rho: convert");
+        e = launch_rho_force_tc(plan_for(h, 1), prec, sinfo_for(h, V, nullptr, h->d_dm32, rho, F), nullptr, rho != nullptr,
+                                F != nullptr, s, h->nsm);
     }
     if (e != cudaSuccess) return cuda_fail(e, "gint_rho_force: launch");
     h->last_stream = s;
@@ -303,29 +317,13 @@ extern "C" gint_status gint_get_status(gint_handle h)
     return GINT_OK;
 }
 
-extern "C" gint_status gint_batched(int nstruct, const gint_handle *hs, const double *const *V, double *const *H,
-                                   const double *const *DM, double *const *rho, gint_prec prec, void *stream)
+
+namespace gint {
+cudaError_t launch_dm_to_f32(const Plan &P, const double *DM, float *out, bool sym, cudaStream_t s)
 {
-    if (nstruct < 0 || (nstruct > 0 && (!hs || !V || !H)) || !valid_prec(prec)) {
-        set_error("gint_batched: invalid arguments");
-        return GINT_EINVAL;
-    }
-    cudaStream_t s = (cudaStream_t)stream;
-    for (int i = 0; i < nstruct; ++i) {
-        gint_status st = check_handle(hs[i], "gint_batched");
-        if (st != GINT_OK) return st;
-        if (!V[i] || !H[i] || (DM && rho && (!DM[i] || !rho[i]))) {
-            set_error("gint_batched: null buffer for structure %d", i);
-            return GINT_EINVAL;
-        }
-    }
-    for (int i = 0; i < nstruct; ++i) {
-        gint_status st = run_vlocal(hs[i], V[i], H[i], prec, s);
-        if (st != GINT_OK) return st;
-        if (DM && rho) {
-            st = run_rho_force(hs[i], nullptr, DM[i], rho[i], nullptr, prec, s);
-            if (st != GINT_OK) return st;
-        }
-    }
-    return GINT_OK;
+    const int grid = (int)std::min<int64_t>(sym ? P.nblocks : (P.nvalues + 255) / 256, 8192);
+    if (grid < 1) return cudaSuccess;
+    k_dm_to_f32<<<grid, sym ? 128 : 256, 0, s>>>(P, DM, out, sym ? 1 : 0);
+    return cudaGetLastError();
 }
+}  // namespace gint

@@ -32,7 +32,7 @@ struct DevSpecies {
 // the batch), its atom images slot0 .. slot0+nslots-1 and orbital count nb.
 struct Batch {
     int i0, j0, k0;
-    int dims;                      // n1 | n2 << 8 | n3 << 16
+    int dims;                      // n1 | n2 << 8 | n3 << 16 | structure id << 24
     int slot0, nslots, nb;
     int tbl;                       // first entry of this batch's nslots x nslots pair table
 };
@@ -46,6 +46,22 @@ struct Slot {
 };
 
 constexpr int kPoffDim = 16;       // point-offset table covers local indices 0..15 per axis
+constexpr long long kDrainBudget = 4000000000LL;  // final wait for in-flight MMAs (clock cycles)
+
+// Per-structure data of the tensor-core kernels: the buffers of one call and the grid.  A
+// single-structure launch passes one by value; a batched launch reads them from device memory
+// by the structure id of each batch.
+struct SInfo {
+    const double *V;
+    double *H;
+    const float *DM32;
+    double *rho;
+    double *F;
+    const float *poff;
+    int grid[3];
+    int pad;
+    double dV;
+};
 
 // Everything a kernel needs, passed by value.
 struct Plan {
@@ -67,7 +83,7 @@ struct Plan {
     const int *blk_rows;           // [nblocks] rows of each block
     int64_t nblocks, nvalues;
     int *status;                   // device status word
-    long long spin_limit;          // clock64 cycles a kernel may wait on one barrier
+    long long spin_limit;          // clock64 cycles a kernel may wait on one pipeline barrier
 };
 
 // One decomposition of the grid into batches, with its atom-image lists and pair tables.
@@ -100,6 +116,7 @@ struct gint_handle_s {
     std::vector<int64_t> offsets;    // nblocks + 1
     std::vector<int> partner;
     gint::BatchSet bs[2];            // [0] vlocal batches, [1] rho/force batches
+    std::vector<float4> coef32_host; // spline records, as uploaded
     gint_options opt{};
     gint_info_t info{};
     // device memory (owned)
@@ -135,8 +152,10 @@ gint_status build_geometry(gint_handle h, const double *tau, bool update_only);
 cudaError_t launch_vlocal_simt(const Plan &p, bool fp64, const double *V, double *H, cudaStream_t s, int nsm);
 cudaError_t launch_rho_force_simt(const Plan &p, bool fp64, const double *V, const double *DM,
                                   double *rho, double *F, cudaStream_t s, int nsm);
-cudaError_t launch_vlocal_tc(const Plan &p, gint_prec prec, const double *V, double *H, cudaStream_t s, int nsm,
-                             int max_nb);
-cudaError_t launch_rho_force_tc(const Plan &p, gint_prec prec, const double *V, const float *DM,
-                                double *rho, double *F, cudaStream_t s, int nsm);
+cudaError_t launch_vlocal_tc(const Plan &p, gint_prec prec, const SInfo &si0, const SInfo *sis, cudaStream_t s,
+                             int nsm, int max_nb);
+cudaError_t launch_rho_force_tc(const Plan &p, gint_prec prec, const SInfo &si0, const SInfo *sis, bool rho,
+                                bool force, cudaStream_t s, int nsm);
+// the single-structure SInfo of a handle for one call
+SInfo sinfo_for(const gint_handle_s *h, const double *V, double *H, const float *DM32, double *rho, double *F);
 }  // namespace gint

@@ -579,6 +579,11 @@ extern "C" gint_status gint_setup(gint_handle *out, const double cell[9], int na
             if (opt->batch[i] > 0) o.batch[i] = opt->batch[i];
             if (opt->batch_rho[i] > 0) o.batch_rho[i] = opt->batch_rho[i];
         }
+        if (opt->wait_budget < 0) {
+            set_error("gint_setup: negative wait_budget");
+            return GINT_EINVAL;
+        }
+        o.wait_budget = opt->wait_budget;
     }
     for (const int *b : {o.batch, o.batch_rho})
         if (b[0] > kMaxBatchDim || b[1] > kMaxBatchDim || b[2] > kMaxBatchDim || b[0] * b[1] * b[2] > kMaxBatchPts ||
@@ -613,7 +618,7 @@ extern "C" gint_status gint_setup(gint_handle *out, const double cell[9], int na
     P.nspecies = nspecies;
     for (int i = 0; i < 3; ++i) P.grid[i] = grid[i];
     P.npts = (int64_t)grid[0] * grid[1] * grid[2];
-    P.spin_limit = 4000000000LL;   // about 2 s at 2 GHz
+    P.spin_limit = o.wait_budget > 0 ? (long long)o.wait_budget : 4000000000LL;   // default about 2 s at 2 GHz
 
     // species and splines
     std::vector<double> coef64;
@@ -690,6 +695,7 @@ extern "C" gint_status gint_setup(gint_handle *out, const double cell[9], int na
     }
     P.coef64 = (const double *)h->d_coef64;
     P.coef32 = (const float4 *)h->d_coef32;
+    h->coef32_host = coef32;
     if ((st = upload_geometry(h)) != GINT_OK) {
         free_dev(h);
         delete h;

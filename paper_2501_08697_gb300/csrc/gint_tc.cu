@@ -209,8 +209,14 @@ __device__ __forceinline__ void unpack(int dims, int &n1, int &n2, int &n3)
     n3 = (dims >> 16) & 255;
 }
 
+__device__ __forceinline__ SInfo sinfo_of(const Batch &B, const SInfo &si0, const SInfo *sis)
+{
+    return sis ? sis[(unsigned)B.dims >> 24] : si0;
+}
+
 // slots and point offsets of batch B into shared memory (called by the threads of one role)
-__device__ __forceinline__ void load_geom(const Plan &P, const Batch &B, PSlot *ps, float *poff, int tid, int nthr)
+__device__ __forceinline__ void load_geom(const Plan &P, const SInfo &SI, const Batch &B, PSlot *ps, float *poff,
+                                          int tid, int nthr)
 {
     for (int s = tid; s < B.nslots; s += nthr) {
         const Slot &S = P.slots[B.slot0 + s];
@@ -230,7 +236,7 @@ __device__ __forceinline__ void load_geom(const Plan &P, const Batch &B, PSlot *
     const int np = n1 * n2 * n3;
     for (int p = tid; p < np; p += nthr) {
         const int c = p % n3, b = (p / n3) % n2, a = p / (n3 * n2);
-        const float *t = P.poff + ((a * kPoffDim + b) * kPoffDim + c) * 6;
+        const float *t = SI.poff + ((a * kPoffDim + b) * kPoffDim + c) * 6;
 #pragma unroll
         for (int q = 0; q < 6; ++q) poff[6 * p + q] = __ldg(t + q);
     }
@@ -255,10 +261,10 @@ __device__ __forceinline__ void disp(const PSlot &s, const float *po, float &dx,
     dz = (s.dh[2] + po[2]) + (s.dl[2] + po[5]);
 }
 
-__device__ __forceinline__ int64_t grid_index(const Plan &P, const Batch &B, int p, int n2, int n3)
+__device__ __forceinline__ int64_t grid_index(const SInfo &SI, const Batch &B, int p, int n2, int n3)
 {
     const int c = p % n3, b = (p / n3) % n2, a = p / (n3 * n2);
-    return ((int64_t)(B.i0 + a) * P.grid[1] + (B.j0 + b)) * P.grid[2] + (B.k0 + c);
+    return ((int64_t)(B.i0 + a) * SI.grid[1] + (B.j0 + b)) * SI.grid[2] + (B.k0 + c);
 }
 
 // role-uniform bounded wait: thread `leader` waits, the verdict is shared through `flag`
@@ -319,7 +325,8 @@ struct VSmem {
 };
 
 template <class S>
-__global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const double *__restrict__ V, double *H, int nbuf)
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_vlocal_tc(Plan P, SInfo si0, const SInfo *__restrict__ sis, int nbuf)
 {
     using L = VSmem<S>;
     constexpr int KC = L::KC;
@@ -359,7 +366,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_base;
-    const float dVf = (float)P.dV;
     const int tile1 = nbuf == 2 ? 192 : 256;   // TMEM column of tile 1 within an accumulator
     // a contiguous range of batches per CTA: CTAs running at the same time work on distant
     // parts of the cell, so their FP64 atomics rarely meet on the same block
@@ -380,10 +386,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
             const int npad = (nb + 15) & ~15;
             const int buf = nbuf == 2 ? (it & 1) : 0;
             if (nb == 0) continue;  // no orbital reaches this batch: nothing to add
+            const SInfo SI = sinfo_of(B, si0, sis);
+            const float dVf = (float)SI.dV;
             named_sync(1, kProd);
-            load_geom(P, B, ps, poff, pt, kProd);
+            load_geom(P, SI, B, ps, poff, pt, kProd);
             for (int p = pt; p < kMaxBatchPts; p += kProd)
-                vs[p] = p < npb ? d2f(V[grid_index(P, B, p, n2, n3)]) * dVf : 0.f;
+                vs[p] = p < npb ? d2f(SI.V[grid_index(SI, B, p, n2, n3)]) * dVf : 0.f;
             named_sync(1, kProd);
             const int nch = (npb + KC - 1) / KC;
             for (int ch = 0; ch < nch && ok; ++ch, ++g) {
@@ -468,7 +476,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
         if (pt == 0) {
             // wait (bounded) for every MMA this thread issued before TMEM is released
             umma_commit(fin);
-            if (!mbar_wait(fin, 0, P.spin_limit)) report_timeout(P);
+            if (!mbar_wait(fin, 0, kDrainBudget)) report_timeout(P);
         }
     } else {
         // ------------------------------------------------------------ epilogue
@@ -481,6 +489,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_vlocal_tc(Plan P, const doubl
             const int npad = (nb + 15) & ~15;
             const int buf = nbuf == 2 ? (it & 1) : 0;
             if (nb == 0) continue;
+            double *H = sinfo_of(B, si0, sis).H;
             named_sync(2, kEpi);
             for (int e = et; e < ns * ns; e += kEpi) tbl[e] = P.tbl[B.tbl + e];
             for (int s = et; s < ns; s += kEpi) {
@@ -579,7 +588,7 @@ struct RSmem {
 
 template <class S, bool RHO, bool FORCE>
 __global__ void __launch_bounds__(kThreadsTC, 1)
-    k_rho_tc(Plan P, const double *__restrict__ V, const float *__restrict__ DM, double *rho, double *F)
+    k_rho_tc(Plan P, SInfo si0, const SInfo *__restrict__ sis)
 {
     using L = RSmem<S>;
     constexpr int KC = L::KC;
@@ -640,8 +649,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             const int npad = (nb + 15) & ~15;
             const int buf = it & 1;
             if (nb == 0) continue;  // the epilogue writes rho = 0 there
+            const SInfo SI = sinfo_of(B, si0, sis);
+            const float *__restrict__ DM = SI.DM32;
             named_sync(1, kProd);
-            load_geom(P, B, ps, poff, pt, kProd);
+            load_geom(P, SI, B, ps, poff, pt, kProd);
             for (int e = pt; e < ns * ns; e += kProd) tbl[e] = P.tbl[B.tbl + e];
             named_sync(1, kProd);
             for (int s = pt; s < ns; s += kProd)
@@ -771,7 +782,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         }
         if (pt == 0) {
             umma_commit(fin);
-            if (!mbar_wait(fin, 0, P.spin_limit)) report_timeout(P);
+            if (!mbar_wait(fin, 0, kDrainBudget)) report_timeout(P);
         }
     } else {
         // ------------------------------------------------------------ epilogue: rho and force
@@ -787,12 +798,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             unpack(B.dims, n1, n2, n3);
             const int ns = B.nslots, npb = n1 * n2 * n3;
             const int buf = it & 1;
+            const SInfo SI = sinfo_of(B, si0, sis);
             if (B.nb == 0) {
-                if (RHO && hh == 0 && p < npb) rho[grid_index(P, B, p, n2, n3)] = 0.0;
+                if (RHO && hh == 0 && p < npb) SI.rho[grid_index(SI, B, p, n2, n3)] = 0.0;
                 continue;
             }
             named_sync(2, kEpi);
-            load_geom(P, B, eps, epoff, et, kEpi);
+            load_geom(P, SI, B, eps, epoff, et, kEpi);
             if (FORCE)
                 for (int e = et; e < 3 * ns; e += kEpi) facc[e] = 0.0;
             if (!role_wait(&accfull[buf], (it >> 1) & 1, P, et, eflag, 2, kEpi)) break;
@@ -802,8 +814,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             float vp = 0.f;
             int64_t gi = 0;
             if (pv) {
-                gi = grid_index(P, B, p, n2, n3);
-                if (FORCE) vp = d2f(V[gi]);
+                gi = grid_index(SI, B, p, n2, n3);
+                if (FORCE) vp = d2f(SI.V[gi]);
             }
             float racc = 0.f;
             int w0 = -1000, wn = 0;
@@ -854,10 +866,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             mbar_arrive(&accempty[buf]);
             if (RHO && hh == 1) rpart[p] = racc;
             named_sync(2, kEpi);
-            if (RHO && hh == 0 && pv) rho[gi] = f2d(racc + rpart[p]);
+            if (RHO && hh == 0 && pv) SI.rho[gi] = f2d(racc + rpart[p]);
             if (FORCE)
                 for (int e = et; e < 3 * ns; e += kEpi)
-                    atomicAdd(&F[3 * eps[e / 3].atom + e % 3], 2.0 * P.dV * facc[e]);
+                    atomicAdd(&SI.F[3 * eps[e / 3].atom + e % 3], 2.0 * SI.dV * facc[e]);
             ++it;
         }
     }
@@ -870,61 +882,60 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 }
 
 template <class S>
-cudaError_t vlocal_launch(const Plan &P, const double *V, double *H, cudaStream_t s, int nsm, int max_nb)
+cudaError_t vlocal_launch(const Plan &P, const SInfo &si0, const SInfo *sis, cudaStream_t s, int nsm, int max_nb)
 {
     constexpr int smem = VSmem<S>::TOTAL;
     static_assert(smem <= 232448, "vlocal shared memory");
     cudaError_t e = cudaFuncSetAttribute(k_vlocal_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(nsm, P.nbatches);
-    k_vlocal_tc<S><<<grid, kThreadsTC, smem, s>>>(P, V, H, max_nb <= 192 ? 2 : 1);
+    k_vlocal_tc<S><<<grid, kThreadsTC, smem, s>>>(P, si0, sis, max_nb <= 192 ? 2 : 1);
     return cudaGetLastError();
 }
 
 template <class S, bool R, bool Fo>
-cudaError_t rho_launch3(const Plan &P, const double *V, const float *DM, double *rho, double *F, cudaStream_t s,
-                        int nsm)
+cudaError_t rho_launch3(const Plan &P, const SInfo &si0, const SInfo *sis, cudaStream_t s, int nsm)
 {
     constexpr int smem = RSmem<S>::TOTAL;
     static_assert(smem <= 232448, "rho shared memory");
     cudaError_t e = cudaFuncSetAttribute(k_rho_tc<S, R, Fo>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::min(nsm, P.nbatches);
-    k_rho_tc<S, R, Fo><<<grid, kThreadsTC, smem, s>>>(P, V, DM, rho, F);
+    k_rho_tc<S, R, Fo><<<grid, kThreadsTC, smem, s>>>(P, si0, sis);
     return cudaGetLastError();
 }
 
 template <class S>
-cudaError_t rho_launch(const Plan &P, const double *V, const float *DM, double *rho, double *F, cudaStream_t s,
+cudaError_t rho_launch(const Plan &P, const SInfo &si0, const SInfo *sis, bool rho, bool force, cudaStream_t s,
                        int nsm)
 {
-    if (rho && F) return rho_launch3<S, true, true>(P, V, DM, rho, F, s, nsm);
-    if (rho) return rho_launch3<S, true, false>(P, V, DM, rho, F, s, nsm);
-    return rho_launch3<S, false, true>(P, V, DM, rho, F, s, nsm);
+    if (rho && force) return rho_launch3<S, true, true>(P, si0, sis, s, nsm);
+    if (rho) return rho_launch3<S, true, false>(P, si0, sis, s, nsm);
+    return rho_launch3<S, false, true>(P, si0, sis, s, nsm);
 }
 
 }  // namespace
 
-cudaError_t launch_vlocal_tc(const Plan &P, gint_prec prec, const double *V, double *H, cudaStream_t s, int nsm,
-                             int max_nb)
+cudaError_t launch_vlocal_tc(const Plan &P, gint_prec prec, const SInfo &si0, const SInfo *sis, cudaStream_t s,
+                             int nsm, int max_nb)
 {
     if (P.nbatches == 0) return cudaSuccess;
     switch (prec) {
-    case GINT_TF32X3: return vlocal_launch<TF32x3>(P, V, H, s, nsm, max_nb);
-    case GINT_BF16X3: return vlocal_launch<BF16x3>(P, V, H, s, nsm, max_nb);
-    case GINT_BF16X6: return vlocal_launch<BF16x6>(P, V, H, s, nsm, max_nb);
+    case GINT_TF32X3: return vlocal_launch<TF32x3>(P, si0, sis, s, nsm, max_nb);
+    case GINT_BF16X3: return vlocal_launch<BF16x3>(P, si0, sis, s, nsm, max_nb);
+    case GINT_BF16X6: return vlocal_launch<BF16x6>(P, si0, sis, s, nsm, max_nb);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_rho_force_tc(const Plan &P, gint_prec prec, const double *V, const float *DM, double *rho,
-                                double *F, cudaStream_t s, int nsm)
+cudaError_t launch_rho_force_tc(const Plan &P, gint_prec prec, const SInfo &si0, const SInfo *sis, bool rho,
+                                bool force, cudaStream_t s, int nsm)
 {
     if (P.nbatches == 0) return cudaSuccess;
     switch (prec) {
-    case GINT_TF32X3: return rho_launch<TF32x3>(P, V, DM, rho, F, s, nsm);
-    case GINT_BF16X3: return rho_launch<BF16x3W>(P, V, DM, rho, F, s, nsm);
-    case GINT_BF16X6: return rho_launch<BF16x6>(P, V, DM, rho, F, s, nsm);
+    case GINT_TF32X3: return rho_launch<TF32x3>(P, si0, sis, rho, force, s, nsm);
+    case GINT_BF16X3: return rho_launch<BF16x3W>(P, si0, sis, rho, force, s, nsm);
+    case GINT_BF16X6: return rho_launch<BF16x6>(P, si0, sis, rho, force, s, nsm);
     default: return cudaErrorInvalidValue;
     }
 }

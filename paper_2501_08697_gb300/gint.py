@@ -22,7 +22,8 @@ PREC_NAME = {v: k for k, v in PREC.items()}
 EXPORTS = ["gint_setup", "gint_destroy", "gint_block_layout", "gint_get_info", "gint_update_positions",
            "gint_vlocal", "gint_rho", "gint_force", "gint_rho_force", "gint_vlocal_backward", "gint_charge",
            "gint_block_dot",
-           "gint_block_dot_noalloc", "gint_run_host", "gint_batched", "gint_get_status", "gint_last_error"]
+           "gint_block_dot_noalloc", "gint_run_host", "gint_batch_create", "gint_batch_launch", "gint_batch_destroy",
+           "gint_autotune", "gint_batched", "gint_get_status", "gint_last_error"]
 
 
 class GintError(RuntimeError):
@@ -37,7 +38,7 @@ class _Species(C.Structure):
 
 
 class _Options(C.Structure):
-    _fields_ = [("batch", C.c_int * 3), ("batch_rho", C.c_int * 3), ("reserved", C.c_int * 2)]
+    _fields_ = [("batch", C.c_int * 3), ("batch_rho", C.c_int * 3), ("wait_budget", C.c_int), ("reserved", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -84,6 +85,10 @@ def load(build_if_missing: bool = True):
         lib.gint_block_dot_noalloc.argtypes = [vp, vp, vp, vp, vp]
         lib.gint_run_host.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp]
         lib.gint_batched.argtypes = [i32, P(vp), P(vp), P(vp), P(vp), P(vp), i32, vp]
+        lib.gint_batch_create.argtypes = [P(vp), i32, P(vp), P(vp), P(vp), P(vp), P(vp), i32]
+        lib.gint_batch_launch.argtypes = [vp, vp]
+        lib.gint_batch_destroy.argtypes = [vp]
+        lib.gint_autotune.argtypes = [P(d), i32, P(i32), P(d), i32, P(_Species), P(i32), i32, P(_Options), P(d), P(d)]
         lib.gint_get_status.argtypes = [vp]
         lib.gint_last_error.restype = C.c_char_p
         for name in EXPORTS:
@@ -160,7 +165,7 @@ class Handle:
             pass
 
 
-def gint_setup(cell, species, tau, tables, grid, batch=(4, 4, 4), batch_rho=(4, 4, 8)) -> Handle:
+def gint_setup(cell, species, tau, tables, grid, batch=(4, 4, 4), batch_rho=(4, 4, 8), wait_budget=0) -> Handle:
     """cell [3,3] rows (bohr), species [natoms] ints, tau [natoms,3] (bohr), tables: list of
     objects with .l, .rcut, .dr, .ftab [nrad, ntab], .dfdr0 (see synth.SpeciesTables)."""
     lib = load()
@@ -186,6 +191,7 @@ def gint_setup(cell, species, tau, tables, grid, batch=(4, 4, 4), batch_rho=(4, 
     for i in range(3):
         opt.batch[i] = int(batch[i])
         opt.batch_rho[i] = int(batch_rho[i])
+    opt.wait_budget = int(wait_budget)
     out = C.c_void_p()
     _check(lib.gint_setup(C.byref(out), cell.ctypes.data_as(C.POINTER(C.c_double)), len(species),
                           species.ctypes.data_as(C.POINTER(C.c_int)), tau.ctypes.data_as(C.POINTER(C.c_double)),
@@ -274,10 +280,78 @@ def gint_batched(handles, V, H, DM=None, rho=None, prec="fp64", stream=None):
                                arr(rho) if rho is not None else None, _prec(prec), _stream(stream)))
 
 
+class Batch:
+    """A multi-structure job: one persistent launch per kernel over all structures, replayed
+    from a CUDA graph.  Keeps references to the handles and tensors it is bound to."""
+
+    def __init__(self, handles, V, H, DM=None, rho=None, prec="tf32x3"):
+        n = len(handles)
+        arr = lambda xs: (C.c_void_p * n)(*[_ptr(x) for x in xs])
+        hs = (C.c_void_p * n)(*[h.ptr.value for h in handles])
+        out = C.c_void_p()
+        _check(load().gint_batch_create(C.byref(out), n, hs, arr(V), arr(H), arr(DM) if DM is not None else None,
+                                        arr(rho) if rho is not None else None, _prec(prec)))
+        self._ptr = out
+        self._keep = (list(handles), list(V), list(H), list(DM or []), list(rho or []))
+
+    def launch(self, stream=None):
+        _check(load().gint_batch_launch(self._ptr, _stream(stream)))
+
+    def close(self):
+        if self._ptr:
+            load().gint_batch_destroy(self._ptr)
+            self._ptr = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gint_batch_create(handles, V, H, DM=None, rho=None, prec="tf32x3") -> Batch:
+    return Batch(handles, V, H, DM, rho, prec)
+
+
+def gint_batch_launch(b: Batch, stream=None):
+    b.launch(stream)
+
+
+def gint_batch_destroy(b: Batch):
+    b.close()
+
+
+def gint_autotune(st, prec="tf32x3"):
+    """Fastest (batch, batch_rho) shapes for a synth.Structure on the current device, with
+    their vlocal and rho times in ms."""
+    lib = load()
+    cell = np.ascontiguousarray(st.cell, np.float64).reshape(9)
+    species = np.ascontiguousarray(st.species, np.int32)
+    tau = np.ascontiguousarray(st.tau, np.float64).reshape(-1)
+    keep = []
+    sp = (_Species * len(st.tables))()
+    for i, t in enumerate(st.tables):
+        l = np.ascontiguousarray(t.l, np.int32)
+        f = np.ascontiguousarray(t.ftab, np.float64)
+        d0 = np.ascontiguousarray(t.dfdr0, np.float64)
+        keep += [l, f, d0]
+        sp[i].nrad, sp[i].l, sp[i].rcut, sp[i].dr = len(l), l.ctypes.data_as(C.POINTER(C.c_int)), float(t.rcut), float(t.dr)
+        sp[i].ntab, sp[i].ftab = int(f.shape[-1]), f.ctypes.data_as(C.POINTER(C.c_double))
+        sp[i].dfdr0 = d0.ctypes.data_as(C.POINTER(C.c_double))
+    grid = (C.c_int * 3)(*[int(g) for g in st.grid])
+    best = _Options()
+    tv, tr = C.c_double(), C.c_double()
+    _check(lib.gint_autotune(cell.ctypes.data_as(C.POINTER(C.c_double)), len(species),
+                             species.ctypes.data_as(C.POINTER(C.c_int)), tau.ctypes.data_as(C.POINTER(C.c_double)),
+                             len(st.tables), sp, grid, _prec(prec), C.byref(best), C.byref(tv), C.byref(tr)))
+    return tuple(best.batch), tuple(best.batch_rho), tv.value, tr.value
+
+
 def gint_get_status(h: Handle):
     return load().gint_get_status(h.ptr)
 
 
-def setup_structure(st, batch=(4, 4, 4), batch_rho=(4, 4, 8), tau=None) -> Handle:
+def setup_structure(st, batch=(4, 4, 4), batch_rho=(4, 4, 8), tau=None, wait_budget=0) -> Handle:
     """Convenience: gint_setup from a synth.Structure."""
-    return gint_setup(st.cell, st.species, st.tau if tau is None else tau, st.tables, st.grid, batch, batch_rho)
+    return gint_setup(st.cell, st.species, st.tau if tau is None else tau, st.tables, st.grid, batch, batch_rho,
+                      wait_budget)

@@ -226,26 +226,45 @@ def _rot_from_quat(q):
 
 def water_box(nmol=64, L=23.5, grid=None, min_oo=5.0, seed=BASE_SEED, h_basis="2s1p",
               name=None) -> Structure:
-    """O on a jittered cubic lattice (rejection until min O-O >= min_oo), H at 1.809 bohr,
-    HOH angle 104.5 deg, orientation from a uniform random quaternion (Shoemake)."""
+    """O positions with minimum periodic O-O distance min_oo: a jittered cubic lattice when its
+    spacing allows (the 64-molecule box: 4x4x4 in 23.5 bohr), otherwise random sequential
+    addition (bounded attempts).  H at 1.809 bohr, HOH angle 104.5 deg, orientation from a
+    uniform random quaternion (Shoemake)."""
     n = int(math.ceil(nmol ** (1.0 / 3.0) - 1e-9))
     sp = L / n
-    sites = np.array([[i, j, k] for i in range(n) for j in range(n) for k in range(n)], float)
-    pick = np.argsort(uniform(stream_key(seed, 21), len(sites)), kind="stable")[:nmol]
-    base = (sites[np.sort(pick)] + 0.5) * sp
     cell = np.diag([L, L, L]).astype(np.float64)
-    jitter = 0.4
-    attempt = 0
-    while True:
-        u = uniform(stream_key(seed, 22, attempt), 3 * nmol).reshape(nmol, 3)
-        opos = base + jitter * (2 * u - 1)
-        d = opos[:, None, :] - opos[None, :, :]
+
+    def min_dist(pos):
+        d = pos[:, None, :] - pos[None, :, :]
         d -= L * np.round(d / L)
-        dist = np.sqrt((d ** 2).sum(-1)) + np.eye(nmol) * 1e9
-        if dist.min() >= min_oo:
-            break
-        attempt += 1
-        jitter *= 0.9
+        return (np.sqrt((d ** 2).sum(-1)) + np.eye(len(pos)) * 1e9).min()
+
+    if sp >= min_oo:
+        sites = np.array([[i, j, k] for i in range(n) for j in range(n) for k in range(n)], float)
+        pick = np.argsort(uniform(stream_key(seed, 21), len(sites)), kind="stable")[:nmol]
+        base = (sites[np.sort(pick)] + 0.5) * sp
+        # per-coordinate jitter below (sp - min_oo)/(2 sqrt 3) keeps every distance >= min_oo
+        jitter = min(0.4, 0.999 * (sp - min_oo) / (2 * math.sqrt(3)))
+        u = uniform(stream_key(seed, 22), 3 * nmol).reshape(nmol, 3)
+        opos = base + jitter * (2 * u - 1)
+    else:
+        opos = np.zeros((0, 3))
+        key = stream_key(seed, 24)
+        draw = 0
+        while len(opos) < nmol:
+            for _ in range(100000):
+                cand = L * uniform(key, 3, start=draw)
+                draw += 3
+                if len(opos) == 0:
+                    break
+                d = opos - cand
+                d -= L * np.round(d / L)
+                if np.sqrt((d ** 2).sum(-1)).min() >= min_oo:
+                    break
+            else:
+                raise ValueError(f"water_box: cannot place {nmol} molecules {min_oo} bohr apart in {L} bohr")
+            opos = np.vstack([opos, cand])
+    assert min_dist(opos) >= min_oo - 1e-9
     roh, ang = 1.809, math.radians(104.5)
     h1 = roh * np.array([math.sin(ang / 2), 0.0, math.cos(ang / 2)])
     h2 = roh * np.array([-math.sin(ang / 2), 0.0, math.cos(ang / 2)])

@@ -214,6 +214,25 @@ __device__ __forceinline__ SInfo sinfo_of(const Batch &B, const SInfo &si0, cons
     return sis ? sis[(unsigned)B.dims >> 24] : si0;
 }
 
+// structure info of the current batch, reloaded only when the structure id changes (a CTA's
+// contiguous batch range spans few structures)
+struct SInfoCache {
+    int sid;
+    SInfo v;
+    __device__ __forceinline__ SInfoCache(const SInfo &si0) : sid(-1), v(si0) {}
+    __device__ __forceinline__ SInfo get(const Batch &B, const SInfo *sis)
+    {
+        if (sis) {
+            const int id = (int)((unsigned)B.dims >> 24);
+            if (id != sid) {
+                sid = id;
+                v = sis[id];
+            }
+        }
+        return v;
+    }
+};
+
 // slots and point offsets of batch B into shared memory (called by the threads of one role)
 __device__ __forceinline__ void load_geom(const Plan &P, const SInfo &SI, const Batch &B, PSlot *ps, float *poff,
                                           int tid, int nthr)
@@ -378,6 +397,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         int g = 0;  // chunk counter (stage = g & 1)
         int it = 0; // batches with MMAs issued
         bool ok = true;
+        SInfoCache sic(si0);
         for (int bi = bbeg; bi < bend && ok; ++bi) {
             const Batch B = P.batches[bi];
             int n1, n2, n3;
@@ -386,7 +406,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             const int npad = (nb + 15) & ~15;
             const int buf = nbuf == 2 ? (it & 1) : 0;
             if (nb == 0) continue;  // no orbital reaches this batch: nothing to add
-            const SInfo SI = sinfo_of(B, si0, sis);
+            const SInfo SI = sic.get(B, sis);
             const float dVf = (float)SI.dV;
             named_sync(1, kProd);
             load_geom(P, SI, B, ps, poff, pt, kProd);
@@ -483,13 +503,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const int et = tid - kProd, ew = et >> 5, lane = et & 31;
         const int q = ew & 3, hh = ew >> 2;  // TMEM lane quadrant, column half
         int it = 0;
+        SInfoCache sic(si0);
         for (int bi = bbeg; bi < bend; ++bi) {
             const Batch B = P.batches[bi];
             const int ns = B.nslots, nb = B.nb;
             const int npad = (nb + 15) & ~15;
             const int buf = nbuf == 2 ? (it & 1) : 0;
             if (nb == 0) continue;
-            double *H = sinfo_of(B, si0, sis).H;
+            double *H = sic.get(B, sis).H;
             named_sync(2, kEpi);
             for (int e = et; e < ns * ns; e += kEpi) tbl[e] = P.tbl[B.tbl + e];
             for (int s = et; s < ns; s += kEpi) {
@@ -641,6 +662,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const int pt = tid;
         int g = 0, it = 0;
         bool ok = true;
+        SInfoCache sic(si0);
         for (int bi = bbeg; bi < bend && ok; ++bi) {
             const Batch B = P.batches[bi];
             int n1, n2, n3;
@@ -649,7 +671,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             const int npad = (nb + 15) & ~15;
             const int buf = it & 1;
             if (nb == 0) continue;  // the epilogue writes rho = 0 there
-            const SInfo SI = sinfo_of(B, si0, sis);
+            const SInfo SI = sic.get(B, sis);
             const float *__restrict__ DM = SI.DM32;
             named_sync(1, kProd);
             load_geom(P, SI, B, ps, poff, pt, kProd);
@@ -792,13 +814,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const int p = q * 32 + lane;  // TMEM lane = point of the batch
         float *w = win + ew * kWin * 32;
         int it = 0;
+        SInfoCache sic(si0);
         for (int bi = bbeg; bi < bend; ++bi) {
             const Batch B = P.batches[bi];
             int n1, n2, n3;
             unpack(B.dims, n1, n2, n3);
             const int ns = B.nslots, npb = n1 * n2 * n3;
             const int buf = it & 1;
-            const SInfo SI = sinfo_of(B, si0, sis);
+            const SInfo SI = sic.get(B, sis);
             if (B.nb == 0) {
                 if (RHO && hh == 0 && p < npb) SI.rho[grid_index(SI, B, p, n2, n3)] = 0.0;
                 continue;

@@ -32,7 +32,7 @@ struct gint_batch_s {
     Plan plan[3];                    // combined plans: [0] vlocal (batches <= 192 orbitals),
                                      // [1] rho, [2] vlocal of structures with larger batches
     int max_nb_v[3] = {0, 0, 0};
-    void *d_mem[12] = {nullptr};
+    void *d_mem[15] = {nullptr};    // [3w..3w+2] batches, slots, tables; [9] splines; [12+w] CTA ranges
     SInfo *d_sinfo = nullptr;
     int *d_status = nullptr;
     cudaStream_t cap = nullptr;
@@ -171,6 +171,7 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
         std::vector<Batch> bat;
         std::vector<Slot> sl;
         std::vector<int> tbl;
+        std::vector<int> seg{0};
         const int src = w == 1 ? 1 : 0;
         for (int i = 0; i < nstruct; ++i) {
             const BatchSet &bs = hs[i]->bs[src];
@@ -188,6 +189,7 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
                 sl.push_back(S);
             }
             tbl.insert(tbl.end(), bs.tbl.begin(), bs.tbl.end());
+            seg.push_back((int)bat.size());
             b->max_nb_v[w] = std::max(b->max_nb_v[w], bs.max_nb);
         }
         if ((e = upload_vec(&b->d_mem[3 * w + 0], bat)) != cudaSuccess ||
@@ -196,7 +198,17 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
             free_batch(b);
             return cuda_fail(e, "gint_batch_create: upload");
         }
+        // one segment per structure: every CTA works on the same structure at about the same
+        // time, so the block stores being accumulated stay few (and in L2)
+        const std::vector<int2> rng = segment_ranges(bat.data(), seg, b->nsm, w == 1 ? 1 : 0);
+        if ((e = upload_vec(&b->d_mem[12 + w], rng)) != cudaSuccess) {
+            free_batch(b);
+            return cuda_fail(e, "gint_batch_create: upload");
+        }
         Plan p = base;
+        p.rng = (const int2 *)b->d_mem[12 + w];
+        p.npart = b->nsm;
+        p.nseg = (int)seg.size() - 1;
         p.batches = (const Batch *)b->d_mem[3 * w + 0];
         p.slots = (const Slot *)b->d_mem[3 * w + 1];
         p.tbl = (const int *)b->d_mem[3 * w + 2];

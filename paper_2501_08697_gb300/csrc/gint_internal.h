@@ -84,6 +84,8 @@ struct Plan {
     int64_t nblocks, nvalues;
     int *status;                   // device status word
     long long spin_limit;          // clock64 cycles a kernel may wait on one pipeline barrier
+    const int2 *rng;               // [nseg][npart]: batch range [x, y) of each CTA of a persistent
+    int npart, nseg;               //   launch per segment, or null for equal counts per CTA
 };
 
 // One decomposition of the grid into batches, with its atom-image lists and pair tables.
@@ -96,8 +98,18 @@ struct BatchSet {
     int limit_nb = 256;              // batches with more orbitals are split
     int max_nb = 0, max_slots = 0;
     double flops_dense = 0.0;
-    void *d_batches = nullptr, *d_slots = nullptr, *d_tbl = nullptr;
+    std::vector<int2> rng;           // cost-balanced CTA ranges of the persistent kernels
+    void *d_batches = nullptr, *d_slots = nullptr, *d_tbl = nullptr, *d_rng = nullptr;
 };
+
+// Split batches [0, n) into at most nparts contiguous ranges of about equal estimated cost
+// (kind 0: vlocal, 1: rho/force); returns the nparts' + 1 range bounds.
+std::vector<int> partition_batches(const Batch *b, size_t n, int nparts, int kind);
+
+// CTA ranges of a persistent launch of npart CTAs over consecutive segments [seg[i], seg[i+1])
+// of a batch list: each segment is split by cost over min(npart, its batches) CTAs, the CTAs
+// that receive work rotating from one segment to the next; other CTAs get an empty range.
+std::vector<int2> segment_ranges(const Batch *b, const std::vector<int> &seg, int npart, int kind);
 
 }  // namespace gint
 
@@ -142,6 +154,9 @@ inline Plan plan_for(const gint_handle_s *h, int which)
     p.slots = (const Slot *)b.d_slots;
     p.tbl = (const int *)b.d_tbl;
     p.nbatches = (int)b.batches.size();
+    p.rng = (const int2 *)b.d_rng;
+    p.npart = (int)b.rng.size();
+    p.nseg = 1;
     return p;
 }
 void set_error(const char *fmt, ...);

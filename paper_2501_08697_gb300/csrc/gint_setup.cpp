@@ -475,6 +475,56 @@ gint_status build_geometry(gint_handle h, const double *tau, bool update_only)
     return GINT_OK;
 }
 
+// Estimated cost of one batch in a persistent tensor-core kernel.  The producers evaluate every
+// orbital of the batch at every point (npts x nb), the epilogue handles the nb x nb result
+// (vlocal: the upper triangle scattered into H) or the npts x nb result (rho: one dot product
+// and, for the force, the orbital gradients per point); a fixed part covers barriers and the
+// pipeline hand-offs.  The weights are relative clock-cycle costs measured per batch on Si and
+// water workloads; only their ratios matter.
+static double batch_cost(const Batch &B, int kind)
+{
+    const double np = (double)((B.dims & 255) * ((B.dims >> 8) & 255) * ((B.dims >> 16) & 255));
+    const double nb = (double)B.nb;
+    return kind == 0 ? 2000.0 + 2.6 * np * nb + 0.65 * nb * nb : 4000.0 + 4.0 * np * nb + 1.0 * nb * nb;
+}
+
+std::vector<int> partition_batches(const Batch *b, size_t n, int nparts, int kind)
+{
+    nparts = (int)std::min<size_t>((size_t)std::max(nparts, 1), std::max<size_t>(n, 1));
+    std::vector<double> pre(n + 1, 0.0);
+    for (size_t i = 0; i < n; ++i) pre[i + 1] = pre[i] + batch_cost(b[i], kind);
+    std::vector<int> part(nparts + 1, 0);
+    part[nparts] = (int)n;
+    size_t j = 0;
+    for (int k = 1; k < nparts; ++k) {
+        const double target = pre[n] * k / nparts;
+        while (j < n && pre[j + 1] <= target) ++j;
+        // the boundary nearer to the target, keeping every range non-empty
+        size_t cut = (j < n && target - pre[j] > pre[j + 1] - target) ? j + 1 : j;
+        cut = std::max<size_t>(cut, (size_t)part[k - 1] + 1);
+        cut = std::min<size_t>(cut, n - (size_t)(nparts - k));
+        part[k] = (int)cut;
+    }
+    return part;
+}
+
+std::vector<int2> segment_ranges(const Batch *b, const std::vector<int> &seg, int npart, int kind)
+{
+    const int nseg = (int)seg.size() - 1;
+    std::vector<int2> rng((size_t)nseg * npart, make_int2(0, 0));
+    int rot = 0;
+    for (int g = 0; g < nseg; ++g) {
+        const int n = seg[g + 1] - seg[g];
+        if (n == 0) continue;
+        const std::vector<int> part = partition_batches(b + seg[g], (size_t)n, npart, kind);
+        const int np = (int)part.size() - 1;
+        for (int j = 0; j < np; ++j)
+            rng[(size_t)g * npart + (j + rot) % npart] = make_int2(seg[g] + part[j], seg[g] + part[j + 1]);
+        rot = (rot + np) % npart;
+    }
+    return rng;
+}
+
 }  // namespace gint
 
 // ---------------------------------------------------------------------------------------
@@ -496,7 +546,7 @@ static void free_dev(gint_handle h)
 {
     void *ptrs[] = {h->d_coef64, h->d_coef32, h->d_partner, h->d_blkoff, h->d_blkrows, h->d_status, h->d_dmsym,
                     h->d_dm32, h->d_poff, h->d_red, h->d_hostio, h->bs[0].d_batches, h->bs[0].d_slots, h->bs[0].d_tbl,
-                    h->bs[1].d_batches, h->bs[1].d_slots, h->bs[1].d_tbl};
+                    h->bs[0].d_rng, h->bs[1].d_batches, h->bs[1].d_slots, h->bs[1].d_tbl, h->bs[1].d_rng};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -511,6 +561,9 @@ static gint_status upload_geometry(gint_handle h)
             if ((e = upload(&b.d_batches, b.batches)) != cudaSuccess) return cuda_fail(e, "upload batches");
             if ((e = upload(&b.d_slots, b.slots)) != cudaSuccess) return cuda_fail(e, "upload slots");
             if ((e = upload(&b.d_tbl, b.tbl)) != cudaSuccess) return cuda_fail(e, "upload tables");
+            const int nb = (int)b.batches.size();
+            b.rng = segment_ranges(b.batches.data(), {0, nb}, std::max(1, std::min(h->nsm, nb)), w);
+            if ((e = upload(&b.d_rng, b.rng)) != cudaSuccess) return cuda_fail(e, "upload CTA ranges");
         }
         if ((e = upload(&h->d_partner, h->partner)) != cudaSuccess) return cuda_fail(e, "upload partner");
         if ((e = upload(&h->d_blkoff, h->offsets)) != cudaSuccess) return cuda_fail(e, "upload offsets");

@@ -233,6 +233,38 @@ struct SInfoCache {
     }
 };
 
+// The batches of this CTA, in order: per segment (the whole list, or one structure of a
+// multi-structure job) one contiguous range.  Contiguous ranges keep the CTAs that run at the
+// same time on distant parts of a cell, so their FP64 atomics rarely meet on one block; the
+// segments keep all CTAs on the same structure at about the same time.
+struct CtaRange {
+    const int2 *rng;
+    int npart, nseg, seg, cur, end;
+    __device__ __forceinline__ CtaRange(const Plan &P) : rng(P.rng), npart(P.npart), nseg(P.nseg), seg(0)
+    {
+        if (rng) {
+            const int2 r = rng[blockIdx.x];
+            cur = r.x;
+            end = r.y;
+        } else {
+            nseg = 1;
+            cur = (int)((int64_t)P.nbatches * blockIdx.x / gridDim.x);
+            end = (int)((int64_t)P.nbatches * (blockIdx.x + 1) / gridDim.x);
+        }
+    }
+    __device__ __forceinline__ bool next(int &bi)
+    {
+        while (cur >= end) {
+            if (++seg >= nseg) return false;
+            const int2 r = rng[seg * npart + blockIdx.x];
+            cur = r.x;
+            end = r.y;
+        }
+        bi = cur++;
+        return true;
+    }
+};
+
 // slots and point offsets of batch B into shared memory (called by the threads of one role)
 __device__ __forceinline__ void load_geom(const Plan &P, const SInfo &SI, const Batch &B, PSlot *ps, float *poff,
                                           int tid, int nthr)
@@ -386,10 +418,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_base;
     const int tile1 = nbuf == 2 ? 192 : 256;   // TMEM column of tile 1 within an accumulator
-    // a contiguous range of batches per CTA: CTAs running at the same time work on distant
-    // parts of the cell, so their FP64 atomics rarely meet on the same block
-    const int bbeg = (int)((int64_t)P.nbatches * blockIdx.x / gridDim.x);
-    const int bend = (int)((int64_t)P.nbatches * (blockIdx.x + 1) / gridDim.x);
 
     if (tid < kProd) {
         // ------------------------------------------------------------ producers + MMA issue
@@ -398,7 +426,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         int it = 0; // batches with MMAs issued
         bool ok = true;
         SInfoCache sic(si0);
-        for (int bi = bbeg; bi < bend && ok; ++bi) {
+        CtaRange cr(P);
+        for (int bi = 0; ok && cr.next(bi);) {
             const Batch B = P.batches[bi];
             int n1, n2, n3;
             unpack(B.dims, n1, n2, n3);
@@ -504,7 +533,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const int q = ew & 3, hh = ew >> 2;  // TMEM lane quadrant, column half
         int it = 0;
         SInfoCache sic(si0);
-        for (int bi = bbeg; bi < bend; ++bi) {
+        CtaRange cr(P);
+        for (int bi = 0; cr.next(bi);) {
             const Batch B = P.batches[bi];
             const int ns = B.nslots, nb = B.nb;
             const int npad = (nb + 15) & ~15;
@@ -654,8 +684,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_base;
-    const int bbeg = (int)((int64_t)P.nbatches * blockIdx.x / gridDim.x);
-    const int bend = (int)((int64_t)P.nbatches * (blockIdx.x + 1) / gridDim.x);
 
     if (tid < kProd) {
         // ------------------------------------------------------------ producers + MMA issue
@@ -663,7 +691,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         int g = 0, it = 0;
         bool ok = true;
         SInfoCache sic(si0);
-        for (int bi = bbeg; bi < bend && ok; ++bi) {
+        CtaRange cr(P);
+        for (int bi = 0; ok && cr.next(bi);) {
             const Batch B = P.batches[bi];
             int n1, n2, n3;
             unpack(B.dims, n1, n2, n3);
@@ -815,7 +844,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         float *w = win + ew * kWin * 32;
         int it = 0;
         SInfoCache sic(si0);
-        for (int bi = bbeg; bi < bend; ++bi) {
+        CtaRange cr(P);
+        for (int bi = 0; cr.next(bi);) {
             const Batch B = P.batches[bi];
             int n1, n2, n3;
             unpack(B.dims, n1, n2, n3);
@@ -911,7 +941,7 @@ cudaError_t vlocal_launch(const Plan &P, const SInfo &si0, const SInfo *sis, cud
     static_assert(smem <= 232448, "vlocal shared memory");
     cudaError_t e = cudaFuncSetAttribute(k_vlocal_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const int grid = std::min(nsm, P.nbatches);
+    const int grid = P.rng ? P.npart : std::min(nsm, P.nbatches);
     k_vlocal_tc<S><<<grid, kThreadsTC, smem, s>>>(P, si0, sis, max_nb <= 192 ? 2 : 1);
     return cudaGetLastError();
 }
@@ -923,7 +953,7 @@ cudaError_t rho_launch3(const Plan &P, const SInfo &si0, const SInfo *sis, cudaS
     static_assert(smem <= 232448, "rho shared memory");
     cudaError_t e = cudaFuncSetAttribute(k_rho_tc<S, R, Fo>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const int grid = std::min(nsm, P.nbatches);
+    const int grid = P.rng ? P.npart : std::min(nsm, P.nbatches);
     k_rho_tc<S, R, Fo><<<grid, kThreadsTC, smem, s>>>(P, si0, sis);
     return cudaGetLastError();
 }

@@ -8,19 +8,20 @@
 // BF16x6); the products of total order <= 1 (TF32x3, BF16x3) or <= 2 (BF16x6) accumulate in
 // FP32 in tensor memory (TMEM); the cross-batch sums (block store, rho(r), forces) are FP64.
 //
-// One persistent CTA per SM, 16 warps:
-//   warps 0-7  producers: orbital values (FP32, spline x solid harmonic) into an FP32 staging
+// One persistent CTA per SM, 20 warps (the producers carry most of the CUDA-core work):
+//   warps 0-11 producers: orbital values (FP32, spline x solid harmonic) into an FP32 staging
 //              tile, then split into the canonical K-major no-swizzle shared-memory layout
 //              (8-row x 16-byte core matrices; the K-direction core-matrix stride is padded
 //              to 144 bytes so 16-byte stores from a warp spread over all banks); thread 0
 //              also issues the MMAs and commits them to mbarriers.
-//   warps 8-15 epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes 32(w%4)..;
+//   warps 12-19 epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes 32(w%4)..;
 //              the two warps of a lane quadrant share the columns or the atom images),
 //              then the FP64 scatter into the block store (vlocal) or rho(r)/force (rho).
 // Accumulators are double-buffered in TMEM so the epilogue of batch i overlaps the MMAs of
 // batch i+1.  No FP64 arithmetic runs in the hot loops (GB300's FP64 rate is 1/64 of FP32):
 // offsets come as FP32 hi/lo pairs, dV is folded into the FP32 operand, FP32 -> FP64 for the
-// atomics is done with integer bit operations, and the density matrix is read as FP32.
+// reductions (red.global.add.f64, no return value) is done with integer bit operations, and the
+// density matrix is read as FP32.
 // Every mbarrier wait is bounded (clock64 budget); a wait that runs out records
 // GINT_ETIMEOUT in the status word and the CTA drains and exits without deadlock.
 #include <cuda_bf16.h>
@@ -30,7 +31,7 @@
 namespace gint {
 namespace {
 
-constexpr int kProd = 256;        // producer threads
+constexpr int kProd = 384;        // producer threads (12 warps)
 constexpr int kEpi = 256;         // epilogue threads (two warps per TMEM lane quadrant)
 constexpr int kThreadsTC = kProd + kEpi;
 constexpr int kLBO = 144;         // bytes between core matrices along K
@@ -87,6 +88,12 @@ __device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_
     else
         asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(d),
                      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// FP64 add to global memory without a return value (the scatters never read the old value)
+__device__ __forceinline__ void red_add_f64(double *a, double v)
+{
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(a), "d"(v) : "memory");
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -593,7 +600,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         }
 #pragma unroll
                         for (int rr = 0; rr < 8; ++rr)
-                            if (go[rr]) atomicAdd(adr[rr], f2d_fast(val[rr]));
+                            if (go[rr]) red_add_f64(adr[rr], f2d_fast(val[rr]));
                     }
                     __syncwarp();
                 }
@@ -615,12 +622,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 template <class S>
 struct RSmem {
     static constexpr int KC = S::KCM * S::CG;              // orbitals per chunk
+    static constexpr int RING = KC == 16 ? 32 : KC;        // staging rows (orbital ring, see k_rho_tc)
     static constexpr int ARR_A = arr_bytes<S>(kMaxBatchPts);
     static constexpr int ARR_B = arr_bytes<S>(kMaxNb);
     static constexpr int STAGE = S::NT * (ARR_A + ARR_B);
     static constexpr int NSTAGE = 2;
-    static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [KC][128]
-    static constexpr int OFF_PSLOT = OFF_STG + KC * kMaxBatchPts * 4;       // producer PSlot[64]
+    static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [RING][128]
+    static constexpr int OFF_PSLOT = OFF_STG + RING * kMaxBatchPts * 4;     // producer PSlot[64]
     static constexpr int OFF_POFF = OFF_PSLOT + kMaxSlots * (int)sizeof(PSlot);
     static constexpr int OFF_TBL = OFF_POFF + kMaxBatchPts * 24;            // int [64*64]
     static constexpr int OFF_OMAP = OFF_TBL + kMaxSlots * kMaxSlots * 4;    // oslot[256], oidx[256]
@@ -642,7 +650,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     k_rho_tc(Plan P, SInfo si0, const SInfo *__restrict__ sis)
 {
     using L = RSmem<S>;
-    constexpr int KC = L::KC;
+    constexpr int KC = L::KC, RING = L::RING;
     constexpr int SBO = S::KCM * kLBO;
     extern __shared__ __align__(1024) unsigned char sm[];
     float *stg = reinterpret_cast<float *>(sm + L::OFF_STG);
@@ -690,6 +698,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const int pt = tid;
         int g = 0, it = 0;
         bool ok = true;
+        // Orbital ring: when every slot fits (KC + norb - 1 <= RING rows), the orbitals of a slot
+        // are evaluated once, in the chunk where the slot starts, into staging rows
+        // (orbital index) mod RING, and later chunks read the rows they carry over.  Otherwise
+        // each chunk evaluates every slot overlapping it and keeps its own columns.
+        int maxnorb = 0;
+        for (int i = 0; i < P.nspecies; ++i) maxnorb = max(maxnorb, P.sp[i].norb);
+        const bool ring = KC + maxnorb - 1 <= RING;
         SInfoCache sic(si0);
         CtaRange cr(P);
         for (int bi = 0; ok && cr.next(bi);) {
@@ -717,29 +732,51 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 const int stage = g & 1;
                 const int k0 = ch * KC, k1 = min(k0 + KC, nb);
                 const int s_lo = oslot[k0], s_hi = oslot[k1 - 1];
-                const int nsc = s_hi - s_lo + 1;
-                // phase 1: orbital values of the chunk's orbitals at all points -> staging [KC][128]
-                for (int w = pt; w < kMaxBatchPts * nsc; w += kProd) {
-                    const int p = w % kMaxBatchPts, s = s_lo + w / kMaxBatchPts;
-                    const PSlot sl = ps[s];
-                    float *col = stg + p;
-                    const int base_k = sl.off - k0;
-                    if (p < npb) {
-                        float dx, dy, dz;
-                        disp(sl, poff + 6 * p, dx, dy, dz);
-                        eval_phi_f32(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) {
-                            const int k = base_k + o;
-                            if (k >= 0 && k < KC) col[k * kMaxBatchPts] = v;
-                        });
-                    } else {
-                        for (int o = 0; o < sl.norb; ++o) {
-                            const int k = base_k + o;
-                            if (k >= 0 && k < KC) col[k * kMaxBatchPts] = 0.f;
+                // staging row of chunk column k: rbase + k
+                const int rbase = ring ? (k0 & (RING - 1)) : 0;
+                // phase 1: orbital values at all points -> staging rows
+                if (ring) {
+                    const int s_first = ps[s_lo].off >= k0 ? s_lo : s_lo + 1;  // slots starting here
+                    const int nsc = s_hi - s_first + 1;
+                    for (int w = pt; w < kMaxBatchPts * nsc; w += kProd) {
+                        const int p = w % kMaxBatchPts, s = s_first + w / kMaxBatchPts;
+                        const PSlot sl = ps[s];
+                        float *col = stg + p;
+                        if (p < npb) {
+                            float dx, dy, dz;
+                            disp(sl, poff + 6 * p, dx, dy, dz);
+                            eval_phi_f32(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) {
+                                col[((sl.off + o) & (RING - 1)) * kMaxBatchPts] = v;
+                            });
+                        } else {
+                            for (int o = 0; o < sl.norb; ++o) col[((sl.off + o) & (RING - 1)) * kMaxBatchPts] = 0.f;
+                        }
+                    }
+                } else {
+                    const int nsc = s_hi - s_lo + 1;
+                    for (int w = pt; w < kMaxBatchPts * nsc; w += kProd) {
+                        const int p = w % kMaxBatchPts, s = s_lo + w / kMaxBatchPts;
+                        const PSlot sl = ps[s];
+                        float *col = stg + p;
+                        const int base_k = sl.off - k0;
+                        if (p < npb) {
+                            float dx, dy, dz;
+                            disp(sl, poff + 6 * p, dx, dy, dz);
+                            eval_phi_f32(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) {
+                                const int k = base_k + o;
+                                if (k >= 0 && k < KC) col[k * kMaxBatchPts] = v;
+                            });
+                        } else {
+                            for (int o = 0; o < sl.norb; ++o) {
+                                const int k = base_k + o;
+                                if (k >= 0 && k < KC) col[k * kMaxBatchPts] = 0.f;
+                            }
                         }
                     }
                 }
+                // columns past the last orbital of the batch (last chunk only)
                 for (int w = pt; w < (KC - (k1 - k0)) * kMaxBatchPts; w += kProd)
-                    stg[(k1 - k0) * kMaxBatchPts + w] = 0.f;
+                    stg[(rbase + k1 - k0) * kMaxBatchPts + w] = 0.f;
                 // gather tables of the chunk: element (nu, k) of B is DM32[gbase[b][k] + o_nu * gna[k]]
                 // with b the slot of nu (gbase = -1: no block, or k past the last orbital)
                 for (int w = pt; w < ns * KC; w += kProd) {
@@ -766,7 +803,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     for (int t = 0; t < S::NT; ++t) da[t] = base + t * L::ARR_A + cm_off<S>(p, kc);
                     float x[S::CG];
 #pragma unroll
-                    for (int i = 0; i < S::CG; ++i) x[i] = stg[(kc * S::CG + i) * kMaxBatchPts + p];
+                    for (int i = 0; i < S::CG; ++i) x[i] = stg[(rbase + kc * S::CG + i) * kMaxBatchPts + p];
                     split_store<S>(x, da);
                 }
                 // phase 2b: B = D rows nu (N), K = orbitals mu of the chunk: D(b_nu, a_mu)[o_nu][o_mu]
@@ -922,7 +959,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             if (RHO && hh == 0 && pv) SI.rho[gi] = f2d(racc + rpart[p]);
             if (FORCE)
                 for (int e = et; e < 3 * ns; e += kEpi)
-                    atomicAdd(&SI.F[3 * eps[e / 3].atom + e % 3], 2.0 * SI.dV * facc[e]);
+                    red_add_f64(&SI.F[3 * eps[e / 3].atom + e % 3], 2.0 * SI.dV * facc[e]);
             ++it;
         }
     }

@@ -27,6 +27,11 @@ def structure(name):
         return S.water_box(8, (8 * 23.5 ** 3 / 64) ** (1 / 3), seed=S.BASE_SEED + 63, name="water8")
     if name == "water1_vacuum":   # one molecule in a large box: batches with no orbitals
         return S.water_box(1, 16.0, grid=(64, 64, 72), seed=S.BASE_SEED + 64, name="water1_vacuum")
+    if name == "si8_2d":          # 18 orbitals per atom (2s2p2d): slots wider than 17 orbitals
+        st = S.si_diamond((1, 1, 1), grid=(36, 36, 40), sigma=0.05, seed=S.BASE_SEED + 65, name="si8_2d")
+        spec = S.SpeciesSpec("Si", 7.0, [(0, 0.3), (0, 0.8), (1, 0.3), (1, 0.8), (2, 0.5), (2, 1.1)])
+        st.tables = [S.species_tables(spec)]
+        return st
     if name == "si64":
         return S.workload("si64")
     if name == "water64":

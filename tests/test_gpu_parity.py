@@ -16,7 +16,7 @@ TOL = {"fp64": 1e-11, "fp32": 1e-6, "tf32x3": 1e-6, "bf16x6": 1e-6, "bf16x3": 5e
 FORCE_TOL = {"fp64": 1e-10, "fp32": 2e-6, "tf32x3": 2e-6, "bf16x6": 2e-6, "bf16x3": 1e-4}
 SIMT = ["fp64", "fp32"]
 ALL = ["fp64", "fp32", "tf32x3", "bf16x3", "bf16x6"]
-CASES = ["si8", "si8_ragged", "si16_strained", "water8", "water1_vacuum"]
+CASES = ["si8", "si8_ragged", "si16_strained", "water8", "water1_vacuum", "si8_2d"]
 TC = ["tf32x3", "bf16x3", "bf16x6"]
 
 

@@ -5,7 +5,9 @@ block, every grid point and every atom.  Si512 (192^3) is too large for the orac
 H is compared on every block (I, J, R) whose first atom I is one of 4 seeded atoms (the oracle
 integrates all grid points within rc of any image of I, which makes those blocks complete),
 rho on 1e5 seeded grid points, and the force on the same 4 atoms.  Tolerances as in
-test_gpu_parity: FP64 1e-11, TF32x3 / BF16x6 1e-6 (relative Frobenius)."""
+test_gpu_parity: FP64 1e-11, TF32x3 / BF16x6 1e-6 (relative Frobenius); the force on only 4
+atoms (12 numbers, each a sum with heavy cancellation) is held to 2e-6, and the force on all
+512 atoms to 1e-6 against the FP64 GPU force."""
 import numpy as np
 import pytest
 
@@ -49,7 +51,7 @@ def test_full_parity(G, name):
         _, H, rho, F = _gpu_outputs(G, ref["st"], ref["V"], ref["DM"], prec, h)
         eH, er, eF = rel_fro(H, ref["H"]), rel_fro(rho, ref["rho"]), rel_fro(F, ref["F"])
         print(f"{name} {prec}: H {eH:.2e} rho {er:.2e} F {eF:.2e}")
-        assert eH <= TOL[prec] and er <= TOL[prec] and eF <= 2 * TOL[prec]
+        assert eH <= TOL[prec] and er <= TOL[prec] and eF <= TOL[prec]
 
 
 @pytest.fixture(scope="module")
@@ -73,6 +75,9 @@ def si512_sample():
                 rpts=rpts, rho=rho_ref)
 
 
+_fp64_forces = {}
+
+
 @pytest.mark.parametrize("prec", ["fp64", "tf32x3", "bf16x6"])
 def test_si512_sampled_parity(G, si512_sample, prec):
     r = si512_sample
@@ -84,6 +89,14 @@ def test_si512_sampled_parity(G, si512_sample, prec):
     eF = rel_fro(F[r["atoms"]], r["F"])
     print(f"si512 {prec}: H({len(r['idx'])} values) {eH:.2e} rho(1e5 pts) {er:.2e} F(4 atoms) {eF:.2e}")
     assert eH <= TOL[prec] and er <= TOL[prec] and eF <= 2 * TOL[prec]
+    if prec == "fp64":
+        _fp64_forces[0] = F
+    elif 0 in _fp64_forces:
+        # every atom: the split-precision force against the FP64 GPU force, itself pinned to
+        # the oracle at 1e-11 on the sampled atoms
+        eFa = rel_fro(F, _fp64_forces[0])
+        print(f"si512 {prec}: F(all {len(F)} atoms, vs FP64 GPU) {eFa:.2e}")
+        assert eFa <= TOL[prec]
     # properties at full size: the adjoint identity and the charge identity in FP64
     dV = h.info["dV"]
     tr = float((r["DM"] * H).sum())

@@ -167,6 +167,20 @@ gint_status gint_force(gint_handle h, const double *V_dev, const double *DM_dev,
 gint_status gint_rho_force(gint_handle h, const double *V_dev, const double *DM_dev,
                            double *rho_dev, double *F_dev, gint_prec prec, void *stream);
 
+/* Strain derivative of L = Sum_blocks Sum_mu,nu DM_mu,nu V_mu,nu(R), the grid part of the
+ * stress of Eq. stress (sigma_ab = -(1/Omega) dE/deps_ab, Sec. III; the LCAO stress follows
+ * the force formulas, Sec. IV.D).  A homogeneous strain maps every vector x -> (1 + eps) x:
+ * cell, atoms, lattice translations and grid points (fractional grid coordinates fixed); the
+ * grid values of V are held fixed and dV scales with det(1 + eps).  Then
+ *   dL/deps_ab = delta_ab dV Sum_r V rho(r)
+ *              + 2 dV Sum_r V(r) Sum_mu d/dx_a phi_mu(d_mu) (d_mu)_b (Phi sym(DM))_r,mu
+ * with d_mu = r - tau_I - R the displacement from the orbital's centre.
+ *   V      device, npts doubles;   DM  device, block layout (symmetrised in the block sense)
+ *   dLde   device, 9 doubles, row-major [a][b], overwritten
+ * Asynchronous on `stream`; errors as gint_force. */
+gint_status gint_strain_derivative(gint_handle h, const double *V_dev, const double *DM_dev,
+                                   double *dLde_dev, gint_prec prec, void *stream);
+
 /* Backward of gint_vlocal for L = Sum_blocks Sum_mu,nu gH_mu,nu V_mu,nu(R) (gH: device, block
  * layout, e.g. the incoming gradient of H):
  *   gV (device, npts)       <- dL/dV(r)   = dV * rho(r) built from the block-symmetric part of gH

@@ -13,6 +13,8 @@
  *   force     Pulay term of Eq. force_lcao (Sec. IV.D): derivative of
  *             L = Sum_blocks Sum rho_mu,nu(R) V_mu,nu(R) with respect to the atom positions
  *             through the basis functions only (V(r) held fixed).
+ *   strain    derivative of the same L with respect to a homogeneous strain of cell, atoms
+ *             and grid (the grid part of the stress of Eq. stress), V(r) grid values fixed.
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the independent checker of the CUDA library: it
  * shares no code, header, table or helper with it.  Only the tests, the smoke check and the
@@ -377,6 +379,7 @@ static int64_t or_find(const int *keys, int64_t nblocks, const int *key)
 /* ------------------------------------------------------------------ per-point orbital list */
 typedef struct {
     int atom, n[3], norb;
+    double d[3];                 /* r - tau_I - R_n */
     double phi[OR_MAXORB];
     double grad[OR_MAXORB * 3];
 } or_rec;
@@ -408,6 +411,7 @@ static int or_collect(const or_ctx *c, const double r[3], or_rec *rec, int cap, 
                     if (nrec >= cap) return -1;
                     or_rec *q = &rec[nrec++];
                     q->atom = I; q->n[0] = n1; q->n[1] = n2; q->n[2] = n3;
+                    q->d[0] = d[0]; q->d[1] = d[1]; q->d[2] = d[2];
                     q->norb = or_phi(S, d, q->phi, want_grad ? q->grad : NULL);
                 }
     }
@@ -582,6 +586,70 @@ int oracle_dLdtau(const or_ctx *c, const double *V, int64_t nblocks, const int *
         free(part[t]);
     }
     free(part);
+    return err;
+}
+
+/* Derivative of L with respect to a homogeneous strain eps (stress, Eq. stress: sigma =
+ * -(1/Omega) dE/deps).  The strain maps every vector x -> (1 + eps) x: cell, atoms, lattice
+ * translations and grid points (the grid keeps its fractional coordinates); the values V(r) on
+ * the grid are held fixed and dV scales with det(1 + eps).  With d = r - tau_I - R_n,
+ *   dL/deps_ab = delta_ab L
+ *              + dV Sum_r V(r) Sum_{x} Sum_{mu in x} d/dx_a phi_mu(d_x) d_x,b .
+ *                Sum_{y, nu} (DM(x,y)_mu,nu + DM(y,x)_nu,mu) phi_nu
+ * with L = dV Sum_r V(r) rho(r).  out[3 a + b] = dL/deps_ab. */
+int oracle_dLdeps(const or_ctx *c, const double *V, int64_t nblocks, const int *keys,
+                  const int64_t *offsets, const double *DM, double *out, int64_t npts, const int64_t *pts)
+{
+    int nt = or_nthreads();
+    int err = 0;
+    double *part = (double *)calloc((size_t)nt * 10, sizeof(double));
+    int64_t count = pts ? npts : c->npts;
+#pragma omp parallel
+    {
+        double *acc = part + 10 * or_tid();   /* [0..8] strain sums, [9] Sum V rho */
+        or_rec *rec = (or_rec *)malloc(sizeof(or_rec) * OR_MAXREC);
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t q = 0; q < count; ++q) {
+            int64_t p = pts ? pts[q] : q;
+            double r[3];
+            or_point(c, p, r);
+            int nrec = or_collect(c, r, rec, OR_MAXREC, 1);
+            if (nrec < 0) { err = -1; continue; }
+            double rho = 0.0;
+            for (int x = 0; x < nrec; ++x) {
+                double g[3] = {0, 0, 0};
+                for (int y = 0; y < nrec; ++y) {
+                    int key[5] = {rec[x].atom, rec[y].atom, rec[y].n[0] - rec[x].n[0],
+                                  rec[y].n[1] - rec[x].n[1], rec[y].n[2] - rec[x].n[2]};
+                    int keyT[5] = {rec[y].atom, rec[x].atom, -key[2], -key[3], -key[4]};
+                    int64_t b = or_find(keys, nblocks, key);
+                    int64_t bt = or_find(keys, nblocks, keyT);
+                    if (b < 0 || bt < 0) { err = -2; continue; }
+                    const double *blk = DM + offsets[b];
+                    const double *blkT = DM + offsets[bt];
+                    int nI = rec[x].norb, nJ = rec[y].norb;
+                    for (int mu = 0; mu < nI; ++mu) {
+                        double s = 0.0;
+                        for (int nu = 0; nu < nJ; ++nu)
+                            s += (blk[mu * nJ + nu] + blkT[nu * nI + mu]) * rec[y].phi[nu];
+                        for (int k = 0; k < 3; ++k) g[k] += rec[x].grad[3 * mu + k] * s;
+                        /* rho(r) = Sum DM phi phi, each ordered pair once (s holds both orders) */
+                        rho += 0.5 * rec[x].phi[mu] * s;
+                    }
+                }
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) acc[3 * a + b] += V[p] * g[a] * rec[x].d[b];
+            }
+            acc[9] += V[p] * rho;
+        }
+        free(rec);
+    }
+    double tot[10] = {0};
+    for (int t = 0; t < nt; ++t)
+        for (int k = 0; k < 10; ++k) tot[k] += part[10 * t + k];
+    free(part);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) out[3 * a + b] = c->dV * tot[3 * a + b] + (a == b ? c->dV * tot[9] : 0.0);
     return err;
 }
 

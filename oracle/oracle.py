@@ -52,6 +52,7 @@ def _load():
             lib.oracle_vlocal.argtypes = [C.c_void_p, P(d), i64, P(i), P(i64), P(d), i64, P(i64)]
             lib.oracle_rho.argtypes = [C.c_void_p, i64, P(i), P(i64), P(d), P(d), i64, P(i64)]
             lib.oracle_dLdtau.argtypes = [C.c_void_p, P(d), i64, P(i), P(i64), P(d), P(d), i64, P(i64)]
+            lib.oracle_dLdeps.argtypes = [C.c_void_p, P(d), i64, P(i), P(i64), P(d), P(d), i64, P(i64)]
             lib.oracle_points_near_atom.restype = i64
             lib.oracle_points_near_atom.argtypes = [C.c_void_p, i, i64, P(i64)]
             lib.oracle_threads.restype = i
@@ -175,6 +176,20 @@ class Oracle:
 
     def force(self, V, DM, pts=None):
         return -self.dLdtau(V, DM, pts)
+
+    def dLdeps(self, V, DM, pts=None):
+        """dL/deps_ab (3x3) under a homogeneous strain of cell, atoms and grid with the grid
+        values of V held fixed; the stress of Eq. (stress) is -dL/deps / Omega."""
+        keys, offs = self.pairs()
+        V = np.ascontiguousarray(V, np.float64).reshape(-1)
+        DM = np.ascontiguousarray(DM, np.float64)
+        out = np.zeros(9, np.float64)
+        n, keep, pp = self._pts(pts)
+        rc = self._lib.oracle_dLdeps(self.ctx, _p(V, C.c_double), len(keys), _p(keys, C.c_int),
+                                     _p(offs, C.c_int64), _p(DM, C.c_double), _p(out, C.c_double), n, pp)
+        if rc != 0:
+            raise RuntimeError(f"oracle_dLdeps failed ({rc})")
+        return out.reshape(3, 3)
 
     def points_near_atom(self, I):
         n = self._lib.oracle_points_near_atom(self.ctx, I, 0, None)

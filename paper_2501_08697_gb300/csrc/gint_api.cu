@@ -149,27 +149,31 @@ gint_status run_vlocal(gint_handle h, const double *V, double *H, gint_prec prec
 }
 
 gint_status run_rho_force(gint_handle h, const double *V, const double *DM, double *rho, double *F, gint_prec prec,
-                          cudaStream_t s)
+                          cudaStream_t s, double *dLde = nullptr)
 {
     cudaError_t e;
     const bool simt = (prec == GINT_FP64 || prec == GINT_FP32);
+    const bool grad = F || dLde;   // derivatives use the block-symmetric part of the DM
     if (F && (e = cudaMemsetAsync(F, 0, sizeof(double) * 3 * h->natoms, s)) != cudaSuccess)
         return cuda_fail(e, "gint_force: memset");
+    if (dLde && (e = cudaMemsetAsync(dLde, 0, sizeof(double) * 9, s)) != cudaSuccess)
+        return cuda_fail(e, "gint_strain: memset");
     if (simt) {
-        // CUDA-core kernels read FP64; the force needs the block-symmetric part
+        // CUDA-core kernels read FP64
         const double *D = DM;
-        if (F && h->info.nblocks > 0) {
+        if (grad && h->info.nblocks > 0) {
             k_symmetrise<<<(int)std::min<int64_t>(h->info.nblocks, 8192), 128, 0, s>>>(h->plan, DM, h->d_dmsym);
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gint_force: symmetrise");
             D = h->d_dmsym;
         }
-        e = launch_rho_force_simt(plan_for(h, 1), prec == GINT_FP64, V, D, rho, F, s, h->nsm);
+        e = launch_rho_force_simt(plan_for(h, 1), prec == GINT_FP64, V, D, rho, F, dLde, s, h->nsm);
     } else {
         // tensor-core kernels gather the density matrix in FP32 (split again on chip)
-        if (h->info.nvalues > 0 && (e = launch_dm_to_f32(h->plan, DM, h->d_dm32, F != nullptr, s)) != cudaSuccess)
+        if (h->info.nvalues > 0 && (e = launch_dm_to_f32(h->plan, DM, h->d_dm32, grad, s)) != cudaSuccess)
             return cuda_fail(e, "gint_rho: convert");
-        e = launch_rho_force_tc(plan_for(h, 1), prec, sinfo_for(h, V, nullptr, h->d_dm32, rho, F), nullptr, rho != nullptr,
-                                F != nullptr, s, h->nsm);
+        SInfo si = sinfo_for(h, V, nullptr, h->d_dm32, rho, F);
+        si.dLde = dLde;
+        e = launch_rho_force_tc(plan_for(h, 1), prec, si, nullptr, rho != nullptr, grad, s, h->nsm);
     }
     if (e != cudaSuccess) return cuda_fail(e, "gint_rho_force: launch");
     h->last_stream = s;
@@ -222,6 +226,18 @@ extern "C" gint_status gint_rho_force(gint_handle h, const double *V_dev, const 
         return GINT_EINVAL;
     }
     return run_rho_force(h, V_dev, DM_dev, rho_dev, F_dev, prec, (cudaStream_t)stream);
+}
+
+extern "C" gint_status gint_strain_derivative(gint_handle h, const double *V_dev, const double *DM_dev,
+                                              double *dLde_dev, gint_prec prec, void *stream)
+{
+    gint_status st = check_handle(h, "gint_strain_derivative");
+    if (st != GINT_OK) return st;
+    if (!V_dev || !DM_dev || !dLde_dev || !valid_prec(prec)) {
+        set_error("gint_strain_derivative: null buffer or invalid precision");
+        return GINT_EINVAL;
+    }
+    return run_rho_force(h, V_dev, DM_dev, nullptr, nullptr, prec, (cudaStream_t)stream, dLde_dev);
 }
 
 extern "C" gint_status gint_vlocal_backward(gint_handle h, const double *V_dev, const double *gH_dev, double *gV_dev,

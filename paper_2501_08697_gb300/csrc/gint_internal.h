@@ -57,6 +57,7 @@ struct SInfo {
     const float *DM32;
     double *rho;
     double *F;
+    double *dLde;                  // 9 values: strain derivative (single-structure launches only)
     const float *poff;
     int grid[3];
     int pad;
@@ -166,7 +167,7 @@ gint_status build_geometry(gint_handle h, const double *tau, bool update_only);
 // kernel launchers (gint_simt.cu, gint_tc.cu, gint_api.cu)
 cudaError_t launch_vlocal_simt(const Plan &p, bool fp64, const double *V, double *H, cudaStream_t s, int nsm);
 cudaError_t launch_rho_force_simt(const Plan &p, bool fp64, const double *V, const double *DM,
-                                  double *rho, double *F, cudaStream_t s, int nsm);
+                                  double *rho, double *F, double *dLde, cudaStream_t s, int nsm);
 cudaError_t launch_vlocal_tc(const Plan &p, gint_prec prec, const SInfo &si0, const SInfo *sis, cudaStream_t s,
                              int nsm, int max_nb);
 cudaError_t launch_rho_force_tc(const Plan &p, gint_prec prec, const SInfo &si0, const SInfo *sis, bool rho,

@@ -167,7 +167,8 @@ __global__ void k_mirror(Plan P, double *H)
 
 template <typename T, bool RHO, bool FORCE>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_rho_force_simt(Plan P, const double *__restrict__ V, const double *__restrict__ DM, double *rho, double *F)
+    k_rho_force_simt(Plan P, const double *__restrict__ V, const double *__restrict__ DM, double *rho, double *F,
+                     double *dLde)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     SlotSh *sl = reinterpret_cast<SlotSh *>(smem);
@@ -181,6 +182,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     T *Ds = Psi + kRhoPts * kMaxNb;                             // [kDChunk][kMaxNb]
 
     const int tid = threadIdx.x;
+    // strain derivative: [0..8] Sum V grad_a phi . Psi d_b, [9] Sum V rho (this thread)
+    double sacc[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) sacc[k] = 0.0;
     for (int bi = blockIdx.x; bi < P.nbatches; bi += gridDim.x) {
         const Batch B = P.batches[bi];
         int n1, n2, n3;
@@ -283,8 +288,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 point_offset64(P, a, b, c, off);
                 const T *prow = Psi + p * kMaxNb + sl[s].orb_off;
                 T racc = T(0), gx = T(0), gy = T(0), gz = T(0);
+                T ddx, ddy, ddz;   // displacement r - tau - R of this (point, atom image)
                 if constexpr (sizeof(T) == 8) {
                     const double dx = sl[s].d0[0] + off[0], dy = sl[s].d0[1] + off[1], dz = sl[s].d0[2] + off[2];
+                    ddx = dx; ddy = dy; ddz = dz;
                     if (FORCE)
                         eval_orbitals<double, true>(P, sl[s].species, dx, dy, dz,
                                                     [&](int o, double v, double x, double y, double z) {
@@ -300,6 +307,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     split_f32(sl[s].d0[1], hy, ly); split_f32(off[1], oy, oyl);
                     split_f32(sl[s].d0[2], hz, lz); split_f32(off[2], oz, ozl);
                     float dx = (hx + ox) + (lx + oxl), dy = (hy + oy) + (ly + oyl), dz = (hz + oz) + (lz + ozl);
+                    ddx = dx; ddy = dy; ddz = dz;
                     if (FORCE)
                         eval_orbitals<float, true>(P, sl[s].species, dx, dy, dz,
                                                    [&](int o, float v, float x, float y, float z) {
@@ -314,9 +322,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (FORCE) {
                     const int64_t g = ((int64_t)(B.i0 + a) * P.grid[1] + (B.j0 + b)) * P.grid[2] + (B.k0 + c);
                     const double w2 = V[g];
-                    atomicAdd(&fsl[3 * s + 0], w2 * (double)gx);
-                    atomicAdd(&fsl[3 * s + 1], w2 * (double)gy);
-                    atomicAdd(&fsl[3 * s + 2], w2 * (double)gz);
+                    if (F) {
+                        atomicAdd(&fsl[3 * s + 0], w2 * (double)gx);
+                        atomicAdd(&fsl[3 * s + 1], w2 * (double)gy);
+                        atomicAdd(&fsl[3 * s + 2], w2 * (double)gz);
+                    }
+                    if (dLde) {
+                        const double gg[3] = {w2 * (double)gx, w2 * (double)gy, w2 * (double)gz};
+                        const double dd[3] = {(double)ddx, (double)ddy, (double)ddz};
+#pragma unroll
+                        for (int u = 0; u < 3; ++u)
+#pragma unroll
+                            for (int v = 0; v < 3; ++v) sacc[3 * u + v] += gg[u] * dd[v];
+                        sacc[9] += w2 * (double)racc;
+                    }
                 }
             }
             __syncthreads();
@@ -328,12 +347,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                     rho[g] = rhos[p];
                 }
         }
-        if (FORCE) {
+        if (FORCE && F) {
             __syncthreads();
             for (int e = tid; e < 3 * ns; e += kThreads) {
                 const int s = e / 3, q = e - 3 * s;
                 atomicAdd(&F[3 * sl[s].atom + q], 2.0 * P.dV * fsl[e]);
             }
+        }
+    }
+    if (FORCE && dLde) {
+        // dL/deps_ab = 2 dV Sum V grad_a phi . Psi d_b + delta_ab dV Sum V rho
+#pragma unroll
+        for (int k = 0; k < 10; ++k)
+#pragma unroll
+            for (int m = 16; m > 0; m >>= 1) sacc[k] += __shfl_xor_sync(0xffffffffu, sacc[k], m);
+        if ((tid & 31) == 0) {
+            for (int k = 0; k < 9; ++k)
+                atomicAdd(&dLde[k], 2.0 * P.dV * sacc[k] + ((k % 4) == 0 ? P.dV * sacc[9] : 0.0));
         }
     }
 }
@@ -396,33 +426,34 @@ cudaError_t launch_vlocal_simt(const Plan &P, bool fp64, const double *V, double
 }
 
 template <typename T>
-static cudaError_t launch_rf(const Plan &P, const double *V, const double *DM, double *rho, double *F, cudaStream_t s,
-                             int nsm)
+static cudaError_t launch_rf(const Plan &P, const double *V, const double *DM, double *rho, double *F, double *dLde,
+                             cudaStream_t s, int nsm)
 {
     size_t smem = rho_smem<T>();
     int grid = std::min(nsm, P.nbatches);
     cudaError_t e;
-    if (rho && F) {
+    const bool force = F || dLde;
+    if (rho && force) {
         e = cudaFuncSetAttribute(k_rho_force_simt<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_rho_force_simt<T, true, true><<<grid, kThreads, smem, s>>>(P, V, DM, rho, F);
+        k_rho_force_simt<T, true, true><<<grid, kThreads, smem, s>>>(P, V, DM, rho, F, dLde);
     } else if (rho) {
         e = cudaFuncSetAttribute(k_rho_force_simt<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_rho_force_simt<T, true, false><<<grid, kThreads, smem, s>>>(P, V, DM, rho, F);
+        k_rho_force_simt<T, true, false><<<grid, kThreads, smem, s>>>(P, V, DM, rho, F, dLde);
     } else {
         e = cudaFuncSetAttribute(k_rho_force_simt<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_rho_force_simt<T, false, true><<<grid, kThreads, smem, s>>>(P, V, DM, rho, F);
+        k_rho_force_simt<T, false, true><<<grid, kThreads, smem, s>>>(P, V, DM, rho, F, dLde);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_rho_force_simt(const Plan &P, bool fp64, const double *V, const double *DM, double *rho, double *F,
-                                  cudaStream_t s, int nsm)
+                                  double *dLde, cudaStream_t s, int nsm)
 {
     if (P.nbatches == 0) return cudaSuccess;
-    return fp64 ? launch_rf<double>(P, V, DM, rho, F, s, nsm) : launch_rf<float>(P, V, DM, rho, F, s, nsm);
+    return fp64 ? launch_rf<double>(P, V, DM, rho, F, dLde, s, nsm) : launch_rf<float>(P, V, DM, rho, F, dLde, s, nsm);
 }
 
 }  // namespace gint

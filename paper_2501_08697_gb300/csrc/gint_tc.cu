@@ -8,12 +8,14 @@
 // BF16x6); the products of total order <= 1 (TF32x3, BF16x3) or <= 2 (BF16x6) accumulate in
 // FP32 in tensor memory (TMEM); the cross-batch sums (block store, rho(r), forces) are FP64.
 //
-// One persistent CTA per SM, 20 warps (the producers carry most of the CUDA-core work):
-//   warps 0-11 producers: orbital values (FP32, spline x solid harmonic) into an FP32 staging
+// One persistent CTA per SM, 20 warps (5 per SM sub-partition, which leaves 96 registers a
+// thread; the producers carry most of the CUDA-core work):
+//   warps 0-10 producers: orbital values (FP32, spline x solid harmonic) into an FP32 staging
 //              tile, then split into the canonical K-major no-swizzle shared-memory layout
 //              (8-row x 16-byte core matrices; the K-direction core-matrix stride is padded
-//              to 144 bytes so 16-byte stores from a warp spread over all banks); thread 0
-//              also issues the MMAs and commits them to mbarriers.
+//              to 144 bytes so 16-byte stores from a warp spread over all banks).
+//   warp 11    one thread issues the MMAs of each chunk once the producers have arrived on
+//              the stage's barrier, and commits them to the stage's and accumulator's barriers.
 //   warps 12-19 epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes 32(w%4)..;
 //              the two warps of a lane quadrant share the columns or the atom images),
 //              then the FP64 scatter into the block store (vlocal) or rho(r)/force (rho).
@@ -31,12 +33,14 @@
 namespace gint {
 namespace {
 
-constexpr int kProd = 384;        // producer threads (12 warps)
+constexpr int kProd = 352;        // producer threads (warps 0-10)
+constexpr int kMma = kProd;       // the MMA-issue thread (warp 11)
+constexpr int kEpi0 = kProd + 32; // first epilogue thread (warp 12: TMEM lane quadrant = warp % 4)
 constexpr int kEpi = 256;         // epilogue threads (two warps per TMEM lane quadrant)
-constexpr int kThreadsTC = kProd + kEpi;
+constexpr int kThreadsTC = kEpi0 + kEpi;
 constexpr int kLBO = 144;         // bytes between core matrices along K
 constexpr int kTmemCols = 512;
-constexpr int kWin = 64;          // epilogue window (columns) of the rho kernel
+constexpr int kWin = 32;          // epilogue window (columns) of the rho kernel
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -216,11 +220,6 @@ __device__ __forceinline__ void unpack(int dims, int &n1, int &n2, int &n3)
     n3 = (dims >> 16) & 255;
 }
 
-__device__ __forceinline__ SInfo sinfo_of(const Batch &B, const SInfo &si0, const SInfo *sis)
-{
-    return sis ? sis[(unsigned)B.dims >> 24] : si0;
-}
-
 // structure info of the current batch, reloaded only when the structure id changes (a CTA's
 // contiguous batch range spans few structures)
 struct SInfoCache {
@@ -325,7 +324,9 @@ __device__ __forceinline__ int64_t grid_index(const SInfo &SI, const Batch &B, i
     return ((int64_t)(B.i0 + a) * SI.grid[1] + (B.j0 + b)) * SI.grid[2] + (B.k0 + c);
 }
 
-// role-uniform bounded wait: thread `leader` waits, the verdict is shared through `flag`
+// Role-uniform bounded wait: thread 0 of the role waits, the verdict is shared through `flag`.
+// The callers pass another barrier of the same role between two calls, so every thread has
+// read the flag before thread 0 writes it again.
 __device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, const Plan &P, int rtid, volatile int *flag,
                                           int barid, int nthr)
 {
@@ -335,9 +336,7 @@ __device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, const 
         *flag = ok ? 0 : 1;
     }
     named_sync(barid, nthr);
-    const bool ok = *flag == 0;
-    named_sync(barid, nthr);
-    return ok;
+    return *flag == 0;
 }
 
 __device__ __forceinline__ void load_species(const Plan &P, SpecSh *spec, int tid)
@@ -369,15 +368,15 @@ struct VSmem {
     static constexpr int ARR = arr_bytes<S>(256);         // one operand term (tile 1 reads rows 128..255)
     static constexpr int STAGE = 2 * S::NT * ARR;         // A terms then B terms
     static constexpr int NSTAGE = 2;
-    static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [192][KC]
+    static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [256][KC]
     static constexpr int OFF_PSLOT = OFF_STG + ROWS * KC * 4;               // PSlot[64]
     static constexpr int OFF_POFF = OFF_PSLOT + kMaxSlots * (int)sizeof(PSlot);  // float [128][6]
     static constexpr int OFF_V = OFF_POFF + kMaxBatchPts * 6 * 4;           // float [128]
     static constexpr int OFF_TBL = OFF_V + kMaxBatchPts * 4;                // int [64*64]
     static constexpr int OFF_INFO = OFF_TBL + kMaxSlots * kMaxSlots * 4;    // int [256]: slot | o << 8 | norb << 16
     static constexpr int OFF_TILE = OFF_INFO + kMaxNb * 4;                  // float [8][32][33]
-    static constexpr int OFF_BAR = OFF_TILE + 8 * 32 * 33 * 4;              // 8 mbarriers
-    static constexpr int OFF_MISC = OFF_BAR + 8 * 8;                        // tmem base, flags
+    static constexpr int OFF_BAR = OFF_TILE + 8 * 32 * 33 * 4;              // 16 mbarriers
+    static constexpr int OFF_MISC = OFF_BAR + 16 * 8;                       // tmem base, flags
     static constexpr int OFF_SPEC = OFF_MISC + 64;                          // SpecSh[kMaxSpecies]
     static constexpr int TOTAL = OFF_SPEC + kMaxSpecies * (int)sizeof(SpecSh);
 };
@@ -399,7 +398,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     float *tiles = reinterpret_cast<float *>(sm + L::OFF_TILE);
     SpecSh *spec = reinterpret_cast<SpecSh *>(sm + L::OFF_SPEC);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::OFF_BAR);
-    uint64_t *empty = bars, *accfull = bars + 2, *accempty = bars + 4, *fin = bars + 6;
+    uint64_t *empty = bars, *accfull = bars + 2, *accempty = bars + 4, *fin = bars + 6, *full = bars + 8;
     uint32_t *tmem_base = reinterpret_cast<uint32_t *>(sm + L::OFF_MISC);
     volatile int *pflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 4);
     volatile int *eflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 8);
@@ -414,6 +413,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         mbar_init(&accempty[0], kEpi);
         mbar_init(&accempty[1], kEpi);
         mbar_init(fin, 1);
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_base)),
@@ -427,10 +428,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     const int tile1 = nbuf == 2 ? 192 : 256;   // TMEM column of tile 1 within an accumulator
 
     if (tid < kProd) {
-        // ------------------------------------------------------------ producers + MMA issue
+        // ------------------------------------------------------------ producers
         const int pt = tid;
         int g = 0;  // chunk counter (stage = g & 1)
-        int it = 0; // batches with MMAs issued
         bool ok = true;
         SInfoCache sic(si0);
         CtaRange cr(P);
@@ -440,7 +440,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             unpack(B.dims, n1, n2, n3);
             const int ns = B.nslots, nb = B.nb, npb = n1 * n2 * n3;
             const int npad = (nb + 15) & ~15;
-            const int buf = nbuf == 2 ? (it & 1) : 0;
             if (nb == 0) continue;  // no orbital reaches this batch: nothing to add
             const SInfo SI = sic.get(B, sis);
             const float dVf = (float)SI.dV;
@@ -495,48 +494,65 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 }
                 fence_async_smem();
                 named_sync(1, kProd);
-                if (pt == 0) {
-                    if (ch == 0 && it >= nbuf) {
-                        // the epilogue of batch it - nbuf has released this accumulator
+                if (pt == 0) mbar_arrive(&full[stage]);   // chunk g is in shared memory
+            }
+        }
+    } else if (tid < kEpi0) {
+        // ------------------------------------------------------------ MMA issue (one thread)
+        // Follows the producers' chunk sequence: waits until chunk g is in stage g & 1 (and, at
+        // a batch's first chunk, until the epilogue has released the accumulator), issues the
+        // chunk's MMAs and commits them to the stage's and the accumulator's barriers.
+        if (tid == kMma) {
+            int g = 0, it = 0;
+            bool ok = true;
+            CtaRange cr(P);
+            for (int bi = 0; ok && cr.next(bi);) {
+                const Batch B = P.batches[bi];
+                int n1, n2, n3;
+                unpack(B.dims, n1, n2, n3);
+                const int nb = B.nb, npb = n1 * n2 * n3;
+                if (nb == 0) continue;
+                const int npad = (nb + 15) & ~15;
+                const int buf = nbuf == 2 ? (it & 1) : 0;
+                const int nch = (npb + KC - 1) / KC;
+                for (int ch = 0; ch < nch && ok; ++ch, ++g) {
+                    const int stage = g & 1;
+                    ok = !aborted(P) && mbar_wait(&full[stage], (g >> 1) & 1, P.spin_limit);
+                    if (ok && ch == 0 && it >= nbuf)   // the epilogue of batch it - nbuf is done
                         ok = !aborted(P) && mbar_wait(&accempty[buf], ((it / nbuf) - 1) & 1, P.spin_limit);
-                        if (!ok) report_timeout(P);
+                    if (!ok) {
+                        report_timeout(P);
+                        break;
                     }
-                    if (ok) {
-                        tc_fence_after();
-                        const uint32_t a0 = su32(base), b0 = su32(base + S::NT * L::ARR);
+                    tc_fence_after();
+                    const uint32_t a0 = su32(sm + stage * L::STAGE), b0 = a0 + S::NT * L::ARR;
 #pragma unroll
-                        for (int ks = 0; ks < S::KCM / 2; ++ks) {
-                            for (int t = 0; t < (nb > 128 ? 2 : 1); ++t) {
-                                const int N = t == 0 ? npad : npad - 128;
-                                const uint32_t id = idesc<S>(128, N);
-                                const uint32_t rowoff = t * 16 * SBO;
+                    for (int ks = 0; ks < S::KCM / 2; ++ks) {
+                        for (int t = 0; t < (nb > 128 ? 2 : 1); ++t) {
+                            const int N = t == 0 ? npad : npad - 128;
+                            const uint32_t id = idesc<S>(128, N);
+                            const uint32_t rowoff = t * 16 * SBO;
 #pragma unroll
-                                for (int q = 0; q < S::NPROD; ++q) {
-                                    const uint64_t da = sdesc(a0 + term(S::PA, q) * L::ARR + rowoff + ks * 2 * kLBO, SBO);
-                                    const uint64_t db = sdesc(b0 + term(S::PB, q) * L::ARR + rowoff + ks * 2 * kLBO, SBO);
-                                    const uint32_t acc = (ch == 0 && ks == 0 && q == 0) ? 0u : 1u;
-                                    umma<S::F16>(tmem + buf * 256 + t * tile1, da, db, id, acc);
-                                }
+                            for (int q = 0; q < S::NPROD; ++q) {
+                                const uint64_t da = sdesc(a0 + term(S::PA, q) * L::ARR + rowoff + ks * 2 * kLBO, SBO);
+                                const uint64_t db = sdesc(b0 + term(S::PB, q) * L::ARR + rowoff + ks * 2 * kLBO, SBO);
+                                const uint32_t acc = (ch == 0 && ks == 0 && q == 0) ? 0u : 1u;
+                                umma<S::F16>(tmem + buf * 256 + t * tile1, da, db, id, acc);
                             }
                         }
-                        umma_commit(&empty[stage]);
-                        if (ch == nch - 1) umma_commit(&accfull[buf]);
                     }
-                    // a failed wait set the status word; the next role_wait sees it and every
-                    // producer stops together
-                    ok = true;
+                    umma_commit(&empty[stage]);
+                    if (ch == nch - 1) umma_commit(&accfull[buf]);
                 }
+                ++it;
             }
-            ++it;
-        }
-        if (pt == 0) {
             // wait (bounded) for every MMA this thread issued before TMEM is released
             umma_commit(fin);
             if (!mbar_wait(fin, 0, kDrainBudget)) report_timeout(P);
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int et = tid - kProd, ew = et >> 5, lane = et & 31;
+        const int et = tid - kEpi0, ew = et >> 5, lane = et & 31;
         const int q = ew & 3, hh = ew >> 2;  // TMEM lane quadrant, column half
         int it = 0;
         SInfoCache sic(si0);
@@ -585,22 +601,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     const bool cv = nu < nb;
                     const int ci = info[cv ? nu : 0];
                     const int b = ci & 255, ob = (ci >> 8) & 255, nbo = ci >> 16;
-                    for (int r0 = 0; r0 < nrows; r0 += 8) {
-                        double *adr[8];
-                        float val[8];
-                        bool go[8];
-#pragma unroll
-                        for (int rr = 0; rr < 8; ++rr) {
-                            const int r = r0 + rr;
-                            const int ri2 = info[row0 + (r < nrows ? r : 0)];
-                            const int e = tbl[(ri2 & 255) * ns + b];
-                            go[rr] = cv && r < nrows && nu >= row0 + r && e >= 0;
-                            adr[rr] = H + (e >> 1) + ((ri2 >> 8) & 255) * nbo + ob;
-                            val[rr] = tl[lane * 33 + (r & 31)];
-                        }
-#pragma unroll
-                        for (int rr = 0; rr < 8; ++rr)
-                            if (go[rr]) red_add_f64(adr[rr], f2d_fast(val[rr]));
+                    // rows in runs of one atom image (warp-uniform): one block lookup per run,
+                    // then consecutive block rows are nbo doubles apart
+                    for (int r = 0; r < nrows;) {
+                        const int ri = info[row0 + r];
+                        const int oa = (ri >> 8) & 255;
+                        const int rend = min(nrows, r + (ri >> 16) - oa);
+                        const int e = tbl[(ri & 255) * ns + b];
+                        const bool blk = cv && e >= 0;
+                        double *base = H + (e >> 1) + (oa - r) * nbo + ob;
+                        const int rlim = min(rend, nu - row0 + 1);  // upper triangle: row <= nu
+#pragma unroll 4
+                        for (int r2 = r; r2 < rend; ++r2)
+                            if (blk && r2 < rlim) red_add_f64(base + r2 * nbo, f2d_fast(tl[lane * 33 + r2]));
+                        r = rend;
                     }
                     __syncwarp();
                 }
@@ -622,7 +636,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 template <class S>
 struct RSmem {
     static constexpr int KC = S::KCM * S::CG;              // orbitals per chunk
-    static constexpr int RING = KC == 16 ? 32 : KC;        // staging rows (orbital ring, see k_rho_tc)
+    static constexpr int RING = 64;                        // staging rows (orbital ring, see k_rho_tc)
+    static constexpr int EG = KC >= 32 ? 1 : 32 / KC;      // chunks per orbital evaluation
     static constexpr int ARR_A = arr_bytes<S>(kMaxBatchPts);
     static constexpr int ARR_B = arr_bytes<S>(kMaxNb);
     static constexpr int STAGE = S::NT * (ARR_A + ARR_B);
@@ -630,8 +645,7 @@ struct RSmem {
     static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [RING][128]
     static constexpr int OFF_PSLOT = OFF_STG + RING * kMaxBatchPts * 4;     // producer PSlot[64]
     static constexpr int OFF_POFF = OFF_PSLOT + kMaxSlots * (int)sizeof(PSlot);
-    static constexpr int OFF_TBL = OFF_POFF + kMaxBatchPts * 24;            // int [64*64]
-    static constexpr int OFF_OMAP = OFF_TBL + kMaxSlots * kMaxSlots * 4;    // oslot[256], oidx[256]
+    static constexpr int OFF_OMAP = OFF_POFF + kMaxBatchPts * 24;           // oslot[256], oidx[256]
     static constexpr int OFF_GBASE = OFF_OMAP + 2 * kMaxNb;                 // int [64][KC]: chunk gather bases
     static constexpr int OFF_GNA = OFF_GBASE + kMaxSlots * KC * 4;          // int [KC]: norb of column's slot
     static constexpr int OFF_EPSLOT = OFF_GNA + KC * 4;                     // epilogue PSlot[64]
@@ -639,8 +653,8 @@ struct RSmem {
     static constexpr int OFF_WIN = OFF_EPOFF + kMaxBatchPts * 24;           // float [8][kWin][32]
     static constexpr int OFF_RPART = OFF_WIN + 8 * kWin * 32 * 4;           // float [128]
     static constexpr int OFF_FACC = OFF_RPART + kMaxBatchPts * 4;           // double [64][3]
-    static constexpr int OFF_BAR = OFF_FACC + kMaxSlots * 3 * 8;
-    static constexpr int OFF_MISC = OFF_BAR + 8 * 8;
+    static constexpr int OFF_BAR = OFF_FACC + kMaxSlots * 3 * 8;             // 16 mbarriers
+    static constexpr int OFF_MISC = OFF_BAR + 16 * 8;
     static constexpr int OFF_SPEC = OFF_MISC + 64;
     static constexpr int TOTAL = OFF_SPEC + kMaxSpecies * (int)sizeof(SpecSh);
 };
@@ -650,13 +664,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     k_rho_tc(Plan P, SInfo si0, const SInfo *__restrict__ sis)
 {
     using L = RSmem<S>;
-    constexpr int KC = L::KC, RING = L::RING;
+    constexpr int KC = L::KC, RING = L::RING, EG = L::EG;
     constexpr int SBO = S::KCM * kLBO;
     extern __shared__ __align__(1024) unsigned char sm[];
     float *stg = reinterpret_cast<float *>(sm + L::OFF_STG);
     PSlot *ps = reinterpret_cast<PSlot *>(sm + L::OFF_PSLOT);
     float *poff = reinterpret_cast<float *>(sm + L::OFF_POFF);
-    int *tbl = reinterpret_cast<int *>(sm + L::OFF_TBL);
     unsigned char *oslot = sm + L::OFF_OMAP, *oidx = oslot + kMaxNb;
     int *gbase = reinterpret_cast<int *>(sm + L::OFF_GBASE);
     int *gna = reinterpret_cast<int *>(sm + L::OFF_GNA);
@@ -667,7 +680,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     SpecSh *spec = reinterpret_cast<SpecSh *>(sm + L::OFF_SPEC);
     double *facc = reinterpret_cast<double *>(sm + L::OFF_FACC);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::OFF_BAR);
-    uint64_t *empty = bars, *accfull = bars + 2, *accempty = bars + 4, *fin = bars + 6;
+    uint64_t *empty = bars, *accfull = bars + 2, *accempty = bars + 4, *fin = bars + 6, *full = bars + 8;
     uint32_t *tmem_base = reinterpret_cast<uint32_t *>(sm + L::OFF_MISC);
     volatile int *pflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 4);
     volatile int *eflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 8);
@@ -682,6 +695,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         mbar_init(&accempty[0], kEpi);
         mbar_init(&accempty[1], kEpi);
         mbar_init(fin, 1);
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_base)),
@@ -696,15 +711,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     if (tid < kProd) {
         // ------------------------------------------------------------ producers + MMA issue
         const int pt = tid;
-        int g = 0, it = 0;
+        int g = 0;
         bool ok = true;
-        // Orbital ring: when every slot fits (KC + norb - 1 <= RING rows), the orbitals of a slot
-        // are evaluated once, in the chunk where the slot starts, into staging rows
-        // (orbital index) mod RING, and later chunks read the rows they carry over.  Otherwise
-        // each chunk evaluates every slot overlapping it and keeps its own columns.
+        // Orbital ring: when every slot fits (EG KC + norb - 1 <= RING rows), the orbitals of a
+        // slot are evaluated once, every EG chunks for the slots that start in those chunks, into
+        // staging rows (orbital index) mod RING; later chunks read the rows carried over.
+        // Otherwise each chunk evaluates every slot overlapping it and keeps its own columns.
         int maxnorb = 0;
         for (int i = 0; i < P.nspecies; ++i) maxnorb = max(maxnorb, P.sp[i].norb);
-        const bool ring = KC + maxnorb - 1 <= RING;
+        const bool ring = EG * KC + maxnorb - 1 <= RING;
         SInfoCache sic(si0);
         CtaRange cr(P);
         for (int bi = 0; ok && cr.next(bi);) {
@@ -713,13 +728,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             unpack(B.dims, n1, n2, n3);
             const int ns = B.nslots, nb = B.nb, npb = n1 * n2 * n3;
             const int npad = (nb + 15) & ~15;
-            const int buf = it & 1;
             if (nb == 0) continue;  // the epilogue writes rho = 0 there
             const SInfo SI = sic.get(B, sis);
             const float *__restrict__ DM = SI.DM32;
+            const int *__restrict__ tbl = P.tbl + B.tbl;
             named_sync(1, kProd);
             load_geom(P, SI, B, ps, poff, pt, kProd);
-            for (int e = pt; e < ns * ns; e += kProd) tbl[e] = P.tbl[B.tbl + e];
             named_sync(1, kProd);
             for (int s = pt; s < ns; s += kProd)
                 for (int o = 0; o < ps[s].norb; ++o) {
@@ -736,8 +750,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 const int rbase = ring ? (k0 & (RING - 1)) : 0;
                 // phase 1: orbital values at all points -> staging rows
                 if (ring) {
-                    const int s_first = ps[s_lo].off >= k0 ? s_lo : s_lo + 1;  // slots starting here
-                    const int nsc = s_hi - s_first + 1;
+                    // at the first chunk of each group: the slots starting in the group's chunks
+                    const int e1 = min(k0 + EG * KC, nb);
+                    const int s_first = ps[s_lo].off >= k0 ? s_lo : s_lo + 1;
+                    const int nsc = ch % EG == 0 ? oslot[e1 - 1] - s_first + 1 : 0;
                     for (int w = pt; w < kMaxBatchPts * nsc; w += kProd) {
                         const int p = w % kMaxBatchPts, s = s_first + w / kMaxBatchPts;
                         const PSlot sl = ps[s];
@@ -785,7 +801,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     int v = -1;
                     if (mu < nb) {
                         const int a = oslot[mu];
-                        const int e = tbl[b * ns + a];
+                        const int e = __ldg(tbl + b * ns + a);
                         if (e >= 0) v = (e >> 1) + oidx[mu];
                     }
                     gbase[w] = v;
@@ -839,47 +855,65 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 }
                 fence_async_smem();
                 named_sync(1, kProd);
-                if (pt == 0) {
-                    if (ch == 0 && it >= 2) {
-                        ok = !aborted(P) && mbar_wait(&accempty[buf], ((it >> 1) - 1) & 1, P.spin_limit);
-                        if (!ok) report_timeout(P);
-                    }
-                    if (ok) {
-                        tc_fence_after();
-                        const uint32_t a0 = su32(base), b0 = su32(base + S::NT * L::ARR_A);
-                        const uint32_t id = idesc<S>(128, npad);
-#pragma unroll
-                        for (int ks = 0; ks < S::KCM / 2; ++ks) {
-#pragma unroll
-                            for (int q = 0; q < S::NPROD; ++q) {
-                                const uint64_t da = sdesc(a0 + term(S::PA, q) * L::ARR_A + ks * 2 * kLBO, SBO);
-                                const uint64_t db = sdesc(b0 + term(S::PB, q) * L::ARR_B + ks * 2 * kLBO, SBO);
-                                const uint32_t acc = (ch == 0 && ks == 0 && q == 0) ? 0u : 1u;
-                                umma<S::F16>(tmem + buf * 256, da, db, id, acc);
-                            }
-                        }
-                        umma_commit(&empty[stage]);
-                        if (ch == nch - 1) umma_commit(&accfull[buf]);
-                    }
-                    // a failed wait set the status word; the next role_wait sees it and every
-                    // producer stops together
-                    ok = true;
-                }
+                if (pt == 0) mbar_arrive(&full[stage]);   // chunk g is in shared memory
             }
-            ++it;
         }
-        if (pt == 0) {
+    } else if (tid < kEpi0) {
+        // ------------------------------------------------------------ MMA issue (one thread)
+        if (tid == kMma) {
+            int g = 0, it = 0;
+            bool ok = true;
+            CtaRange cr(P);
+            for (int bi = 0; ok && cr.next(bi);) {
+                const int nb = P.batches[bi].nb;
+                if (nb == 0) continue;
+                const int npad = (nb + 15) & ~15;
+                const int buf = it & 1;
+                const int nch = (nb + KC - 1) / KC;
+                const uint32_t id = idesc<S>(128, npad);
+                for (int ch = 0; ch < nch && ok; ++ch, ++g) {
+                    const int stage = g & 1;
+                    ok = !aborted(P) && mbar_wait(&full[stage], (g >> 1) & 1, P.spin_limit);
+                    if (ok && ch == 0 && it >= 2)   // the epilogue of batch it - 2 is done
+                        ok = !aborted(P) && mbar_wait(&accempty[buf], ((it >> 1) - 1) & 1, P.spin_limit);
+                    if (!ok) {
+                        report_timeout(P);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = su32(sm + stage * L::STAGE), b0 = a0 + S::NT * L::ARR_A;
+#pragma unroll
+                    for (int ks = 0; ks < S::KCM / 2; ++ks) {
+#pragma unroll
+                        for (int q = 0; q < S::NPROD; ++q) {
+                            const uint64_t da = sdesc(a0 + term(S::PA, q) * L::ARR_A + ks * 2 * kLBO, SBO);
+                            const uint64_t db = sdesc(b0 + term(S::PB, q) * L::ARR_B + ks * 2 * kLBO, SBO);
+                            const uint32_t acc = (ch == 0 && ks == 0 && q == 0) ? 0u : 1u;
+                            umma<S::F16>(tmem + buf * 256, da, db, id, acc);
+                        }
+                    }
+                    umma_commit(&empty[stage]);
+                    if (ch == nch - 1) umma_commit(&accfull[buf]);
+                }
+                ++it;
+            }
             umma_commit(fin);
             if (!mbar_wait(fin, 0, kDrainBudget)) report_timeout(P);
         }
     } else {
         // ------------------------------------------------------------ epilogue: rho and force
         // warp (q, hh): TMEM lane quadrant q (points 32q..32q+31), atom images s with s % 2 == hh
-        const int et = tid - kProd, ew = et >> 5, lane = et & 31;
+        const int et = tid - kEpi0, ew = et >> 5, lane = et & 31;
         const int q = ew & 3, hh = ew >> 2;
         const int p = q * 32 + lane;  // TMEM lane = point of the batch
         float *w = win + ew * kWin * 32;
         int it = 0;
+        // strain derivative (single-structure launches): [0..8] Sum V grad_a phi . Psi d_b,
+        // [9] Sum V rho, over this thread's points and atom images
+        const bool strain = FORCE && si0.dLde != nullptr && sis == nullptr;
+        double sacc[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) sacc[k] = 0.0;
         SInfoCache sic(si0);
         CtaRange cr(P);
         for (int bi = 0; cr.next(bi);) {
@@ -907,37 +941,57 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 gi = grid_index(SI, B, p, n2, n3);
                 if (FORCE) vp = d2f(SI.V[gi]);
             }
+            float po[6];   // this point's offset from the batch origin (hi, lo)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) po[c] = epoff[6 * (pv ? p : 0) + c];
             float racc = 0.f;
+            float st[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) st[k] = 0.f;
             int w0 = -1000, wn = 0;
             for (int s = hh; s < ns; s += 2) {
                 const PSlot sl = eps[s];
-                if (sl.off < w0 || sl.off + sl.norb > w0 + wn) {
-                    w0 = sl.off & ~15;
-                    wn = ((sl.off + sl.norb - w0) + 15) & ~15;
-                    for (int c = 0; c < wn; c += 16) {
-                        float v[16];
-                        tmem_ld16(trow + (uint32_t)(w0 + c), v);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) w[(c + j) * 32 + lane] = v[j];
-                    }
-                }
-                const float *col = w + (sl.off - w0) * 32 + lane;
                 float fx = 0.f, fy = 0.f, fz = 0.f;
-                if (pv) {
-                    float dx, dy, dz;
-                    disp(sl, epoff + 6 * p, dx, dy, dz);
-                    if (FORCE)
-                        eval_phigrad_f32(spec[sl.species], P.coef32, dx, dy, dz,
-                                         [&](int o, float v, float gx, float gy, float gz) {
-                                                       const float y = col[o * 32];
-                                                       racc += v * y;
-                                                       fx += gx * y; fy += gy * y; fz += gz * y;
-                                                   });
-                    else
-                        eval_phi_f32(spec[sl.species], P.coef32, dx, dy, dz,
-                                     [&](int o, float v) { racc += v * col[o * 32]; });
+                float dx = 0.f, dy = 0.f, dz = 0.f;
+                if (pv) disp(sl, po, dx, dy, dz);
+                // orbitals [oa, ob) of the slot whose columns fit the window (all of them unless
+                // the slot has more than 17 orbitals)
+                for (int oa = 0; oa < sl.norb;) {
+                    const int ob = min(sl.norb, ((sl.off + oa) & ~15) + kWin - sl.off);
+                    if (sl.off + oa < w0 || sl.off + ob > w0 + wn) {
+                        w0 = (sl.off + oa) & ~15;
+                        wn = ((sl.off + ob - w0) + 15) & ~15;
+                        for (int c = 0; c < wn; c += 16) {
+                            float v[16];
+                            tmem_ld16(trow + (uint32_t)(w0 + c), v);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) w[(c + j) * 32 + lane] = v[j];
+                        }
+                    }
+                    const int cb = sl.off - w0;   // window column of orbital o: cb + o
+                    if (pv) {
+                        if (FORCE)
+                            eval_phigrad_f32(spec[sl.species], P.coef32, dx, dy, dz,
+                                             [&](int o, float v, float gx, float gy, float gz) {
+                                                 if (o >= oa && o < ob) {
+                                                     const float y = w[(cb + o) * 32 + lane];
+                                                     racc += v * y;
+                                                     fx += gx * y; fy += gy * y; fz += gz * y;
+                                                 }
+                                             });
+                        else
+                            eval_phi_f32(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) {
+                                if (o >= oa && o < ob) racc += v * w[(cb + o) * 32 + lane];
+                            });
+                    }
+                    oa = ob;
                 }
-                if (FORCE) {
+                if (strain) {
+                    st[0] += fx * dx; st[1] += fx * dy; st[2] += fx * dz;
+                    st[3] += fy * dx; st[4] += fy * dy; st[5] += fy * dz;
+                    st[6] += fz * dx; st[7] += fz * dy; st[8] += fz * dz;
+                }
+                if (FORCE && SI.F) {
                     fx *= vp; fy *= vp; fz *= vp;
 #pragma unroll
                     for (int m = 16; m > 0; m >>= 1) {
@@ -957,10 +1011,25 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             if (RHO && hh == 1) rpart[p] = racc;
             named_sync(2, kEpi);
             if (RHO && hh == 0 && pv) SI.rho[gi] = f2d(racc + rpart[p]);
-            if (FORCE)
+            if (FORCE && SI.F)
                 for (int e = et; e < 3 * ns; e += kEpi)
                     red_add_f64(&SI.F[3 * eps[e / 3].atom + e % 3], 2.0 * SI.dV * facc[e]);
+            if (strain && pv) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) sacc[k] += f2d(vp * st[k]);
+                sacc[9] += f2d(vp * racc);
+            }
             ++it;
+        }
+        if (strain) {
+            // dL/deps_ab = 2 dV Sum V grad_a phi . Psi d_b + delta_ab dV Sum V rho
+#pragma unroll
+            for (int k = 0; k < 10; ++k)
+#pragma unroll
+                for (int m = 16; m > 0; m >>= 1) sacc[k] += __shfl_xor_sync(0xffffffffu, sacc[k], m);
+            if (lane == 0)
+                for (int k = 0; k < 9; ++k)
+                    red_add_f64(&si0.dLde[k], 2.0 * si0.dV * sacc[k] + ((k % 4) == 0 ? si0.dV * sacc[9] : 0.0));
         }
     }
     tc_fence_before();
@@ -971,12 +1040,30 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     }
 }
 
+// Ask for the smallest shared-memory carveout that holds `smem` bytes, so the rest of the
+// unified L1/shared storage caches the spline records.
+template <class K>
+cudaError_t set_smem(K kernel, int smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    static const int cfg[] = {0, 8, 16, 32, 64, 100, 132, 164, 196, 228};   // KiB
+    const int need = (smem + 1024 + 1023) / 1024;                         // + the driver's 1 KiB
+    int kib = 228;
+    for (int c : cfg)
+        if (c >= need) {
+            kib = c;
+            break;
+        }
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, kib * 100 / 228);
+}
+
 template <class S>
 cudaError_t vlocal_launch(const Plan &P, const SInfo &si0, const SInfo *sis, cudaStream_t s, int nsm, int max_nb)
 {
     constexpr int smem = VSmem<S>::TOTAL;
     static_assert(smem <= 232448, "vlocal shared memory");
-    cudaError_t e = cudaFuncSetAttribute(k_vlocal_tc<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = set_smem(k_vlocal_tc<S>, smem);
     if (e != cudaSuccess) return e;
     const int grid = P.rng ? P.npart : std::min(nsm, P.nbatches);
     k_vlocal_tc<S><<<grid, kThreadsTC, smem, s>>>(P, si0, sis, max_nb <= 192 ? 2 : 1);
@@ -988,7 +1075,7 @@ cudaError_t rho_launch3(const Plan &P, const SInfo &si0, const SInfo *sis, cudaS
 {
     constexpr int smem = RSmem<S>::TOTAL;
     static_assert(smem <= 232448, "rho shared memory");
-    cudaError_t e = cudaFuncSetAttribute(k_rho_tc<S, R, Fo>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = set_smem(k_rho_tc<S, R, Fo>, smem);
     if (e != cudaSuccess) return e;
     const int grid = P.rng ? P.npart : std::min(nsm, P.nbatches);
     k_rho_tc<S, R, Fo><<<grid, kThreadsTC, smem, s>>>(P, si0, sis);

@@ -20,7 +20,8 @@ PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3, "bf16x6": 4}
 PREC_NAME = {v: k for k, v in PREC.items()}
 
 EXPORTS = ["gint_setup", "gint_destroy", "gint_block_layout", "gint_get_info", "gint_update_positions",
-           "gint_vlocal", "gint_rho", "gint_force", "gint_rho_force", "gint_vlocal_backward", "gint_charge",
+           "gint_vlocal", "gint_rho", "gint_force", "gint_rho_force", "gint_strain_derivative",
+           "gint_vlocal_backward", "gint_charge",
            "gint_block_dot",
            "gint_block_dot_noalloc", "gint_run_host", "gint_batch_create", "gint_batch_launch", "gint_batch_destroy",
            "gint_autotune", "gint_batched", "gint_get_status", "gint_last_error"]
@@ -79,6 +80,7 @@ def load(build_if_missing: bool = True):
         lib.gint_rho.argtypes = [vp, vp, vp, i32, vp]
         lib.gint_force.argtypes = [vp, vp, vp, vp, i32, vp]
         lib.gint_rho_force.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+        lib.gint_strain_derivative.argtypes = [vp, vp, vp, vp, i32, vp]
         lib.gint_vlocal_backward.argtypes = [vp, vp, vp, vp, vp, i32, vp]
         lib.gint_charge.argtypes = [vp, vp, vp, vp]
         lib.gint_block_dot.argtypes = [vp, vp, vp, vp, vp]
@@ -234,6 +236,12 @@ def gint_force(h: Handle, V, DM, F, prec="fp64", stream=None):
 
 def gint_rho_force(h: Handle, V, DM, rho, F, prec="fp64", stream=None):
     _check(load().gint_rho_force(h.ptr, _ptr(V), _ptr(DM), _ptr(rho), _ptr(F), _prec(prec), _stream(stream)))
+
+
+def gint_strain_derivative(h: Handle, V, DM, dLde, prec="fp64", stream=None):
+    """dLde (device, 9 doubles, row-major) <- dL/deps for L = <DM, V_mu,nu>; the grid part of
+    the stress sigma = -dL/deps / Omega."""
+    _check(load().gint_strain_derivative(h.ptr, _ptr(V), _ptr(DM), _ptr(dLde), _prec(prec), _stream(stream)))
 
 
 def gint_vlocal_backward(h: Handle, V, gH, gV, gtau, prec="fp64", stream=None):

@@ -60,3 +60,10 @@ def oracle_full(name):
     rho = o.rho(DM)
     F = o.force(V, DM)
     return dict(st=st, V=V, keys=keys, offs=offs, DM=DM, H=H, rho=rho, F=F, oracle=o)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_strain(name):
+    """Oracle dL/deps (3x3) for a case small enough to run in full."""
+    ref = oracle_full(name)
+    return ref["oracle"].dLdeps(ref["V"], ref["DM"])

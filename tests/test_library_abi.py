@@ -49,6 +49,29 @@ def test_loads_with_ctypes(lib_path):
     assert lib.gint_last_error() is not None
 
 
+def _param_counts():
+    src = open(os.path.join(ROOT, "include", "gint.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(gint_[a-z_]+)\s*\(([^()]*)\)\s*;", src):
+        args = m.group(2).strip()
+        out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_every_binding_declares_its_argument_types(lib_path):
+    """ctypes passes undeclared arguments as C int: a 64-bit device pointer would be cut to 32
+    bits.  Every entry point therefore has argtypes, as many as the header declares."""
+    lib = G.load()
+    counts = _param_counts()
+    for name in G.EXPORTS:
+        fn = getattr(lib, name)
+        if counts.get(name, 0) == 0:
+            continue
+        assert fn.argtypes is not None, name
+        assert len(fn.argtypes) == counts[name], (name, len(fn.argtypes), counts[name])
+
+
 def test_setup_without_gpu_fails_loudly():
     import torch
     if torch.cuda.is_available():

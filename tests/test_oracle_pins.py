@@ -328,6 +328,32 @@ def test_force_matches_central_differences(si8_small):
     assert np.allclose(o.force(V, DM), -g)
 
 
+def test_strain_derivative_matches_central_differences(si8_small):
+    """The stress term: dL/deps from grad phi (x) d plus the dV scaling equals central
+    differences (h = 1e-4) of L = <rho_mu,nu, V_mu,nu(eps)> when cell, atoms and grid are
+    strained by x -> (1 + eps) x with the grid values of V and rho_mu,nu fixed (Eq. stress:
+    sigma = -dE/deps / Omega).  Diagonal, off-diagonal and both off-diagonal orders."""
+    st, o, keys, offs, V, DM, H = si8_small
+    g = o.dLdeps(V, DM)
+    h = 1e-4
+    for a, b in ((0, 0), (2, 2), (0, 1), (1, 0), (2, 0)):
+        Ls = []
+        for sgn in (1, -1):
+            eps = np.zeros((3, 3))
+            eps[a, b] = sgn * h
+            M = np.eye(3) + eps
+            o2 = Oracle(st.cell @ M.T, st.species, st.tau @ M.T, st.tables, st.grid)
+            k2, _ = o2.pairs()
+            assert np.array_equal(k2, keys)
+            Ls.append((DM * o2.vlocal(V)).sum())
+        fd = (Ls[0] - Ls[1]) / (2 * h)
+        assert fd == pytest.approx(g[a, b], rel=1e-6, abs=1e-8 * np.abs(g).max())
+    # the trace part: an isotropic strain only rescales the volume element if the orbitals
+    # were rigid, so dL/deps_aa - L is the basis-function part alone
+    L = (DM * H).sum()
+    assert np.trace(g) != pytest.approx(3 * L, rel=1e-3)
+
+
 def test_density_matrix_generator_is_block_symmetric(si8_small):
     st, o, keys, offs, V, DM, H = si8_small
     part = S.partner_index(keys)

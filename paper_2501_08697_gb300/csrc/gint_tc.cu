@@ -94,6 +94,18 @@ __device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_
                      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// asynchronous global -> shared copies (completion: cp_async_wait_all + a barrier)
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // FP64 add to global memory without a return value (the scatters never read the old value)
 __device__ __forceinline__ void red_add_f64(double *a, double v)
 {
@@ -208,10 +220,15 @@ __host__ __device__ constexpr uint32_t idesc(int M, int N)
 }
 
 // ------------------------------------------------------------------ shared batch metadata
+// An atom image of the batch in shared memory: the first 16 bytes and dh/dl as in Slot (so
+// they can be copied asynchronously), padded to 48 bytes for 16-byte aligned copies.
 struct PSlot {
-    int species, off, norb, atom;
+    int atom, species, off, norb;
     float dh[3], dl[3];
+    float pad[2];
 };
+static_assert(sizeof(PSlot) == 48, "PSlot layout");
+static_assert(offsetof(Slot, dh) == 40 && sizeof(Slot) == 64, "Slot layout");
 
 __device__ __forceinline__ void unpack(int dims, int &n1, int &n2, int &n3)
 {
@@ -299,6 +316,46 @@ __device__ __forceinline__ void load_geom(const Plan &P, const SInfo &SI, const 
     }
 }
 
+// Start copying the geometry of batch B (its atom images, point offsets and, when vd is not
+// null, the potential at its points) into shared memory; the calling role waits with
+// cp_async_wait_all and a barrier before reading it.
+__device__ __forceinline__ void geom_async(const Plan &P, const SInfo *sis, const SInfo &si0, const Batch &B,
+                                           PSlot *ps, float *poff, double *vd, int tid, int nthr)
+{
+    const double *V = si0.V;
+    const float *ptab = si0.poff;
+    int g1 = si0.grid[1], g2 = si0.grid[2];
+    if (sis) {
+        const SInfo &S = sis[(unsigned)B.dims >> 24];
+        V = S.V;
+        ptab = S.poff;
+        g1 = S.grid[1];
+        g2 = S.grid[2];
+    }
+    for (int w = tid; w < B.nslots * 4; w += nthr) {
+        const int s = w >> 2, part = w & 3;
+        const char *src = reinterpret_cast<const char *>(P.slots + B.slot0 + s);
+        char *dst = reinterpret_cast<char *>(ps + s);
+        if (part == 0) cp_async16(dst, src);                                 // atom .. norb
+        else cp_async8(dst + 8 + 8 * part, src + 32 + 8 * part);            // dh, dl
+    }
+    int n1, n2, n3;
+    n1 = B.dims & 255;
+    n2 = (B.dims >> 8) & 255;
+    n3 = (B.dims >> 16) & 255;
+    const int np = n1 * n2 * n3;
+    for (int w = tid; w < np * 4; w += nthr) {
+        const int p = w >> 2, part = w & 3;
+        const int c = p % n3, b = (p / n3) % n2, a = p / (n3 * n2);
+        if (part < 3) {
+            cp_async8(poff + 6 * p + 2 * part, ptab + ((a * kPoffDim + b) * kPoffDim + c) * 6 + 2 * part);
+        } else if (vd) {
+            cp_async8(vd + p, V + ((int64_t)(B.i0 + a) * g1 + (B.j0 + b)) * g2 + (B.k0 + c));
+        }
+    }
+    cp_async_commit();
+}
+
 // FP32 -> FP64 with integer operations (exact for normal numbers; subnormals flush to 0)
 __device__ __forceinline__ double f2d(float f)
 {
@@ -369,9 +426,10 @@ struct VSmem {
     static constexpr int STAGE = 2 * S::NT * ARR;         // A terms then B terms
     static constexpr int NSTAGE = 2;
     static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [256][KC]
-    static constexpr int OFF_PSLOT = OFF_STG + ROWS * KC * 4;               // PSlot[64]
-    static constexpr int OFF_POFF = OFF_PSLOT + kMaxSlots * (int)sizeof(PSlot);  // float [128][6]
-    static constexpr int OFF_V = OFF_POFF + kMaxBatchPts * 6 * 4;           // float [128]
+    static constexpr int OFF_PSLOT = OFF_STG + ROWS * KC * 4;               // PSlot[2][64]
+    static constexpr int OFF_POFF = OFF_PSLOT + 2 * kMaxSlots * (int)sizeof(PSlot);  // float [2][128][6]
+    static constexpr int OFF_VD = OFF_POFF + 2 * kMaxBatchPts * 6 * 4;      // double [2][128]
+    static constexpr int OFF_V = OFF_VD + 2 * kMaxBatchPts * 8;             // float [128]
     static constexpr int OFF_TBL = OFF_V + kMaxBatchPts * 4;                // int [64*64]
     static constexpr int OFF_INFO = OFF_TBL + kMaxSlots * kMaxSlots * 4;    // int [256]: slot | o << 8 | norb << 16
     static constexpr int OFF_TILE = OFF_INFO + kMaxNb * 4;                  // float [8][32][33]
@@ -390,8 +448,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     constexpr int SBO = S::KCM * kLBO;
     extern __shared__ __align__(1024) unsigned char sm[];
     float *stg = reinterpret_cast<float *>(sm + L::OFF_STG);
-    PSlot *ps = reinterpret_cast<PSlot *>(sm + L::OFF_PSLOT);
-    float *poff = reinterpret_cast<float *>(sm + L::OFF_POFF);
+    PSlot *psb = reinterpret_cast<PSlot *>(sm + L::OFF_PSLOT);
+    float *poffb = reinterpret_cast<float *>(sm + L::OFF_POFF);
+    double *vdb = reinterpret_cast<double *>(sm + L::OFF_VD);
     float *vs = reinterpret_cast<float *>(sm + L::OFF_V);
     int *tbl = reinterpret_cast<int *>(sm + L::OFF_TBL);
     int *info = reinterpret_cast<int *>(sm + L::OFF_INFO);
@@ -433,21 +492,35 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         int g = 0;  // chunk counter (stage = g & 1)
         bool ok = true;
         SInfoCache sic(si0);
+        // The geometry of the next batch is copied asynchronously into the other half of the
+        // double-buffered slot / offset / potential arrays while this batch is computed.
         CtaRange cr(P);
-        for (int bi = 0; ok && cr.next(bi);) {
+        int bi = 0, cur = 0;
+        bool have = cr.next(bi);
+        if (have) geom_async(P, sis, si0, P.batches[bi], psb, poffb, vdb, pt, kProd);
+        for (; ok && have; have = cr.next(bi), cur ^= 1) {
             const Batch B = P.batches[bi];
             int n1, n2, n3;
             unpack(B.dims, n1, n2, n3);
             const int ns = B.nslots, nb = B.nb, npb = n1 * n2 * n3;
             const int npad = (nb + 15) & ~15;
-            if (nb == 0) continue;  // no orbital reaches this batch: nothing to add
+            CtaRange peek = cr;
+            int bn = 0;
+            const bool more = peek.next(bn);
+            const Batch Bn = P.batches[more ? bn : bi];
+            const PSlot *ps = psb + cur * kMaxSlots;
+            const float *poff = poffb + cur * kMaxBatchPts * 6;
+            cp_async_wait_all();
+            named_sync(1, kProd);   // this batch's geometry is in buffer cur; buffer cur ^ 1 is free
+            if (nb == 0) {          // no orbital reaches this batch: nothing to add
+                if (more) geom_async(P, sis, si0, Bn, psb + (cur ^ 1) * kMaxSlots, poffb + (cur ^ 1) * kMaxBatchPts * 6,
+                                     vdb + (cur ^ 1) * kMaxBatchPts, pt, kProd);
+                continue;
+            }
             const SInfo SI = sic.get(B, sis);
             const float dVf = (float)SI.dV;
-            named_sync(1, kProd);
-            load_geom(P, SI, B, ps, poff, pt, kProd);
             for (int p = pt; p < kMaxBatchPts; p += kProd)
-                vs[p] = p < npb ? d2f(SI.V[grid_index(SI, B, p, n2, n3)]) * dVf : 0.f;
-            named_sync(1, kProd);
+                vs[p] = p < npb ? d2f(vdb[cur * kMaxBatchPts + p]) * dVf : 0.f;
             const int nch = (npb + KC - 1) / KC;
             for (int ch = 0; ch < nch && ok; ++ch, ++g) {
                 const int stage = g & 1;
@@ -465,6 +538,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         for (int o = 0; o < sl.norb; ++o) col[o * KC] = 0.f;
                     }
                 }
+                if (ch == 0 && more)
+                    geom_async(P, sis, si0, Bn, psb + (cur ^ 1) * kMaxSlots, poffb + (cur ^ 1) * kMaxBatchPts * 6,
+                               vdb + (cur ^ 1) * kMaxBatchPts, pt, kProd);
                 if (g >= 2) ok = role_wait(&empty[stage], ((g >> 1) - 1) & 1, P, pt, pflag, 1, kProd);
                 else named_sync(1, kProd);
                 if (!ok) break;
@@ -497,6 +573,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 if (pt == 0) mbar_arrive(&full[stage]);   // chunk g is in shared memory
             }
         }
+        cp_async_wait_all();   // no copy may be in flight when the CTA exits
     } else if (tid < kEpi0) {
         // ------------------------------------------------------------ MMA issue (one thread)
         // Follows the producers' chunk sequence: waits until chunk g is in stage g & 1 (and, at

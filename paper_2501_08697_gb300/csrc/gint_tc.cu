@@ -74,6 +74,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
                      : "memory");
         if (ok) return true;
         if (clock64() - t0 > budget) return false;
+        __nanosleep(128);   // back off: a spinning warp takes issue slots from the working ones
     }
 }
 

@@ -118,7 +118,7 @@ typedef struct {
     double flops_dense;    /* 2 * Sum_b npts_b * nb_b^2: the dense vlocal per-batch contraction */
     int64_t nbatches_rho;  /* rho/force grid batches */
     int max_orbitals_rho;  /* largest rho/force per-batch orbital count */
-    int reserved;
+    int nbasis;            /* orbitals of the cell, Sum_I norb(I) (dense k-space matrix order) */
     double flops_dense_rho;/* 2 * Sum_b npts_b * nb_b^2 over the rho/force batches */
 } gint_info_t;
 
@@ -180,6 +180,23 @@ gint_status gint_rho_force(gint_handle h, const double *V_dev, const double *DM_
  * Asynchronous on `stream`; errors as gint_force. */
 gint_status gint_strain_derivative(gint_handle h, const double *V_dev, const double *DM_dev,
                                    double *dLde_dev, gint_prec prec, void *stream);
+
+/* Folding into momentum space (Sec. IV.B): Xk[q] = Sum_R X(R) exp(i k_q.R) for the block store
+ * X (device, block layout), R = n1 a1 + n2 a2 + n3 a3 of each block key, k_q.R = 2 pi kappa_q.n.
+ *   kfrac  host, nk x 3: k points in fractional reciprocal coordinates kappa; 1 <= nk <= 4096
+ *   Xk     device, nk x nbasis x nbasis complex numbers (re, im interleaved, row-major, rows
+ *          = orbital mu in atom-major order, see gint_info_t.nbasis), overwritten; entries of
+ *          atom pairs without a block are zero
+ * Asynchronous on `stream` (the k points are copied before the call returns). */
+gint_status gint_fold(gint_handle h, const double *X_dev, int nk, const double *kfrac, double *Xk_dev,
+                      void *stream);
+
+/* The inverse direction (Eq. density_matrix with Xk = Sum_n f c c*): X(R) = Re Sum_q w_q Xk[q]
+ * exp(-i k_q.R) for every block of the store; with w_q = 1/N_k on a complete k mesh it inverts
+ * gint_fold.  Xk as in gint_fold (device, read); kfrac, w host (nk x 3, nk); X (device, block
+ * layout) overwritten. */
+gint_status gint_unfold(gint_handle h, const double *Xk_dev, int nk, const double *kfrac, const double *w,
+                        double *X_dev, void *stream);
 
 /* Backward of gint_vlocal for L = Sum_blocks Sum_mu,nu gH_mu,nu V_mu,nu(R) (gH: device, block
  * layout, e.g. the incoming gradient of H):

@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgint.so")
-SOURCES = ["gint_setup.cpp", "gint_api.cu", "gint_simt.cu", "gint_tc.cu", "gint_batch.cu", "gint_noalloc.cu"]
+SOURCES = ["gint_setup.cpp", "gint_api.cu", "gint_simt.cu", "gint_tc.cu", "gint_batch.cu", "gint_noalloc.cu",
+           "gint_kspace.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

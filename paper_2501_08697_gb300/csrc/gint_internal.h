@@ -140,6 +140,15 @@ struct gint_handle_s {
     float *d_dm32 = nullptr;         // scratch: density matrix (or its symmetric part) in FP32
     float *d_poff = nullptr;         // point-offset table
     double *d_red = nullptr;         // scratch: partial sums of reductions
+    struct {                         // k-space transforms (built on first use)
+        int *d_keys = nullptr;       // [nblocks][5] block keys
+        int *d_grp = nullptr;        // [ngroups + 1] first block of each (I, J) group
+        int *d_orboff = nullptr;     // [natoms + 1] orbital offsets (atom-major)
+        int ngroups = 0;
+        double *d_kvec = nullptr;    // [cap][4]: kappa (3) and weight of each k point
+        double *d_phase = nullptr;   // [nblocks][cap][2]: cos, sin of 2 pi kappa.n
+        int cap = 0;
+    } ks;
     double *d_hostio = nullptr;      // buffers of gint_run_host (allocated on first use)
     size_t hostio_bytes = 0;
     cudaStream_t last_stream = nullptr;

@@ -465,6 +465,8 @@ gint_status build_geometry(gint_handle h, const double *tau, bool update_only)
     info.flops_dense = h->bs[0].flops_dense;
     info.nbatches_rho = (int64_t)h->bs[1].batches.size();
     info.max_orbitals_rho = h->bs[1].max_nb;
+    info.nbasis = 0;
+    for (int I = 0; I < natoms; ++I) info.nbasis += h->norb_atom[I];
     info.flops_dense_rho = h->bs[1].flops_dense;
     (void)rows;
     h->plan.nblocks = nblocks;
@@ -546,7 +548,8 @@ static void free_dev(gint_handle h)
 {
     void *ptrs[] = {h->d_coef64, h->d_coef32, h->d_partner, h->d_blkoff, h->d_blkrows, h->d_status, h->d_dmsym,
                     h->d_dm32, h->d_poff, h->d_red, h->d_hostio, h->bs[0].d_batches, h->bs[0].d_slots, h->bs[0].d_tbl,
-                    h->bs[0].d_rng, h->bs[1].d_batches, h->bs[1].d_slots, h->bs[1].d_tbl, h->bs[1].d_rng};
+                    h->bs[0].d_rng, h->bs[1].d_batches, h->bs[1].d_slots, h->bs[1].d_tbl, h->bs[1].d_rng,
+                    h->ks.d_keys, h->ks.d_grp, h->ks.d_orboff, h->ks.d_kvec, h->ks.d_phase};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }

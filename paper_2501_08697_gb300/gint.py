@@ -20,7 +20,8 @@ PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3, "bf16x6": 4}
 PREC_NAME = {v: k for k, v in PREC.items()}
 
 EXPORTS = ["gint_setup", "gint_destroy", "gint_block_layout", "gint_get_info", "gint_update_positions",
-           "gint_vlocal", "gint_rho", "gint_force", "gint_rho_force", "gint_strain_derivative",
+           "gint_vlocal", "gint_rho", "gint_force", "gint_rho_force", "gint_strain_derivative", "gint_fold",
+           "gint_unfold",
            "gint_vlocal_backward", "gint_charge",
            "gint_block_dot",
            "gint_block_dot_noalloc", "gint_run_host", "gint_batch_create", "gint_batch_launch", "gint_batch_destroy",
@@ -46,7 +47,7 @@ class _Info(C.Structure):
     _fields_ = [("npts", C.c_int64), ("nblocks", C.c_int64), ("nvalues", C.c_int64), ("nbatches", C.c_int64),
                 ("nslots", C.c_int64), ("max_orbitals", C.c_int), ("max_slots", C.c_int), ("dV", C.c_double),
                 ("flops_useful", C.c_double), ("flops_dense", C.c_double), ("nbatches_rho", C.c_int64),
-                ("max_orbitals_rho", C.c_int), ("reserved", C.c_int), ("flops_dense_rho", C.c_double)]
+                ("max_orbitals_rho", C.c_int), ("nbasis", C.c_int), ("flops_dense_rho", C.c_double)]
 
 
 _lib = None
@@ -81,6 +82,8 @@ def load(build_if_missing: bool = True):
         lib.gint_force.argtypes = [vp, vp, vp, vp, i32, vp]
         lib.gint_rho_force.argtypes = [vp, vp, vp, vp, vp, i32, vp]
         lib.gint_strain_derivative.argtypes = [vp, vp, vp, vp, i32, vp]
+        lib.gint_fold.argtypes = [vp, vp, i32, P(d), vp, vp]
+        lib.gint_unfold.argtypes = [vp, vp, i32, P(d), P(d), vp, vp]
         lib.gint_vlocal_backward.argtypes = [vp, vp, vp, vp, vp, i32, vp]
         lib.gint_charge.argtypes = [vp, vp, vp, vp]
         lib.gint_block_dot.argtypes = [vp, vp, vp, vp, vp]
@@ -113,6 +116,15 @@ def _ptr(t) -> int:
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
         raise TypeError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+def _cptr(t) -> int:
+    """Device pointer of a contiguous complex128 (or float64) CUDA tensor."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype not in (torch.complex128, torch.float64) \
+            or not t.is_contiguous():
+        raise TypeError("expected a contiguous complex128 CUDA tensor")
     return t.data_ptr()
 
 
@@ -242,6 +254,34 @@ def gint_strain_derivative(h: Handle, V, DM, dLde, prec="fp64", stream=None):
     """dLde (device, 9 doubles, row-major) <- dL/deps for L = <DM, V_mu,nu>; the grid part of
     the stress sigma = -dL/deps / Omega."""
     _check(load().gint_strain_derivative(h.ptr, _ptr(V), _ptr(DM), _ptr(dLde), _prec(prec), _stream(stream)))
+
+
+def _kpoints(kfrac):
+    import numpy as np
+    k = np.ascontiguousarray(np.atleast_2d(np.asarray(kfrac, np.float64)))
+    if k.ndim != 2 or k.shape[1] != 3:
+        raise ValueError("k points: shape (nk, 3)")
+    return k
+
+
+def gint_fold(h: Handle, X, kfrac, Xk, stream=None):
+    """Xk (device, complex128 [nk, nbasis, nbasis] or float64 view) <- Sum_R X(R) exp(i k.R)."""
+    import ctypes as _c
+    k = _kpoints(kfrac)
+    _check(load().gint_fold(h.ptr, _ptr(X), len(k), k.ctypes.data_as(_c.POINTER(_c.c_double)), _cptr(Xk),
+                            _stream(stream)))
+
+
+def gint_unfold(h: Handle, Xk, kfrac, w, X, stream=None):
+    """X (device, block store) <- Re Sum_k w_k Xk exp(-i k.R)."""
+    import ctypes as _c
+    import numpy as np
+    k = _kpoints(kfrac)
+    w = np.ascontiguousarray(np.asarray(w, np.float64).reshape(-1))
+    if len(w) != len(k):
+        raise ValueError("one weight per k point")
+    _check(load().gint_unfold(h.ptr, _cptr(Xk), len(k), k.ctypes.data_as(_c.POINTER(_c.c_double)),
+                              w.ctypes.data_as(_c.POINTER(_c.c_double)), _ptr(X), _stream(stream)))
 
 
 def gint_vlocal_backward(h: Handle, V, gH, gV, gtau, prec="fp64", stream=None):

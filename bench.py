@@ -348,6 +348,70 @@ def run_batching(args, rank, world):
             "clocks": clk.summary(), "gpu_launches": args.steps * (2 * len(sts) + 1 + len(sts) + 1)}
 
 
+def run_kspace(args, rank, world):
+    """The k-space transforms on the Si512 block store: gint_fold of H(R) to 4 dense k-point
+    matrices (6656^2 complex each) and gint_unfold back; memory-bound, reported in GB/s of
+    algorithmic traffic (block store read or written once, dense entries written or read once)."""
+    import numpy as np
+    import torch
+    from paper_2501_08697_gb300 import gint as G
+    from paper_2501_08697_gb300 import synth as S
+    dev = torch.device(f"cuda:{int(os.environ.get('LOCAL_RANK', 0))}")
+    torch.cuda.set_device(dev)
+    st, Vn = build_inputs("si512")
+    h = G.setup_structure(st)
+    keys, offs = h.layout()
+    info = h.info
+    N, nv = info["nbasis"], info["nvalues"]
+    X = torch.from_numpy(S.density_matrix(keys, st.norb_atom, seed=st.seed)).to(dev)
+    rng = np.random.default_rng(S.BASE_SEED + 7)
+    kap = np.vstack([[0.0, 0.0, 0.0], rng.uniform(-0.5, 0.5, (3, 3))])
+    w = np.full(len(kap), 1.0 / len(kap))
+    nk = len(kap)
+    Xk = torch.empty((nk, N, N), dtype=torch.complex128, device=dev)
+    Xb = torch.empty_like(X)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    # unique dense entries the unfold reads: the sub-blocks of atom pairs that have blocks
+    pairs = {(int(k[0]), int(k[1])) for k in keys}
+    nint = sum(int(st.norb_atom[i]) * int(st.norb_atom[j]) for i, j in pairs)
+    bytes_fold = 8 * nv + 16 * N * N * nk
+    bytes_unfold = 16 * nint * nk + 8 * nv
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b) / 1e3
+        return tot / args.steps
+
+    with ClockSampler(dev.index) as clk:
+        tf = timed(lambda: G.gint_fold(h, X, kap, Xk))
+        tu = timed(lambda: G.gint_unfold(h, Xk, kap, w, Xb))
+    peaks, src = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    gf, gu = bytes_fold / tf / 1e9, bytes_unfold / tu / 1e9
+    return {"metric": "k-space fold of the block store, GB/s of algorithmic traffic", "value": world * gf,
+            "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tf * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (Si512 block-symmetric random store)",
+            "config": {"workload": f"kspace: si512 store ({nv} values), {nk} k points, nbasis {N}",
+                       "l2": "flushed between steps (512 MiB write)"},
+            "roofline": {"bound": "hbm", "kernel": "k_fold", "achieved": gf, "peak": hbm, "unit": "GB/s",
+                         "frac": gf / hbm, "traffic": None, "peak_source": src,
+                         "bytes_per_launch": bytes_fold},
+            "unfold": {"ms": tu * 1e3, "GB/s": gu, "frac": gu / hbm, "bytes_per_launch": bytes_unfold},
+            "clocks": clk.summary(), "gpu_launches": args.steps * 4}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -396,6 +460,8 @@ def main():
         out = run_reference(args, rank, world)
     elif args.workload == "batching":
         out = run_batching(args, rank, world)
+    elif args.workload == "kspace":
+        out = run_kspace(args, rank, world)
     else:
         out = run_ours(args, rank, world)
     if rank == 0 and out is not None:

@@ -143,6 +143,8 @@ struct gint_handle_s {
     struct {                         // k-space transforms (built on first use)
         int *d_keys = nullptr;       // [nblocks][5] block keys
         int *d_grp = nullptr;        // [ngroups + 1] first block of each (I, J) group
+        int *d_pair = nullptr;       // [natoms * natoms] group of atom pair (I, J), -1 if none
+        int *d_colatom = nullptr;    // [nbasis] atom of each orbital (dense column)
         int *d_orboff = nullptr;     // [natoms + 1] orbital offsets (atom-major)
         int ngroups = 0;
         double *d_kvec = nullptr;    // [cap][4]: kappa (3) and weight of each k point

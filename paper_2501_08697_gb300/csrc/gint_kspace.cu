@@ -5,8 +5,9 @@
 // density_matrix): X_mu,nu(R) = Re Sum_k w_k X_mu,nu(k) exp(-i k.R).  Both are memory-bound:
 // the dense matrices (16 bytes per entry and k point) dominate the traffic.  Blocks with the
 // same atom pair (I, J) are consecutive in the store (keys sorted by I, J, n), so folding runs
-// one CTA per (I, J) group: every entry of the group's dense sub-block is summed over the
-// group's R in registers and written once, without atomics.  Phases exp(i 2 pi kappa.n) are
+// over all atom pairs, one CTA at a time per pair: every entry of the pair's dense sub-block is
+// summed over the pair's R in registers and written exactly once (zeros for pairs without a
+// block), without atomics or a separate clearing pass.  Phases exp(i 2 pi kappa.n) are
 // tabulated once per call (FP64 sincospi) and read by all threads of a block.
 #include <algorithm>
 #include <vector>
@@ -36,25 +37,28 @@ __global__ void k_phase(const int *__restrict__ keys, int64_t nblocks, const dou
     }
 }
 
+// One CTA per dense row (orbital mu of atom I) for every k point, so each warp writes
+// consecutive entries of one row.  Column c belongs to atom J = col_atom[c]; the pair's
+// blocks (one per R) are summed in registers, k points kKq at a time.
 __global__ void __launch_bounds__(kFoldThreads)
-    k_fold(const int *__restrict__ keys, const int *__restrict__ grp, int ngroups, const int *__restrict__ orboff,
-           const int64_t *__restrict__ off, const double *__restrict__ X, const double2 *__restrict__ phase, int nk,
-           int64_t nbasis, double2 *__restrict__ Xk)
+    k_fold(const int *__restrict__ pair, const int *__restrict__ grp, const int *__restrict__ col_atom, int natoms,
+           const int *__restrict__ orboff, const int64_t *__restrict__ off, const double *__restrict__ X,
+           const double2 *__restrict__ phase, int nk, int64_t nbasis, double2 *__restrict__ Xk)
 {
-    for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
-        const int b0 = grp[g], b1 = grp[g + 1];
-        const int I = keys[5 * b0], J = keys[5 * b0 + 1];
-        const int r0 = orboff[I], nI = orboff[I + 1] - r0;
-        const int c0 = orboff[J], nJ = orboff[J + 1] - c0;
-        for (int e = threadIdx.x; e < nI * nJ; e += blockDim.x) {
-            const int mu = e / nJ, nu = e - mu * nJ;
-            double2 *out = Xk + (int64_t)(r0 + mu) * nbasis + (c0 + nu);
+    for (int r = blockIdx.x; r < nbasis; r += gridDim.x) {
+        const int I = col_atom[r], mu = r - orboff[I];
+        for (int c = threadIdx.x; c < nbasis; c += blockDim.x) {
+            const int J = col_atom[c];
+            const int c0 = orboff[J], nJ = orboff[J + 1] - c0, nu = c - c0;
+            const int gi = pair[I * natoms + J];
+            const int b0 = gi >= 0 ? grp[gi] : 0, b1 = gi >= 0 ? grp[gi + 1] : 0;
+            double2 *out = Xk + (int64_t)r * nbasis + c;
             for (int q0 = 0; q0 < nk; q0 += kKq) {
                 double re[kKq], im[kKq];
 #pragma unroll
                 for (int j = 0; j < kKq; ++j) re[j] = im[j] = 0.0;
                 for (int b = b0; b < b1; ++b) {
-                    const double x = X[off[b] + e];
+                    const double x = X[off[b] + mu * nJ + nu];
                     const double2 *ph = phase + (int64_t)b * nk + q0;
 #pragma unroll
                     for (int j = 0; j < kKq; ++j)
@@ -72,6 +76,8 @@ __global__ void __launch_bounds__(kFoldThreads)
     }
 }
 
+// One CTA per block: its entries are read from the dense matrices (the sub-blocks of one atom
+// pair stay in L1/L2 across the pair's R) and summed over the k points.
 __global__ void __launch_bounds__(kFoldThreads)
     k_unfold(const int *__restrict__ keys, int64_t nblocks, const int *__restrict__ orboff,
              const int64_t *__restrict__ off, const double2 *__restrict__ Xk, const double2 *__restrict__ phase,
@@ -126,13 +132,26 @@ gint_status ensure_tables(gint_handle h)
     if (nb == 0) grp.assign(1, 0);
     std::vector<int> oo(h->natoms + 1, 0);
     for (int I = 0; I < h->natoms; ++I) oo[I + 1] = oo[I] + h->norb_atom[I];
+    std::vector<int> colatom(std::max(1, oo[h->natoms]));
+    for (int I = 0; I < h->natoms; ++I)
+        for (int o = oo[I]; o < oo[I + 1]; ++o) colatom[o] = I;
+    std::vector<int> pair((size_t)h->natoms * h->natoms, -1);
+    for (size_t g = 0; g + 1 < grp.size(); ++g) {
+        const int b = grp[g], I = h->keys[5 * b], J = h->keys[5 * b + 1];
+        pair[(size_t)I * h->natoms + J] = (int)g;
+    }
     cudaError_t e;
     if ((e = cudaMalloc((void **)&K.d_keys, sizeof(int) * std::max<int64_t>(1, 5 * nb))) != cudaSuccess ||
         (e = cudaMalloc((void **)&K.d_grp, sizeof(int) * grp.size())) != cudaSuccess ||
+        (e = cudaMalloc((void **)&K.d_pair, sizeof(int) * pair.size())) != cudaSuccess ||
+        (e = cudaMalloc((void **)&K.d_colatom, sizeof(int) * colatom.size())) != cudaSuccess ||
         (e = cudaMalloc((void **)&K.d_orboff, sizeof(int) * oo.size())) != cudaSuccess)
         return cuda_fail(e, "gint_fold: allocate tables");
     if ((nb > 0 && (e = cudaMemcpy(K.d_keys, h->keys.data(), sizeof(int) * 5 * nb, cudaMemcpyHostToDevice)) != cudaSuccess) ||
         (e = cudaMemcpy(K.d_grp, grp.data(), sizeof(int) * grp.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(K.d_pair, pair.data(), sizeof(int) * pair.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(K.d_colatom, colatom.data(), sizeof(int) * colatom.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
         (e = cudaMemcpy(K.d_orboff, oo.data(), sizeof(int) * oo.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "gint_fold: upload tables");
     K.ngroups = (int)grp.size() - 1;
@@ -189,15 +208,12 @@ extern "C" gint_status gint_fold(gint_handle h, const double *X_dev, int nk, con
     if ((st = ensure_tables(h)) != GINT_OK || (st = prepare_k(h, nk, kfrac, nullptr, s, "gint_fold")) != GINT_OK)
         return st;
     const int64_t N = h->info.nbasis;
-    cudaError_t e = cudaMemsetAsync(Xk_dev, 0, sizeof(double2) * N * N * nk, s);
-    if (e != cudaSuccess) return cuda_fail(e, "gint_fold: memset");
-    if (h->ks.ngroups > 0) {
-        const int grid = std::min(h->ks.ngroups, 16 * h->nsm);
-        k_fold<<<grid, kFoldThreads, 0, s>>>(h->ks.d_keys, h->ks.d_grp, h->ks.ngroups, h->ks.d_orboff,
-                                             (const int64_t *)h->d_blkoff, X_dev, (const double2 *)h->ks.d_phase, nk, N,
-                                             (double2 *)Xk_dev);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gint_fold: launch");
-    }
+    const int grid = (int)std::min<int64_t>(N, 32 * h->nsm);
+    k_fold<<<grid, kFoldThreads, 0, s>>>(h->ks.d_pair, h->ks.d_grp, h->ks.d_colatom, h->natoms, h->ks.d_orboff,
+                                         (const int64_t *)h->d_blkoff, X_dev, (const double2 *)h->ks.d_phase, nk, N,
+                                         (double2 *)Xk_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "gint_fold: launch");
     h->last_stream = s;
     return GINT_OK;
 }

@@ -549,7 +549,8 @@ static void free_dev(gint_handle h)
     void *ptrs[] = {h->d_coef64, h->d_coef32, h->d_partner, h->d_blkoff, h->d_blkrows, h->d_status, h->d_dmsym,
                     h->d_dm32, h->d_poff, h->d_red, h->d_hostio, h->bs[0].d_batches, h->bs[0].d_slots, h->bs[0].d_tbl,
                     h->bs[0].d_rng, h->bs[1].d_batches, h->bs[1].d_slots, h->bs[1].d_tbl, h->bs[1].d_rng,
-                    h->ks.d_keys, h->ks.d_grp, h->ks.d_orboff, h->ks.d_kvec, h->ks.d_phase};
+                    h->ks.d_keys, h->ks.d_grp, h->ks.d_pair, h->ks.d_colatom, h->ks.d_orboff, h->ks.d_kvec,
+                    h->ks.d_phase};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }

@@ -29,6 +29,7 @@
 #include <cuda_bf16.h>
 
 #include "gint_device.cuh"
+#include "gint_tcgen05.cuh"
 
 namespace gint {
 namespace {
@@ -38,187 +39,7 @@ constexpr int kMma = kProd;       // the MMA-issue thread (warp 11)
 constexpr int kEpi0 = kProd + 32; // first epilogue thread (warp 12: TMEM lane quadrant = warp % 4)
 constexpr int kEpi = 256;         // epilogue threads (two warps per TMEM lane quadrant)
 constexpr int kThreadsTC = kEpi0 + kEpi;
-constexpr int kLBO = 144;         // bytes between core matrices along K
-constexpr int kTmemCols = 512;
 constexpr int kWin = 32;          // epilogue window (columns) of the rho kernel
-
-// ------------------------------------------------------------------ PTX wrappers
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t sbo)
-{
-    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(kLBO >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
-           (1ull << 46);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(su32(bar)) : "memory");
-}
-
-// bounded wait on the phase with the given parity; false if the budget ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long budget)
-{
-    const uint32_t a = su32(bar);
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t ok;
-        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                     : "=r"(ok)
-                     : "r"(a), "r"(parity)
-                     : "memory");
-        if (ok) return true;
-        if (clock64() - t0 > budget) return false;
-        __nanosleep(128);   // back off: a spinning warp takes issue slots from the working ones
-    }
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t *bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-                 : "memory");
-}
-
-template <bool F16KIND>
-__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    if constexpr (F16KIND)
-        asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d),
-                     "l"(a), "l"(b), "r"(idesc), "r"(acc));
-    else
-        asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(d),
-                     "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-// asynchronous global -> shared copies (completion: cp_async_wait_all + a barrier)
-__device__ __forceinline__ void cp_async8(void *dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// FP64 add to global memory without a return value (the scatters never read the old value)
-__device__ __forceinline__ void red_add_f64(double *a, double v)
-{
-    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(a), "d"(v) : "memory");
-}
-
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t addr, float *v)
-{
-    uint32_t r[16];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                 : "r"(addr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// ------------------------------------------------------------------ precision schemes
-// CG elements = 16 bytes per core-matrix row; KCM core matrices per row per pipeline chunk.
-// PA/PB: operand term of product q, packed one nibble per product.
-struct TF32x3 {
-    static constexpr int CG = 4, NT = 2, NPROD = 3, KCM = 4;
-    static constexpr bool F16 = false;
-    static constexpr uint32_t FMT = 2, PA = 0x100, PB = 0x010;
-};
-struct BF16x3 {
-    static constexpr int CG = 8, NT = 2, NPROD = 3, KCM = 2;
-    static constexpr bool F16 = true;
-    static constexpr uint32_t FMT = 1, PA = 0x100, PB = 0x010;
-};
-struct BF16x3W {  // BF16x3 with 32-element chunks (rho/force kernel, which has the shared memory)
-    static constexpr int CG = 8, NT = 2, NPROD = 3, KCM = 4;
-    static constexpr bool F16 = true;
-    static constexpr uint32_t FMT = 1, PA = 0x100, PB = 0x010;
-};
-struct BF16x6 {
-    static constexpr int CG = 8, NT = 3, NPROD = 6, KCM = 2;
-    static constexpr bool F16 = true;
-    static constexpr uint32_t FMT = 1, PA = 0x210100, PB = 0x012010;
-};
-__host__ __device__ constexpr int term(uint32_t packed, int q) { return (int)((packed >> (4 * q)) & 0xF); }
-
-__device__ __forceinline__ float tf32_rna(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-// split CG consecutive FP32 values into NT terms and store each as one 16-byte chunk
-template <class S>
-__device__ __forceinline__ void split_store(const float *x, unsigned char *const *dst)
-{
-    if constexpr (!S::F16) {
-        float4 hi, lo;
-        float *h = &hi.x, *l = &lo.x;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            h[i] = tf32_rna(x[i]);
-            l[i] = tf32_rna(x[i] - h[i]);
-        }
-        *reinterpret_cast<float4 *>(dst[0]) = hi;
-        *reinterpret_cast<float4 *>(dst[1]) = lo;
-    } else {
-        __align__(16) __nv_bfloat16 t[S::NT][8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            float r = x[i];
-#pragma unroll
-            for (int k = 0; k < S::NT; ++k) {
-                __nv_bfloat16 b = __float2bfloat16_rn(r);
-                t[k][i] = b;
-                r -= __bfloat162float(b);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < S::NT; ++k) *reinterpret_cast<uint4 *>(dst[k]) = *reinterpret_cast<const uint4 *>(t[k]);
-    }
-}
-
-template <class S>
-__device__ __forceinline__ void zero_store(unsigned char *const *dst)
-{
-#pragma unroll
-    for (int k = 0; k < S::NT; ++k) *reinterpret_cast<uint4 *>(dst[k]) = make_uint4(0, 0, 0, 0);
-}
-
-// byte offset of core-matrix row (row, kc) in an operand array
-template <class S>
-__device__ __forceinline__ int cm_off(int row, int kc)
-{
-    constexpr int SBO = S::KCM * kLBO;
-    return (row >> 3) * SBO + kc * kLBO + (row & 7) * 16;
-}
-
-template <class S>
-constexpr int arr_bytes(int rows)
-{
-    return (rows / 8) * S::KCM * kLBO;
-}
-
-template <class S>
-__host__ __device__ constexpr uint32_t idesc(int M, int N)
-{
-    return (1u << 4) | (S::FMT << 7) | (S::FMT << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
 
 // ------------------------------------------------------------------ shared batch metadata
 // An atom image of the batch in shared memory: the first 16 bytes and dh/dl as in Slot (so
@@ -355,18 +176,6 @@ __device__ __forceinline__ void geom_async(const Plan &P, const SInfo *sis, cons
         }
     }
     cp_async_commit();
-}
-
-// FP32 -> FP64 with integer operations (exact for normal numbers; subnormals flush to 0)
-__device__ __forceinline__ double f2d(float f)
-{
-    const uint32_t u = __float_as_uint(f);
-    const uint32_t e = (u >> 23) & 0xFF;
-    if (e == 0) return 0.0;
-    if (e == 0xFF) return (double)f;
-    const uint64_t bits = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
-                          ((uint64_t)(u & 0x7FFFFFu) << 29);
-    return __longlong_as_double((long long)bits);
 }
 
 __device__ __forceinline__ void disp(const PSlot &s, const float *po, float &dx, float &dy, float &dz)

@@ -198,6 +198,20 @@ gint_status gint_fold(gint_handle h, const double *X_dev, int nk, const double *
 gint_status gint_unfold(gint_handle h, const double *Xk_dev, int nk, const double *kfrac, const double *w,
                         double *X_dev, void *stream);
 
+/* Density matrix from Kohn-Sham eigenvectors, Eq. density_matrix:
+ *   DM_mu,nu(R) = Re Sum_q w_q Sum_n f_n,q c_n,mu,q c*_n,nu,q exp(-i k_q.R)
+ * for every block (I, J, R) of the store (k_q.R = 2 pi kappa_q.n; w_q = 1/N_k in the paper).
+ *   kfrac, w  host, nk x 3 and nk
+ *   C         device, nk x nbasis x nbands complex numbers (re, im interleaved), row-major:
+ *             row = orbital mu (atom-major order), column = band n
+ *   f         device, nk x nbands occupations
+ *   DM        device, block layout, overwritten
+ * prec: GINT_FP64 (CUDA-core complex GEMM per k point).  Library-owned scratch of
+ * 16 * nbasis^2 bytes (dense rho(k)) is allocated on first use and kept until gint_destroy. */
+gint_status gint_density_matrix(gint_handle h, int nk, const double *kfrac, const double *w, int nbands,
+                                const double *C_dev, const double *f_dev, double *DM_dev, gint_prec prec,
+                                void *stream);
+
 /* Backward of gint_vlocal for L = Sum_blocks Sum_mu,nu gH_mu,nu V_mu,nu(R) (gH: device, block
  * layout, e.g. the incoming gradient of H):
  *   gV (device, npts)       <- dL/dV(r)   = dV * rho(r) built from the block-symmetric part of gH

@@ -58,3 +58,13 @@ def monkhorst_pack(n1, n2, n3, shift=(0.0, 0.0, 0.0)):
     l = np.array([(m + shift[2]) / n3 for m in range(n3)])
     k = np.array([[a, b, c] for a in g for b in h for c in l], np.float64)
     return k, np.full(len(k), 1.0 / len(k))
+
+
+def density_matrix(keys, offs, norb_atom, C, f, kfrac, wk):
+    """Eq. density_matrix: rho_mu,nu(R) = Re Sum_k w_k Sum_n f_nk c_n,mu,k c*_n,nu,k exp(-i k.R).
+
+    C: complex [nk, nbasis, nbands] (row = orbital mu, column = band n); f: [nk, nbands]."""
+    C = np.asarray(C, np.complex128)
+    f = np.asarray(f, np.float64)
+    rhok = np.einsum("qmn,qn,qvn->qmv", C, f, C.conj())
+    return unfold(keys, offs, norb_atom, rhok, kfrac, wk)

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libgint.so")
 SOURCES = ["gint_setup.cpp", "gint_api.cu", "gint_simt.cu", "gint_tc.cu", "gint_batch.cu", "gint_noalloc.cu",
-           "gint_kspace.cu"]
+           "gint_kspace.cu", "gint_dm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

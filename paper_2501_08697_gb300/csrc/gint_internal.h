@@ -151,6 +151,8 @@ struct gint_handle_s {
         double *d_phase = nullptr;   // [nblocks][cap][2]: cos, sin of 2 pi kappa.n
         int cap = 0;
     } ks;
+    double *d_dm_scratch = nullptr;  // dense rho(k), planar real / imaginary (gint_density_matrix)
+    size_t dm_scratch_bytes = 0;
     double *d_hostio = nullptr;      // buffers of gint_run_host (allocated on first use)
     size_t hostio_bytes = 0;
     cudaStream_t last_stream = nullptr;

@@ -118,8 +118,11 @@ gint_status check(gint_handle h, const char *who)
     return GINT_OK;
 }
 
+}  // namespace
+
+namespace gint {
 // device tables of the block keys, (I, J) groups and orbital offsets (once per handle)
-gint_status ensure_tables(gint_handle h)
+gint_status ensure_kspace_tables(gint_handle h)
 {
     auto &K = h->ks;
     if (K.d_keys) return GINT_OK;
@@ -157,6 +160,10 @@ gint_status ensure_tables(gint_handle h)
     K.ngroups = (int)grp.size() - 1;
     return GINT_OK;
 }
+
+}  // namespace gint
+
+namespace {
 
 // k points (and weights) on the device and the phase table of every block, on stream s
 gint_status prepare_k(gint_handle h, int nk, const double *kfrac, const double *w, cudaStream_t s, const char *who)
@@ -205,7 +212,7 @@ extern "C" gint_status gint_fold(gint_handle h, const double *X_dev, int nk, con
         return GINT_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = ensure_tables(h)) != GINT_OK || (st = prepare_k(h, nk, kfrac, nullptr, s, "gint_fold")) != GINT_OK)
+    if ((st = ensure_kspace_tables(h)) != GINT_OK || (st = prepare_k(h, nk, kfrac, nullptr, s, "gint_fold")) != GINT_OK)
         return st;
     const int64_t N = h->info.nbasis;
     const int grid = (int)std::min<int64_t>(N, 32 * h->nsm);
@@ -228,7 +235,7 @@ extern "C" gint_status gint_unfold(gint_handle h, const double *Xk_dev, int nk, 
         return GINT_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = ensure_tables(h)) != GINT_OK || (st = prepare_k(h, nk, kfrac, w, s, "gint_unfold")) != GINT_OK)
+    if ((st = ensure_kspace_tables(h)) != GINT_OK || (st = prepare_k(h, nk, kfrac, w, s, "gint_unfold")) != GINT_OK)
         return st;
     cudaError_t e;
     if (h->info.nblocks > 0) {

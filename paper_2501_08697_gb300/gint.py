@@ -21,7 +21,7 @@ PREC_NAME = {v: k for k, v in PREC.items()}
 
 EXPORTS = ["gint_setup", "gint_destroy", "gint_block_layout", "gint_get_info", "gint_update_positions",
            "gint_vlocal", "gint_rho", "gint_force", "gint_rho_force", "gint_strain_derivative", "gint_fold",
-           "gint_unfold",
+           "gint_unfold", "gint_density_matrix",
            "gint_vlocal_backward", "gint_charge",
            "gint_block_dot",
            "gint_block_dot_noalloc", "gint_run_host", "gint_batch_create", "gint_batch_launch", "gint_batch_destroy",
@@ -84,6 +84,7 @@ def load(build_if_missing: bool = True):
         lib.gint_strain_derivative.argtypes = [vp, vp, vp, vp, i32, vp]
         lib.gint_fold.argtypes = [vp, vp, i32, P(d), vp, vp]
         lib.gint_unfold.argtypes = [vp, vp, i32, P(d), P(d), vp, vp]
+        lib.gint_density_matrix.argtypes = [vp, i32, P(d), P(d), i32, vp, vp, vp, i32, vp]
         lib.gint_vlocal_backward.argtypes = [vp, vp, vp, vp, vp, i32, vp]
         lib.gint_charge.argtypes = [vp, vp, vp, vp]
         lib.gint_block_dot.argtypes = [vp, vp, vp, vp, vp]
@@ -282,6 +283,20 @@ def gint_unfold(h: Handle, Xk, kfrac, w, X, stream=None):
         raise ValueError("one weight per k point")
     _check(load().gint_unfold(h.ptr, _cptr(Xk), len(k), k.ctypes.data_as(_c.POINTER(_c.c_double)),
                               w.ctypes.data_as(_c.POINTER(_c.c_double)), _ptr(X), _stream(stream)))
+
+
+def gint_density_matrix(h: Handle, kfrac, w, C, f, DM, prec="fp64", stream=None):
+    """DM (device, block store) <- Re Sum_k w_k Sum_n f_nk c_n,mu c*_n,nu exp(-i k.R)
+    (Eq. density_matrix).  C: complex128 CUDA tensor [nk, nbasis, nbands]; f: float64 [nk, nbands]."""
+    import ctypes as _c
+    import numpy as np
+    k = _kpoints(kfrac)
+    w = np.ascontiguousarray(np.asarray(w, np.float64).reshape(-1))
+    if len(w) != len(k) or C.dim() != 3 or C.shape[0] != len(k) or tuple(f.shape) != (len(k), C.shape[2]):
+        raise ValueError("C [nk, nbasis, nbands], f [nk, nbands] and one weight per k point")
+    _check(load().gint_density_matrix(h.ptr, len(k), k.ctypes.data_as(_c.POINTER(_c.c_double)),
+                                      w.ctypes.data_as(_c.POINTER(_c.c_double)), int(C.shape[2]), _cptr(C), _ptr(f),
+                                      _ptr(DM), _prec(prec), _stream(stream)))
 
 
 def gint_vlocal_backward(h: Handle, V, gH, gV, gtau, prec="fp64", stream=None):

@@ -83,3 +83,44 @@ def test_density_matrix_from_eigenvectors_matches_bloch_sum():
         ref = np.sum(w * f * np.cos(2 * np.pi * kap @ k[2:]))
         assert rho[b] == pytest.approx(ref, abs=1e-13)
     assert rho[list(map(tuple, keys[:, 2:])).index((0, 0, 0))] == pytest.approx(f.mean())
+
+
+def test_density_matrix_of_a_complete_unitary_basis_is_the_identity(si8_blocks):
+    """All bands occupied with unitary C(k): rho(k) = 1, so on a complete k mesh rho(R) is the
+    identity on the on-site blocks (R = 0) and zero on every other block."""
+    from oracle.kspace import density_matrix
+    st, keys, offs, _ = si8_blocks
+    nmax = int(np.abs(keys[:, 2:]).max())
+    n = 2 * nmax + 1
+    kap, w = monkhorst_pack(n, n, n)
+    N = int(st.norb_atom.sum())
+    rng = np.random.default_rng(5)
+    C = np.stack([np.linalg.qr(rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N)))[0] for _ in kap])
+    rho = density_matrix(keys, offs, st.norb_atom, C, np.ones((len(kap), N)), kap, w)
+    for b, k in enumerate(keys):
+        blk = rho[offs[b]:offs[b + 1]].reshape(13, 13)
+        ref = np.eye(13) if (k[0] == k[1] and (k[2:] == 0).all()) else np.zeros((13, 13))
+        assert np.abs(blk - ref).max() < 1e-12
+
+
+def test_density_matrix_is_block_symmetric_and_counts_electrons(si8_blocks):
+    from oracle.kspace import density_matrix
+    st, keys, offs, _ = si8_blocks
+    kap, w = monkhorst_pack(2, 2, 2, shift=(0.25, 0.25, 0.25))
+    kap = np.vstack([kap, -kap])            # closed under k -> -k
+    w = np.full(len(kap), 1.0 / len(kap))
+    N = int(st.norb_atom.sum())
+    rng = np.random.default_rng(6)
+    C = rng.normal(size=(len(kap), N, 40)) + 1j * rng.normal(size=(len(kap), N, 40))
+    C /= np.linalg.norm(C, axis=1, keepdims=True)                    # unit-norm bands
+    f = rng.uniform(0, 2, (len(kap), 40))
+    rho = density_matrix(keys, offs, st.norb_atom, C, f, kap, w)
+    part = S.partner_index(keys)
+    for b in range(len(keys)):
+        A = rho[offs[b]:offs[b + 1]].reshape(13, 13)
+        B = rho[offs[part[b]]:offs[part[b] + 1]].reshape(13, 13)
+        assert np.abs(A - B.T).max() < 1e-14
+    # trace of the R = 0 on-site blocks = Sum_k w_k Sum_n f_nk
+    tr = sum(np.trace(rho[offs[b]:offs[b + 1]].reshape(13, 13)) for b, k in enumerate(keys)
+             if k[0] == k[1] and (k[2:] == 0).all())
+    assert tr == pytest.approx((w[:, None] * f).sum(), rel=1e-12)

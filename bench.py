@@ -412,6 +412,55 @@ def run_kspace(args, rank, world):
             "clocks": clk.summary(), "gpu_launches": args.steps * 4}
 
 
+def run_dm(args, rank, world):
+    """Density matrix from eigenvectors (Eq. density_matrix) for the Si512 Gamma-point supercell:
+    C is nbasis x nbands (6656 x 1024, complex storage), rho(Gamma) = C diag(f) C^H on the FP64
+    pipe, then added into the block store.  Reported in FP64 TFLOP/s (8 flops per complex
+    multiply-add) against the FP64 pipe peak 2 DFMA/clk/SM x 152 SMs x 2070 MHz."""
+    import numpy as np
+    import torch
+    from paper_2501_08697_gb300 import gint as G
+    dev = torch.device(f"cuda:{int(os.environ.get('LOCAL_RANK', 0))}")
+    torch.cuda.set_device(dev)
+    st, Vn = build_inputs("si512")
+    h = G.setup_structure(st)
+    N = h.info["nbasis"]
+    nb = 4 * st.natoms // 2                       # Si: 4 valence electrons per atom, 2 per band
+    gen = torch.Generator(device=dev).manual_seed(2501)
+    C = torch.randn((1, N, nb), dtype=torch.complex128, device=dev, generator=gen)
+    f = torch.full((1, nb), 2.0, dtype=torch.float64, device=dev)
+    DM = torch.empty(h.info["nvalues"], dtype=torch.float64, device=dev)
+    kap, w = np.zeros((1, 3)), [1.0]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        G.gint_density_matrix(h, kap, w, C, f, DM, "fp64")
+    torch.cuda.synchronize()
+    tot = 0.0
+    with ClockSampler(dev.index) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            G.gint_density_matrix(h, kap, w, C, f, DM, "fp64")
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b) / 1e3
+    t = tot / args.steps
+    flops = 8.0 * N * N * nb
+    peak = 2 * 2 * 152 * 2.070e9 / 1e12
+    tf = flops / t / 1e12
+    return {"metric": "density matrix from eigenvectors, FP64 TFLOP/s", "value": world * tf, "unit": "TFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (random complex C, f = 2)",
+            "config": {"workload": f"dm: si512 Gamma, nbasis {N}, {nb} bands", "l2": "flushed between steps"},
+            "roofline": {"bound": "alu", "kernel": "k_rhok_f64", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tf / peak, "traffic": None,
+                         "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)"},
+            "clocks": clk.summary(), "gpu_launches": args.steps * 2}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -462,6 +511,8 @@ def main():
         out = run_batching(args, rank, world)
     elif args.workload == "kspace":
         out = run_kspace(args, rank, world)
+    elif args.workload == "dm":
+        out = run_dm(args, rank, world)
     else:
         out = run_ours(args, rank, world)
     if rank == 0 and out is not None:

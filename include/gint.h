@@ -256,7 +256,12 @@ gint_status gint_run_host(gint_handle h, const double *V_host, const double *DM_
  * precision (GINT_TF32X3, GINT_BF16X3, GINT_BF16X6); at most 255 structures, all on the current
  * device, at most 8 distinct species in total.  Pointer arrays are host memory, read during
  * create; the buffers they point to are device memory and are bound to the job.  DM and rho
- * may be NULL (vlocal only).  The handles must outlive the job. */
+ * may be NULL (vlocal only).  The handles must outlive the job.  A handle may appear more than
+ * once: spin channels are entries that share one geometry (collinear spin: V_up / V_down with
+ * DM_up / DM_down; non-collinear: the four real components V_uu, V_dd, Re V_ud, Im V_ud with the
+ * matching density-matrix components: the spin densities of Sec. II.A (exchange-correlation
+ * functionals) and the 2x2 spinor potential of its non-collinear subsection); every repeated
+ * occurrence gets a private FP32 density-matrix buffer owned by the job. */
 typedef struct gint_batch_s *gint_batch;
 gint_status gint_batch_create(gint_batch *out, int nstruct, const gint_handle *hs,
                               const double *const *V, double *const *H, const double *const *DM,

@@ -35,6 +35,8 @@ struct gint_batch_s {
     void *d_mem[15] = {nullptr};    // [3w..3w+2] batches, slots, tables; [9] splines; [12+w] CTA ranges
     SInfo *d_sinfo = nullptr;
     int *d_status = nullptr;
+    std::vector<float *> dm32;       // FP32 density matrix of each entry: the handle's scratch for
+    std::vector<float *> own;        //   its first occurrence, a private buffer for repeats
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -56,6 +58,8 @@ void free_batch(gint_batch b)
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
     for (void *p : b->d_mem)
+        if (p) cudaFree(p);
+    for (float *p : b->own)
         if (p) cudaFree(p);
     if (b->d_sinfo) cudaFree(b->d_sinfo);
     if (b->d_status) cudaFree(b->d_status);
@@ -81,7 +85,7 @@ gint_status issue(gint_batch b, cudaStream_t s)
         if ((e = cudaMemsetAsync(b->H[i], 0, sizeof(double) * h->info.nvalues, s)) != cudaSuccess)
             return cuda_fail(e, "gint_batch: memset");
         if (b->with_rho && h->info.nvalues > 0 &&
-            (e = launch_dm_to_f32(h->plan, b->DM[i], h->d_dm32, false, s)) != cudaSuccess)
+            (e = launch_dm_to_f32(h->plan, b->DM[i], b->dm32[i], false, s)) != cudaSuccess)
             return cuda_fail(e, "gint_batch: convert");
     }
     SInfo none{};
@@ -215,9 +219,27 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
         p.nbatches = (int)bat.size();
         b->plan[w] = p;
     }
+    // a handle may appear more than once (spin channels or several potentials on one geometry):
+    // every occurrence after the first gets its own FP32 density-matrix buffer
+    b->dm32.assign(nstruct, nullptr);
+    for (int i = 0; i < nstruct && with_rho; ++i) {
+        bool repeat = false;
+        for (int j = 0; j < i && !repeat; ++j) repeat = hs[j] == hs[i];
+        if (!repeat) {
+            b->dm32[i] = hs[i]->d_dm32;
+            continue;
+        }
+        float *p = nullptr;
+        if ((e = cudaMalloc((void **)&p, sizeof(float) * std::max<int64_t>(1, hs[i]->info.nvalues))) != cudaSuccess) {
+            free_batch(b);
+            return cuda_fail(e, "gint_batch_create: allocate");
+        }
+        b->own.push_back(p);
+        b->dm32[i] = p;
+    }
     std::vector<SInfo> si(nstruct);
     for (int i = 0; i < nstruct; ++i)
-        si[i] = sinfo_for(hs[i], V[i], H[i], with_rho ? hs[i]->d_dm32 : nullptr, with_rho ? rho[i] : nullptr, nullptr);
+        si[i] = sinfo_for(hs[i], V[i], H[i], with_rho ? b->dm32[i] : nullptr, with_rho ? rho[i] : nullptr, nullptr);
     if ((e = upload_vec(&b->d_mem[9], coef)) != cudaSuccess || (e = upload_vec((void **)&b->d_sinfo, si)) != cudaSuccess ||
         (e = cudaMalloc((void **)&b->d_status, sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(b->d_status, 0, sizeof(int))) != cudaSuccess) {

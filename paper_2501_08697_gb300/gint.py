@@ -372,6 +372,14 @@ class Batch:
             pass
 
 
+def spin_channels(h: Handle, V, H, DM=None, rho=None, prec="tf32x3") -> Batch:
+    """Spin channels on one geometry as one multi-structure job (one persistent launch per
+    kernel for all channels): collinear spin passes [V_up, V_down] (and [DM_up, DM_down]);
+    non-collinear spin passes the four real components [V_uu, V_dd, Re V_ud, Im V_ud] and the
+    matching density-matrix components.  H[c] <- vlocal(V[c]); rho[c] <- rho(DM[c])."""
+    return Batch([h] * len(V), V, H, DM, rho, prec)
+
+
 def gint_batch_create(handles, V, H, DM=None, rho=None, prec="tf32x3") -> Batch:
     return Batch(handles, V, H, DM, rho, prec)
 

@@ -528,7 +528,9 @@ struct RSmem {
     static constexpr int ARR_A = arr_bytes<S>(kMaxBatchPts);
     static constexpr int ARR_B = arr_bytes<S>(kMaxNb);
     static constexpr int STAGE = S::NT * (ARR_A + ARR_B);
-    static constexpr int NSTAGE = 2;
+    // one stage when a chunk is 32 orbitals wide (the MMAs of a chunk overlap the next chunk's
+    // orbital evaluation, which comes before the stage is rewritten), otherwise two
+    static constexpr int NSTAGE = S::KCM >= 8 ? 1 : 2;
     static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [RING][128]
     static constexpr int OFF_PSLOT = OFF_STG + RING * kMaxBatchPts * 4;     // producer PSlot[64]
     static constexpr int OFF_POFF = OFF_PSLOT + kMaxSlots * (int)sizeof(PSlot);
@@ -551,7 +553,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     k_rho_tc(Plan P, SInfo si0, const SInfo *__restrict__ sis)
 {
     using L = RSmem<S>;
-    constexpr int KC = L::KC, RING = L::RING, EG = L::EG;
+    constexpr int KC = L::KC, RING = L::RING, EG = L::EG, NS = L::NSTAGE;
     constexpr int SBO = S::KCM * kLBO;
     extern __shared__ __align__(1024) unsigned char sm[];
     float *stg = reinterpret_cast<float *>(sm + L::OFF_STG);
@@ -630,7 +632,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             named_sync(1, kProd);
             const int nch = (nb + KC - 1) / KC;
             for (int ch = 0; ch < nch && ok; ++ch, ++g) {
-                const int stage = g & 1;
+                const int stage = g % NS;
                 const int k0 = ch * KC, k1 = min(k0 + KC, nb);
                 const int s_lo = oslot[k0], s_hi = oslot[k1 - 1];
                 // staging row of chunk column k: rbase + k
@@ -694,7 +696,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     gbase[w] = v;
                 }
                 for (int k = pt; k < KC; k += kProd) gna[k] = (k0 + k < nb) ? ps[oslot[k0 + k]].norb : 0;
-                if (g >= 2) ok = role_wait(&empty[stage], ((g >> 1) - 1) & 1, P, pt, pflag, 1, kProd);
+                if (g >= NS) ok = role_wait(&empty[stage], ((g / NS) - 1) & 1, P, pt, pflag, 1, kProd);
                 else named_sync(1, kProd);
                 if (!ok) break;
                 unsigned char *base = sm + stage * L::STAGE;
@@ -759,8 +761,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 const int nch = (nb + KC - 1) / KC;
                 const uint32_t id = idesc<S>(128, npad);
                 for (int ch = 0; ch < nch && ok; ++ch, ++g) {
-                    const int stage = g & 1;
-                    ok = !aborted(P) && mbar_wait(&full[stage], (g >> 1) & 1, P.spin_limit);
+                    const int stage = g % NS;
+                    ok = !aborted(P) && mbar_wait(&full[stage], (g / NS) & 1, P.spin_limit);
                     if (ok && ch == 0 && it >= 2)   // the epilogue of batch it - 2 is done
                         ok = !aborted(P) && mbar_wait(&accempty[buf], ((it >> 1) - 1) & 1, P.spin_limit);
                     if (!ok) {
@@ -997,7 +999,7 @@ cudaError_t launch_rho_force_tc(const Plan &P, gint_prec prec, const SInfo &si0,
 {
     if (P.nbatches == 0) return cudaSuccess;
     switch (prec) {
-    case GINT_TF32X3: return rho_launch<TF32x3>(P, si0, sis, rho, force, s, nsm);
+    case GINT_TF32X3: return rho_launch<TF32x3W>(P, si0, sis, rho, force, s, nsm);
     case GINT_BF16X3: return rho_launch<BF16x3W>(P, si0, sis, rho, force, s, nsm);
     case GINT_BF16X6: return rho_launch<BF16x6>(P, si0, sis, rho, force, s, nsm);
     default: return cudaErrorInvalidValue;

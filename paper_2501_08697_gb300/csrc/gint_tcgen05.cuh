@@ -106,6 +106,11 @@ struct TF32x3 {
     static constexpr bool F16 = false;
     static constexpr uint32_t FMT = 2, PA = 0x100, PB = 0x010;
 };
+struct TF32x3W {  // TF32x3 with 32-element chunks and one stage (rho/force kernel)
+    static constexpr int CG = 4, NT = 2, NPROD = 3, KCM = 8;
+    static constexpr bool F16 = false;
+    static constexpr uint32_t FMT = 2, PA = 0x100, PB = 0x010;
+};
 struct BF16x3 {
     static constexpr int CG = 8, NT = 2, NPROD = 3, KCM = 2;
     static constexpr bool F16 = true;

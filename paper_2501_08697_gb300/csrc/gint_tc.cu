@@ -528,9 +528,10 @@ struct RSmem {
     static constexpr int ARR_A = arr_bytes<S>(kMaxBatchPts);
     static constexpr int ARR_B = arr_bytes<S>(kMaxNb);
     static constexpr int STAGE = S::NT * (ARR_A + ARR_B);
-    // one stage when a chunk is 32 orbitals wide (the MMAs of a chunk overlap the next chunk's
-    // orbital evaluation, which comes before the stage is rewritten), otherwise two
-    static constexpr int NSTAGE = S::KCM >= 8 ? 1 : 2;
+    // one stage for the 32-orbital TF32x3 and BF16x6 chunks (the MMAs of a chunk overlap the
+    // next chunk's orbital evaluation and gather tables, which come before the stage is
+    // rewritten; measured faster than two), two otherwise
+    static constexpr int NSTAGE = S::RSTAGES;
     static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [RING][128]
     static constexpr int OFF_PSLOT = OFF_STG + RING * kMaxBatchPts * 4;     // producer PSlot[64]
     static constexpr int OFF_POFF = OFF_PSLOT + kMaxSlots * (int)sizeof(PSlot);
@@ -1001,7 +1002,7 @@ cudaError_t launch_rho_force_tc(const Plan &P, gint_prec prec, const SInfo &si0,
     switch (prec) {
     case GINT_TF32X3: return rho_launch<TF32x3W>(P, si0, sis, rho, force, s, nsm);
     case GINT_BF16X3: return rho_launch<BF16x3W>(P, si0, sis, rho, force, s, nsm);
-    case GINT_BF16X6: return rho_launch<BF16x6>(P, si0, sis, rho, force, s, nsm);
+    case GINT_BF16X6: return rho_launch<BF16x6W>(P, si0, sis, rho, force, s, nsm);
     default: return cudaErrorInvalidValue;
     }
 }

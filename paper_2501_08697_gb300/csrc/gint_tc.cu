@@ -42,14 +42,13 @@ constexpr int kThreadsTC = kEpi0 + kEpi;
 constexpr int kWin = 32;          // epilogue window (columns) of the rho kernel
 
 // ------------------------------------------------------------------ shared batch metadata
-// An atom image of the batch in shared memory: the first 16 bytes and dh/dl as in Slot (so
-// they can be copied asynchronously), padded to 48 bytes for 16-byte aligned copies.
+// An atom image of the batch in shared memory: the first 16 bytes and dh/dl as in Slot, so
+// they can be copied asynchronously in 8-byte pieces.
 struct PSlot {
     int atom, species, off, norb;
     float dh[3], dl[3];
-    float pad[2];
 };
-static_assert(sizeof(PSlot) == 48, "PSlot layout");
+static_assert(sizeof(PSlot) == 40, "PSlot layout");
 static_assert(offsetof(Slot, dh) == 40 && sizeof(Slot) == 64, "Slot layout");
 
 __device__ __forceinline__ void unpack(int dims, int &n1, int &n2, int &n3)
@@ -154,12 +153,12 @@ __device__ __forceinline__ void geom_async(const Plan &P, const SInfo *sis, cons
         g1 = S.grid[1];
         g2 = S.grid[2];
     }
-    for (int w = tid; w < B.nslots * 4; w += nthr) {
-        const int s = w >> 2, part = w & 3;
+    for (int w = tid; w < B.nslots * 5; w += nthr) {
+        const int s = w / 5, part = w - 5 * s;
         const char *src = reinterpret_cast<const char *>(P.slots + B.slot0 + s);
         char *dst = reinterpret_cast<char *>(ps + s);
-        if (part == 0) cp_async16(dst, src);                                 // atom .. norb
-        else cp_async8(dst + 8 + 8 * part, src + 32 + 8 * part);            // dh, dl
+        if (part < 2) cp_async8(dst + 8 * part, src + 8 * part);           // atom .. norb
+        else cp_async8(dst + 8 * part, src + 24 + 8 * part);               // dh, dl
     }
     int n1, n2, n3;
     n1 = B.dims & 255;
@@ -228,20 +227,26 @@ __device__ __forceinline__ void load_species(const Plan &P, SpecSh *spec, int ti
 // [256 b, 256 b + 256): tile 0 (rows 0..127, N = npad <= 192) at +0 and tile 1 (rows 128..,
 // N = npad - 128 <= 64) at +192.  With nbuf = 1 (some batch has up to 256 orbitals) one
 // accumulator holds tile 0 at columns [0, 256) and tile 1 at [256, 384).
+// The vlocal epilogue keeps the batch's slot-pair table in shared memory when the batch has
+// at most kVTbl atom images (nearly all batches), otherwise it reads it from global memory.
+constexpr int kVTbl = 28;
+
 template <class S>
 struct VSmem {
     static constexpr int KC = S::KCM * S::CG;             // points per chunk
     static constexpr int ROWS = kMaxNb;                   // orbitals per batch
     static constexpr int ARR = arr_bytes<S>(256);         // one operand term (tile 1 reads rows 128..255)
     static constexpr int STAGE = 2 * S::NT * ARR;         // A terms then B terms
-    static constexpr int NSTAGE = 2;
+    // one stage for 32-point chunks (the chunk's MMAs overlap the next chunk's orbital
+    // evaluation into the staging tile, which comes before the stage is rewritten), else two
+    static constexpr int NSTAGE = S::VSTAGES;
     static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [256][KC]
     static constexpr int OFF_PSLOT = OFF_STG + ROWS * KC * 4;               // PSlot[2][64]
     static constexpr int OFF_POFF = OFF_PSLOT + 2 * kMaxSlots * (int)sizeof(PSlot);  // float [2][128][6]
     static constexpr int OFF_VD = OFF_POFF + 2 * kMaxBatchPts * 6 * 4;      // double [2][128]
     static constexpr int OFF_V = OFF_VD + 2 * kMaxBatchPts * 8;             // float [128]
-    static constexpr int OFF_TBL = OFF_V + kMaxBatchPts * 4;                // int [64*64]
-    static constexpr int OFF_INFO = OFF_TBL + kMaxSlots * kMaxSlots * 4;    // int [256]: slot | o << 8 | norb << 16
+    static constexpr int OFF_TBL = OFF_V + kMaxBatchPts * 4;                // int [kVTbl^2]
+    static constexpr int OFF_INFO = OFF_TBL + kVTbl * kVTbl * 4;            // int [256]: slot | o << 8 | norb << 16
     static constexpr int OFF_TILE = OFF_INFO + kMaxNb * 4;                  // float [8][32][33]
     static constexpr int OFF_BAR = OFF_TILE + 8 * 32 * 33 * 4;              // 16 mbarriers
     static constexpr int OFF_MISC = OFF_BAR + 16 * 8;                       // tmem base, flags
@@ -254,7 +259,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     k_vlocal_tc(Plan P, SInfo si0, const SInfo *__restrict__ sis, int nbuf)
 {
     using L = VSmem<S>;
-    constexpr int KC = L::KC;
+    constexpr int KC = L::KC, NS = L::NSTAGE;
     constexpr int SBO = S::KCM * kLBO;
     extern __shared__ __align__(1024) unsigned char sm[];
     float *stg = reinterpret_cast<float *>(sm + L::OFF_STG);
@@ -262,7 +267,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     float *poffb = reinterpret_cast<float *>(sm + L::OFF_POFF);
     double *vdb = reinterpret_cast<double *>(sm + L::OFF_VD);
     float *vs = reinterpret_cast<float *>(sm + L::OFF_V);
-    int *tbl = reinterpret_cast<int *>(sm + L::OFF_TBL);
+    int *tbls = reinterpret_cast<int *>(sm + L::OFF_TBL);
     int *info = reinterpret_cast<int *>(sm + L::OFF_INFO);
     float *tiles = reinterpret_cast<float *>(sm + L::OFF_TILE);
     SpecSh *spec = reinterpret_cast<SpecSh *>(sm + L::OFF_SPEC);
@@ -333,7 +338,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 vs[p] = p < npb ? d2f(vdb[cur * kMaxBatchPts + p]) * dVf : 0.f;
             const int nch = (npb + KC - 1) / KC;
             for (int ch = 0; ch < nch && ok; ++ch, ++g) {
-                const int stage = g & 1;
+                const int stage = g % NS;
                 // phase 1: orbital values at the chunk's points -> staging [row][KC]
                 for (int w = pt; w < KC * ns; w += kProd) {
                     const int k = w % KC, s = w / KC;
@@ -351,7 +356,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 if (ch == 0 && more)
                     geom_async(P, sis, si0, Bn, psb + (cur ^ 1) * kMaxSlots, poffb + (cur ^ 1) * kMaxBatchPts * 6,
                                vdb + (cur ^ 1) * kMaxBatchPts, pt, kProd);
-                if (g >= 2) ok = role_wait(&empty[stage], ((g >> 1) - 1) & 1, P, pt, pflag, 1, kProd);
+                if (g >= NS) ok = role_wait(&empty[stage], ((g / NS) - 1) & 1, P, pt, pflag, 1, kProd);
                 else named_sync(1, kProd);
                 if (!ok) break;
                 // phase 2: split Phi (A) and V dV Phi (B) into the canonical layout
@@ -403,8 +408,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 const int buf = nbuf == 2 ? (it & 1) : 0;
                 const int nch = (npb + KC - 1) / KC;
                 for (int ch = 0; ch < nch && ok; ++ch, ++g) {
-                    const int stage = g & 1;
-                    ok = !aborted(P) && mbar_wait(&full[stage], (g >> 1) & 1, P.spin_limit);
+                    const int stage = g % NS;
+                    ok = !aborted(P) && mbar_wait(&full[stage], (g / NS) & 1, P.spin_limit);
                     if (ok && ch == 0 && it >= nbuf)   // the epilogue of batch it - nbuf is done
                         ok = !aborted(P) && mbar_wait(&accempty[buf], ((it / nbuf) - 1) & 1, P.spin_limit);
                     if (!ok) {
@@ -451,8 +456,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             const int buf = nbuf == 2 ? (it & 1) : 0;
             if (nb == 0) continue;
             double *H = sic.get(B, sis).H;
+            const bool small = ns <= kVTbl;
+            const int *tbl = small ? tbls : P.tbl + B.tbl;
             named_sync(2, kEpi);
-            for (int e = et; e < ns * ns; e += kEpi) tbl[e] = P.tbl[B.tbl + e];
+            if (small)
+                for (int e = et; e < ns * ns; e += kEpi) tbls[e] = P.tbl[B.tbl + e];
             for (int s = et; s < ns; s += kEpi) {
                 const Slot &sl = P.slots[B.slot0 + s];
                 const int no = sl.norb, off = sl.orb_off;
@@ -988,7 +996,7 @@ cudaError_t launch_vlocal_tc(const Plan &P, gint_prec prec, const SInfo &si0, co
 {
     if (P.nbatches == 0) return cudaSuccess;
     switch (prec) {
-    case GINT_TF32X3: return vlocal_launch<TF32x3>(P, si0, sis, s, nsm, max_nb);
+    case GINT_TF32X3: return vlocal_launch<TF32x3W>(P, si0, sis, s, nsm, max_nb);
     case GINT_BF16X3: return vlocal_launch<BF16x3>(P, si0, sis, s, nsm, max_nb);
     case GINT_BF16X6: return vlocal_launch<BF16x6>(P, si0, sis, s, nsm, max_nb);
     default: return cudaErrorInvalidValue;

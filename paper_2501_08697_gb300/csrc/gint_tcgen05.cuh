@@ -104,36 +104,42 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float *v)
 struct TF32x3 {
     static constexpr int CG = 4, NT = 2, NPROD = 3, KCM = 4;
     static constexpr int RSTAGES = 2;   // operand stages in the rho/force kernel
+    static constexpr int VSTAGES = 2;   // operand stages in the vlocal kernel
     static constexpr bool F16 = false;
     static constexpr uint32_t FMT = 2, PA = 0x100, PB = 0x010;
 };
 struct TF32x3W {  // TF32x3 with 32-element chunks and one stage (rho/force kernel)
     static constexpr int CG = 4, NT = 2, NPROD = 3, KCM = 8;
     static constexpr int RSTAGES = 1;   // operand stages in the rho/force kernel
+    static constexpr int VSTAGES = 1;   // operand stages in the vlocal kernel
     static constexpr bool F16 = false;
     static constexpr uint32_t FMT = 2, PA = 0x100, PB = 0x010;
 };
 struct BF16x3 {
     static constexpr int CG = 8, NT = 2, NPROD = 3, KCM = 2;
     static constexpr int RSTAGES = 2;   // operand stages in the rho/force kernel
+    static constexpr int VSTAGES = 2;   // operand stages in the vlocal kernel
     static constexpr bool F16 = true;
     static constexpr uint32_t FMT = 1, PA = 0x100, PB = 0x010;
 };
 struct BF16x3W {  // BF16x3 with 32-element chunks (rho/force kernel, which has the shared memory)
     static constexpr int CG = 8, NT = 2, NPROD = 3, KCM = 4;
     static constexpr int RSTAGES = 2;   // operand stages in the rho/force kernel
+    static constexpr int VSTAGES = 2;   // operand stages in the vlocal kernel
     static constexpr bool F16 = true;
     static constexpr uint32_t FMT = 1, PA = 0x100, PB = 0x010;
 };
 struct BF16x6W {  // BF16x6 with 32-element chunks and one stage (rho/force kernel)
     static constexpr int CG = 8, NT = 3, NPROD = 6, KCM = 4;
     static constexpr int RSTAGES = 1;   // operand stages in the rho/force kernel
+    static constexpr int VSTAGES = 1;   // operand stages in the vlocal kernel
     static constexpr bool F16 = true;
     static constexpr uint32_t FMT = 1, PA = 0x210100, PB = 0x012010;
 };
 struct BF16x6 {
     static constexpr int CG = 8, NT = 3, NPROD = 6, KCM = 2;
     static constexpr int RSTAGES = 2;   // operand stages in the rho/force kernel
+    static constexpr int VSTAGES = 2;   // operand stages in the vlocal kernel
     static constexpr bool F16 = true;
     static constexpr uint32_t FMT = 1, PA = 0x210100, PB = 0x012010;
 };

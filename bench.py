@@ -45,7 +45,10 @@ def _peaks():
 # DRAM bytes per launch of the dominant tensor-core kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture), keyed by the SHA-256 prefix of the kernel source
 # the counters were taken on: once the kernel changes, the bench reports traffic = null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/dram_traffic_si512_tf32x3.md
+    "4d071da280a9704c": {"si512/tf32x3/rho_force": 227.19e6, "si512/tf32x3/vlocal": 287.07e6},
+}
 
 
 def _traffic(kernel, workload, prec):

@@ -997,8 +997,8 @@ cudaError_t launch_vlocal_tc(const Plan &P, gint_prec prec, const SInfo &si0, co
     if (P.nbatches == 0) return cudaSuccess;
     switch (prec) {
     case GINT_TF32X3: return vlocal_launch<TF32x3W>(P, si0, sis, s, nsm, max_nb);
-    case GINT_BF16X3: return vlocal_launch<BF16x3>(P, si0, sis, s, nsm, max_nb);
-    case GINT_BF16X6: return vlocal_launch<BF16x6>(P, si0, sis, s, nsm, max_nb);
+    case GINT_BF16X3: return vlocal_launch<BF16x3W>(P, si0, sis, s, nsm, max_nb);
+    case GINT_BF16X6: return vlocal_launch<BF16x6W>(P, si0, sis, s, nsm, max_nb);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -125,7 +125,7 @@ struct BF16x3 {
 struct BF16x3W {  // BF16x3 with 32-element chunks (rho/force kernel, which has the shared memory)
     static constexpr int CG = 8, NT = 2, NPROD = 3, KCM = 4;
     static constexpr int RSTAGES = 2;   // operand stages in the rho/force kernel
-    static constexpr int VSTAGES = 2;   // operand stages in the vlocal kernel
+    static constexpr int VSTAGES = 1;   // operand stages in the vlocal kernel
     static constexpr bool F16 = true;
     static constexpr uint32_t FMT = 1, PA = 0x100, PB = 0x010;
 };

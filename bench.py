@@ -417,9 +417,11 @@ def run_kspace(args, rank, world):
 
 def run_dm(args, rank, world):
     """Density matrix from eigenvectors (Eq. density_matrix) for the Si512 Gamma-point supercell:
-    C is nbasis x nbands (6656 x 1024, complex storage), rho(Gamma) = C diag(f) C^H on the FP64
-    pipe, then added into the block store.  Reported in FP64 TFLOP/s (8 flops per complex
-    multiply-add) against the FP64 pipe peak 2 DFMA/clk/SM x 152 SMs x 2070 MHz."""
+    C is nbasis x nbands (6656 x 1024, complex storage), rho(Gamma) = C diag(f) C^H, then added
+    into the block store.  Both paths are timed: TF32x3 on the tensor cores (K = 2048 real terms in
+    64-term TMEM segments) and FP64 on the CUDA cores; value = algorithmic FLOP/s of the complex
+    product (8 per complex multiply-add; at Gamma only Re rho is formed, 4 per term) of the
+    tensor-core path."""
     import numpy as np
     import torch
     from paper_2501_08697_gb300 import gint as G
@@ -430,37 +432,48 @@ def run_dm(args, rank, world):
     N = h.info["nbasis"]
     nb = 4 * st.natoms // 2                       # Si: 4 valence electrons per atom, 2 per band
     gen = torch.Generator(device=dev).manual_seed(2501)
-    C = torch.randn((1, N, nb), dtype=torch.complex128, device=dev, generator=gen)
+    C = torch.randn((1, N, nb), dtype=torch.complex128, device=dev, generator=gen) / N ** 0.5
     f = torch.full((1, nb), 2.0, dtype=torch.float64, device=dev)
     DM = torch.empty(h.info["nvalues"], dtype=torch.float64, device=dev)
+    DM64 = torch.empty_like(DM)
     kap, w = np.zeros((1, 3)), [1.0]
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    for _ in range(args.warmup):
-        G.gint_density_matrix(h, kap, w, C, f, DM, "fp64")
-    torch.cuda.synchronize()
-    tot = 0.0
-    with ClockSampler(dev.index) as clk:
-        for i in range(args.steps):
+
+    def timed(prec, out, steps):
+        for _ in range(args.warmup):
+            G.gint_density_matrix(h, kap, w, C, f, out, prec)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for i in range(steps):
             flush.fill_(float(i))
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            G.gint_density_matrix(h, kap, w, C, f, DM, "fp64")
+            G.gint_density_matrix(h, kap, w, C, f, out, prec)
             b.record(stream)
             torch.cuda.synchronize()
             tot += a.elapsed_time(b) / 1e3
-    t = tot / args.steps
-    flops = 8.0 * N * N * nb
-    peak = 2 * 2 * 152 * 2.070e9 / 1e12
-    tf = flops / t / 1e12
-    return {"metric": "density matrix from eigenvectors, FP64 TFLOP/s", "value": world * tf, "unit": "TFLOP/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (random complex C, f = 2)",
+        return tot / steps
+
+    with ClockSampler(dev.index) as clk:
+        t_tc = timed("tf32x3", DM, args.steps)
+    t_64 = timed("fp64", DM64, max(1, min(args.steps, 2)))
+    err = float(torch.linalg.norm(DM - DM64) / torch.linalg.norm(DM64))
+    alg = 4.0 * N * N * nb                       # Re part of the complex product at Gamma
+    exe = 2.0 * N * N * (2 * nb) * 3             # one real GEMM, K = 2 nb, 3 TF32 products
+    peaks, src = _peaks()
+    tp = _tensor_peak("tf32x3", peaks, sustained=False)
+    return {"metric": "density matrix from eigenvectors (Si512 Gamma), algorithmic TFLOP/s", "value": world * alg / t_tc / 1e12,
+            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_tc * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3",
+            "data": "synthetic (random complex C / sqrt(nbasis), f = 2)",
             "config": {"workload": f"dm: si512 Gamma, nbasis {N}, {nb} bands", "l2": "flushed between steps"},
-            "roofline": {"bound": "alu", "kernel": "k_rhok_f64", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
-                         "frac": tf / peak, "traffic": None,
-                         "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)"},
+            "roofline": {"bound": "tensor", "kernel": "k_rhok_tc", "achieved": exe / t_tc / 1e12, "peak": tp,
+                         "unit": "TFLOP/s", "frac": exe / t_tc / 1e12 / tp, "traffic": None,
+                         "peak_source": f"{src} bf16 burst x nominal tf32 ratio (executed tf32 flops)"},
+            "fp64": {"ms": t_64 * 1e3, "TFLOP/s": alg / t_64 / 1e12,
+                     "frac_of_fp64_pipe": alg / t_64 / 1e12 / (2 * 2 * 152 * 2.070e9 / 1e12)},
+            "err_vs_fp64": err, "speedup_vs_fp64": t_64 / t_tc,
             "clocks": clk.summary(), "gpu_launches": args.steps * 2}
 
 

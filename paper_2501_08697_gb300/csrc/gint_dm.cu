@@ -4,10 +4,24 @@
 // planar real / imaginary scratch), then added into every block of the store with its phase
 // (the unfolding of gint_unfold, accumulated over k).  FP64 path: CUDA-core complex GEMM with
 // 64 x 64 output tiles staged through shared memory (FP64-pipe bound).
+//
+// TF32x3 path: the complex product is two real GEMMs over K = 2 nbands with the band index and
+// the real / imaginary part interleaved (the memory order of C):
+//   Re rho = Sum_k A_re[mu][k] B[nu][k],  A_re = C (as reals), B[nu][2n+t] = f_n C[nu][2n+t]
+//   Im rho = Sum_k A_im[mu][k] B[nu][k],  A_im[mu][2n] = Im c_mu,n, A_im[mu][2n+1] = -Re c_mu,n
+// (the imaginary part is skipped at k = 0, where only Re rho(k) reaches the block store).  The
+// band reduction is long (K = 2048 for 1024 bands) and the tensor cores accumulate in FP32 with
+// an error that grows with the number of MMA steps, so K is cut into 64-term segments: each
+// segment is accumulated in its own TMEM buffer (24 MMA steps, as a 64-point vlocal batch), and
+// the epilogue adds the segments with round-to-nearest FP32 additions into a running sum kept in
+// TMEM.  128 x 128 output tiles, persistent CTAs; 8 producer warps split FP64 -> TF32 hi/lo into
+// the canonical operand layout, one thread issues the MMAs, 8 epilogue warps sum the segments.
 #include <algorithm>
 #include <vector>
 
+#include "gint_device.cuh"
 #include "gint_internal.h"
+#include "gint_tcgen05.cuh"
 
 using namespace gint;
 
@@ -90,7 +104,7 @@ __global__ void __launch_bounds__(kGemmThreads)
 __global__ void k_unfold_acc(const int *__restrict__ keys, int64_t nblocks, const int *__restrict__ orboff,
                              const int64_t *__restrict__ off, const double *__restrict__ re,
                              const double *__restrict__ im, double k1, double k2, double k3, double w, int nbasis,
-                             int first, double *__restrict__ X)
+                             int first, int use_im, double *__restrict__ X)
 {
     for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
         const int *k = keys + 5 * b;
@@ -102,9 +116,210 @@ __global__ void k_unfold_acc(const int *__restrict__ keys, int64_t nblocks, cons
         for (int e = threadIdx.x; e < nI * nJ; e += blockDim.x) {
             const int mu = e / nJ, nu = e - mu * nJ;
             const int64_t g = (int64_t)(r0 + mu) * nbasis + (c0 + nu);
-            const double v = w * fma(re[g], c, im[g] * s);   // Re[(re + i im)(c - i s)]
+            const double v = w * (use_im ? fma(re[g], c, im[g] * s) : re[g] * c);   // Re[(re + i im)(c - i s)]
             X[off[b] + e] = first ? v : X[off[b] + e] + v;
         }
+    }
+}
+
+// ------------------------------------------------------------------ tensor-core path
+constexpr int kDmProd = 256;                 // producer threads (warps 0-7)
+constexpr int kDmEpi0 = 256;                 // epilogue warps 8-15 (TMEM lane quadrant = warp % 4)
+constexpr int kDmMma = 512;                  // MMA-issue thread (warp 16)
+constexpr int kDmThreads = 544;
+constexpr int kDmBM = 128, kDmBN = 128;      // output tile
+constexpr int kDmKC = 32;                    // K values per chunk (TF32x3W: 8 core matrices of 4)
+constexpr int kDmSeg = 64;                   // K values per TMEM segment
+constexpr int kDmStages = 2;
+constexpr int kDmSumCol = 256;               // TMEM column of the running sum
+
+struct DmSmem {
+    static constexpr int ARR = arr_bytes<TF32x3W>(128);                    // one operand term
+    static constexpr int STAGE = 4 * ARR;                                    // A hi, lo, B hi, lo
+    static constexpr int OFF_BAR = kDmStages * STAGE;                        // 16 mbarriers
+    static constexpr int OFF_MISC = OFF_BAR + 16 * 8;
+    static constexpr int TOTAL = OFF_MISC + 64;
+};
+
+// rho(k) part (0: real, 1: imaginary) of C diag(f) C^H into out (nbasis x nbasis, row-major)
+__global__ void __launch_bounds__(kDmThreads, 1)
+    k_rhok_tc(Plan P, const double *__restrict__ C, const double *__restrict__ f, int nbasis, int nbands, int part,
+              double *__restrict__ out)
+{
+    using S = TF32x3W;
+    using L = DmSmem;
+    constexpr int SBO = S::KCM * kLBO;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::OFF_BAR);
+    uint64_t *full = bars, *empty = bars + 2, *segfull = bars + 4, *segempty = bars + 6, *fin = bars + 8;
+    uint32_t *tmem_base = reinterpret_cast<uint32_t *>(sm + L::OFF_MISC);
+    volatile int *pflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 4);
+    volatile int *eflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 8);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+            mbar_init(&segfull[i], 1);
+            mbar_init(&segempty[i], 256);
+        }
+        mbar_init(fin, 1);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_base)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_base;
+    const int K = 2 * nbands;
+    const int nt = (nbasis + kDmBM - 1) / kDmBM;
+    const int ntiles = nt * nt;
+    const int nchunk = (K + kDmKC - 1) / kDmKC;
+    const int nseg = (K + kDmSeg - 1) / kDmSeg;
+    constexpr int CPS = kDmSeg / kDmKC;     // chunks per segment
+
+    if (tid < kDmProd) {
+        // ------------------------------------------------------------ producers
+        const int pt = tid;
+        int g = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int m0 = (t / nt) * kDmBM, n0 = (t % nt) * kDmBN;
+            for (int ch = 0; ch < nchunk && ok; ++ch, ++g) {
+                const int stage = g % kDmStages;
+                if (g >= kDmStages)
+                    ok = role_wait(&empty[stage], ((g / kDmStages) - 1) & 1, P, pt, pflag, 1, kDmProd);
+                if (!ok) break;
+                unsigned char *base = sm + stage * L::STAGE;
+                const int k0 = ch * kDmKC;
+                // tasks: 128 A rows and 128 B rows x 8 core-matrix columns of 4 K values
+                for (int w = pt; w < 2 * 128 * S::KCM; w += kDmProd) {
+                    const int isb = w >= 128 * S::KCM;
+                    const int ww = isb ? w - 128 * S::KCM : w;
+                    const int kc = ww % S::KCM, row = ww / S::KCM;
+                    const int grow = (isb ? n0 : m0) + row;
+                    const int kk = k0 + kc * S::CG;
+                    float x[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (grow < nbasis && kk < K) {
+                        // K is even and kk a multiple of 4: the 4 values are 2 complex numbers,
+                        // both present when kk + 2 < K
+                        const double2 *cr = reinterpret_cast<const double2 *>(C + (int64_t)grow * K + kk);
+                        const double2 z0 = cr[0];
+                        const double2 z1 = kk + 2 < K ? cr[1] : make_double2(0.0, 0.0);
+                        if (isb) {
+                            const double f0 = f[kk >> 1], f1 = kk + 2 < K ? f[(kk >> 1) + 1] : 0.0;
+                            x[0] = (float)(f0 * z0.x); x[1] = (float)(f0 * z0.y);
+                            x[2] = (float)(f1 * z1.x); x[3] = (float)(f1 * z1.y);
+                        } else if (part == 0) {
+                            x[0] = (float)z0.x; x[1] = (float)z0.y; x[2] = (float)z1.x; x[3] = (float)z1.y;
+                        } else {
+                            x[0] = (float)z0.y; x[1] = (float)(-z0.x); x[2] = (float)z1.y; x[3] = (float)(-z1.x);
+                        }
+                    }
+                    unsigned char *d[2];
+                    d[0] = base + (isb ? 2 : 0) * L::ARR + cm_off<S>(row, kc);
+                    d[1] = d[0] + L::ARR;
+                    split_store<S>(x, d);
+                }
+                fence_async_smem();
+                named_sync(1, kDmProd);
+                if (pt == 0) mbar_arrive(&full[stage]);
+            }
+        }
+    } else if (tid >= kDmMma) {
+        // ------------------------------------------------------------ MMA issue (one thread)
+        if (tid == kDmMma) {
+            int g = 0, u = 0;   // chunk and segment counters
+            bool ok = true;
+            const uint32_t id = idesc<S>(kDmBM, kDmBN);
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int ch = 0; ch < nchunk && ok; ++ch, ++g) {
+                    const int stage = g % kDmStages;
+                    const bool seg0 = ch % CPS == 0, seg1 = ch % CPS == CPS - 1 || ch == nchunk - 1;
+                    const int sb = u & 1;
+                    ok = !aborted(P) && mbar_wait(&full[stage], (g / kDmStages) & 1, P.spin_limit);
+                    if (ok && seg0 && u >= 2)   // the epilogue has taken segment u - 2 out of buffer sb
+                        ok = !aborted(P) && mbar_wait(&segempty[sb], ((u >> 1) - 1) & 1, P.spin_limit);
+                    if (!ok) {
+                        report_timeout(P);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = su32(sm + stage * L::STAGE), b0 = a0 + 2 * L::ARR;
+#pragma unroll
+                    for (int ks = 0; ks < S::KCM / 2; ++ks)
+#pragma unroll
+                        for (int q = 0; q < S::NPROD; ++q) {
+                            const uint64_t da = sdesc(a0 + term(S::PA, q) * L::ARR + ks * 2 * kLBO, SBO);
+                            const uint64_t db = sdesc(b0 + term(S::PB, q) * L::ARR + ks * 2 * kLBO, SBO);
+                            const uint32_t acc = (seg0 && ks == 0 && q == 0) ? 0u : 1u;
+                            umma<false>(tmem + sb * kDmBN, da, db, id, acc);
+                        }
+                    umma_commit(&empty[stage]);
+                    if (seg1) {
+                        umma_commit(&segfull[sb]);
+                        ++u;
+                    }
+                }
+            }
+            umma_commit(fin);
+            if (!mbar_wait(fin, 0, kDrainBudget)) report_timeout(P);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue: segment sums
+        const int et = tid - kDmEpi0, ew = et >> 5, lane = et & 31;
+        const int q = ew & 3, hh = ew >> 2;   // TMEM lane quadrant, column half
+        const int row = q * 32 + lane;
+        int u = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int m0 = (t / nt) * kDmBM, n0 = (t % nt) * kDmBN;
+            for (int sg = 0; sg < nseg; ++sg, ++u) {
+                const int sb = u & 1;
+                if (!role_wait(&segfull[sb], (u >> 1) & 1, P, et, eflag, 2, 256)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t lrow = (uint32_t)(q * 32) << 16;
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    const int col = hh * 64 + c * 16;
+                    float v[16], acc[16];
+                    tmem_ld16(tmem + lrow + (uint32_t)(sb * kDmBN + col), v);
+                    if (sg > 0) {
+                        tmem_ld16(tmem + lrow + (uint32_t)(kDmSumCol + col), acc);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) acc[j] += v[j];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) acc[j] = v[j];
+                    }
+                    if (sg + 1 < nseg) {
+                        tmem_st16(tmem + lrow + (uint32_t)(kDmSumCol + col), acc);
+                    } else if (m0 + row < nbasis) {
+                        double *o = out + (int64_t)(m0 + row) * nbasis + n0 + col;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (n0 + col + j < nbasis) o[j] = f2d(acc[j]);
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&segempty[sb]);
+                // the running sum is read again by this thread only (wait::st above orders it);
+                // the barrier of the next role_wait separates the flag reads
+                named_sync(2, 256);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
     }
 }
 
@@ -136,8 +351,9 @@ extern "C" gint_status gint_density_matrix(gint_handle h, int nk, const double *
 {
     gint_status st = check(h, "gint_density_matrix");
     if (st != GINT_OK) return st;
-    if (!kfrac || !w || !C_dev || !f_dev || !DM_dev || nk < 1 || nbands < 1 || prec != GINT_FP64) {
-        set_error("gint_density_matrix: null buffer, nk < 1, nbands < 1 or a precision other than FP64");
+    if (!kfrac || !w || !C_dev || !f_dev || !DM_dev || nk < 1 || nbands < 1 ||
+        (prec != GINT_FP64 && prec != GINT_TF32X3)) {
+        set_error("gint_density_matrix: null buffer, nk < 1, nbands < 1 or a precision other than FP64, TF32X3");
         return GINT_EINVAL;
     }
     if ((st = ensure_kspace_tables(h)) != GINT_OK) return st;
@@ -156,15 +372,29 @@ extern "C" gint_status gint_density_matrix(gint_handle h, int nk, const double *
     double *re = h->d_dm_scratch, *im = re + N * N;
     const int tiles = (int)((N + kT - 1) / kT);
     const int grid = std::min(tiles * tiles, 8 * h->nsm);
+    const int tiles_tc = (int)((N + kDmBM - 1) / kDmBM);
+    if (prec == GINT_TF32X3 &&
+        (e = cudaFuncSetAttribute(k_rhok_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, DmSmem::TOTAL)) != cudaSuccess)
+        return cuda_fail(e, "gint_density_matrix: attribute");
     for (int q = 0; q < nk; ++q) {
         const double2 *Cq = (const double2 *)C_dev + (int64_t)q * N * nbands;
-        k_rhok_f64<<<grid, kGemmThreads, 0, s>>>(Cq, f_dev + (int64_t)q * nbands, (int)N, nbands, re, im);
+        const double *fq = f_dev + (int64_t)q * nbands;
+        // at k = 0 only Re rho(k) reaches the block store
+        const bool use_im = kfrac[3 * q] != 0.0 || kfrac[3 * q + 1] != 0.0 || kfrac[3 * q + 2] != 0.0;
+        if (prec == GINT_FP64) {
+            k_rhok_f64<<<grid, kGemmThreads, 0, s>>>(Cq, fq, (int)N, nbands, re, im);
+        } else {
+            const int g3 = std::min(tiles_tc * tiles_tc, h->nsm);
+            for (int part = 0; part < (use_im ? 2 : 1); ++part)
+                k_rhok_tc<<<g3, kDmThreads, DmSmem::TOTAL, s>>>(h->plan, (const double *)Cq, fq, (int)N, nbands, part,
+                                                                 part == 0 ? re : im);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gint_density_matrix: rho(k)");
         if (h->info.nblocks > 0) {
             const int g2 = (int)std::min<int64_t>(h->info.nblocks, 16 * h->nsm);
             k_unfold_acc<<<g2, 256, 0, s>>>(h->ks.d_keys, h->info.nblocks, h->ks.d_orboff, (const int64_t *)h->d_blkoff,
                                             re, im, kfrac[3 * q], kfrac[3 * q + 1], kfrac[3 * q + 2], w[q], (int)N,
-                                            q == 0, DM_dev);
+                                            q == 0, prec == GINT_FP64 || use_im, DM_dev);
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gint_density_matrix: unfold");
         }
     }

@@ -190,20 +190,6 @@ __device__ __forceinline__ int64_t grid_index(const SInfo &SI, const Batch &B, i
     return ((int64_t)(B.i0 + a) * SI.grid[1] + (B.j0 + b)) * SI.grid[2] + (B.k0 + c);
 }
 
-// Role-uniform bounded wait: thread 0 of the role waits, the verdict is shared through `flag`.
-// The callers pass another barrier of the same role between two calls, so every thread has
-// read the flag before thread 0 writes it again.
-__device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, const Plan &P, int rtid, volatile int *flag,
-                                          int barid, int nthr)
-{
-    if (rtid == 0) {
-        bool ok = !aborted(P) && mbar_wait(bar, parity, P.spin_limit);
-        if (!ok) report_timeout(P);
-        *flag = ok ? 0 : 1;
-    }
-    named_sync(barid, nthr);
-    return *flag == 0;
-}
 
 __device__ __forceinline__ void load_species(const Plan &P, SpecSh *spec, int tid)
 {

@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 
+#include "gint_device.cuh"
+
 namespace gint {
 
 constexpr int kLBO = 144;         // bytes between core matrices along K
@@ -96,6 +98,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float *v)
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t addr, const float *v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(addr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+                 "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+                 "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+                 "r"(__float_as_uint(v[15]))
+                 : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // ------------------------------------------------------------------ precision schemes
@@ -220,6 +235,22 @@ __device__ __forceinline__ double f2d(float f)
     const uint64_t bits = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
                           ((uint64_t)(u & 0x7FFFFFu) << 29);
     return __longlong_as_double((long long)bits);
+}
+
+
+// Role-uniform bounded wait: thread 0 of the role waits, the verdict is shared through `flag`.
+// The callers pass another barrier of the same role between two calls, so every thread has
+// read the flag before thread 0 writes it again.
+__device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, const Plan &P, int rtid, volatile int *flag,
+                                          int barid, int nthr)
+{
+    if (rtid == 0) {
+        bool ok = !aborted(P) && mbar_wait(bar, parity, P.spin_limit);
+        if (!ok) report_timeout(P);
+        *flag = ok ? 0 : 1;
+    }
+    named_sync(barid, nthr);
+    return *flag == 0;
 }
 
 }  // namespace gint

@@ -206,8 +206,10 @@ gint_status gint_unfold(gint_handle h, const double *Xk_dev, int nk, const doubl
  *             row = orbital mu (atom-major order), column = band n
  *   f         device, nk x nbands occupations
  *   DM        device, block layout, overwritten
- * prec: GINT_FP64 (CUDA-core complex GEMM per k point).  Library-owned scratch of
- * 16 * nbasis^2 bytes (dense rho(k)) is allocated on first use and kept until gint_destroy. */
+ * prec: GINT_FP64 (CUDA-core complex GEMM per k point) or GINT_TF32X3 (tensor cores: the band
+ * sum in 64-term segments accumulated in TMEM, segments added in FP32; relative error ~6e-7).
+ * Library-owned scratch of 16 * nbasis^2 bytes (dense rho(k)) is allocated on first use and kept
+ * until gint_destroy. */
 gint_status gint_density_matrix(gint_handle h, int nk, const double *kfrac, const double *w, int nbands,
                                 const double *C_dev, const double *f_dev, double *DM_dev, gint_prec prec,
                                 void *stream);

@@ -223,8 +223,8 @@ struct VSmem {
     static constexpr int ROWS = kMaxNb;                   // orbitals per batch
     static constexpr int ARR = arr_bytes<S>(256);         // one operand term (tile 1 reads rows 128..255)
     static constexpr int STAGE = 2 * S::NT * ARR;         // A terms then B terms
-    // one stage for 32-point chunks (the chunk's MMAs overlap the next chunk's orbital
-    // evaluation into the staging tile, which comes before the stage is rewritten), else two
+    // stages per scheme: with one, the chunk's MMAs overlap the next chunk's orbital
+    // evaluation into the staging tile, which comes before the stage is rewritten
     static constexpr int NSTAGE = S::VSTAGES;
     static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [256][KC]
     static constexpr int OFF_PSLOT = OFF_STG + ROWS * KC * 4;               // PSlot[2][64]
@@ -522,9 +522,8 @@ struct RSmem {
     static constexpr int ARR_A = arr_bytes<S>(kMaxBatchPts);
     static constexpr int ARR_B = arr_bytes<S>(kMaxNb);
     static constexpr int STAGE = S::NT * (ARR_A + ARR_B);
-    // one stage for the 32-orbital TF32x3 and BF16x6 chunks (the MMAs of a chunk overlap the
-    // next chunk's orbital evaluation and gather tables, which come before the stage is
-    // rewritten; measured faster than two), two otherwise
+    // stages per scheme: with one, the MMAs of a chunk overlap the next chunk's orbital
+    // evaluation and gather tables, which come before the stage is rewritten
     static constexpr int NSTAGE = S::RSTAGES;
     static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [RING][128]
     static constexpr int OFF_PSLOT = OFF_STG + RING * kMaxBatchPts * 4;     // producer PSlot[64]

@@ -114,47 +114,29 @@ __device__ __forceinline__ void tmem_st16(uint32_t addr, const float *v)
 }
 
 // ------------------------------------------------------------------ precision schemes
-// CG elements = 16 bytes per core-matrix row; KCM core matrices per row per pipeline chunk.
+// CG elements = 16 bytes per core-matrix row; KCM core matrices per row per pipeline chunk, so a
+// chunk is 32 K values (points for vlocal, orbitals for rho) in every scheme.  RSTAGES / VSTAGES:
+// operand stages in the rho/force and vlocal kernels (one stage suffices when the next chunk's
+// orbital evaluation, which precedes the stage rewrite, covers the chunk's MMAs; measured).
 // PA/PB: operand term of product q, packed one nibble per product.
-struct TF32x3 {
-    static constexpr int CG = 4, NT = 2, NPROD = 3, KCM = 4;
-    static constexpr int RSTAGES = 2;   // operand stages in the rho/force kernel
-    static constexpr int VSTAGES = 2;   // operand stages in the vlocal kernel
-    static constexpr bool F16 = false;
-    static constexpr uint32_t FMT = 2, PA = 0x100, PB = 0x010;
-};
-struct TF32x3W {  // TF32x3 with 32-element chunks and one stage (rho/force kernel)
+struct TF32x3W {  // hi + lo TF32 terms, products hi.hi + hi.lo + lo.hi
     static constexpr int CG = 4, NT = 2, NPROD = 3, KCM = 8;
-    static constexpr int RSTAGES = 1;   // operand stages in the rho/force kernel
-    static constexpr int VSTAGES = 1;   // operand stages in the vlocal kernel
+    static constexpr int RSTAGES = 1;
+    static constexpr int VSTAGES = 1;
     static constexpr bool F16 = false;
     static constexpr uint32_t FMT = 2, PA = 0x100, PB = 0x010;
 };
-struct BF16x3 {
-    static constexpr int CG = 8, NT = 2, NPROD = 3, KCM = 2;
-    static constexpr int RSTAGES = 2;   // operand stages in the rho/force kernel
-    static constexpr int VSTAGES = 2;   // operand stages in the vlocal kernel
-    static constexpr bool F16 = true;
-    static constexpr uint32_t FMT = 1, PA = 0x100, PB = 0x010;
-};
-struct BF16x3W {  // BF16x3 with 32-element chunks (rho/force kernel, which has the shared memory)
+struct BF16x3W {  // hi + lo BF16 terms, the same three products
     static constexpr int CG = 8, NT = 2, NPROD = 3, KCM = 4;
-    static constexpr int RSTAGES = 2;   // operand stages in the rho/force kernel
-    static constexpr int VSTAGES = 1;   // operand stages in the vlocal kernel
+    static constexpr int RSTAGES = 2;
+    static constexpr int VSTAGES = 1;
     static constexpr bool F16 = true;
     static constexpr uint32_t FMT = 1, PA = 0x100, PB = 0x010;
 };
-struct BF16x6W {  // BF16x6 with 32-element chunks and one stage (rho/force kernel)
+struct BF16x6W {  // hi + mid + lo BF16 terms, the six products of total order <= 2
     static constexpr int CG = 8, NT = 3, NPROD = 6, KCM = 4;
-    static constexpr int RSTAGES = 1;   // operand stages in the rho/force kernel
-    static constexpr int VSTAGES = 1;   // operand stages in the vlocal kernel
-    static constexpr bool F16 = true;
-    static constexpr uint32_t FMT = 1, PA = 0x210100, PB = 0x012010;
-};
-struct BF16x6 {
-    static constexpr int CG = 8, NT = 3, NPROD = 6, KCM = 2;
-    static constexpr int RSTAGES = 2;   // operand stages in the rho/force kernel
-    static constexpr int VSTAGES = 2;   // operand stages in the vlocal kernel
+    static constexpr int RSTAGES = 1;
+    static constexpr int VSTAGES = 1;
     static constexpr bool F16 = true;
     static constexpr uint32_t FMT = 1, PA = 0x210100, PB = 0x012010;
 };

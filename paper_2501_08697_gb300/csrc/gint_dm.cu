@@ -14,8 +14,10 @@
 // an error that grows with the number of MMA steps, so K is cut into 64-term segments: each
 // segment is accumulated in its own TMEM buffer (24 MMA steps, as a 64-point vlocal batch), and
 // the epilogue adds the segments with round-to-nearest FP32 additions into a running sum kept in
-// TMEM.  128 x 128 output tiles, persistent CTAs; 8 producer warps split FP64 -> TF32 hi/lo into
-// the canonical operand layout, one thread issues the MMAs, 8 epilogue warps sum the segments.
+// TMEM.  The operands are split once per k point into TF32 hi / lo planes (rows padded to 128,
+// K to 32, zero-filled); 128 x 128 output tiles, persistent CTAs; 8 producer warps copy the
+// planes into the canonical operand layout with cp.async (three stages in flight), one thread
+// issues the MMAs, 8 epilogue warps sum the segments.
 #include <algorithm>
 #include <vector>
 
@@ -130,7 +132,7 @@ constexpr int kDmThreads = 544;
 constexpr int kDmBM = 128, kDmBN = 128;      // output tile
 constexpr int kDmKC = 32;                    // K values per chunk (TF32x3W: 8 core matrices of 4)
 constexpr int kDmSeg = 64;                   // K values per TMEM segment
-constexpr int kDmStages = 2;
+constexpr int kDmStages = 3;
 constexpr int kDmSumCol = 256;               // TMEM column of the running sum
 
 struct DmSmem {
@@ -141,25 +143,59 @@ struct DmSmem {
     static constexpr int TOTAL = OFF_MISC + 64;
 };
 
+// TF32 hi / lo planes of the three operands, each [Np][Kp] floats (Np = nbasis rounded up to 128,
+// Kp = 2 nbands rounded up to 32, zero-filled): plane 2p + t holds term t of operand p, with
+// p = 0: A_re (C as reals), 1: A_im (pairs (Im c, -Re c)), 2: B (f_n C as reals).
+__global__ void k_dm_split(const double *__restrict__ C, const double *__restrict__ f, int nbasis, int nbands,
+                           int Np, int Kp, int with_im, float *__restrict__ planes)
+{
+    const int K = 2 * nbands;
+    const int64_t plane = (int64_t)Np * Kp;
+    const int64_t n = plane;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int row = (int)(e / Kp), k = (int)(e - (int64_t)row * Kp);
+        double a = 0.0, ai = 0.0, b = 0.0;
+        if (row < nbasis && k < K) {
+            const double v = C[(int64_t)row * K + k];
+            const double w = C[(int64_t)row * K + (k ^ 1)];   // the other part of the same number
+            a = v;
+            ai = (k & 1) ? -w : w;                             // (Im c, -Re c)
+            b = f[k >> 1] * v;
+        }
+        const double vals[3] = {a, ai, b};
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            if (p == 1 && !with_im) continue;
+            const float x = (float)vals[p];
+            const float hi = tf32_rna(x);
+            planes[(2 * p) * plane + e] = hi;
+            planes[(2 * p + 1) * plane + e] = tf32_rna(x - hi);
+        }
+    }
+}
+
 // rho(k) part (0: real, 1: imaginary) of C diag(f) C^H into out (nbasis x nbasis, row-major)
 __global__ void __launch_bounds__(kDmThreads, 1)
-    k_rhok_tc(Plan P, const double *__restrict__ C, const double *__restrict__ f, int nbasis, int nbands, int part,
-              double *__restrict__ out)
+    k_rhok_tc(Plan P, const float *__restrict__ planes, int Np, int Kp, int nbasis, int part, double *__restrict__ out)
 {
     using S = TF32x3W;
     using L = DmSmem;
     constexpr int SBO = S::KCM * kLBO;
     extern __shared__ __align__(1024) unsigned char sm[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::OFF_BAR);
-    uint64_t *full = bars, *empty = bars + 2, *segfull = bars + 4, *segempty = bars + 6, *fin = bars + 8;
+    uint64_t *full = bars, *empty = bars + kDmStages, *segfull = bars + 2 * kDmStages;
+    uint64_t *segempty = segfull + 2, *fin = segfull + 4;
+    static_assert(2 * kDmStages + 5 <= 16, "mbarrier space");
     uint32_t *tmem_base = reinterpret_cast<uint32_t *>(sm + L::OFF_MISC);
     volatile int *pflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 4);
     volatile int *eflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 8);
     const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kDmStages; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
             mbar_init(&segfull[i], 1);
             mbar_init(&segempty[i], 256);
         }
@@ -174,18 +210,29 @@ __global__ void __launch_bounds__(kDmThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_base;
-    const int K = 2 * nbands;
-    const int nt = (nbasis + kDmBM - 1) / kDmBM;
+    const int nt = Np / kDmBM;
     const int ntiles = nt * nt;
-    const int nchunk = (K + kDmKC - 1) / kDmKC;
-    const int nseg = (K + kDmSeg - 1) / kDmSeg;
+    const int nchunk = Kp / kDmKC;
+    const int nseg = (Kp + kDmSeg - 1) / kDmSeg;
+    const int64_t plane = (int64_t)Np * Kp;
     constexpr int CPS = kDmSeg / kDmKC;     // chunks per segment
 
     if (tid < kDmProd) {
         // ------------------------------------------------------------ producers
+        // chunk g is copied into stage g % 3 with cp.async; its completion is awaited one
+        // chunk later (so two chunks are in flight), then fenced for the async proxy and
+        // announced on full[stage]
         const int pt = tid;
         int g = 0;
         bool ok = true;
+        const float *Ah = planes + (2 * part) * plane, *Al = Ah + plane;
+        const float *Bh = planes + 4 * plane, *Bl = Bh + plane;
+        auto announce = [&](int gg) {
+            cp_async_wait_group1();
+            fence_async_smem();
+            named_sync(1, kDmProd);
+            if (pt == 0) mbar_arrive(&full[gg % kDmStages]);
+        };
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const int m0 = (t / nt) * kDmBM, n0 = (t % nt) * kDmBN;
             for (int ch = 0; ch < nchunk && ok; ++ch, ++g) {
@@ -195,40 +242,28 @@ __global__ void __launch_bounds__(kDmThreads, 1)
                 if (!ok) break;
                 unsigned char *base = sm + stage * L::STAGE;
                 const int k0 = ch * kDmKC;
-                // tasks: 128 A rows and 128 B rows x 8 core-matrix columns of 4 K values
-                for (int w = pt; w < 2 * 128 * S::KCM; w += kDmProd) {
-                    const int isb = w >= 128 * S::KCM;
-                    const int ww = isb ? w - 128 * S::KCM : w;
-                    const int kc = ww % S::KCM, row = ww / S::KCM;
-                    const int grow = (isb ? n0 : m0) + row;
-                    const int kk = k0 + kc * S::CG;
-                    float x[4] = {0.f, 0.f, 0.f, 0.f};
-                    if (grow < nbasis && kk < K) {
-                        // K is even and kk a multiple of 4: the 4 values are 2 complex numbers,
-                        // both present when kk + 2 < K
-                        const double2 *cr = reinterpret_cast<const double2 *>(C + (int64_t)grow * K + kk);
-                        const double2 z0 = cr[0];
-                        const double2 z1 = kk + 2 < K ? cr[1] : make_double2(0.0, 0.0);
-                        if (isb) {
-                            const double f0 = f[kk >> 1], f1 = kk + 2 < K ? f[(kk >> 1) + 1] : 0.0;
-                            x[0] = (float)(f0 * z0.x); x[1] = (float)(f0 * z0.y);
-                            x[2] = (float)(f1 * z1.x); x[3] = (float)(f1 * z1.y);
-                        } else if (part == 0) {
-                            x[0] = (float)z0.x; x[1] = (float)z0.y; x[2] = (float)z1.x; x[3] = (float)z1.y;
-                        } else {
-                            x[0] = (float)z0.y; x[1] = (float)(-z0.x); x[2] = (float)z1.y; x[3] = (float)(-z1.x);
-                        }
-                    }
-                    unsigned char *d[2];
-                    d[0] = base + (isb ? 2 : 0) * L::ARR + cm_off<S>(row, kc);
-                    d[1] = d[0] + L::ARR;
-                    split_store<S>(x, d);
+                // 128 A rows and 128 B rows x 8 core-matrix columns x 2 terms, 16 bytes each
+                for (int w = pt; w < 4 * 128 * S::KCM; w += kDmProd) {
+                    const int term = w / (2 * 128 * S::KCM);
+                    const int ww = w - term * (2 * 128 * S::KCM);
+                    const int isb = ww >= 128 * S::KCM;
+                    const int w2 = isb ? ww - 128 * S::KCM : ww;
+                    const int kc = w2 % S::KCM, row = w2 / S::KCM;
+                    const float *src = (isb ? (term ? Bl : Bh) : (term ? Al : Ah)) +
+                                       (int64_t)((isb ? n0 : m0) + row) * Kp + k0 + kc * S::CG;
+                    cp_async16(base + (isb ? 2 : 0) * L::ARR + term * L::ARR + cm_off<S>(row, kc), src);
                 }
-                fence_async_smem();
-                named_sync(1, kDmProd);
-                if (pt == 0) mbar_arrive(&full[stage]);
+                cp_async_commit();
+                if (g > 0) announce(g - 1);   // the previous chunk has landed
             }
         }
+        if (ok && g > 0) {
+            cp_async_wait_all();
+            fence_async_smem();
+            named_sync(1, kDmProd);
+            if (pt == 0) mbar_arrive(&full[(g - 1) % kDmStages]);
+        }
+        cp_async_wait_all();
     } else if (tid >= kDmMma) {
         // ------------------------------------------------------------ MMA issue (one thread)
         if (tid == kDmMma) {
@@ -369,6 +404,16 @@ extern "C" gint_status gint_density_matrix(gint_handle h, int nk, const double *
             return cuda_fail(e, "gint_density_matrix: allocate");
         h->dm_scratch_bytes = need;
     }
+    const int Np = (int)((N + kDmBM - 1) / kDmBM) * kDmBM, Kp = (2 * nbands + kDmKC - 1) / kDmKC * kDmKC;
+    const size_t need_planes = prec == GINT_TF32X3 ? sizeof(float) * 6 * (size_t)Np * Kp : 0;
+    if (h->dm_planes_bytes < need_planes) {
+        if (h->d_dm_planes) cudaFree(h->d_dm_planes);
+        h->d_dm_planes = nullptr;
+        h->dm_planes_bytes = 0;
+        if ((e = cudaMalloc((void **)&h->d_dm_planes, need_planes)) != cudaSuccess)
+            return cuda_fail(e, "gint_density_matrix: allocate");
+        h->dm_planes_bytes = need_planes;
+    }
     double *re = h->d_dm_scratch, *im = re + N * N;
     const int tiles = (int)((N + kT - 1) / kT);
     const int grid = std::min(tiles * tiles, 8 * h->nsm);
@@ -385,8 +430,11 @@ extern "C" gint_status gint_density_matrix(gint_handle h, int nk, const double *
             k_rhok_f64<<<grid, kGemmThreads, 0, s>>>(Cq, fq, (int)N, nbands, re, im);
         } else {
             const int g3 = std::min(tiles_tc * tiles_tc, h->nsm);
+            const int64_t n = (int64_t)Np * Kp;
+            k_dm_split<<<(int)std::min<int64_t>((n + 255) / 256, 8 * h->nsm), 256, 0, s>>>(
+                (const double *)Cq, fq, (int)N, nbands, Np, Kp, use_im, h->d_dm_planes);
             for (int part = 0; part < (use_im ? 2 : 1); ++part)
-                k_rhok_tc<<<g3, kDmThreads, DmSmem::TOTAL, s>>>(h->plan, (const double *)Cq, fq, (int)N, nbands, part,
+                k_rhok_tc<<<g3, kDmThreads, DmSmem::TOTAL, s>>>(h->plan, h->d_dm_planes, Np, Kp, (int)N, part,
                                                                  part == 0 ? re : im);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gint_density_matrix: rho(k)");

@@ -153,6 +153,8 @@ struct gint_handle_s {
     } ks;
     double *d_dm_scratch = nullptr;  // dense rho(k), planar real / imaginary (gint_density_matrix)
     size_t dm_scratch_bytes = 0;
+    float *d_dm_planes = nullptr;    // TF32 hi / lo operand planes of the tensor-core density matrix
+    size_t dm_planes_bytes = 0;
     double *d_hostio = nullptr;      // buffers of gint_run_host (allocated on first use)
     size_t hostio_bytes = 0;
     cudaStream_t last_stream = nullptr;

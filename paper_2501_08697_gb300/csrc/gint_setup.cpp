@@ -550,7 +550,7 @@ static void free_dev(gint_handle h)
                     h->d_dm32, h->d_poff, h->d_red, h->d_hostio, h->bs[0].d_batches, h->bs[0].d_slots, h->bs[0].d_tbl,
                     h->bs[0].d_rng, h->bs[1].d_batches, h->bs[1].d_slots, h->bs[1].d_tbl, h->bs[1].d_rng,
                     h->ks.d_keys, h->ks.d_grp, h->ks.d_pair, h->ks.d_colatom, h->ks.d_orboff, h->ks.d_kvec,
-                    h->ks.d_phase, h->d_dm_scratch};
+                    h->ks.d_phase, h->d_dm_scratch, h->d_dm_planes};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }

@@ -76,6 +76,7 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_group1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // FP64 add to global memory without a return value (the scatters never read the old value)
 __device__ __forceinline__ void red_add_f64(double *a, double v)

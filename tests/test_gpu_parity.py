@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-11, "fp32": 1e-6, "tf32x3": 1e-6, "bf16x6": 1e-6, "bf16x3": 5e-5}
-FORCE_TOL = {"fp64": 1e-10, "fp32": 2e-6, "tf32x3": 2e-6, "bf16x6": 2e-6, "bf16x3": 1e-4}
+FORCE_TOL = {"fp64": 1e-10, "fp32": 1e-6, "tf32x3": 1e-6, "bf16x6": 1e-6, "bf16x3": 1e-4}
 SIMT = ["fp64", "fp32"]
 ALL = ["fp64", "fp32", "tf32x3", "bf16x3", "bf16x6"]
 CASES = ["si8", "si8_ragged", "si16_strained", "water8", "water1_vacuum", "si8_2d"]
@@ -87,9 +87,9 @@ def test_tensor_core_batch_shapes(G, batch, prec):
     """One-tile (<= 128 orbitals), two-tile and split batches; ragged grid.  Batches of at
     most 64 points keep the tensor-core FP32 accumulation within 1e-6 for vlocal."""
     ref, h, H, rho, F = _run(G, "si8_ragged", prec, batch)
-    assert rel_fro(H, ref["H"]) <= 1e-6
-    assert rel_fro(rho, ref["rho"]) <= 1e-6
-    assert rel_fro(F, ref["F"]) <= 2e-6
+    eH, er, eF = rel_fro(H, ref["H"]), rel_fro(rho, ref["rho"]), rel_fro(F, ref["F"])
+    print(f"si8_ragged {prec} batch {batch}: H {eH:.2e} rho {er:.2e} F {eF:.2e}")
+    assert eH <= 1e-6 and er <= 1e-6 and eF <= 1e-6
 
 
 @pytest.mark.parametrize("batch", [(4, 4, 4), (8, 4, 4), (2, 2, 2), (8, 8, 2)])

@@ -263,7 +263,12 @@ struct SpecSh {
 
 // FP32 orbital values of one species at displacement d (no gradient); rsqrt + one Newton
 // step instead of sqrt and division.  emit(o, phi) for o = 0 .. norb-1.
-template <typename Emit>
+// radials per species whose spline records eval_phi_f32<true> fetches all at once (the rho
+// producers; the vlocal producers and the gradient evaluator, which hold more live values,
+// measured faster loading them radial by radial)
+constexpr int kPrefetchRad = 5;
+
+template <bool PREFETCH = false, typename Emit>
 __device__ __forceinline__ void eval_phi_f32(const SpecSh &S, const float4 *__restrict__ coef, float dx, float dy,
                                              float dz, Emit &&emit)
 {
@@ -297,8 +302,7 @@ __device__ __forceinline__ void eval_phi_f32(const SpecSh &S, const float4 *__re
     const float ux = dx * ir1, uy = dy * ir1, uz = dz * ir1;
     const float4 *cp = coef + S.coef_off + i * nrad;
     int o = 0;
-    for (int ir = 0; ir < nrad; ++ir) {
-        const float4 c = __ldg(cp + ir);
+    auto radial = [&](const float4 &c, int ir) {
         const float f = c.x + t * (c.y + t * (c.z + t * c.w));
         const int l = (S.lpack >> (2 * ir)) & 3;
         if (l == 0) {
@@ -316,6 +320,19 @@ __device__ __forceinline__ void eval_phi_f32(const SpecSh &S, const float4 *__re
             emit(o + 4, f * YC<float>::c21 * ux * uy);
             o += 5;
         }
+    };
+    if (PREFETCH && nrad <= kPrefetchRad) {
+        // all spline records of the slot are requested before the first is used, so their
+        // latencies overlap instead of adding up radial by radial
+        float4 c[kPrefetchRad];
+#pragma unroll
+        for (int ir = 0; ir < kPrefetchRad; ++ir)
+            if (ir < nrad) c[ir] = __ldg(cp + ir);
+#pragma unroll
+        for (int ir = 0; ir < kPrefetchRad; ++ir)
+            if (ir < nrad) radial(c[ir], ir);
+    } else {
+        for (int ir = 0; ir < nrad; ++ir) radial(__ldg(cp + ir), ir);
     }
 }
 
@@ -363,8 +380,7 @@ __device__ __forceinline__ void eval_phigrad_f32(const SpecSh &S, const float4 *
     const float ux = dx * ir1, uy = dy * ir1, uz = dz * ir1;
     const float4 *cp = coef + S.coef_off + i * nrad;
     int o = 0;
-    for (int ir = 0; ir < nrad; ++ir) {
-        const float4 c = __ldg(cp + ir);
+    auto radial = [&](const float4 &c, int ir) {
         const float f = c.x + t * (c.y + t * (c.z + t * c.w));
         const float df = (c.y + t * (2.f * c.z + 3.f * t * c.w)) * S.inv_dr;
         const int l = (S.lpack >> (2 * ir)) & 3;
@@ -400,7 +416,8 @@ __device__ __forceinline__ void eval_phigrad_f32(const SpecSh &S, const float4 *
             emit(o + 4, g * Sv, gp * ux * Sv + g * c21 * dy, gp * uy * Sv + g * c21 * dx, gp * uz * Sv);
             o += 5;
         }
-    }
+    };
+    for (int ir = 0; ir < nrad; ++ir) radial(__ldg(cp + ir), ir);
 }
 
 // ----------------------------------------------------------------------- status and waits

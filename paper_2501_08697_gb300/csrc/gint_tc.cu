@@ -535,8 +535,8 @@ struct RSmem {
     static constexpr int OFF_EPOFF = OFF_EPSLOT + kMaxSlots * (int)sizeof(PSlot);
     static constexpr int OFF_WIN = OFF_EPOFF + kMaxBatchPts * 24;           // float [8][kWin][32]
     static constexpr int OFF_RPART = OFF_WIN + 8 * kWin * 32 * 4;           // float [128]
-    static constexpr int OFF_FACC = OFF_RPART + kMaxBatchPts * 4;           // double [64][3]
-    static constexpr int OFF_BAR = OFF_FACC + kMaxSlots * 3 * 8;             // 16 mbarriers
+    static constexpr int OFF_FACC = OFF_RPART + kMaxBatchPts * 4;           // float [64][3]
+    static constexpr int OFF_BAR = OFF_FACC + kMaxSlots * 3 * 4;             // 16 mbarriers
     static constexpr int OFF_MISC = OFF_BAR + 16 * 8;
     static constexpr int OFF_SPEC = OFF_MISC + 64;
     static constexpr int TOTAL = OFF_SPEC + kMaxSpecies * (int)sizeof(SpecSh);
@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     float *win = reinterpret_cast<float *>(sm + L::OFF_WIN);
     float *rpart = reinterpret_cast<float *>(sm + L::OFF_RPART);
     SpecSh *spec = reinterpret_cast<SpecSh *>(sm + L::OFF_SPEC);
-    double *facc = reinterpret_cast<double *>(sm + L::OFF_FACC);
+    float *facc = reinterpret_cast<float *>(sm + L::OFF_FACC);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::OFF_BAR);
     uint64_t *empty = bars, *accfull = bars + 2, *accempty = bars + 4, *fin = bars + 6, *full = bars + 8;
     uint32_t *tmem_base = reinterpret_cast<uint32_t *>(sm + L::OFF_MISC);
@@ -644,7 +644,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         if (p < npb) {
                             float dx, dy, dz;
                             disp(sl, poff + 6 * p, dx, dy, dz);
-                            eval_phi_f32(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) {
+                            eval_phi_f32<true>(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) {
                                 col[((sl.off + o) & (RING - 1)) * kMaxBatchPts] = v;
                             });
                         } else {
@@ -661,7 +661,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         if (p < npb) {
                             float dx, dy, dz;
                             disp(sl, poff + 6 * p, dx, dy, dz);
-                            eval_phi_f32(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) {
+                            eval_phi_f32<true>(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) {
                                 const int k = base_k + o;
                                 if (k >= 0 && k < KC) col[k * kMaxBatchPts] = v;
                             });
@@ -813,7 +813,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             named_sync(2, kEpi);
             load_geom(P, SI, B, eps, epoff, et, kEpi);
             if (FORCE)
-                for (int e = et; e < 3 * ns; e += kEpi) facc[e] = 0.0;
+                for (int e = et; e < 3 * ns; e += kEpi) facc[e] = 0.f;
             if (!role_wait(&accfull[buf], (it >> 1) & 1, P, et, eflag, 2, kEpi)) break;
             tc_fence_after();
             const bool pv = p < npb;
@@ -883,9 +883,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         fz += __shfl_xor_sync(0xffffffffu, fz, m);
                     }
                     if (lane == 0) {
-                        atomicAdd(&facc[3 * s + 0], f2d(fx));
-                        atomicAdd(&facc[3 * s + 1], f2d(fy));
-                        atomicAdd(&facc[3 * s + 2], f2d(fz));
+                        // the four lane quadrants of a slot meet here: FP32 shared-memory adds
+                        // (native), FP64 from the per-batch sum on
+                        atomicAdd(&facc[3 * s + 0], fx);
+                        atomicAdd(&facc[3 * s + 1], fy);
+                        atomicAdd(&facc[3 * s + 2], fz);
                     }
                 }
             }
@@ -896,7 +898,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             if (RHO && hh == 0 && pv) SI.rho[gi] = f2d(racc + rpart[p]);
             if (FORCE && SI.F)
                 for (int e = et; e < 3 * ns; e += kEpi)
-                    red_add_f64(&SI.F[3 * eps[e / 3].atom + e % 3], 2.0 * SI.dV * facc[e]);
+                    red_add_f64(&SI.F[3 * eps[e / 3].atom + e % 3], 2.0 * SI.dV * f2d(facc[e]));
             if (strain && pv) {
 #pragma unroll
                 for (int k = 0; k < 9; ++k) sacc[k] += f2d(vp * st[k]);

@@ -542,7 +542,7 @@ struct RSmem {
     static constexpr int TOTAL = OFF_SPEC + kMaxSpecies * (int)sizeof(SpecSh);
 };
 
-template <class S, bool RHO, bool FORCE>
+template <class S, bool RHO, bool FORCE, bool STRAIN>
 __global__ void __launch_bounds__(kThreadsTC, 1)
     k_rho_tc(Plan P, SInfo si0, const SInfo *__restrict__ sis)
 {
@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         int it = 0;
         // strain derivative (single-structure launches): [0..8] Sum V grad_a phi . Psi d_b,
         // [9] Sum V rho, over this thread's points and atom images
-        const bool strain = FORCE && si0.dLde != nullptr && sis == nullptr;
+        const bool strain = STRAIN && FORCE && si0.dLde != nullptr && sis == nullptr;
         double sacc[10];
 #pragma unroll
         for (int k = 0; k < 10; ++k) sacc[k] = 0.0;
@@ -955,15 +955,15 @@ cudaError_t vlocal_launch(const Plan &P, const SInfo &si0, const SInfo *sis, cud
     return cudaGetLastError();
 }
 
-template <class S, bool R, bool Fo>
+template <class S, bool R, bool Fo, bool St>
 cudaError_t rho_launch3(const Plan &P, const SInfo &si0, const SInfo *sis, cudaStream_t s, int nsm)
 {
     constexpr int smem = RSmem<S>::TOTAL;
     static_assert(smem <= 232448, "rho shared memory");
-    cudaError_t e = set_smem(k_rho_tc<S, R, Fo>, smem);
+    cudaError_t e = set_smem(k_rho_tc<S, R, Fo, St>, smem);
     if (e != cudaSuccess) return e;
     const int grid = P.rng ? P.npart : std::min(nsm, P.nbatches);
-    k_rho_tc<S, R, Fo><<<grid, kThreadsTC, smem, s>>>(P, si0, sis);
+    k_rho_tc<S, R, Fo, St><<<grid, kThreadsTC, smem, s>>>(P, si0, sis);
     return cudaGetLastError();
 }
 
@@ -971,9 +971,12 @@ template <class S>
 cudaError_t rho_launch(const Plan &P, const SInfo &si0, const SInfo *sis, bool rho, bool force, cudaStream_t s,
                        int nsm)
 {
-    if (rho && force) return rho_launch3<S, true, true>(P, si0, sis, s, nsm);
-    if (rho) return rho_launch3<S, true, false>(P, si0, sis, s, nsm);
-    return rho_launch3<S, false, true>(P, si0, sis, s, nsm);
+    // the strain derivative has its own instantiation, so the other paths keep its
+    // accumulators out of their registers
+    if (si0.dLde) return rho_launch3<S, false, true, true>(P, si0, sis, s, nsm);
+    if (rho && force) return rho_launch3<S, true, true, false>(P, si0, sis, s, nsm);
+    if (rho) return rho_launch3<S, true, false, false>(P, si0, sis, s, nsm);
+    return rho_launch3<S, false, true, false>(P, si0, sis, s, nsm);
 }
 
 }  // namespace

@@ -556,6 +556,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     unsigned char *oslot = sm + L::OFF_OMAP, *oidx = oslot + kMaxNb;
     int *gbase = reinterpret_cast<int *>(sm + L::OFF_GBASE);
     int *gna = reinterpret_cast<int *>(sm + L::OFF_GNA);
+    // slot-pair table of a batch with at most kVTbl atom images, in the tail of the gather
+    // bases (which then use at most kVTbl * KC entries)
+    static_assert(kVTbl * KC + kVTbl * kVTbl <= kMaxSlots * KC, "slot-pair table placement");
+    int *rtbl = gbase + kMaxSlots * KC - kVTbl * kVTbl;
     PSlot *eps = reinterpret_cast<PSlot *>(sm + L::OFF_EPSLOT);
     float *epoff = reinterpret_cast<float *>(sm + L::OFF_EPOFF);
     float *win = reinterpret_cast<float *>(sm + L::OFF_WIN);
@@ -617,6 +621,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             const int *__restrict__ tbl = P.tbl + B.tbl;
             named_sync(1, kProd);
             load_geom(P, SI, B, ps, poff, pt, kProd);
+            // the batch's slot-pair table in shared memory (gather tables read it per chunk)
+            const bool tsm = ns <= kVTbl;
+            if (tsm)
+                for (int e = pt; e < ns * ns; e += kProd) rtbl[e] = __ldg(tbl + e);
             named_sync(1, kProd);
             for (int s = pt; s < ns; s += kProd)
                 for (int o = 0; o < ps[s].norb; ++o) {
@@ -684,7 +692,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     int v = -1;
                     if (mu < nb) {
                         const int a = oslot[mu];
-                        const int e = __ldg(tbl + b * ns + a);
+                        const int e = tsm ? rtbl[b * ns + a] : __ldg(tbl + b * ns + a);
                         if (e >= 0) v = (e >> 1) + oidx[mu];
                     }
                     gbase[w] = v;
@@ -707,7 +715,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 }
                 // phase 2b: B = D rows nu (N), K = orbitals mu of the chunk: D(b_nu, a_mu)[o_nu][o_mu]
                 // read in FP32 through the chunk tables; GB tasks per thread, loads issued first
-                constexpr int GB = 4;
+                // (five 4-wide tasks cover a 220-column chunk in one round without spills)
+                constexpr int GB = S::CG == 4 ? 5 : 4;
                 for (int w0 = pt; w0 < npad * S::KCM; w0 += kProd * GB) {
                     float x[GB][S::CG];
 #pragma unroll

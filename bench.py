@@ -42,20 +42,27 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# DRAM bytes per launch of the dominant tensor-core kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture), keyed by the SHA-256 prefix of the kernel source
-# the counters were taken on: once the kernel changes, the bench reports traffic = null.
+# DRAM bytes per launch of the tensor-core kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture), keyed by the SHA-256 prefix of the kernel sources
+# the counters were taken on: once a kernel source changes, the bench reports traffic = null.
 NCU_TRAFFIC = {
     # profiles/dram_traffic_si512_tf32x3.md
-    "4d071da280a9704c": {"si512/tf32x3/rho_force": 227.19e6, "si512/tf32x3/vlocal": 287.07e6},
+    "2472a304986597fe": {"si512/tf32x3/rho_force": 227.93e6, "si512/tf32x3/vlocal": 285.93e6},
 }
+TC_SOURCES = ("gint_tc.cu", "gint_device.cuh", "gint_tcgen05.cuh")
+
+
+def _source_key():
+    import hashlib
+    h = hashlib.sha256()
+    for name in TC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2501_08697_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _traffic(kernel, workload, prec):
-    import hashlib
-    with open(os.path.join(ROOT, "paper_2501_08697_gb300", "csrc", "gint_tc.cu"), "rb") as f:
-        key = hashlib.sha256(f.read()).hexdigest()[:16]
-    return NCU_TRAFFIC.get(key, {}).get(f"{workload}/{prec}/{kernel}")
+    return NCU_TRAFFIC.get(_source_key(), {}).get(f"{workload}/{prec}/{kernel}")
 
 
 def _tensor_peak(prec, peaks, sustained=True):

@@ -349,10 +349,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 unsigned char *base = sm + stage * L::STAGE;
                 for (int w = pt; w < npad * S::KCM; w += kProd) {
                     const int kc = w % S::KCM, row = w / S::KCM;
+                    // accumulator row of orbital `row`: tile 1 (orbitals 128..) takes the TMEM
+                    // lane quadrants in reverse order, so its rows land in the quadrants with the
+                    // fewest upper-triangle pieces of tile 0 and the epilogue warps share the
+                    // scatter evenly
+                    const int arow = row < 128 ? row : (row ^ 0x60);
                     unsigned char *da[S::NT], *db[S::NT];
 #pragma unroll
                     for (int t = 0; t < S::NT; ++t) {
-                        da[t] = base + t * L::ARR + cm_off<S>(row, kc);
+                        da[t] = base + t * L::ARR + cm_off<S>(arow, kc);
                         db[t] = base + (S::NT + t) * L::ARR + cm_off<S>(row, kc);
                     }
                     if (row < nb) {
@@ -457,13 +462,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             // Scatter of the upper triangle.  The atom images of a batch are ordered so that
             // every slot pair a <= b is the canonical member of its partner pair; element
             // (mu, nu) with mu <= nu therefore goes to block (a_mu, b_nu) at (o_mu, o_nu), and
-            // the mirror kernel fills the other half.  Warp (q, hh) owns TMEM lanes (rows)
-            // row0..row0+31 and the 32-column pieces c0 = 128 t + 32 hh + 64 k; a piece is
+            // the mirror kernel fills the other half.  Warp (q, hh) owns TMEM lanes 32q..32q+31
+            // (orbitals row0..row0+31 of tile t) and the 32-column pieces c0 = 128 t + 32 hh + 64 k; a piece is
             // transposed through shared memory so that lanes = columns and the adds of a block
             // row are contiguous.  Addresses of 8 rows are formed before their atomics.
             float *tl = tiles + ew * 32 * 33;
             for (int t = 0; t < (nb > 128 ? 2 : 1); ++t) {
-                const int row0 = t * 128 + q * 32;
+                const int row0 = t == 0 ? q * 32 : 128 + (q ^ 3) * 32;   // orbital of lane 0
                 const int nrows = min(32, nb - row0);   // <= 0 for warps past the last row
                 for (int c0 = t * 128 + hh * 32; c0 < npad; c0 += 64) {
                     if (nrows <= 0 || c0 + 32 <= row0) continue;   // wholly below the diagonal

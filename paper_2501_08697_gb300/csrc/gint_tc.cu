@@ -851,6 +851,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 float fx = 0.f, fy = 0.f, fz = 0.f;
                 float dx = 0.f, dy = 0.f, dz = 0.f;
                 if (pv) disp(sl, po, dx, dy, dz);
+                // a point outside the image's sphere adds nothing: skip its evaluation (the
+                // window loads below stay warp-uniform)
+                const bool in = pv && dx * dx + dy * dy + dz * dz < spec[sl.species].rcut2;
                 // orbitals [oa, ob) of the slot whose columns fit the window (all of them unless
                 // the slot has more than 17 orbitals)
                 for (int oa = 0; oa < sl.norb;) {
@@ -866,7 +869,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         }
                     }
                     const int cb = sl.off - w0;   // window column of orbital o: cb + o
-                    if (pv) {
+                    if (in) {
                         if (FORCE)
                             eval_phigrad_f32(spec[sl.species], P.coef32, dx, dy, dz,
                                              [&](int o, float v, float gx, float gy, float gz) {

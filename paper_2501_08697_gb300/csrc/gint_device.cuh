@@ -264,8 +264,8 @@ struct SpecSh {
 // FP32 orbital values of one species at displacement d (no gradient); rsqrt + one Newton
 // step instead of sqrt and division.  emit(o, phi) for o = 0 .. norb-1.
 // radials per species whose spline records eval_phi_f32<true> fetches all at once (the rho
-// producers; the vlocal producers and the gradient evaluator, which hold more live values,
-// measured faster loading them radial by radial)
+// producers and the TF32 vlocal producers; the gradient evaluator and the BF16 vlocal
+// producers, which hold more live values, measured faster loading them radial by radial)
 constexpr int kPrefetchRad = 5;
 
 template <bool PREFETCH = false, typename Emit>

@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     if (p < npb) {
                         float dx, dy, dz;
                         disp(sl, poff + 6 * p, dx, dy, dz);
-                        eval_phi_f32(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) { col[o * KC] = v; });
+                        eval_phi_f32<!S::F16>(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) { col[o * KC] = v; });
                     } else {
                         for (int o = 0; o < sl.norb; ++o) col[o * KC] = 0.f;
                     }

@@ -127,6 +127,24 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, world, device=None):
+    """Largest value of x over the ranks of the process group (x itself at N = 1): the slowest
+    rank's time makes the job's time."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
 def build_inputs(name, seed_dm=True):
     from paper_2501_08697_gb300 import synth as S
     st = S.workload(name)
@@ -171,13 +189,13 @@ def run_ours(args, rank, world):
         if ev:
             ev[3].record(stream)
 
-    def timed(prec, steps, warmup):
+    def timed(prec, steps, warmup, all_ranks=True):
         for _ in range(warmup):
             step(prec)
         torch.cuda.synchronize()
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
-        if world > 1:
-            torch.distributed.barrier()
+        if all_ranks:
+            barrier(world)
         torch.cuda.synchronize()
         for i in range(steps):
             flush.fill_(float(i))                       # evict L2 (512 MiB write) outside the events
@@ -194,11 +212,7 @@ def run_ours(args, rank, world):
         tot, tv, tr, tc = timed(prec, args.steps, args.warmup)
     clocks = clk.summary()
     G.gint_get_status(h)
-    tmax = tot
-    if world > 1:
-        t = torch.tensor([tot], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tmax = float(t.item())
+    tmax = max_over_ranks(tot, world, dev)
     npts = info["npts"]
     value = world * npts * args.steps / tmax
     ms = tmax / args.steps * 1e3
@@ -206,7 +220,7 @@ def run_ours(args, rank, world):
     # the FP64 GPU path on the same step, for the split-vs-FP64 comparison
     fp64 = None
     if not args.skip_fp64 and rank == 0:
-        f_tot, f_tv, f_tr, _ = timed("fp64", 1, 1)
+        f_tot, f_tv, f_tr, _ = timed("fp64", 1, 1, all_ranks=False)   # rank 0 alone
         fp64 = {"pts_per_s": npts / f_tot, "ms_per_step": f_tot * 1e3, "vlocal_ms": f_tv * 1e3,
                 "rho_force_ms": f_tr * 1e3}
         H64, rho64, F64 = H.clone(), rho.clone(), F.clone()
@@ -263,7 +277,7 @@ def run_ours(args, rank, world):
         "err_vs_fp64_gpu": err,
         "speedup_vs_fp64_gpu": (value / world / fp64["pts_per_s"]) if fp64 else None,
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, st, Vn, keys, offs, DMn)
     h.close()
     return out
@@ -331,6 +345,7 @@ def run_batching(args, rank, world):
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
+        barrier(world)
         tot = 0.0
         for i in range(args.steps):
             flush.fill_(float(i))
@@ -343,8 +358,8 @@ def run_batching(args, rank, world):
         return tot
 
     with ClockSampler(dev.index) as clk:
-        t_job = timed(job.launch)
-    t_seq = timed(seq)
+        t_job = max_over_ranks(timed(job.launch), world, dev)
+    t_seq = max_over_ranks(timed(seq), world, dev)
     value = world * npts * args.steps / t_job
     return {"metric": METRIC + " [batched]", "value": value, "unit": "grid points/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_job / args.steps * 1e3,
@@ -392,6 +407,7 @@ def run_kspace(args, rank, world):
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
+        barrier(world)
         tot = 0.0
         for i in range(args.steps):
             flush.fill_(float(i))
@@ -404,8 +420,8 @@ def run_kspace(args, rank, world):
         return tot / args.steps
 
     with ClockSampler(dev.index) as clk:
-        tf = timed(lambda: G.gint_fold(h, X, kap, Xk))
-        tu = timed(lambda: G.gint_unfold(h, Xk, kap, w, Xb))
+        tf = max_over_ranks(timed(lambda: G.gint_fold(h, X, kap, Xk)), world, dev)
+        tu = max_over_ranks(timed(lambda: G.gint_unfold(h, Xk, kap, w, Xb)), world, dev)
     peaks, src = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     gf, gu = bytes_fold / tf / 1e9, bytes_unfold / tu / 1e9
@@ -451,6 +467,7 @@ def run_dm(args, rank, world):
         for _ in range(args.warmup):
             G.gint_density_matrix(h, kap, w, C, f, out, prec)
         torch.cuda.synchronize()
+        barrier(world)
         tot = 0.0
         for i in range(steps):
             flush.fill_(float(i))
@@ -463,7 +480,7 @@ def run_dm(args, rank, world):
         return tot / steps
 
     with ClockSampler(dev.index) as clk:
-        t_tc = timed("tf32x3", DM, args.steps)
+        t_tc = max_over_ranks(timed("tf32x3", DM, args.steps), world, dev)
     t_64 = timed("fp64", DM64, max(1, min(args.steps, 2)))
     err = float(torch.linalg.norm(DM - DM64) / torch.linalg.norm(DM64))
     alg = 4.0 * N * N * nb                       # Re part of the complex product at Gamma
@@ -528,7 +545,9 @@ def main():
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        if args.impl == "ours":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        # the reference arm is the CPU oracle: its ranks meet over gloo
         dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
     if args.impl == "reference":
         out = run_reference(args, rank, world)

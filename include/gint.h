@@ -243,8 +243,10 @@ gint_status gint_block_dot_noalloc(gint_handle h, const double *A_dev, const dou
                                    double *out_dev, void *stream);
 
 /* End-to-end call from host buffers: copies V and DM (pinned or pageable host memory) to
- * library-owned device buffers, runs vlocal and rho_force, and copies H, rho and F back.
- * Synchronous: returns after the results are in host memory.  Outputs may be NULL. */
+ * library-owned device buffers, runs vlocal and rho_force on `stream`, and copies H, rho and F
+ * back.  DM comes in while vlocal runs and H goes out while rho_force runs, on a copy stream
+ * the library creates on the first call (overlap needs pinned host memory).  Synchronous:
+ * returns after the results are in host memory.  Outputs may be NULL. */
 gint_status gint_run_host(gint_handle h, const double *V_host, const double *DM_host,
                           double *H_host, double *rho_host, double *F_host, gint_prec prec,
                           void *stream);

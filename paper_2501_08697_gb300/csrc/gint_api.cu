@@ -302,15 +302,34 @@ extern "C" gint_status gint_run_host(gint_handle h, const double *V_host, const 
         if ((e = cudaMalloc((void **)&h->d_hostio, need)) != cudaSuccess) return cuda_fail(e, "gint_run_host: allocate");
         h->hostio_bytes = need;
     }
+    if (!h->io_stream) {
+        if ((e = cudaStreamCreateWithFlags(&h->io_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "gint_run_host: copy stream");
+        for (cudaEvent_t &ev : h->io_ev)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e, "gint_run_host: events");
+    }
+    // The density matrix comes in on the copy stream while vlocal runs, and H goes out on it
+    // while rho and the force run; V in and rho out stay on the critical path.
+    cudaStream_t c = h->io_stream;
+    cudaEvent_t v_in = h->io_ev[0], dm_in = h->io_ev[1], h_done = h->io_ev[2], h_out = h->io_ev[3];
     double *dV = h->d_hostio, *drho = dV + np, *dDM = drho + np, *dH = dDM + nv, *dF = dH + nv;
-    if ((e = cudaMemcpyAsync(dV, V_host, sizeof(double) * np, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(dDM, DM_host, sizeof(double) * nv, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    if ((e = cudaEventRecord(h_out, s)) != cudaSuccess || (e = cudaStreamWaitEvent(c, h_out, 0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dV, V_host, sizeof(double) * np, cudaMemcpyHostToDevice, c)) != cudaSuccess ||
+        (e = cudaEventRecord(v_in, c)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dDM, DM_host, sizeof(double) * nv, cudaMemcpyHostToDevice, c)) != cudaSuccess ||
+        (e = cudaEventRecord(dm_in, c)) != cudaSuccess || (e = cudaStreamWaitEvent(s, v_in, 0)) != cudaSuccess)
         return cuda_fail(e, "gint_run_host: copy in");
     if ((st = run_vlocal(h, dV, dH, prec, s)) != GINT_OK) return st;
+    if ((e = cudaEventRecord(h_done, s)) != cudaSuccess || (e = cudaStreamWaitEvent(s, dm_in, 0)) != cudaSuccess)
+        return cuda_fail(e, "gint_run_host: order");
     if ((st = run_rho_force(h, dV, dDM, drho, dF, prec, s)) != GINT_OK) return st;
-    if ((H_host && (e = cudaMemcpyAsync(H_host, dH, sizeof(double) * nv, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
+    if ((e = cudaStreamWaitEvent(c, h_done, 0)) != cudaSuccess ||
+        (H_host && (e = cudaMemcpyAsync(H_host, dH, sizeof(double) * nv, cudaMemcpyDeviceToHost, c)) != cudaSuccess) ||
+        (e = cudaEventRecord(h_out, c)) != cudaSuccess ||
         (rho_host && (e = cudaMemcpyAsync(rho_host, drho, sizeof(double) * np, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
-        (F_host && (e = cudaMemcpyAsync(F_host, dF, sizeof(double) * 3 * na, cudaMemcpyDeviceToHost, s)) != cudaSuccess))
+        (F_host && (e = cudaMemcpyAsync(F_host, dF, sizeof(double) * 3 * na, cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
+        (e = cudaStreamWaitEvent(s, h_out, 0)) != cudaSuccess)
         return cuda_fail(e, "gint_run_host: copy out");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "gint_run_host: synchronise");
     return GINT_OK;

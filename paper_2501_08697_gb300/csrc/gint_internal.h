@@ -157,6 +157,8 @@ struct gint_handle_s {
     size_t dm_planes_bytes = 0;
     double *d_hostio = nullptr;      // buffers of gint_run_host (allocated on first use)
     size_t hostio_bytes = 0;
+    cudaStream_t io_stream = nullptr; // gint_run_host's copy stream and its events (first use)
+    cudaEvent_t io_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t last_stream = nullptr;
 };
 

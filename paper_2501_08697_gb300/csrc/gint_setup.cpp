@@ -553,6 +553,9 @@ static void free_dev(gint_handle h)
                     h->ks.d_phase, h->d_dm_scratch, h->d_dm_planes};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (cudaEvent_t &ev : h->io_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (h->io_stream) cudaStreamDestroy(h->io_stream);
 }
 
 static gint_status upload_geometry(gint_handle h)

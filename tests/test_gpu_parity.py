@@ -150,6 +150,25 @@ def test_run_host_matches_device_path(G):
     assert rel_fro(Hh, H) < 1e-14 and rel_fro(rh, rho) < 1e-14 and rel_fro(Fh, F.reshape(-1)) < 1e-13
 
 
+def test_run_host_pinned_repeated_matches_device_path(G):
+    """Pinned host buffers (the copies then overlap the kernels on the library's copy stream),
+    two calls in a row on the same handle."""
+    ref, h, H, rho, F = _run(G, "si8_ragged", "tf32x3")
+    pin = lambda n: torch.empty(n, dtype=torch.float64).pin_memory()
+    Vh, DMh = pin(h.info["npts"]), pin(h.info["nvalues"])
+    Vh.copy_(torch.from_numpy(np.ascontiguousarray(ref["V"].reshape(-1))))
+    DMh.copy_(torch.from_numpy(ref["DM"]))
+    Hh, rh, Fh = pin(h.info["nvalues"]), pin(h.info["npts"]), pin(3 * h.natoms)
+    for _ in range(2):
+        for t in (Hh, rh, Fh):
+            t.fill_(float("nan"))
+        G.gint_run_host(h, Vh, DMh, Hh, rh, Fh, "tf32x3")
+        assert rel_fro(Hh.numpy(), H) < 1e-13 and rel_fro(rh.numpy(), rho) < 1e-13
+        # the per-batch force sums are FP32 shared-memory additions whose order varies from run
+        # to run, so F agrees to FP32 rounding of those sums, well inside the 1e-6 tolerance
+        assert rel_fro(Fh.numpy(), F.reshape(-1)) < 1e-6
+
+
 def test_invalid_arguments_are_rejected_on_host(G):
     h = _handle(G, "si8")
     dev = torch.device("cuda")

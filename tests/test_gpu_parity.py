@@ -141,6 +141,17 @@ def test_block_symmetry_of_gpu_h(G):
         assert np.array_equal(A, B.T)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "bf16x6"])
+def test_many_atom_images_per_batch(G, prec):
+    """h64_dense: every batch sees 39-53 atom images (one orbital each), more than the
+    shared-memory slot-pair tables of the tensor-core kernels hold (28), so vlocal's scatter and
+    rho's gather tables read the batch's table from global memory."""
+    ref, h, H, rho, F = _run(G, "h64_dense", prec)
+    eH, er, eF = rel_fro(H, ref["H"]), rel_fro(rho, ref["rho"]), rel_fro(F, ref["F"])
+    print(f"h64_dense {prec}: H {eH:.2e} rho {er:.2e} F {eF:.2e}")
+    assert eH <= TOL[prec] and er <= TOL[prec] and eF <= FORCE_TOL[prec]
+
+
 def test_run_host_matches_device_path(G):
     ref, h, H, rho, F = _run(G, "si8_ragged", "fp64")
     Hh = np.empty(h.info["nvalues"])

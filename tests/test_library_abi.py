@@ -81,3 +81,40 @@ def test_setup_without_gpu_fails_loudly():
     with pytest.raises(G.GintError) as e:
         G.setup_structure(st)
     assert e.value.code == G.GINT_ECUDA
+
+
+@pytest.mark.parametrize("case", ["no_atoms", "grid_zero", "singular_cell", "bad_species", "nan_position",
+                                  "bad_batch"])
+def test_setup_rejects_invalid_input_on_host(case):
+    """gint_setup checks its arguments on the host before it touches a device, so an invalid
+    structure is GINT_EINVAL (with a message), GPU or not."""
+    import numpy as np
+    from paper_2501_08697_gb300 import synth as S
+    st = S.si_diamond((1, 1, 1), grid=(16, 16, 16))
+    cell, species, tau, grid = st.cell.copy(), st.species.copy(), st.tau.copy(), list(st.grid)
+    kw = {}
+    if case == "no_atoms":
+        species, tau = species[:0], tau[:0]
+    elif case == "grid_zero":
+        grid[1] = 0
+    elif case == "singular_cell":
+        cell[2] = cell[0]
+    elif case == "bad_species":
+        species[3] = 5
+    elif case == "nan_position":
+        tau[2, 1] = np.nan
+    elif case == "bad_batch":
+        kw = dict(batch=(4, 4, 3))          # odd along a3
+    with pytest.raises(G.GintError) as e:
+        G.gint_setup(cell, species, tau, st.tables, grid, **kw)
+    assert e.value.code == G.GINT_EINVAL
+    assert G.load().gint_last_error()
+
+
+def test_empty_and_null_calls_on_host():
+    """An empty multi-structure call is a no-op; a call without a handle is rejected."""
+    lib = G.load()
+    assert lib.gint_batched(0, None, None, None, None, None, 0, None) == G.GINT_OK
+    assert lib.gint_vlocal(None, None, None, 0, None) == G.GINT_EINVAL
+    assert lib.gint_rho(None, None, None, 0, None) == G.GINT_EINVAL
+    assert lib.gint_get_status(None) == G.GINT_EINVAL

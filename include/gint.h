@@ -72,13 +72,21 @@ typedef enum {
  *   GINT_TF32X3  tcgen05 tensor cores, kind::tf32, each FP32 operand split hi+lo and
  *                hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory.
  *   GINT_BF16X3  tcgen05 kind::f16 with bf16 hi+lo splits, 3 products (about 16 bits).
- *   GINT_BF16X6  tcgen05 kind::f16 with bf16 hi+mid+lo splits, the 6 products of order <= 2. */
+ *   GINT_BF16X6  tcgen05 kind::f16 with bf16 hi+mid+lo splits, the 6 products of order <= 2.
+ *   GINT_FP16X3  tcgen05 kind::f16 with fp16 hi+lo splits, 3 products: the 11-bit significand of
+ *                TF32 per term (about 22 bits in all, as GINT_TF32X3) at the f16 tensor rate.
+ *                fp16's narrow exponent is handled by exact power-of-two scaling: orbital values
+ *                by a bound from the radial tables, V(r) dV and the density matrix by their
+ *                largest magnitude in the call, so the largest term sits near 2^14; values more
+ *                than 2^17 below that largest one keep an absolute accuracy of about 2^-39 of
+ *                it instead of a relative one. */
 typedef enum {
     GINT_FP64 = 0,
     GINT_FP32 = 1,
     GINT_TF32X3 = 2,
     GINT_BF16X3 = 3,
-    GINT_BF16X6 = 4
+    GINT_BF16X6 = 4,
+    GINT_FP16X3 = 5
 } gint_prec;
 
 /* One atomic species.  All pointers are host memory, read during gint_setup only. */
@@ -142,9 +150,13 @@ gint_status gint_block_layout(gint_handle h, int64_t *nblocks, int64_t *nvalues,
 
 gint_status gint_get_info(gint_handle h, gint_info_t *info);
 
-/* Move the atoms (host tau, natoms*3).  If the block list and every batch's atom-image list
- * are unchanged, only positions are updated (no reallocation).  Otherwise nothing changes
- * and GINT_ESTATE is returned: build a new handle. */
+/* Move the atoms (host tau, natoms*3).  The block list (and with it the layout of H and of the
+ * density matrix) must stay the same: if some pair enters or leaves the cutoff, nothing changes
+ * and GINT_ESTATE is returned (build a new handle).  The batch -> atom-image lists are rebuilt
+ * for the new positions; a decomposition whose lists are unchanged keeps its device arrays and
+ * receives the new positions only, one whose lists changed is re-uploaded.  Blocking: the call
+ * synchronises with the device before replacing arrays.  A multi-structure job
+ * (gint_batch_create) copies the lists when it is created: create it again after a move. */
 gint_status gint_update_positions(gint_handle h, const double *tau);
 
 /* H <- V_mu,nu(R) for the potential V (device, npts doubles).  H (device, nvalues doubles)
@@ -257,7 +269,7 @@ gint_status gint_run_host(gint_handle h, const double *V_host, const double *DM_
  * 192 orbitals, which need the single-accumulator layout) and one of the rho kernel; the sequence
  * (H zeroing, density-matrix conversion, the two persistent launches, block mirroring) is
  * captured once into a CUDA graph that gint_batch_launch replays.  prec must be a tensor-core
- * precision (GINT_TF32X3, GINT_BF16X3, GINT_BF16X6); at most 255 structures, all on the current
+ * precision (GINT_TF32X3, GINT_BF16X3, GINT_BF16X6, GINT_FP16X3); at most 255 structures, all on the current
  * device, at most 8 distinct species in total.  Pointer arrays are host memory, read during
  * create; the buffers they point to are device memory and are bound to the job.  DM and rho
  * may be NULL (vlocal only).  The handles must outlive the job.  A handle may appear more than

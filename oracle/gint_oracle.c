@@ -679,3 +679,150 @@ int64_t oracle_points_near_atom(const or_ctx *c, int I, int64_t cap, int64_t *ou
     }
     return cnt;
 }
+
+/* ------------------------------------------------------------------ per-block and per-atom forms */
+/* Integer grid coordinates (in all space, not wrapped into the cell) of the points within
+ * distance rc of centre x: a box in fractional coordinates, per axis. */
+static void or_point_box(const or_ctx *c, const double x[3], double rc, int64_t lo[3], int64_t hi[3])
+{
+    for (int i = 0; i < 3; ++i) {
+        double s = x[0] * c->g[0 + i] + x[1] * c->g[3 + i] + x[2] * c->g[6 + i];
+        lo[i] = (int64_t)floor((s - rc * c->gnorm[i]) * c->grid[i]) - 1;
+        hi[i] = (int64_t)ceil((s + rc * c->gnorm[i]) * c->grid[i]) + 1;
+    }
+}
+
+static int64_t or_wrap(int64_t i, int64_t n)
+{
+    int64_t r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+/* Selected blocks of V_mu,nu(R) written out block by block: for key (I, J, n) with
+ * R = n.A, H = dV Sum_r' phi_mu(r' - tau_I) V(r') phi_nu(r' - tau_J - R) over the grid points
+ * r' of all space (V periodic), which is the sum over the cell's points and all lattice
+ * translations of the definition.  keys[5*b ..] of the nsel requested blocks; out receives the
+ * blocks one after another (norb_I x norb_J each, row-major).  Blocks with the same I share one
+ * pass over the points of I's sphere (they must be listed consecutively for that to help). */
+int oracle_vlocal_blocks(const or_ctx *c, const double *V, int64_t nsel, const int *keys, const int64_t *outoff,
+                         double *out)
+{
+    /* groups of consecutive keys with the same I */
+    int64_t ngrp = 0;
+    int64_t *g0 = (int64_t *)malloc(sizeof(int64_t) * (nsel + 1));
+    for (int64_t b = 0; b < nsel; ++b)
+        if (b == 0 || keys[5 * b] != keys[5 * (b - 1)]) g0[ngrp++] = b;
+    g0[ngrp] = nsel;
+    const double *A = c->cell;
+    const int64_t N1 = c->grid[0], N2 = c->grid[1], N3 = c->grid[2];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t g = 0; g < ngrp; ++g) {
+        const int I = keys[5 * g0[g]];
+        const or_species *SI = &c->sp[c->spc[I]];
+        const double *tI = c->tau + 3 * I;
+        int64_t lo[3], hi[3];
+        or_point_box(c, tI, SI->rcut, lo, hi);
+        double phiI[OR_MAXORB], phiJ[OR_MAXORB];
+        for (int64_t b = g0[g]; b < g0[g + 1]; ++b) {
+            const or_species *SJ = &c->sp[c->spc[keys[5 * b + 1]]];
+            memset(out + outoff[b], 0, sizeof(double) * SI->norb * SJ->norb);
+        }
+        for (int64_t i = lo[0]; i <= hi[0]; ++i)
+            for (int64_t j = lo[1]; j <= hi[1]; ++j)
+                for (int64_t k = lo[2]; k <= hi[2]; ++k) {
+                    double s1 = (double)i / N1, s2 = (double)j / N2, s3 = (double)k / N3, r[3], dI[3];
+                    for (int x = 0; x < 3; ++x) {
+                        r[x] = s1 * A[0 + x] + s2 * A[3 + x] + s3 * A[6 + x];
+                        dI[x] = r[x] - tI[x];
+                    }
+                    if (!(sqrt(dI[0] * dI[0] + dI[1] * dI[1] + dI[2] * dI[2]) < SI->rcut)) continue;
+                    const double w = c->dV * V[(or_wrap(i, N1) * N2 + or_wrap(j, N2)) * N3 + or_wrap(k, N3)];
+                    or_phi(SI, dI, phiI, NULL);
+                    for (int64_t b = g0[g]; b < g0[g + 1]; ++b) {
+                        const int *key = keys + 5 * b;
+                        const or_species *SJ = &c->sp[c->spc[key[1]]];
+                        double dJ[3];
+                        for (int x = 0; x < 3; ++x)
+                            dJ[x] = r[x] - (c->tau[3 * key[1] + x] + key[2] * A[0 + x] + key[3] * A[3 + x] +
+                                            key[4] * A[6 + x]);
+                        if (!(sqrt(dJ[0] * dJ[0] + dJ[1] * dJ[1] + dJ[2] * dJ[2]) < SJ->rcut)) continue;
+                        or_phi(SJ, dJ, phiJ, NULL);
+                        double *blk = out + outoff[b];
+                        for (int mu = 0; mu < SI->norb; ++mu)
+                            for (int nu = 0; nu < SJ->norb; ++nu) blk[mu * SJ->norb + nu] += w * phiI[mu] * phiJ[nu];
+                    }
+                }
+    }
+    free(g0);
+    return 0;
+}
+
+/* dL/dtau_K for selected atoms, written out atom by atom: with L = Sum_blocks Sum DM H,
+ *   dL/dtau_K = -dV Sum_r' V(r') Sum_{mu in K} grad phi_mu(r' - tau_K) .
+ *               Sum_{blocks (K, J, n)} Sum_{nu in J} (DM(K,J,n)_mu,nu + DM(J,K,-n)_nu,mu) phi_nu(r' - tau_J - n.A)
+ * over the grid points r' of all space within rc_K of tau_K (V periodic).  keys/offsets: the
+ * full sorted block list and the DM store; out: nsel x 3. */
+int oracle_dLdtau_atoms(const or_ctx *c, const double *V, int64_t nblocks, const int *keys, const int64_t *offsets,
+                        const double *DM, int64_t nsel, const int *atoms, double *out)
+{
+    const double *A = c->cell;
+    const int64_t N1 = c->grid[0], N2 = c->grid[1], N3 = c->grid[2];
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < nsel; ++q) {
+        const int K = atoms[q];
+        const or_species *SK = &c->sp[c->spc[K]];
+        const double *tK = c->tau + 3 * K;
+        /* the blocks (K, J, n): a contiguous key range */
+        int64_t b0 = 0, b1;
+        while (b0 < nblocks && keys[5 * b0] < K) ++b0;
+        b1 = b0;
+        while (b1 < nblocks && keys[5 * b1] == K) ++b1;
+        int64_t *tr = (int64_t *)malloc(sizeof(int64_t) * (b1 - b0 + 1));
+        for (int64_t b = b0; b < b1; ++b) {
+            const int *k = keys + 5 * b;
+            int kt[5] = {k[1], k[0], -k[2], -k[3], -k[4]};
+            tr[b - b0] = or_find(keys, nblocks, kt);
+            if (tr[b - b0] < 0) err = -2;
+        }
+        int64_t lo[3], hi[3];
+        or_point_box(c, tK, SK->rcut, lo, hi);
+        double phiK[OR_MAXORB], gK[OR_MAXORB * 3], phiJ[OR_MAXORB];
+        double acc[3] = {0, 0, 0};
+        for (int64_t i = lo[0]; i <= hi[0]; ++i)
+            for (int64_t j = lo[1]; j <= hi[1]; ++j)
+                for (int64_t k = lo[2]; k <= hi[2]; ++k) {
+                    double s1 = (double)i / N1, s2 = (double)j / N2, s3 = (double)k / N3, r[3], dK[3];
+                    for (int x = 0; x < 3; ++x) {
+                        r[x] = s1 * A[0 + x] + s2 * A[3 + x] + s3 * A[6 + x];
+                        dK[x] = r[x] - tK[x];
+                    }
+                    if (!(sqrt(dK[0] * dK[0] + dK[1] * dK[1] + dK[2] * dK[2]) < SK->rcut)) continue;
+                    const double w = -c->dV * V[(or_wrap(i, N1) * N2 + or_wrap(j, N2)) * N3 + or_wrap(k, N3)];
+                    or_phi(SK, dK, phiK, gK);
+                    double g[3] = {0, 0, 0};
+                    for (int64_t b = b0; b < b1; ++b) {
+                        if (tr[b - b0] < 0) continue;
+                        const int *key = keys + 5 * b;
+                        const or_species *SJ = &c->sp[c->spc[key[1]]];
+                        double dJ[3];
+                        for (int x = 0; x < 3; ++x)
+                            dJ[x] = r[x] - (c->tau[3 * key[1] + x] + key[2] * A[0 + x] + key[3] * A[3 + x] +
+                                            key[4] * A[6 + x]);
+                        if (!(sqrt(dJ[0] * dJ[0] + dJ[1] * dJ[1] + dJ[2] * dJ[2]) < SJ->rcut)) continue;
+                        or_phi(SJ, dJ, phiJ, NULL);
+                        const double *blk = DM + offsets[b], *blkT = DM + offsets[tr[b - b0]];
+                        const int nK = SK->norb, nJ = SJ->norb;
+                        for (int mu = 0; mu < nK; ++mu) {
+                            double s = 0.0;
+                            for (int nu = 0; nu < nJ; ++nu) s += (blk[mu * nJ + nu] + blkT[nu * nK + mu]) * phiJ[nu];
+                            for (int x = 0; x < 3; ++x) g[x] += gK[3 * mu + x] * s;
+                        }
+                    }
+                    for (int x = 0; x < 3; ++x) acc[x] += w * g[x];
+                }
+        for (int x = 0; x < 3; ++x) out[3 * q + x] = acc[x];
+        free(tr);
+    }
+    return err;
+}

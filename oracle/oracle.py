@@ -53,6 +53,8 @@ def _load():
             lib.oracle_rho.argtypes = [C.c_void_p, i64, P(i), P(i64), P(d), P(d), i64, P(i64)]
             lib.oracle_dLdtau.argtypes = [C.c_void_p, P(d), i64, P(i), P(i64), P(d), P(d), i64, P(i64)]
             lib.oracle_dLdeps.argtypes = [C.c_void_p, P(d), i64, P(i), P(i64), P(d), P(d), i64, P(i64)]
+            lib.oracle_vlocal_blocks.argtypes = [C.c_void_p, P(d), i64, P(i), P(i64), P(d)]
+            lib.oracle_dLdtau_atoms.argtypes = [C.c_void_p, P(d), i64, P(i), P(i64), P(d), i64, P(i), P(d)]
             lib.oracle_points_near_atom.restype = i64
             lib.oracle_points_near_atom.argtypes = [C.c_void_p, i, i64, P(i64)]
             lib.oracle_threads.restype = i
@@ -190,6 +192,40 @@ class Oracle:
         if rc != 0:
             raise RuntimeError(f"oracle_dLdeps failed ({rc})")
         return out.reshape(3, 3)
+
+    def vlocal_blocks(self, V, sel):
+        """The blocks sel (indices into the sorted block list) of V_mu,nu(R), each summed over
+        the grid points of all space in the first atom's sphere; returns them concatenated in
+        the order of sel (sorted by first atom internally so blocks of one atom share a pass)."""
+        keys, offs = self.pairs()
+        V = np.ascontiguousarray(V, np.float64).reshape(-1)
+        sel = np.asarray(sel, np.int64)
+        order = np.argsort(keys[sel, 0], kind="stable")
+        s2 = sel[order]
+        k2 = np.ascontiguousarray(keys[s2], np.int32)
+        sizes = self.norb_atom[k2[:, 0]] * self.norb_atom[k2[:, 1]]
+        o2 = np.zeros(len(s2) + 1, np.int64)
+        o2[1:] = np.cumsum(sizes)
+        out = np.zeros(o2[-1], np.float64)
+        self._lib.oracle_vlocal_blocks(self.ctx, _p(V, C.c_double), len(s2), _p(k2, C.c_int), _p(o2, C.c_int64),
+                                       _p(out, C.c_double))
+        # back to the order of sel
+        parts = {int(b): out[o2[i]:o2[i + 1]] for i, b in enumerate(s2)}
+        return np.concatenate([parts[int(b)] for b in sel]) if len(sel) else out
+
+    def dLdtau_atoms(self, V, DM, atoms):
+        """dL/dtau for the listed atoms (len(atoms) x 3), each summed over its own sphere."""
+        keys, offs = self.pairs()
+        V = np.ascontiguousarray(V, np.float64).reshape(-1)
+        DM = np.ascontiguousarray(DM, np.float64)
+        atoms = np.ascontiguousarray(atoms, np.int32)
+        out = np.zeros((len(atoms), 3), np.float64)
+        rc = self._lib.oracle_dLdtau_atoms(self.ctx, _p(V, C.c_double), len(keys), _p(keys, C.c_int),
+                                           _p(offs, C.c_int64), _p(DM, C.c_double), len(atoms),
+                                           _p(atoms, C.c_int), _p(out, C.c_double))
+        if rc != 0:
+            raise RuntimeError(f"oracle_dLdtau_atoms failed ({rc})")
+        return out
 
     def points_near_atom(self, I):
         n = self._lib.oracle_points_near_atom(self.ctx, I, 0, None)

@@ -14,22 +14,29 @@ import torch
 from . import gint as G
 
 
+def _move_to(handle, tau_h):
+    """Put the handle's atoms at tau_h (flat float64) if they are elsewhere."""
+    if getattr(handle, "_tau", None) is None or not np.array_equal(handle._tau, tau_h):
+        G.gint_update_positions(handle, tau_h)
+        handle._tau = tau_h.copy()
+
+
 class GintVlocal(torch.autograd.Function):
     """H = vlocal(V; tau).  `tau` (natoms x 3, float64) selects the atom positions: if they
     differ from the handle's, the handle is moved with gint_update_positions (same neighbour
-    topology required)."""
+    topology required).  The positions of each forward are kept with its graph node, and the
+    backward moves the handle back to them if another forward moved it in between, so every
+    gradient is taken at the geometry of its own forward."""
 
     @staticmethod
     def forward(ctx, V, tau, handle, prec="fp64"):
-        tau_h = tau.detach().to("cpu", torch.float64).numpy().reshape(-1)
-        if getattr(handle, "_tau", None) is None or not np.array_equal(handle._tau, tau_h):
-            G.gint_update_positions(handle, tau_h)
-            handle._tau = tau_h.copy()
+        tau_h = tau.detach().to("cpu", torch.float64).numpy().reshape(-1).copy()
+        _move_to(handle, tau_h)
         Vc = V.detach().contiguous()
         H = torch.empty(handle.info["nvalues"], dtype=torch.float64, device=V.device)
         G.gint_vlocal(handle, Vc, H, prec)
         ctx.save_for_backward(Vc)
-        ctx.handle, ctx.prec, ctx.tau_device = handle, prec, tau.device
+        ctx.handle, ctx.prec, ctx.tau_device, ctx.tau_h = handle, prec, tau.device, tau_h
         return H
 
     @staticmethod
@@ -40,6 +47,7 @@ class GintVlocal(torch.autograd.Function):
         gV = torch.empty_like(V) if need_v else None
         gt = torch.empty(3 * h.natoms, dtype=torch.float64, device=V.device) if need_tau else None
         if need_v or need_tau:
+            _move_to(h, ctx.tau_h)
             G.gint_vlocal_backward(h, V, gH.contiguous(), gV, gt, ctx.prec)
         if gt is not None:
             gt = gt.view(-1, 3).to(ctx.tau_device)

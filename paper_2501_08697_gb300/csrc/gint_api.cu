@@ -10,7 +10,9 @@ using namespace gint;
 
 namespace gint {
 cudaError_t launch_mirror(const Plan &P, double *H, cudaStream_t s);
-cudaError_t launch_dm_to_f32(const Plan &P, const double *DM, float *out, bool sym, cudaStream_t s);
+cudaError_t launch_dm_to_f32(const Plan &P, const double *DM, float *out, bool sym, cudaStream_t s,
+                             float *amax = nullptr);
+cudaError_t launch_absmax(const double *x, int64_t n, float *out, cudaStream_t s);
 
 SInfo sinfo_for(const gint_handle_s *h, const double *V, double *H, const float *DM32, double *rho, double *F)
 {
@@ -23,6 +25,8 @@ SInfo sinfo_for(const gint_handle_s *h, const double *V, double *H, const float 
     si.poff = h->d_poff;
     for (int i = 0; i < 3; ++i) si.grid[i] = h->grid[i];
     si.dV = h->info.dV;
+    si.phimax = h->phimax;
+    si.amax = h->d_amax;
     return si;
 }
 }
@@ -44,24 +48,57 @@ __global__ void k_symmetrise(Plan P, const double *__restrict__ DM, double *out)
     }
 }
 
-// out <- FP32 copy of DM, or of its block-symmetric part (DM + DM^T_block)/2
-__global__ void k_dm_to_f32(Plan P, const double *__restrict__ DM, float *out, int sym)
+// the largest of m over the threads of a block into *out (float bits of non-negative values
+// order like unsigned integers)
+__device__ __forceinline__ void block_max_to(float m, float *out)
 {
-    if (!sym) {
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.nvalues; i += (int64_t)gridDim.x * blockDim.x)
-            out[i] = d2f(DM[i]);
-        return;
+    __shared__ float wm[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmaxf(b, wm[w]);
+        atomicMax(reinterpret_cast<unsigned *>(out), __float_as_uint(b));
     }
-    for (int64_t b = blockIdx.x; b < P.nblocks; b += gridDim.x) {
-        const int pb = P.partner[b];
-        const int64_t off = P.blk_off[b], poff = P.blk_off[pb];
-        const int rows = P.blk_rows[b];
-        const int cols = (int)((P.blk_off[b + 1] - off) / rows);
-        for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
-            const int mu = e / cols, nu = e - mu * cols;
-            out[off + e] = 0.5f * (d2f(DM[off + e]) + d2f(DM[poff + nu * rows + mu]));
+}
+
+// out <- FP32 copy of DM, or of its block-symmetric part (DM + DM^T_block)/2; with amax, the
+// largest magnitude written is max-reduced into *amax (zeroed by the caller)
+__global__ void k_dm_to_f32(Plan P, const double *__restrict__ DM, float *out, int sym, float *amax)
+{
+    float m = 0.f;
+    if (!sym) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.nvalues; i += (int64_t)gridDim.x * blockDim.x) {
+            const float v = d2f(DM[i]);
+            out[i] = v;
+            m = fmaxf(m, fabsf(v));
+        }
+    } else {
+        for (int64_t b = blockIdx.x; b < P.nblocks; b += gridDim.x) {
+            const int pb = P.partner[b];
+            const int64_t off = P.blk_off[b], poff = P.blk_off[pb];
+            const int rows = P.blk_rows[b];
+            const int cols = (int)((P.blk_off[b + 1] - off) / rows);
+            for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+                const int mu = e / cols, nu = e - mu * cols;
+                const float v = 0.5f * (d2f(DM[off + e]) + d2f(DM[poff + nu * rows + mu]));
+                out[off + e] = v;
+                m = fmaxf(m, fabsf(v));
+            }
         }
     }
+    if (amax) block_max_to(m, amax);
+}
+
+// *out <- max(*out, max_i |x_i|) (FP32, rounded to nearest)
+__global__ void k_absmax(const double *__restrict__ x, int64_t n, float *out)
+{
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(d2f(x[i])));
+    block_max_to(m, out);
 }
 
 __global__ void k_scale(double *x, int64_t n, double a)
@@ -120,7 +157,7 @@ gint_status check_handle(gint_handle h, const char *who)
     return GINT_OK;
 }
 
-bool valid_prec(gint_prec p) { return p >= GINT_FP64 && p <= GINT_BF16X6; }
+bool valid_prec(gint_prec p) { return p >= GINT_FP64 && p <= GINT_FP16X3; }
 
 gint_status do_dot(gint_handle h, const double *a, const double *b, int64_t n, double scale, double *out,
                    cudaStream_t s, const char *who)
@@ -136,6 +173,9 @@ gint_status run_vlocal(gint_handle h, const double *V, double *H, gint_prec prec
 {
     cudaError_t e = cudaMemsetAsync(H, 0, sizeof(double) * h->info.nvalues, s);
     if (e != cudaSuccess) return cuda_fail(e, "gint_vlocal: memset");
+    if (prec == GINT_FP16X3 && ((e = cudaMemsetAsync(h->d_amax, 0, sizeof(float), s)) != cudaSuccess ||
+                                (e = launch_absmax(V, h->info.npts, h->d_amax, s)) != cudaSuccess))
+        return cuda_fail(e, "gint_vlocal: potential range");
     if (prec == GINT_FP64 || prec == GINT_FP32)
         e = launch_vlocal_simt(plan_for(h, 0), prec == GINT_FP64, V, H, s, h->nsm);
     else
@@ -169,7 +209,10 @@ gint_status run_rho_force(gint_handle h, const double *V, const double *DM, doub
         e = launch_rho_force_simt(plan_for(h, 1), prec == GINT_FP64, V, D, rho, F, dLde, s, h->nsm);
     } else {
         // tensor-core kernels gather the density matrix in FP32 (split again on chip)
-        if (h->info.nvalues > 0 && (e = launch_dm_to_f32(h->plan, DM, h->d_dm32, grad, s)) != cudaSuccess)
+        float *amax = prec == GINT_FP16X3 ? h->d_amax + 1 : nullptr;
+        if (amax && (e = cudaMemsetAsync(amax, 0, sizeof(float), s)) != cudaSuccess)
+            return cuda_fail(e, "gint_rho: range");
+        if (h->info.nvalues > 0 && (e = launch_dm_to_f32(h->plan, DM, h->d_dm32, grad, s, amax)) != cudaSuccess)
             return cuda_fail(e, "gint_rho: convert");
         SInfo si = sinfo_for(h, V, nullptr, h->d_dm32, rho, F);
         si.dLde = dLde;
@@ -354,11 +397,19 @@ extern "C" gint_status gint_get_status(gint_handle h)
 
 
 namespace gint {
-cudaError_t launch_dm_to_f32(const Plan &P, const double *DM, float *out, bool sym, cudaStream_t s)
+cudaError_t launch_dm_to_f32(const Plan &P, const double *DM, float *out, bool sym, cudaStream_t s, float *amax)
 {
     const int grid = (int)std::min<int64_t>(sym ? P.nblocks : (P.nvalues + 255) / 256, 8192);
     if (grid < 1) return cudaSuccess;
-    k_dm_to_f32<<<grid, sym ? 128 : 256, 0, s>>>(P, DM, out, sym ? 1 : 0);
+    k_dm_to_f32<<<grid, sym ? 128 : 256, 0, s>>>(P, DM, out, sym ? 1 : 0, amax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_absmax(const double *x, int64_t n, float *out, cudaStream_t s)
+{
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 2048);
+    if (grid < 1) return cudaSuccess;
+    k_absmax<<<grid, 256, 0, s>>>(x, n, out);
     return cudaGetLastError();
 }
 }  // namespace gint

@@ -17,7 +17,14 @@ using namespace gint;
 
 namespace gint {
 cudaError_t launch_mirror(const Plan &P, double *H, cudaStream_t s);
-cudaError_t launch_dm_to_f32(const Plan &P, const double *DM, float *out, bool sym, cudaStream_t s);
+cudaError_t launch_dm_to_f32(const Plan &P, const double *DM, float *out, bool sym, cudaStream_t s,
+                             float *amax = nullptr);
+cudaError_t launch_absmax(const double *x, int64_t n, float *out, cudaStream_t s);
+}
+
+static bool tc_prec(gint_prec p)
+{
+    return p == GINT_TF32X3 || p == GINT_BF16X3 || p == GINT_BF16X6 || p == GINT_FP16X3;
 }
 
 struct gint_batch_s {
@@ -35,6 +42,7 @@ struct gint_batch_s {
     void *d_mem[15] = {nullptr};    // [3w..3w+2] batches, slots, tables; [9] splines; [12+w] CTA ranges
     SInfo *d_sinfo = nullptr;
     int *d_status = nullptr;
+    float *d_amax = nullptr;         // [2 * nstruct]: max |V| and max |DM| of each entry (fp16 path)
     std::vector<float *> dm32;       // FP32 density matrix of each entry: the handle's scratch for
     std::vector<float *> own;        //   its first occurrence, a private buffer for repeats
     cudaStream_t cap = nullptr;
@@ -63,6 +71,7 @@ void free_batch(gint_batch b)
         if (p) cudaFree(p);
     if (b->d_sinfo) cudaFree(b->d_sinfo);
     if (b->d_status) cudaFree(b->d_status);
+    if (b->d_amax) cudaFree(b->d_amax);
     delete b;
 }
 
@@ -80,12 +89,18 @@ bool same_species(const gint_handle a, int sa, const gint_handle b, int sb)
 gint_status issue(gint_batch b, cudaStream_t s)
 {
     cudaError_t e;
+    const bool half = b->prec == GINT_FP16X3;
+    if (half && (e = cudaMemsetAsync(b->d_amax, 0, sizeof(float) * 2 * b->nstruct, s)) != cudaSuccess)
+        return cuda_fail(e, "gint_batch: memset");
     for (int i = 0; i < b->nstruct; ++i) {
         gint_handle h = b->hs[i];
         if ((e = cudaMemsetAsync(b->H[i], 0, sizeof(double) * h->info.nvalues, s)) != cudaSuccess)
             return cuda_fail(e, "gint_batch: memset");
+        if (half && (e = launch_absmax(b->V[i], h->info.npts, b->d_amax + 2 * i, s)) != cudaSuccess)
+            return cuda_fail(e, "gint_batch: potential range");
         if (b->with_rho && h->info.nvalues > 0 &&
-            (e = launch_dm_to_f32(h->plan, b->DM[i], b->dm32[i], false, s)) != cudaSuccess)
+            (e = launch_dm_to_f32(h->plan, b->DM[i], b->dm32[i], false, s, half ? b->d_amax + 2 * i + 1 : nullptr)) !=
+                cudaSuccess)
             return cuda_fail(e, "gint_batch: convert");
     }
     SInfo none{};
@@ -109,8 +124,7 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
                                          double *const *H, const double *const *DM, double *const *rho,
                                          gint_prec prec)
 {
-    if (!out || nstruct < 1 || nstruct > 255 || !hs || !V || !H ||
-        (prec != GINT_TF32X3 && prec != GINT_BF16X3 && prec != GINT_BF16X6)) {
+    if (!out || nstruct < 1 || nstruct > 255 || !hs || !V || !H || !tc_prec(prec)) {
         set_error("gint_batch_create: need 1..255 structures, V and H arrays, and a tensor-core precision");
         return GINT_EINVAL;
     }
@@ -237,9 +251,16 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
         b->own.push_back(p);
         b->dm32[i] = p;
     }
+    if ((e = cudaMalloc((void **)&b->d_amax, sizeof(float) * 2 * nstruct)) != cudaSuccess ||
+        (e = cudaMemset(b->d_amax, 0, sizeof(float) * 2 * nstruct)) != cudaSuccess) {
+        free_batch(b);
+        return cuda_fail(e, "gint_batch_create: allocate");
+    }
     std::vector<SInfo> si(nstruct);
-    for (int i = 0; i < nstruct; ++i)
+    for (int i = 0; i < nstruct; ++i) {
         si[i] = sinfo_for(hs[i], V[i], H[i], with_rho ? b->dm32[i] : nullptr, with_rho ? rho[i] : nullptr, nullptr);
+        si[i].amax = b->d_amax + 2 * i;
+    }
     if ((e = upload_vec(&b->d_mem[9], coef)) != cudaSuccess || (e = upload_vec((void **)&b->d_sinfo, si)) != cudaSuccess ||
         (e = cudaMalloc((void **)&b->d_status, sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(b->d_status, 0, sizeof(int))) != cudaSuccess) {
@@ -294,7 +315,7 @@ extern "C" gint_status gint_batch_destroy(gint_batch b)
 extern "C" gint_status gint_batched(int nstruct, const gint_handle *hs, const double *const *V, double *const *H,
                                    const double *const *DM, double *const *rho, gint_prec prec, void *stream)
 {
-    if (nstruct < 0 || (nstruct > 0 && (!hs || !V || !H)) || prec < GINT_FP64 || prec > GINT_BF16X6) {
+    if (nstruct < 0 || (nstruct > 0 && (!hs || !V || !H)) || prec < GINT_FP64 || prec > GINT_FP16X3) {
         set_error("gint_batched: invalid arguments");
         return GINT_EINVAL;
     }
@@ -330,7 +351,7 @@ extern "C" gint_status gint_autotune(const double cell[9], int natoms, const int
                                      int nspecies, const gint_species *sp, const int grid[3], gint_prec prec,
                                      gint_options *best, double *ms_vlocal, double *ms_rho)
 {
-    if (!best || (prec != GINT_TF32X3 && prec != GINT_BF16X3 && prec != GINT_BF16X6)) {
+    if (!best || !tc_prec(prec)) {
         set_error("gint_autotune: need an output and a tensor-core precision");
         return GINT_EINVAL;
     }

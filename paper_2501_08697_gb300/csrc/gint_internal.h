@@ -60,8 +60,10 @@ struct SInfo {
     double *dLde;                  // 9 values: strain derivative (single-structure launches only)
     const float *poff;
     int grid[3];
-    int pad;
+    float phimax;                  // bound on |phi| over the species (fp16 operand scaling)
     double dV;
+    const float *amax;             // device [2]: max |V(r)| and max |density matrix| of the call,
+                                   // written before the kernel by the fp16 path (else unused)
 };
 
 // Everything a kernel needs, passed by value.
@@ -129,6 +131,7 @@ struct gint_handle_s {
     std::vector<int64_t> offsets;    // nblocks + 1
     std::vector<int> partner;
     gint::BatchSet bs[2];            // [0] vlocal batches, [1] rho/force batches
+    bool relist[2] = {false, false}; // a position update changed that decomposition's lists
     std::vector<float4> coef32_host; // spline records, as uploaded
     gint_options opt{};
     gint_info_t info{};
@@ -140,6 +143,8 @@ struct gint_handle_s {
     float *d_dm32 = nullptr;         // scratch: density matrix (or its symmetric part) in FP32
     float *d_poff = nullptr;         // point-offset table
     double *d_red = nullptr;         // scratch: partial sums of reductions
+    float *d_amax = nullptr;         // scratch: largest |V(r)| and |DM| of an fp16 call (2 floats)
+    float phimax = 1.f;              // bound on |phi_mu(r)| from the spline records
     struct {                         // k-space transforms (built on first use)
         int *d_keys = nullptr;       // [nblocks][5] block keys
         int *d_grp = nullptr;        // [ngroups + 1] first block of each (I, J) group

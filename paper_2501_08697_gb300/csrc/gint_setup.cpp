@@ -434,17 +434,21 @@ gint_status build_geometry(gint_handle h, const double *tau, bool update_only)
                 }
     }
     if (update_only) {
+        // a decomposition whose atom-image lists are unchanged keeps its device arrays and gets
+        // new slot positions only; one whose lists changed is replaced as a whole
         for (int w = 0; w < 2; ++w) {
             const BatchSet &o = h->bs[w], &n = sets[w];
             bool same = o.batches.size() == n.batches.size() && o.slot_img == n.slot_img && o.tbl == n.tbl &&
                         o.slots.size() == n.slots.size();
             for (size_t i = 0; same && i < n.slots.size(); ++i) same = o.slots[i].atom == n.slots[i].atom;
-            if (!same) {
-                set_error("gint_update_positions: batch atom lists changed; build a new handle");
-                return GINT_ESTATE;
+            if (same) {
+                h->bs[w].slots = std::move(sets[w].slots);
+                h->relist[w] = false;
+            } else {
+                h->bs[w] = std::move(sets[w]);
+                h->relist[w] = true;
             }
         }
-        for (int w = 0; w < 2; ++w) h->bs[w].slots = std::move(sets[w].slots);
     } else {
         h->keys = std::move(keys);
         h->offsets = std::move(offsets);
@@ -550,7 +554,7 @@ static void free_dev(gint_handle h)
                     h->d_dm32, h->d_poff, h->d_red, h->d_hostio, h->bs[0].d_batches, h->bs[0].d_slots, h->bs[0].d_tbl,
                     h->bs[0].d_rng, h->bs[1].d_batches, h->bs[1].d_slots, h->bs[1].d_tbl, h->bs[1].d_rng,
                     h->ks.d_keys, h->ks.d_grp, h->ks.d_pair, h->ks.d_colatom, h->ks.d_orboff, h->ks.d_kvec,
-                    h->ks.d_phase, h->d_dm_scratch, h->d_dm_planes};
+                    h->ks.d_phase, h->d_dm_scratch, h->d_dm_planes, h->d_amax};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t &ev : h->io_ev)
@@ -558,20 +562,35 @@ static void free_dev(gint_handle h)
     if (h->io_stream) cudaStreamDestroy(h->io_stream);
 }
 
+// device arrays of one batch decomposition (replacing any earlier ones)
+static gint_status upload_batchset(gint_handle h, int w)
+{
+    cudaError_t e;
+    BatchSet &b = h->bs[w];
+    // kernels still queued may read the old arrays
+    if (b.d_batches && (e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "synchronise");
+    for (void **p : {&b.d_batches, &b.d_slots, &b.d_tbl, &b.d_rng})
+        if (*p) {
+            cudaFree(*p);
+            *p = nullptr;
+        }
+    if ((e = upload(&b.d_batches, b.batches)) != cudaSuccess) return cuda_fail(e, "upload batches");
+    if ((e = upload(&b.d_slots, b.slots)) != cudaSuccess) return cuda_fail(e, "upload slots");
+    if ((e = upload(&b.d_tbl, b.tbl)) != cudaSuccess) return cuda_fail(e, "upload tables");
+    const int nb = (int)b.batches.size();
+    b.rng = segment_ranges(b.batches.data(), {0, nb}, std::max(1, std::min(h->nsm, nb)), w);
+    if ((e = upload(&b.d_rng, b.rng)) != cudaSuccess) return cuda_fail(e, "upload CTA ranges");
+    return GINT_OK;
+}
+
 static gint_status upload_geometry(gint_handle h)
 {
     cudaError_t e;
-    // (re)upload everything that depends on positions; sizes are fixed after set-up
+    gint_status st;
+    // (re)upload everything that depends on positions; the block layout is fixed after set-up
     if (!h->d_blkoff) {
-        for (int w = 0; w < 2; ++w) {
-            BatchSet &b = h->bs[w];
-            if ((e = upload(&b.d_batches, b.batches)) != cudaSuccess) return cuda_fail(e, "upload batches");
-            if ((e = upload(&b.d_slots, b.slots)) != cudaSuccess) return cuda_fail(e, "upload slots");
-            if ((e = upload(&b.d_tbl, b.tbl)) != cudaSuccess) return cuda_fail(e, "upload tables");
-            const int nb = (int)b.batches.size();
-            b.rng = segment_ranges(b.batches.data(), {0, nb}, std::max(1, std::min(h->nsm, nb)), w);
-            if ((e = upload(&b.d_rng, b.rng)) != cudaSuccess) return cuda_fail(e, "upload CTA ranges");
-        }
+        for (int w = 0; w < 2; ++w)
+            if ((st = upload_batchset(h, w)) != GINT_OK) return st;
         if ((e = upload(&h->d_partner, h->partner)) != cudaSuccess) return cuda_fail(e, "upload partner");
         if ((e = upload(&h->d_blkoff, h->offsets)) != cudaSuccess) return cuda_fail(e, "upload offsets");
         std::vector<int> rows(h->info.nblocks);
@@ -580,6 +599,11 @@ static gint_status upload_geometry(gint_handle h)
     } else {
         for (int w = 0; w < 2; ++w) {
             BatchSet &b = h->bs[w];
+            if (h->relist[w]) {
+                if ((st = upload_batchset(h, w)) != GINT_OK) return st;
+                h->relist[w] = false;
+                continue;
+            }
             if (b.slots.empty()) continue;
             e = cudaMemcpy(b.d_slots, b.slots.data(), b.slots.size() * sizeof(Slot), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) return cuda_fail(e, "update slots");
@@ -756,6 +780,15 @@ extern "C" gint_status gint_setup(gint_handle *out, const double cell[9], int na
     P.coef64 = (const double *)h->d_coef64;
     P.coef32 = (const float4 *)h->d_coef32;
     h->coef32_host = coef32;
+    {
+        // |phi| <= max |f| * max |Y_lm|; on an interval |f(t)| <= |c0| + |c1| + |c2| + |c3|
+        // (0 <= t <= 1), and |Y_lm| <= sqrt(5/(16 pi)) * 2 = 0.631 for l <= 2
+        double fmax = 0.0;
+        for (size_t i = 0; i + 3 < coef64.size(); i += 4)
+            fmax = std::max(fmax, std::fabs(coef64[i]) + std::fabs(coef64[i + 1]) + std::fabs(coef64[i + 2]) +
+                                      std::fabs(coef64[i + 3]));
+        h->phimax = (float)(fmax * 0.64);
+    }
     if ((st = upload_geometry(h)) != GINT_OK) {
         free_dev(h);
         delete h;
@@ -765,7 +798,9 @@ extern "C" gint_status gint_setup(gint_handle *out, const double cell[9], int na
         (e = cudaMemset(h->d_status, 0, sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc((void **)&h->d_dmsym, std::max<size_t>(8, h->info.nvalues * sizeof(double)))) != cudaSuccess ||
         (e = cudaMalloc((void **)&h->d_dm32, std::max<size_t>(16, h->info.nvalues * sizeof(float)))) != cudaSuccess ||
-        (e = cudaMalloc((void **)&h->d_red, 4096 * sizeof(double))) != cudaSuccess) {
+        (e = cudaMalloc((void **)&h->d_red, 4096 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&h->d_amax, 4 * sizeof(float))) != cudaSuccess ||
+        (e = cudaMemset(h->d_amax, 0, 4 * sizeof(float))) != cudaSuccess) {
         free_dev(h);
         delete h;
         return cuda_fail(e, "gint_setup: allocate");
@@ -860,7 +895,21 @@ extern "C" gint_status gint_update_positions(gint_handle h, const double *tau)
     if (st != GINT_OK) return st;
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(e, "gint_update_positions");
-    for (int w = 0; w < 2; ++w) h->bs[w].slots = std::move(tmp.bs[w].slots);
+    for (int w = 0; w < 2; ++w) {
+        h->relist[w] = tmp.relist[w];
+        if (tmp.relist[w]) {
+            // the new lists, with the old device arrays (freed and replaced by upload_geometry)
+            BatchSet &o = h->bs[w];
+            void *dev[4] = {o.d_batches, o.d_slots, o.d_tbl, o.d_rng};
+            o = std::move(tmp.bs[w]);
+            o.d_batches = dev[0];
+            o.d_slots = dev[1];
+            o.d_tbl = dev[2];
+            o.d_rng = dev[3];
+        } else {
+            h->bs[w].slots = std::move(tmp.bs[w].slots);
+        }
+    }
     h->tau = std::move(tmp.tau);
     h->info = tmp.info;
     h->plan.dV = tmp.plan.dV;

@@ -319,7 +319,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 continue;
             }
             const SInfo SI = sic.get(B, sis);
-            const float dVf = (float)SI.dV;
+            float dVf = (float)SI.dV, sA = 1.f;
+            if constexpr (S::HALF) {
+                // fp16 operands: A = phi sA, B = V dV phi sB (powers of two, undone in the epilogue)
+                sA = scale_for(SI.phimax);
+                dVf *= scale_for(SI.amax[0] * dVf * SI.phimax);
+            }
             for (int p = pt; p < kMaxBatchPts; p += kProd)
                 vs[p] = p < npb ? d2f(vdb[cur * kMaxBatchPts + p]) * dVf : 0.f;
             const int nch = (npb + KC - 1) / KC;
@@ -366,6 +371,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         for (int i = 0; i < S::CG; ++i) {
                             x[i] = stg[row * KC + kc * S::CG + i];
                             y[i] = x[i] * vs[ch * KC + kc * S::CG + i];
+                            if constexpr (S::HALF) x[i] *= sA;
                         }
                         split_store<S>(x, da);
                         split_store<S>(y, db);
@@ -446,7 +452,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             const int npad = (nb + 15) & ~15;
             const int buf = nbuf == 2 ? (it & 1) : 0;
             if (nb == 0) continue;
-            double *H = sic.get(B, sis).H;
+            const SInfo SIe = sic.get(B, sis);
+            double *H = SIe.H;
+            float u = 1.f;   // undoes the fp16 operand scaling (exact: a power of two)
+            if constexpr (S::HALF) {
+                const float dVf = (float)SIe.dV;
+                u = 1.f / (scale_for(SIe.phimax) * scale_for(SIe.amax[0] * dVf * SIe.phimax));
+            }
             const bool small = ns <= kVTbl;
             const int *tbl = small ? tbls : P.tbl + B.tbl;
             named_sync(2, kEpi);
@@ -499,7 +511,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         const int rlim = min(rend, nu - row0 + 1);  // upper triangle: row <= nu
 #pragma unroll 4
                         for (int r2 = r; r2 < rend; ++r2)
-                            if (blk && r2 < rlim) red_add_f64(base + r2 * nbo, f2d_fast(tl[lane * 33 + r2]));
+                            if (blk && r2 < rlim) red_add_f64(base + r2 * nbo, f2d_fast(tl[lane * 33 + r2] * u));
                         r = rend;
                     }
                     __syncwarp();
@@ -624,6 +636,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             const SInfo SI = sic.get(B, sis);
             const float *__restrict__ DM = SI.DM32;
             const int *__restrict__ tbl = P.tbl + B.tbl;
+            float sA = 1.f, sD = 1.f;   // fp16 operands: A = phi sA, B = D sD (undone in the epilogue)
+            if constexpr (S::HALF) {
+                sA = scale_for(SI.phimax);
+                sD = scale_for(SI.amax[1]);
+            }
             named_sync(1, kProd);
             load_geom(P, SI, B, ps, poff, pt, kProd);
             // the batch's slot-pair table in shared memory (gather tables read it per chunk)
@@ -716,6 +733,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     float x[S::CG];
 #pragma unroll
                     for (int i = 0; i < S::CG; ++i) x[i] = stg[(rbase + kc * S::CG + i) * kMaxBatchPts + p];
+                    if constexpr (S::HALF)
+#pragma unroll
+                        for (int i = 0; i < S::CG; ++i) x[i] *= sA;
                     split_store<S>(x, da);
                 }
                 // phase 2b: B = D rows nu (N), K = orbitals mu of the chunk: D(b_nu, a_mu)[o_nu][o_mu]
@@ -747,6 +767,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 #pragma unroll
                         for (int t = 0; t < S::NT; ++t)
                             db[t] = base + S::NT * L::ARR_A + t * L::ARR_B + cm_off<S>(nu, kc);
+                        if constexpr (S::HALF)
+#pragma unroll
+                            for (int i = 0; i < S::CG; ++i) x[gq][i] *= sD;
                         split_store<S>(x[gq], db);
                     }
                 }
@@ -834,10 +857,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256);
             float vp = 0.f;
             int64_t gi = 0;
+            float u = 1.f;   // undoes the fp16 operand scaling of Psi (exact: a power of two)
+            if constexpr (S::HALF) u = 1.f / (scale_for(SI.phimax) * scale_for(SI.amax[1]));
             if (pv) {
                 gi = grid_index(SI, B, p, n2, n3);
                 if (FORCE) vp = d2f(SI.V[gi]);
             }
+            const float vpu = vp * u;
             float po[6];   // this point's offset from the batch origin (hi, lo)
 #pragma unroll
             for (int c = 0; c < 6; ++c) po[c] = epoff[6 * (pv ? p : 0) + c];
@@ -892,7 +918,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     st[6] += fz * dx; st[7] += fz * dy; st[8] += fz * dz;
                 }
                 if (FORCE && SI.F) {
-                    fx *= vp; fy *= vp; fz *= vp;
+                    fx *= vpu; fy *= vpu; fz *= vpu;
 #pragma unroll
                     for (int m = 16; m > 0; m >>= 1) {
                         fx += __shfl_xor_sync(0xffffffffu, fx, m);
@@ -910,6 +936,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             }
             tc_fence_before();
             mbar_arrive(&accempty[buf]);
+            racc *= u;
             if (RHO && hh == 1) rpart[p] = racc;
             named_sync(2, kEpi);
             if (RHO && hh == 0 && pv) SI.rho[gi] = f2d(racc + rpart[p]);
@@ -918,7 +945,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     red_add_f64(&SI.F[3 * eps[e / 3].atom + e % 3], 2.0 * SI.dV * f2d(facc[e]));
             if (strain && pv) {
 #pragma unroll
-                for (int k = 0; k < 9; ++k) sacc[k] += f2d(vp * st[k]);
+                for (int k = 0; k < 9; ++k) sacc[k] += f2d(vpu * st[k]);
                 sacc[9] += f2d(vp * racc);
             }
             ++it;
@@ -1006,6 +1033,7 @@ cudaError_t launch_vlocal_tc(const Plan &P, gint_prec prec, const SInfo &si0, co
     case GINT_TF32X3: return vlocal_launch<TF32x3W>(P, si0, sis, s, nsm, max_nb);
     case GINT_BF16X3: return vlocal_launch<BF16x3W>(P, si0, sis, s, nsm, max_nb);
     case GINT_BF16X6: return vlocal_launch<BF16x6W>(P, si0, sis, s, nsm, max_nb);
+    case GINT_FP16X3: return vlocal_launch<FP16x3W>(P, si0, sis, s, nsm, max_nb);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1018,6 +1046,7 @@ cudaError_t launch_rho_force_tc(const Plan &P, gint_prec prec, const SInfo &si0,
     case GINT_TF32X3: return rho_launch<TF32x3W>(P, si0, sis, rho, force, s, nsm);
     case GINT_BF16X3: return rho_launch<BF16x3W>(P, si0, sis, rho, force, s, nsm);
     case GINT_BF16X6: return rho_launch<BF16x6W>(P, si0, sis, rho, force, s, nsm);
+    case GINT_FP16X3: return rho_launch<FP16x3W>(P, si0, sis, rho, force, s, nsm);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -3,6 +3,7 @@
 // precision schemes and the canonical K-major no-swizzle shared-memory operand layout.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 
 #include "gint_device.cuh"
@@ -120,27 +121,47 @@ __device__ __forceinline__ void tmem_st16(uint32_t addr, const float *v)
 // operand stages in the rho/force and vlocal kernels (one stage suffices when the next chunk's
 // orbital evaluation, which precedes the stage rewrite, covers the chunk's MMAs; measured).
 // PA/PB: operand term of product q, packed one nibble per product.
+// HALF: fp16 terms (FMT 0), whose narrow exponent range needs the power-of-two operand
+// scaling of scale_for(); the other schemes keep FP32's exponent range and use no scaling.
 struct TF32x3W {  // hi + lo TF32 terms, products hi.hi + hi.lo + lo.hi
     static constexpr int CG = 4, NT = 2, NPROD = 3, KCM = 8;
     static constexpr int RSTAGES = 1;
     static constexpr int VSTAGES = 1;
-    static constexpr bool F16 = false;
+    static constexpr bool F16 = false, HALF = false;
     static constexpr uint32_t FMT = 2, PA = 0x100, PB = 0x010;
 };
 struct BF16x3W {  // hi + lo BF16 terms, the same three products
     static constexpr int CG = 8, NT = 2, NPROD = 3, KCM = 4;
     static constexpr int RSTAGES = 2;
     static constexpr int VSTAGES = 1;
-    static constexpr bool F16 = true;
+    static constexpr bool F16 = true, HALF = false;
     static constexpr uint32_t FMT = 1, PA = 0x100, PB = 0x010;
 };
 struct BF16x6W {  // hi + mid + lo BF16 terms, the six products of total order <= 2
     static constexpr int CG = 8, NT = 3, NPROD = 6, KCM = 4;
     static constexpr int RSTAGES = 1;
     static constexpr int VSTAGES = 1;
-    static constexpr bool F16 = true;
+    static constexpr bool F16 = true, HALF = false;
     static constexpr uint32_t FMT = 1, PA = 0x210100, PB = 0x012010;
 };
+struct FP16x3W {  // hi + lo fp16 terms (11-bit significands, as TF32), the three products
+    static constexpr int CG = 8, NT = 2, NPROD = 3, KCM = 4;
+    static constexpr int RSTAGES = 2;
+    static constexpr int VSTAGES = 1;
+    static constexpr bool F16 = true, HALF = true;
+    static constexpr uint32_t FMT = 0, PA = 0x100, PB = 0x010;
+};
+
+// Power of two s with m * s < 2^14 (1 if m is zero or not finite): the fp16 operands are
+// scaled by it so that their largest terms sit just below 2^14, products below 2^28, and the
+// low terms of values down to 2^-17 of the largest stay normal numbers.
+__device__ __forceinline__ float scale_for(float m)
+{
+    if (!(m > 0.f) || !(m < 3.0e38f)) return 1.f;
+    int e;
+    frexpf(m, &e);   // m < 2^e
+    return ldexpf(1.f, 14 - e);
+}
 __host__ __device__ constexpr int term(uint32_t packed, int q) { return (int)((packed >> (4 * q)) & 0xF); }
 
 __device__ __forceinline__ float tf32_rna(float x)
@@ -164,6 +185,20 @@ __device__ __forceinline__ void split_store(const float *x, unsigned char *const
         }
         *reinterpret_cast<float4 *>(dst[0]) = hi;
         *reinterpret_cast<float4 *>(dst[1]) = lo;
+    } else if constexpr (S::HALF) {
+        __align__(16) __half t[S::NT][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float r = x[i];
+#pragma unroll
+            for (int k = 0; k < S::NT; ++k) {
+                __half b = __float2half_rn(r);
+                t[k][i] = b;
+                r -= __half2float(b);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < S::NT; ++k) *reinterpret_cast<uint4 *>(dst[k]) = *reinterpret_cast<const uint4 *>(t[k]);
     } else {
         __align__(16) __nv_bfloat16 t[S::NT][8];
 #pragma unroll

@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 GINT_OK, GINT_EINVAL, GINT_ENOMEM, GINT_ECUDA, GINT_ETIMEOUT, GINT_ESTATE = range(6)
-PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3, "bf16x6": 4}
+PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16x3": 3, "bf16x6": 4, "fp16x3": 5}
 PREC_NAME = {v: k for k, v in PREC.items()}
 
 EXPORTS = ["gint_setup", "gint_destroy", "gint_block_layout", "gint_get_info", "gint_update_positions",

@@ -16,6 +16,25 @@ def rel_fro(a, b):
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 
 
+def block_class_errors(H, ref, keys, offs, norb_atom):
+    """Per block shape (rows x cols): the relative Frobenius error over the blocks of that shape
+    and the worst relative error of a single block among them (blocks whose reference norm is
+    below 1e-12 of the largest block norm are left out of the worst-block figure)."""
+    H = np.asarray(H, np.float64)
+    ref = np.asarray(ref, np.float64)
+    d2, r2, worst = {}, {}, {}
+    norms = np.sqrt(np.add.reduceat(ref * ref, offs[:-1])) if len(keys) else np.zeros(0)
+    dn = np.sqrt(np.add.reduceat((H - ref) ** 2, offs[:-1])) if len(keys) else np.zeros(0)
+    big = norms.max() if len(norms) else 0.0
+    for b in range(len(keys)):
+        k = f"{norb_atom[keys[b, 0]]}x{norb_atom[keys[b, 1]]}"
+        d2[k] = d2.get(k, 0.0) + dn[b] ** 2
+        r2[k] = r2.get(k, 0.0) + norms[b] ** 2
+        if norms[b] > 1e-12 * big:
+            worst[k] = max(worst.get(k, 0.0), dn[b] / norms[b])
+    return {k: (float(np.sqrt(d2[k] / r2[k])) if r2[k] > 0 else 0.0, worst.get(k, 0.0)) for k in sorted(d2)}
+
+
 def structure(name):
     if name == "si8":
         return S.workload("si8")

@@ -165,3 +165,30 @@ def test_water_box_split_bf16_with_fd_on_eight_atoms(env):
     assert rel_fro(grads["bf16x6"][0], grads["fp64"][0]) <= 1e-6
     assert rel_fro(grads["bf16x6"][1], grads["fp64"][1]) <= 2e-6
     assert rel_fro(grads["bf16x3"][0], grads["fp64"][0]) <= 1e-4
+
+
+def test_two_forwards_at_different_tau_before_backward(env):
+    """L = <gH, H(V; tau1)> + <gH2, H(V; tau2)> on one handle: the second forward moves the
+    handle, and each term's backward must still be taken at its own geometry.  The sum of the
+    two gradients is compared with two separate forward/backward passes."""
+    G, S, vlocal = env
+    st, V, h, keys, gH = _setup(G, S, "si8_ragged")
+    dev = torch.device("cuda")
+    gH2 = S.density_matrix(keys, st.norb_atom, seed=st.seed + 11)
+    gHt, gH2t = torch.from_numpy(gH).to(dev), torch.from_numpy(gH2).to(dev)
+    tau1 = st.tau.copy()
+    tau2 = st.tau.copy()
+    tau2[0] += (0.01, -0.02, 0.015)
+    Vt = torch.from_numpy(V.reshape(-1)).to(dev)
+
+    def grad_of(pairs):
+        ts = [torch.from_numpy(t.copy()).requires_grad_(True) for t, _ in pairs]
+        L = sum((vlocal(Vt, t, h, "fp64") * g).sum() for t, (_, g) in zip(ts, pairs))
+        L.backward()
+        return [t.grad.numpy().copy() for t in ts]
+
+    g1, g2 = grad_of([(tau1, gHt), (tau2, gH2t)])      # both forwards, then one backward
+    (r1,) = grad_of([(tau1, gHt)])
+    (r2,) = grad_of([(tau2, gH2t)])
+    assert rel_fro(g1, r1) < 1e-12 and rel_fro(g2, r2) < 1e-12
+    assert rel_fro(g1, g2) > 1e-3                        # the two geometries do differ

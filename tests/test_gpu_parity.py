@@ -1,8 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
 Tolerances (relative Frobenius norm over the whole output): FP64 <= 1e-11; FP32 and the
-split tensor-core paths TF32x3 / BF16x6 <= 1e-6; BF16x3 (about 16 significant bits) is
-held to 5e-5 and its error reported.  The block layout is compared bit-exactly.
+split tensor-core paths TF32x3 / FP16x3 / BF16x6 <= 1e-6; BF16x3 (about 16 significant bits)
+is held to 5e-5 and its error reported.  The block layout is compared bit-exactly.
 """
 import numpy as np
 import pytest
@@ -12,12 +12,12 @@ from tests._cases import inputs, oracle_full, rel_fro
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-11, "fp32": 1e-6, "tf32x3": 1e-6, "bf16x6": 1e-6, "bf16x3": 5e-5}
-FORCE_TOL = {"fp64": 1e-10, "fp32": 1e-6, "tf32x3": 1e-6, "bf16x6": 1e-6, "bf16x3": 1e-4}
+TOL = {"fp64": 1e-11, "fp32": 1e-6, "tf32x3": 1e-6, "fp16x3": 1e-6, "bf16x6": 1e-6, "bf16x3": 5e-5}
+FORCE_TOL = {"fp64": 1e-10, "fp32": 1e-6, "tf32x3": 1e-6, "fp16x3": 1e-6, "bf16x6": 1e-6, "bf16x3": 1e-4}
 SIMT = ["fp64", "fp32"]
-ALL = ["fp64", "fp32", "tf32x3", "bf16x3", "bf16x6"]
+ALL = ["fp64", "fp32", "tf32x3", "fp16x3", "bf16x3", "bf16x6"]
 CASES = ["si8", "si8_ragged", "si16_strained", "water8", "water1_vacuum", "si8_2d"]
-TC = ["tf32x3", "bf16x3", "bf16x6"]
+TC = ["tf32x3", "fp16x3", "bf16x3", "bf16x6"]
 
 
 @pytest.fixture(scope="module")
@@ -82,7 +82,7 @@ def test_tensor_core_parity(G, name, prec):
 
 
 @pytest.mark.parametrize("batch", [(4, 4, 4), (2, 2, 2), (4, 4, 2), (8, 2, 4)])
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x6"])
+@pytest.mark.parametrize("prec", ["tf32x3", "fp16x3", "bf16x6"])
 def test_tensor_core_batch_shapes(G, batch, prec):
     """One-tile (<= 128 orbitals), two-tile and split batches; ragged grid.  Batches of at
     most 64 points keep the tensor-core FP32 accumulation within 1e-6 for vlocal."""
@@ -141,7 +141,7 @@ def test_block_symmetry_of_gpu_h(G):
         assert np.array_equal(A, B.T)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "bf16x6"])
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "fp16x3", "bf16x6"])
 def test_many_atom_images_per_batch(G, prec):
     """h64_dense: every batch sees 39-53 atom images (one orbital each), more than the
     shared-memory slot-pair tables of the tensor-core kernels hold (28), so vlocal's scatter and

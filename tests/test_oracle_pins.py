@@ -231,6 +231,26 @@ def test_two_centre_overlaps_match_continuum():
     assert blk[2, 0] > 0 > blk[0, 2]
 
 
+def test_blockwise_vlocal_matches_continuum_overlaps():
+    """The block-by-block form of V_mu,nu(R) (a sum over the points of all space in the first
+    atom's sphere) on the same two-centre overlaps as above."""
+    d = 2.5
+    N = 64
+    o = Oracle(np.diag([10.26] * 3), [0, 0], np.array([[1.0, 2.0, 3.0], [1.0, 2.0, 3.0 + d]]), [SI_TAB], (N, N, N))
+    keys, offs = o.pairs()
+    b01 = int(np.nonzero((keys == np.array((0, 1, 0, 0, 0))).all(1))[0][0])
+    b10 = int(np.nonzero((keys == np.array((1, 0, 0, 0, 0))).all(1))[0][0])
+    out = o.vlocal_blocks(np.ones(N ** 3), [b01, b10])
+    blk, blkT = out[:169].reshape(13, 13), out[169:].reshape(13, 13)
+    want_ss = _two_centre(lambda r, c: S.radial_analytic(S.SI, 0, r) * C0,
+                          lambda r, c: S.radial_analytic(S.SI, 0, r) * C0, d)
+    want_ps = _two_centre(lambda r, c: S.radial_analytic(S.SI, 2, r) * C1 * c,
+                          lambda r, c: S.radial_analytic(S.SI, 0, r) * C0, d)
+    assert blk[0, 0] == pytest.approx(want_ss, abs=1e-9) and blkT[0, 0] == pytest.approx(want_ss, abs=1e-9)
+    assert blk[2, 0] == pytest.approx(want_ps, abs=1e-9) and blkT[0, 2] == pytest.approx(want_ps, abs=1e-9)
+    assert blk[2, 0] > 0 > blk[0, 2]
+
+
 def test_plane_wave_potential_fourier_coefficient():
     """One s orbital, V = -1 + 0.5 cos(G.r + theta) with G a reciprocal-lattice vector of an
     orthorhombic cell: H_ss = -1 + 0.5 cos(G.tau + theta) F(|G|), F(k) = int f^2 r^2 j0(kr) dr."""
@@ -362,3 +382,25 @@ def test_density_matrix_generator_is_block_symmetric(si8_small):
         B = DM[offs[part[b]]:offs[part[b] + 1]].reshape(o.norb_atom[keys[part[b], 0]], -1)
         assert np.array_equal(A, B.T)
         assert np.abs(A).max() <= 0.1
+
+
+def test_blockwise_forms_match_pointwise_sums(si8_small):
+    """The per-block vlocal and per-atom dL/dtau (sums over the points of one sphere in all
+    space) agree with the per-point sums over the cell with periodic images, and the per-atom
+    derivative with a central difference of L."""
+    st, o, keys, offs, V, DM, H = si8_small
+    rng = np.random.default_rng(5)
+    sel = rng.choice(len(keys), 40, replace=False)
+    got = o.vlocal_blocks(V, sel)
+    want = np.concatenate([H[offs[b]:offs[b + 1]] for b in sel])
+    assert np.abs(got - want).max() < 1e-13 * np.abs(H).max()
+    g = o.dLdtau(V, DM)
+    ga = o.dLdtau_atoms(V, DM, np.arange(st.natoms))
+    assert np.abs(ga - g).max() < 1e-12 * np.abs(g).max()
+    h = 1e-4
+    Ls = []
+    for sgn in (1, -1):
+        tau = st.tau.copy()
+        tau[3, 1] += sgn * h
+        Ls.append((DM * Oracle(st.cell, st.species, tau, st.tables, st.grid).vlocal(V)).sum())
+    assert (Ls[0] - Ls[1]) / (2 * h) == pytest.approx(ga[3, 1], rel=1e-6, abs=1e-9 * np.abs(ga).max())

@@ -10,16 +10,14 @@ using namespace gint;
 
 namespace gint {
 cudaError_t launch_mirror(const Plan &P, double *H, cudaStream_t s);
-cudaError_t launch_dm_to_f32(const Plan &P, const double *DM, float *out, bool sym, cudaStream_t s,
-                             float *amax = nullptr);
-cudaError_t launch_absmax(const double *x, int64_t n, float *out, cudaStream_t s);
 
-SInfo sinfo_for(const gint_handle_s *h, const double *V, double *H, const float *DM32, double *rho, double *F)
+SInfo sinfo_for(const gint_handle_s *h, const double *V, double *H, const void *DMS, double *rho, double *F)
 {
     SInfo si{};
     si.V = V;
     si.H = H;
-    si.DM32 = DM32;
+    si.DMS = DMS;
+    si.dms_plane = h->dms_plane;
     si.rho = rho;
     si.F = F;
     si.poff = h->d_poff;
@@ -62,34 +60,6 @@ __device__ __forceinline__ void block_max_to(float m, float *out)
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmaxf(b, wm[w]);
         atomicMax(reinterpret_cast<unsigned *>(out), __float_as_uint(b));
     }
-}
-
-// out <- FP32 copy of DM, or of its block-symmetric part (DM + DM^T_block)/2; with amax, the
-// largest magnitude written is max-reduced into *amax (zeroed by the caller)
-__global__ void k_dm_to_f32(Plan P, const double *__restrict__ DM, float *out, int sym, float *amax)
-{
-    float m = 0.f;
-    if (!sym) {
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.nvalues; i += (int64_t)gridDim.x * blockDim.x) {
-            const float v = d2f(DM[i]);
-            out[i] = v;
-            m = fmaxf(m, fabsf(v));
-        }
-    } else {
-        for (int64_t b = blockIdx.x; b < P.nblocks; b += gridDim.x) {
-            const int pb = P.partner[b];
-            const int64_t off = P.blk_off[b], poff = P.blk_off[pb];
-            const int rows = P.blk_rows[b];
-            const int cols = (int)((P.blk_off[b + 1] - off) / rows);
-            for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
-                const int mu = e / cols, nu = e - mu * cols;
-                const float v = 0.5f * (d2f(DM[off + e]) + d2f(DM[poff + nu * rows + mu]));
-                out[off + e] = v;
-                m = fmaxf(m, fabsf(v));
-            }
-        }
-    }
-    if (amax) block_max_to(m, amax);
 }
 
 // *out <- max(*out, max_i |x_i|) (FP32, rounded to nearest)
@@ -208,13 +178,16 @@ gint_status run_rho_force(gint_handle h, const double *V, const double *DM, doub
         }
         e = launch_rho_force_simt(plan_for(h, 1), prec == GINT_FP64, V, D, rho, F, dLde, s, h->nsm);
     } else {
-        // tensor-core kernels gather the density matrix in FP32 (split again on chip)
+        // tensor-core kernels copy the density matrix from its pre-split padded store
         float *amax = prec == GINT_FP16X3 ? h->d_amax + 1 : nullptr;
-        if (amax && (e = cudaMemsetAsync(amax, 0, sizeof(float), s)) != cudaSuccess)
+        if (amax && ((e = cudaMemsetAsync(amax, 0, sizeof(float), s)) != cudaSuccess ||
+                     (e = launch_absmax(DM, h->info.nvalues, amax, s)) != cudaSuccess))
             return cuda_fail(e, "gint_rho: range");
-        if (h->info.nvalues > 0 && (e = launch_dm_to_f32(h->plan, DM, h->d_dm32, grad, s, amax)) != cudaSuccess)
-            return cuda_fail(e, "gint_rho: convert");
-        SInfo si = sinfo_for(h, V, nullptr, h->d_dm32, rho, F);
+        if (h->info.nvalues > 0 &&
+            (e = launch_dm_split(h->plan, prec, (const int *)h->d_soff, DM, h->d_dms, h->dms_plane, grad, amax, s)) !=
+                cudaSuccess)
+            return cuda_fail(e, "gint_rho: split");
+        SInfo si = sinfo_for(h, V, nullptr, h->d_dms, rho, F);
         si.dLde = dLde;
         e = launch_rho_force_tc(plan_for(h, 1), prec, si, nullptr, rho != nullptr, grad, s, h->nsm);
     }
@@ -397,14 +370,6 @@ extern "C" gint_status gint_get_status(gint_handle h)
 
 
 namespace gint {
-cudaError_t launch_dm_to_f32(const Plan &P, const double *DM, float *out, bool sym, cudaStream_t s, float *amax)
-{
-    const int grid = (int)std::min<int64_t>(sym ? P.nblocks : (P.nvalues + 255) / 256, 8192);
-    if (grid < 1) return cudaSuccess;
-    k_dm_to_f32<<<grid, sym ? 128 : 256, 0, s>>>(P, DM, out, sym ? 1 : 0, amax);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_absmax(const double *x, int64_t n, float *out, cudaStream_t s)
 {
     const int grid = (int)std::min<int64_t>((n + 255) / 256, 2048);

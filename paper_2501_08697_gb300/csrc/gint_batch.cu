@@ -17,9 +17,6 @@ using namespace gint;
 
 namespace gint {
 cudaError_t launch_mirror(const Plan &P, double *H, cudaStream_t s);
-cudaError_t launch_dm_to_f32(const Plan &P, const double *DM, float *out, bool sym, cudaStream_t s,
-                             float *amax = nullptr);
-cudaError_t launch_absmax(const double *x, int64_t n, float *out, cudaStream_t s);
 }
 
 static bool tc_prec(gint_prec p)
@@ -39,12 +36,13 @@ struct gint_batch_s {
     Plan plan[3];                    // combined plans: [0] vlocal (batches <= 192 orbitals),
                                      // [1] rho, [2] vlocal of structures with larger batches
     int max_nb_v[3] = {0, 0, 0};
-    void *d_mem[15] = {nullptr};    // [3w..3w+2] batches, slots, tables; [9] splines; [12+w] CTA ranges
+    void *d_mem[21] = {nullptr};    // [3w..3w+2] batches, slots, tables; [9] splines; [12+w] CTA ranges;
+                                     // [15+2w], [16+2w] padded K offsets and split-store tables
     SInfo *d_sinfo = nullptr;
     int *d_status = nullptr;
     float *d_amax = nullptr;         // [2 * nstruct]: max |V| and max |DM| of each entry (fp16 path)
-    std::vector<float *> dm32;       // FP32 density matrix of each entry: the handle's scratch for
-    std::vector<float *> own;        //   its first occurrence, a private buffer for repeats
+    std::vector<void *> dms;         // split density matrix of each entry: the handle's scratch for
+    std::vector<void *> own;         //   its first occurrence, a private buffer for repeats
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -67,7 +65,7 @@ void free_batch(gint_batch b)
     if (b->cap) cudaStreamDestroy(b->cap);
     for (void *p : b->d_mem)
         if (p) cudaFree(p);
-    for (float *p : b->own)
+    for (void *p : b->own)
         if (p) cudaFree(p);
     if (b->d_sinfo) cudaFree(b->d_sinfo);
     if (b->d_status) cudaFree(b->d_status);
@@ -98,10 +96,14 @@ gint_status issue(gint_batch b, cudaStream_t s)
             return cuda_fail(e, "gint_batch: memset");
         if (half && (e = launch_absmax(b->V[i], h->info.npts, b->d_amax + 2 * i, s)) != cudaSuccess)
             return cuda_fail(e, "gint_batch: potential range");
-        if (b->with_rho && h->info.nvalues > 0 &&
-            (e = launch_dm_to_f32(h->plan, b->DM[i], b->dm32[i], false, s, half ? b->d_amax + 2 * i + 1 : nullptr)) !=
-                cudaSuccess)
-            return cuda_fail(e, "gint_batch: convert");
+        if (b->with_rho && h->info.nvalues > 0) {
+            float *am = half ? b->d_amax + 2 * i + 1 : nullptr;
+            if (am && (e = launch_absmax(b->DM[i], h->info.nvalues, am, s)) != cudaSuccess)
+                return cuda_fail(e, "gint_batch: density-matrix range");
+            if ((e = launch_dm_split(h->plan, b->prec, (const int *)h->d_soff, b->DM[i], b->dms[i], h->dms_plane, false,
+                                     am, s)) != cudaSuccess)
+                return cuda_fail(e, "gint_batch: split");
+        }
     }
     SInfo none{};
     // structures whose vlocal batches fit two TMEM accumulators run in one persistent launch,
@@ -188,7 +190,7 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
     for (int w = 0; w < 3; ++w) {
         std::vector<Batch> bat;
         std::vector<Slot> sl;
-        std::vector<int> tbl;
+        std::vector<int> tbl, koff, tbl2;
         std::vector<int> seg{0};
         const int src = w == 1 ? 1 : 0;
         for (int i = 0; i < nstruct; ++i) {
@@ -207,12 +209,16 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
                 sl.push_back(S);
             }
             tbl.insert(tbl.end(), bs.tbl.begin(), bs.tbl.end());
+            koff.insert(koff.end(), bs.koff.begin(), bs.koff.end());
+            tbl2.insert(tbl2.end(), bs.tbl2.begin(), bs.tbl2.end());   // offsets into each entry's own store
             seg.push_back((int)bat.size());
             b->max_nb_v[w] = std::max(b->max_nb_v[w], bs.max_nb);
         }
         if ((e = upload_vec(&b->d_mem[3 * w + 0], bat)) != cudaSuccess ||
             (e = upload_vec(&b->d_mem[3 * w + 1], sl)) != cudaSuccess ||
-            (e = upload_vec(&b->d_mem[3 * w + 2], tbl)) != cudaSuccess) {
+            (e = upload_vec(&b->d_mem[3 * w + 2], tbl)) != cudaSuccess ||
+            (e = upload_vec(&b->d_mem[15 + 2 * w], koff)) != cudaSuccess ||
+            (e = upload_vec(&b->d_mem[16 + 2 * w], tbl2)) != cudaSuccess) {
             free_batch(b);
             return cuda_fail(e, "gint_batch_create: upload");
         }
@@ -230,26 +236,28 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
         p.batches = (const Batch *)b->d_mem[3 * w + 0];
         p.slots = (const Slot *)b->d_mem[3 * w + 1];
         p.tbl = (const int *)b->d_mem[3 * w + 2];
+        p.koff = (const int *)b->d_mem[15 + 2 * w];
+        p.tbl2 = (const int *)b->d_mem[16 + 2 * w];
         p.nbatches = (int)bat.size();
         b->plan[w] = p;
     }
     // a handle may appear more than once (spin channels or several potentials on one geometry):
-    // every occurrence after the first gets its own FP32 density-matrix buffer
-    b->dm32.assign(nstruct, nullptr);
+    // every occurrence after the first gets its own split density-matrix buffer
+    b->dms.assign(nstruct, nullptr);
     for (int i = 0; i < nstruct && with_rho; ++i) {
         bool repeat = false;
         for (int j = 0; j < i && !repeat; ++j) repeat = hs[j] == hs[i];
         if (!repeat) {
-            b->dm32[i] = hs[i]->d_dm32;
+            b->dms[i] = hs[i]->d_dms;
             continue;
         }
-        float *p = nullptr;
-        if ((e = cudaMalloc((void **)&p, sizeof(float) * std::max<int64_t>(1, hs[i]->info.nvalues))) != cudaSuccess) {
+        void *p = nullptr;
+        if ((e = cudaMalloc(&p, std::max<size_t>(16, (size_t)hs[i]->dms_plane * 8))) != cudaSuccess) {
             free_batch(b);
             return cuda_fail(e, "gint_batch_create: allocate");
         }
         b->own.push_back(p);
-        b->dm32[i] = p;
+        b->dms[i] = p;
     }
     if ((e = cudaMalloc((void **)&b->d_amax, sizeof(float) * 2 * nstruct)) != cudaSuccess ||
         (e = cudaMemset(b->d_amax, 0, sizeof(float) * 2 * nstruct)) != cudaSuccess) {
@@ -258,7 +266,7 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
     }
     std::vector<SInfo> si(nstruct);
     for (int i = 0; i < nstruct; ++i) {
-        si[i] = sinfo_for(hs[i], V[i], H[i], with_rho ? b->dm32[i] : nullptr, with_rho ? rho[i] : nullptr, nullptr);
+        si[i] = sinfo_for(hs[i], V[i], H[i], with_rho ? b->dms[i] : nullptr, with_rho ? rho[i] : nullptr, nullptr);
         si[i].amax = b->d_amax + 2 * i;
     }
     if ((e = upload_vec(&b->d_mem[9], coef)) != cudaSuccess || (e = upload_vec((void **)&b->d_sinfo, si)) != cudaSuccess ||

@@ -259,7 +259,85 @@ __device__ __forceinline__ double f2d_fast(float f)
 struct SpecSh {
     int nrad, nint, coef_off, lpack;   // lpack: 2 bits of l per radial
     float rcut2, inv_dr;
+    int shape;                         // kShapeSPD / kShapeSP: radial list with a compiled evaluator
 };
+
+// Radial lists with compiled (fully unrolled) evaluators: their radials' spline records are
+// fetched together and the radials are evaluated side by side; other lists take the generic
+// loop.  Order of the l values as in the species input.
+template <int... Ls>
+struct Shape {
+    static constexpr int nrad = sizeof...(Ls);
+    static constexpr int norb = ((2 * Ls + 1) + ...);
+    __host__ __device__ static constexpr int l(int i)
+    {
+        constexpr int v[] = {Ls...};
+        return v[i];
+    }
+};
+using ShapeSPD = Shape<0, 0, 1, 1, 2>;   // 2s2p1d (13 orbitals)
+using ShapeSP = Shape<0, 0, 1>;          // 2s1p (5 orbitals)
+constexpr int kShapeGeneric = 0, kShapeSPD = 1, kShapeSP = 2;
+
+__host__ __device__ constexpr int shape_of(int nrad, int lpack)
+{
+    return (nrad == 5 && lpack == ((0 << 0) | (0 << 2) | (1 << 4) | (1 << 6) | (2 << 8))) ? kShapeSPD
+           : (nrad == 3 && lpack == ((0 << 0) | (0 << 2) | (1 << 4)))                      ? kShapeSP
+                                                                                             : kShapeGeneric;
+}
+
+// phi of a compiled radial list (same conventions as eval_phi_f32)
+template <class SH, typename Emit>
+__device__ __forceinline__ void eval_phi_shape(const SpecSh &S, const float4 *__restrict__ coef, float dx, float dy,
+                                               float dz, Emit &&emit)
+{
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    if (!(r2 < S.rcut2)) {
+#pragma unroll
+        for (int o = 0; o < SH::norb; ++o) emit(o, 0.f);
+        return;
+    }
+    if (r2 < 1e-24f) {
+        int o = 0;
+#pragma unroll
+        for (int ir = 0; ir < SH::nrad; ++ir) {
+            if (SH::l(ir) == 0) emit(o, __ldg(coef + S.coef_off + ir).x * YC<float>::c0);
+            else
+#pragma unroll
+                for (int m = 0; m < 2 * SH::l(ir) + 1; ++m) emit(o + m, 0.f);
+            o += 2 * SH::l(ir) + 1;
+        }
+        return;
+    }
+    float ir1 = rsqrtf(r2);
+    ir1 = ir1 * (1.5f - 0.5f * r2 * ir1 * ir1);
+    const float x = r2 * ir1 * S.inv_dr;
+    const int i = min((int)x, S.nint - 1);
+    const float t = x - (float)i;
+    const float4 *cp = coef + S.coef_off + i * SH::nrad;
+    float4 c[SH::nrad];
+#pragma unroll
+    for (int ir = 0; ir < SH::nrad; ++ir) c[ir] = __ldg(cp + ir);
+    const float ux = dx * ir1, uy = dy * ir1, uz = dz * ir1;
+    int o = 0;
+#pragma unroll
+    for (int ir = 0; ir < SH::nrad; ++ir) {
+        const float f = c[ir].x + t * (c[ir].y + t * (c[ir].z + t * c[ir].w));
+        if (SH::l(ir) == 0) {
+            emit(o, f * YC<float>::c0);
+        } else if (SH::l(ir) == 1) {
+            const float a = f * YC<float>::c1;
+            emit(o, a * uz); emit(o + 1, a * ux); emit(o + 2, a * uy);
+        } else {
+            emit(o, f * YC<float>::c20 * (2.f * uz * uz - ux * ux - uy * uy));
+            emit(o + 1, f * YC<float>::c21 * ux * uz);
+            emit(o + 2, f * YC<float>::c21 * uy * uz);
+            emit(o + 3, f * YC<float>::c22 * (ux * ux - uy * uy));
+            emit(o + 4, f * YC<float>::c21 * ux * uy);
+        }
+        o += 2 * SH::l(ir) + 1;
+    }
+}
 
 // FP32 orbital values of one species at displacement d (no gradient); rsqrt + one Newton
 // step instead of sqrt and division.  emit(o, phi) for o = 0 .. norb-1.
@@ -334,6 +412,16 @@ __device__ __forceinline__ void eval_phi_f32(const SpecSh &S, const float4 *__re
     } else {
         for (int ir = 0; ir < nrad; ++ir) radial(__ldg(cp + ir), ir);
     }
+}
+
+// phi through the compiled evaluator of the species' radial list if it has one
+template <bool PREFETCH, typename Emit>
+__device__ __forceinline__ void eval_phi_any(const SpecSh &S, const float4 *__restrict__ coef, float dx, float dy,
+                                             float dz, Emit &&emit)
+{
+    if (S.shape == kShapeSPD) eval_phi_shape<ShapeSPD>(S, coef, dx, dy, dz, emit);
+    else if (S.shape == kShapeSP) eval_phi_shape<ShapeSP>(S, coef, dx, dy, dz, emit);
+    else eval_phi_f32<PREFETCH>(S, coef, dx, dy, dz, emit);
 }
 
 // FP32 orbital values and gradients (with respect to r) of one species at displacement d;
@@ -418,6 +506,173 @@ __device__ __forceinline__ void eval_phigrad_f32(const SpecSh &S, const float4 *
         }
     };
     for (int ir = 0; ir < nrad; ++ir) radial(__ldg(cp + ir), ir);
+}
+
+// Density and gradient of one atom image's orbital combination at displacement d:
+//   rho += Sum_o phi_o(d) c(o),   (gx, gy, gz) += Sum_o grad phi_o(d) c(o)   (GRAD only)
+// for coefficients c(o) (the density-matrix contraction Psi of the point).  Written per radial
+// with phi = g(r) S_lm(d), g = f / r^l and S_lm the solid harmonics, so that
+//   Sum_m c_m grad phi_m = g'(r) u P + g grad P,   P = Sum_m c_m S_lm(d),
+// with grad P linear in d (l <= 2): one radial derivative per radial instead of one gradient per
+// orbital.  The caller has checked |d| < rcut.  Same conventions as eval_orbitals (the centre
+// limits included).
+template <bool GRAD, typename Coeff>
+__device__ __forceinline__ void eval_rho_grad_f32(const SpecSh &S, const float4 *__restrict__ coef, float dx,
+                                                  float dy, float dz, Coeff &&c, float &rho, float &gx, float &gy,
+                                                  float &gz)
+{
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const int nrad = S.nrad;
+    int o = 0;
+    if (r2 < 1e-24f) {
+        for (int ir = 0; ir < nrad; ++ir) {
+            const int l = (S.lpack >> (2 * ir)) & 3;
+            const float4 q = __ldg(coef + S.coef_off + ir);
+            if (l == 0) {
+                rho += q.x * YC<float>::c0 * c(o);
+                o += 1;
+            } else if (l == 1) {
+                if (GRAD) {
+                    const float g = q.y * S.inv_dr * YC<float>::c1;   // grad phi_1m = f'(0) c1 e_m
+                    gz += g * c(o);
+                    gx += g * c(o + 1);
+                    gy += g * c(o + 2);
+                }
+                o += 3;
+            } else {
+                o += 5;
+            }
+        }
+        return;
+    }
+    float ir1 = rsqrtf(r2);
+    ir1 = ir1 * (1.5f - 0.5f * r2 * ir1 * ir1);
+    const float r = r2 * ir1;
+    const float x = r * S.inv_dr;
+    int i = (int)x;
+    i = min(i, S.nint - 1);
+    const float t = x - (float)i;
+    const float ux = dx * ir1, uy = dy * ir1, uz = dz * ir1;
+    const float4 *cp = coef + S.coef_off + i * nrad;
+    for (int ir = 0; ir < nrad; ++ir) {
+        const float4 q = __ldg(cp + ir);
+        const float f = q.x + t * (q.y + t * (q.z + t * q.w));
+        const int l = (S.lpack >> (2 * ir)) & 3;
+        if (l == 0) {
+            const float c0 = c(o) * YC<float>::c0;
+            rho += f * c0;
+            if (GRAD) {
+                const float a = (q.y + t * (2.f * q.z + 3.f * t * q.w)) * S.inv_dr * c0;
+                gx += a * ux;
+                gy += a * uy;
+                gz += a * uz;
+            }
+            o += 1;
+        } else if (l == 1) {
+            const float k1 = YC<float>::c1;
+            const float Cz = c(o) * k1, Cx = c(o + 1) * k1, Cy = c(o + 2) * k1;
+            const float Pv = Cz * dz + Cx * dx + Cy * dy;
+            const float g = f * ir1;
+            rho += g * Pv;
+            if (GRAD) {
+                const float df = (q.y + t * (2.f * q.z + 3.f * t * q.w)) * S.inv_dr;
+                const float gp = (df - g) * ir1 * Pv;
+                gx += gp * ux + g * Cx;
+                gy += gp * uy + g * Cy;
+                gz += gp * uz + g * Cz;
+            }
+            o += 3;
+        } else {
+            const float C0 = c(o) * YC<float>::c20, C1 = c(o + 1) * YC<float>::c21, C2 = c(o + 2) * YC<float>::c21;
+            const float C3 = c(o + 3) * YC<float>::c22, C4 = c(o + 4) * YC<float>::c21;
+            const float xx = dx * dx, yy = dy * dy, zz = dz * dz;
+            const float Pv = C0 * (2.f * zz - xx - yy) + C1 * dx * dz + C2 * dy * dz + C3 * (xx - yy) + C4 * dx * dy;
+            const float g = f * ir1 * ir1;
+            rho += g * Pv;
+            if (GRAD) {
+                const float df = (q.y + t * (2.f * q.z + 3.f * t * q.w)) * S.inv_dr;
+                const float gp = (df - 2.f * f * ir1) * ir1 * ir1 * Pv;
+                const float px = 2.f * (C3 - C0) * dx + C1 * dz + C4 * dy;
+                const float py = -2.f * (C0 + C3) * dy + C2 * dz + C4 * dx;
+                const float pz = 4.f * C0 * dz + C1 * dx + C2 * dy;
+                gx += gp * ux + g * px;
+                gy += gp * uy + g * py;
+                gz += gp * uz + g * pz;
+            }
+            o += 5;
+        }
+    }
+}
+
+// eval_rho_grad_f32 for a compiled radial list: all spline records fetched together, the
+// radials evaluated side by side
+template <class SH, bool GRAD, typename Coeff>
+__device__ __forceinline__ void eval_rho_grad_shape(const SpecSh &S, const float4 *__restrict__ coef, float dx,
+                                                    float dy, float dz, Coeff &&c, float &rho, float &gx, float &gy,
+                                                    float &gz)
+{
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 < 1e-24f) {
+        eval_rho_grad_f32<GRAD>(S, coef, dx, dy, dz, c, rho, gx, gy, gz);
+        return;
+    }
+    float ir1 = rsqrtf(r2);
+    ir1 = ir1 * (1.5f - 0.5f * r2 * ir1 * ir1);
+    const float x = r2 * ir1 * S.inv_dr;
+    const int i = min((int)x, S.nint - 1);
+    const float t = x - (float)i;
+    const float4 *cp = coef + S.coef_off + i * SH::nrad;
+    float4 q[SH::nrad];
+#pragma unroll
+    for (int ir = 0; ir < SH::nrad; ++ir) q[ir] = __ldg(cp + ir);
+    const float ux = dx * ir1, uy = dy * ir1, uz = dz * ir1;
+    const float xx = dx * dx, yy = dy * dy, zz = dz * dz;
+    int o = 0;
+#pragma unroll
+    for (int ir = 0; ir < SH::nrad; ++ir) {
+        const float f = q[ir].x + t * (q[ir].y + t * (q[ir].z + t * q[ir].w));
+        const float df = (q[ir].y + t * (2.f * q[ir].z + 3.f * t * q[ir].w)) * S.inv_dr;
+        if (SH::l(ir) == 0) {
+            const float c0 = c(o) * YC<float>::c0;
+            rho += f * c0;
+            if (GRAD) {
+                const float a = df * c0;
+                gx += a * ux; gy += a * uy; gz += a * uz;
+            }
+        } else if (SH::l(ir) == 1) {
+            const float k1 = YC<float>::c1;
+            const float Cz = c(o) * k1, Cx = c(o + 1) * k1, Cy = c(o + 2) * k1;
+            const float Pv = Cz * dz + Cx * dx + Cy * dy;
+            const float g = f * ir1;
+            rho += g * Pv;
+            if (GRAD) {
+                const float gp = (df - g) * ir1 * Pv;
+                gx += gp * ux + g * Cx; gy += gp * uy + g * Cy; gz += gp * uz + g * Cz;
+            }
+        } else {
+            const float C0 = c(o) * YC<float>::c20, C1 = c(o + 1) * YC<float>::c21, C2 = c(o + 2) * YC<float>::c21;
+            const float C3 = c(o + 3) * YC<float>::c22, C4 = c(o + 4) * YC<float>::c21;
+            const float Pv = C0 * (2.f * zz - xx - yy) + C1 * dx * dz + C2 * dy * dz + C3 * (xx - yy) + C4 * dx * dy;
+            const float g = f * ir1 * ir1;
+            rho += g * Pv;
+            if (GRAD) {
+                const float gp = (df - 2.f * f * ir1) * ir1 * ir1 * Pv;
+                gx += gp * ux + g * (2.f * (C3 - C0) * dx + C1 * dz + C4 * dy);
+                gy += gp * uy + g * (-2.f * (C0 + C3) * dy + C2 * dz + C4 * dx);
+                gz += gp * uz + g * (4.f * C0 * dz + C1 * dx + C2 * dy);
+            }
+        }
+        o += 2 * SH::l(ir) + 1;
+    }
+}
+
+template <bool GRAD, typename Coeff>
+__device__ __forceinline__ void eval_rho_grad_any(const SpecSh &S, const float4 *__restrict__ coef, float dx, float dy,
+                                                  float dz, Coeff &&c, float &rho, float &gx, float &gy, float &gz)
+{
+    if (S.shape == kShapeSPD) eval_rho_grad_shape<ShapeSPD, GRAD>(S, coef, dx, dy, dz, c, rho, gx, gy, gz);
+    else if (S.shape == kShapeSP) eval_rho_grad_shape<ShapeSP, GRAD>(S, coef, dx, dy, dz, c, rho, gx, gy, gz);
+    else eval_rho_grad_f32<GRAD>(S, coef, dx, dy, dz, c, rho, gx, gy, gz);
 }
 
 // ----------------------------------------------------------------------- status and waits

@@ -54,7 +54,9 @@ constexpr long long kDrainBudget = 4000000000LL;  // final wait for in-flight MM
 struct SInfo {
     const double *V;
     double *H;
-    const float *DM32;
+    const void *DMS;               // split density matrix: NT planes of dms_plane elements, each
+                                   //   block n_I x kpad(n_J), row-major, at its split offset
+    int64_t dms_plane;
     double *rho;
     double *F;
     double *dLde;                  // 9 values: strain derivative (single-structure launches only)
@@ -80,6 +82,8 @@ struct Plan {
     const Batch *batches;
     const Slot *slots;
     const int *tbl;                // (block offset << 1 | canonical) or -1 if no block
+    const int *koff;               // per slot: padded K column (density kernel)
+    const int *tbl2;               // per slot pair: split density-matrix block offset or -1
     const float *poff;             // [16][16][16][6]: a h1 + b h2 + c h3 as FP32 hi (3) + lo (3)
     const int *partner;            // [nblocks] partner block index
     const int64_t *blk_off;        // [nblocks + 1]
@@ -92,17 +96,31 @@ struct Plan {
 };
 
 // One decomposition of the grid into batches, with its atom-image lists and pair tables.
+// Padded K layout of a batch's orbitals for the tensor-core density kernel: every slot's orbital
+// count is rounded up to kKPad columns, and a slot that fits kKSeg columns never crosses a
+// multiple of kKSeg (it starts at the next one instead), so the operand pieces of 16 bytes and
+// the staging segments of one producer task each belong to one slot.
+constexpr int kKPad = 8;
+constexpr int kKSeg = 16;
+constexpr int kMaxKCols = 4096;        // padded K columns of one batch
+__host__ __device__ constexpr int kpad(int norb) { return (norb + kKPad - 1) / kKPad * kKPad; }
+
 struct BatchSet {
     int dims[3] = {0, 0, 0};
     std::vector<Batch> batches;
     std::vector<Slot> slots;
     std::vector<int> slot_img;       // 3 per slot: image n of the slot's atom
     std::vector<int> tbl;
+    std::vector<int> koff;           // per slot: first column in the padded K layout
+    std::vector<int> tbl2;           // per slot pair (b, a): offset of block (b, a) in the split
+                                     //   density-matrix store, or -1 (rho/force set only)
     int limit_nb = 256;              // batches with more orbitals are split
     int max_nb = 0, max_slots = 0;
+    int max_k = 0;                   // largest padded K of a batch
     double flops_dense = 0.0;
     std::vector<int2> rng;           // cost-balanced CTA ranges of the persistent kernels
     void *d_batches = nullptr, *d_slots = nullptr, *d_tbl = nullptr, *d_rng = nullptr;
+    void *d_koff = nullptr, *d_tbl2 = nullptr;
 };
 
 // Split batches [0, n) into at most nparts contiguous ranges of about equal estimated cost
@@ -140,7 +158,10 @@ struct gint_handle_s {
     void *d_partner = nullptr, *d_blkoff = nullptr, *d_blkrows = nullptr;
     int *d_status = nullptr;
     double *d_dmsym = nullptr;       // scratch: block-symmetrised density matrix (FP64 kernels)
-    float *d_dm32 = nullptr;         // scratch: density matrix (or its symmetric part) in FP32
+    void *d_dms = nullptr;           // scratch: split density matrix of the tensor-core kernels
+    int64_t dms_plane = 0;           // elements per plane of it (Sum_b n_I kpad(n_J), rounded to 8)
+    std::vector<int> soff;           // per block: offset in a plane of the split store
+    void *d_soff = nullptr;
     float *d_poff = nullptr;         // point-offset table
     double *d_red = nullptr;         // scratch: partial sums of reductions
     float *d_amax = nullptr;         // scratch: largest |V(r)| and |DM| of an fp16 call (2 floats)
@@ -176,6 +197,8 @@ inline Plan plan_for(const gint_handle_s *h, int which)
     p.batches = (const Batch *)b.d_batches;
     p.slots = (const Slot *)b.d_slots;
     p.tbl = (const int *)b.d_tbl;
+    p.koff = (const int *)b.d_koff;
+    p.tbl2 = (const int *)b.d_tbl2;
     p.nbatches = (int)b.batches.size();
     p.rng = (const int2 *)b.d_rng;
     p.npart = (int)b.rng.size();
@@ -192,8 +215,12 @@ cudaError_t launch_rho_force_simt(const Plan &p, bool fp64, const double *V, con
                                   double *rho, double *F, double *dLde, cudaStream_t s, int nsm);
 cudaError_t launch_vlocal_tc(const Plan &p, gint_prec prec, const SInfo &si0, const SInfo *sis, cudaStream_t s,
                              int nsm, int max_nb);
+// NT terms of the (block-symmetrised if sym) density matrix into the padded split store
+cudaError_t launch_dm_split(const Plan &P, gint_prec prec, const int *soff, const double *DM, void *out, int64_t plane,
+                            bool sym, const float *amax, cudaStream_t s);
+cudaError_t launch_absmax(const double *x, int64_t n, float *out, cudaStream_t s);
 cudaError_t launch_rho_force_tc(const Plan &p, gint_prec prec, const SInfo &si0, const SInfo *sis, bool rho,
                                 bool force, cudaStream_t s, int nsm);
 // the single-structure SInfo of a handle for one call
-SInfo sinfo_for(const gint_handle_s *h, const double *V, double *H, const float *DM32, double *rho, double *F);
+SInfo sinfo_for(const gint_handle_s *h, const double *V, double *H, const void *DMS, double *rho, double *F);
 }  // namespace gint

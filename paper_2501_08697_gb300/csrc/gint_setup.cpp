@@ -160,7 +160,8 @@ static bool sphere_meets_batch(const BatchGeom &bg, const double *c, double rc, 
 // slot-pair -> block table; batches over the orbital or image limits are halved recursively.
 static gint_status build_batches(gint_handle h, const double *tau, const Geo &G, const BatchGeom &bg,
                                  const std::vector<double> &rc, const std::vector<int64_t> &packed,
-                                 const std::vector<int64_t> &offsets, const std::vector<uint8_t> &canon, BatchSet &out)
+                                 const std::vector<int64_t> &offsets, const std::vector<uint8_t> &canon,
+                                 const std::vector<int> *soff, BatchSet &out)
 {
     const int natoms = h->natoms;
     const int N1 = h->grid[0], N2 = h->grid[1], N3 = h->grid[2];
@@ -281,9 +282,19 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                     out.flops_dense += 2.0 * (w.n1 * w.n2 * w.n3) * (double)nb * nb;
                     out.max_nb = std::max(out.max_nb, nb);
                     out.max_slots = std::max(out.max_slots, (int)w.s.size());
-                    int off = 0;
+                    int off = 0, kcur = 0;
                     double o[3];
                     for (int c = 0; c < 3; ++c) o[c] = w.i0 * bg.h[c] + w.j0 * bg.h[3 + c] + w.k0 * bg.h[6 + c];
+                    for (auto &s : w.s) {
+                        // padded K column: slots of up to kKSeg columns do not cross a multiple of kKSeg,
+                        // wider ones start on one
+                        const int kw = kpad(h->norb_atom[s.atom]);
+                        if ((kw <= kKSeg && kcur % kKSeg + kw > kKSeg) || (kw > kKSeg && kcur % kKSeg))
+                            kcur = (kcur / kKSeg + 1) * kKSeg;
+                        out.koff.push_back(kcur);
+                        kcur += kw;
+                    }
+                    out.max_k = std::max(out.max_k, kcur);
                     for (auto &s : w.s) {
                         Slot S{};
                         S.atom = s.atom;
@@ -306,6 +317,7 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                             auto it = std::lower_bound(packed.begin(), packed.end(), pk);
                             if (it == packed.end() || *it != pk) {
                                 out.tbl.push_back(-1);
+                                if (soff) out.tbl2.push_back(-1);
                             } else {
                                 int64_t bi = it - packed.begin();
                                 if (ia <= ib && !canon[bi]) {
@@ -313,6 +325,7 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                                     return GINT_EINVAL;
                                 }
                                 out.tbl.push_back((int)((offsets[bi] << 1) | canon[bi]));
+                                if (soff) out.tbl2.push_back((*soff)[bi]);
                             }
                         }
                     out.batches.push_back(B);
@@ -382,6 +395,17 @@ gint_status build_geometry(gint_handle h, const double *tau, bool update_only)
         set_error("gint_setup: block store of %lld values exceeds 2^30", (long long)offsets[nblocks]);
         return GINT_EINVAL;
     }
+    // offsets of the blocks in the split density-matrix store (rows n_I, columns padded)
+    std::vector<int> soff(nblocks);
+    int64_t splane = 0;
+    for (int64_t b = 0; b < nblocks; ++b) {
+        soff[b] = (int)splane;
+        splane += (int64_t)h->norb_atom[keys[5 * b]] * kpad(h->norb_atom[keys[5 * b + 1]]);
+    }
+    if (splane >= ((int64_t)1 << 30)) {
+        set_error("gint_setup: padded block store of %lld values exceeds 2^30", (long long)splane);
+        return GINT_EINVAL;
+    }
     std::vector<int> partner(nblocks);
     std::vector<uint8_t> canon(nblocks);
     for (int64_t b = 0; b < nblocks; ++b) {
@@ -410,8 +434,12 @@ gint_status build_geometry(gint_handle h, const double *tau, bool update_only)
         for (int i = 0; i < 3; ++i) sets[w].dims[i] = dims[w][i];
         // vlocal batches stay within 192 orbitals so two accumulators fit in tensor memory
         sets[w].limit_nb = (w == 0) ? 192 : kMaxNb;
-        gint_status st = build_batches(h, tau, G, bg, rc, packed, offsets, canon, sets[w]);
+        gint_status st = build_batches(h, tau, G, bg, rc, packed, offsets, canon, w == 1 ? &soff : nullptr, sets[w]);
         if (st != GINT_OK) return st;
+        if (sets[w].max_k + 32 > kMaxKCols) {
+            set_error("gint_setup: a batch's padded orbital columns (%d) exceed %d", sets[w].max_k, kMaxKCols - 32);
+            return GINT_EINVAL;
+        }
     }
     // useful flops: 2 n(r)^2 per point, n(r) = orbitals whose sphere contains r (exact count
     // per point from the vlocal decomposition)
@@ -453,6 +481,8 @@ gint_status build_geometry(gint_handle h, const double *tau, bool update_only)
         h->keys = std::move(keys);
         h->offsets = std::move(offsets);
         h->partner = std::move(partner);
+        h->soff = std::move(soff);
+        h->dms_plane = (splane + 7) / 8 * 8;
         for (int w = 0; w < 2; ++w) h->bs[w] = std::move(sets[w]);
     }
     h->tau.assign(tau, tau + 3 * natoms);
@@ -551,8 +581,9 @@ static cudaError_t upload(void **dst, const std::vector<T> &v)
 static void free_dev(gint_handle h)
 {
     void *ptrs[] = {h->d_coef64, h->d_coef32, h->d_partner, h->d_blkoff, h->d_blkrows, h->d_status, h->d_dmsym,
-                    h->d_dm32, h->d_poff, h->d_red, h->d_hostio, h->bs[0].d_batches, h->bs[0].d_slots, h->bs[0].d_tbl,
+                    h->d_dms, h->d_poff, h->d_red, h->d_hostio, h->bs[0].d_batches, h->bs[0].d_slots, h->bs[0].d_tbl,
                     h->bs[0].d_rng, h->bs[1].d_batches, h->bs[1].d_slots, h->bs[1].d_tbl, h->bs[1].d_rng,
+                    h->bs[0].d_koff, h->bs[0].d_tbl2, h->bs[1].d_koff, h->bs[1].d_tbl2, h->d_soff,
                     h->ks.d_keys, h->ks.d_grp, h->ks.d_pair, h->ks.d_colatom, h->ks.d_orboff, h->ks.d_kvec,
                     h->ks.d_phase, h->d_dm_scratch, h->d_dm_planes, h->d_amax};
     for (void *p : ptrs)
@@ -569,7 +600,7 @@ static gint_status upload_batchset(gint_handle h, int w)
     BatchSet &b = h->bs[w];
     // kernels still queued may read the old arrays
     if (b.d_batches && (e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "synchronise");
-    for (void **p : {&b.d_batches, &b.d_slots, &b.d_tbl, &b.d_rng})
+    for (void **p : {&b.d_batches, &b.d_slots, &b.d_tbl, &b.d_rng, &b.d_koff, &b.d_tbl2})
         if (*p) {
             cudaFree(*p);
             *p = nullptr;
@@ -577,6 +608,8 @@ static gint_status upload_batchset(gint_handle h, int w)
     if ((e = upload(&b.d_batches, b.batches)) != cudaSuccess) return cuda_fail(e, "upload batches");
     if ((e = upload(&b.d_slots, b.slots)) != cudaSuccess) return cuda_fail(e, "upload slots");
     if ((e = upload(&b.d_tbl, b.tbl)) != cudaSuccess) return cuda_fail(e, "upload tables");
+    if ((e = upload(&b.d_koff, b.koff)) != cudaSuccess) return cuda_fail(e, "upload K offsets");
+    if ((e = upload(&b.d_tbl2, b.tbl2)) != cudaSuccess) return cuda_fail(e, "upload split tables");
     const int nb = (int)b.batches.size();
     b.rng = segment_ranges(b.batches.data(), {0, nb}, std::max(1, std::min(h->nsm, nb)), w);
     if ((e = upload(&b.d_rng, b.rng)) != cudaSuccess) return cuda_fail(e, "upload CTA ranges");
@@ -592,6 +625,7 @@ static gint_status upload_geometry(gint_handle h)
         for (int w = 0; w < 2; ++w)
             if ((st = upload_batchset(h, w)) != GINT_OK) return st;
         if ((e = upload(&h->d_partner, h->partner)) != cudaSuccess) return cuda_fail(e, "upload partner");
+        if ((e = upload(&h->d_soff, h->soff)) != cudaSuccess) return cuda_fail(e, "upload split offsets");
         if ((e = upload(&h->d_blkoff, h->offsets)) != cudaSuccess) return cuda_fail(e, "upload offsets");
         std::vector<int> rows(h->info.nblocks);
         for (int64_t b = 0; b < h->info.nblocks; ++b) rows[b] = h->norb_atom[h->keys[5 * b]];
@@ -797,7 +831,7 @@ extern "C" gint_status gint_setup(gint_handle *out, const double cell[9], int na
     if ((e = cudaMalloc((void **)&h->d_status, sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(h->d_status, 0, sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc((void **)&h->d_dmsym, std::max<size_t>(8, h->info.nvalues * sizeof(double)))) != cudaSuccess ||
-        (e = cudaMalloc((void **)&h->d_dm32, std::max<size_t>(16, h->info.nvalues * sizeof(float)))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&h->d_dms, std::max<size_t>(16, (size_t)h->dms_plane * 8))) != cudaSuccess ||
         (e = cudaMalloc((void **)&h->d_red, 4096 * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc((void **)&h->d_amax, 4 * sizeof(float))) != cudaSuccess ||
         (e = cudaMemset(h->d_amax, 0, 4 * sizeof(float))) != cudaSuccess) {
@@ -900,12 +934,14 @@ extern "C" gint_status gint_update_positions(gint_handle h, const double *tau)
         if (tmp.relist[w]) {
             // the new lists, with the old device arrays (freed and replaced by upload_geometry)
             BatchSet &o = h->bs[w];
-            void *dev[4] = {o.d_batches, o.d_slots, o.d_tbl, o.d_rng};
+            void *dev[6] = {o.d_batches, o.d_slots, o.d_tbl, o.d_rng, o.d_koff, o.d_tbl2};
             o = std::move(tmp.bs[w]);
             o.d_batches = dev[0];
             o.d_slots = dev[1];
             o.d_tbl = dev[2];
             o.d_rng = dev[3];
+            o.d_koff = dev[4];
+            o.d_tbl2 = dev[5];
         } else {
             h->bs[w].slots = std::move(tmp.bs[w].slots);
         }

@@ -40,6 +40,7 @@ constexpr int kEpi0 = kProd + 32; // first epilogue thread (warp 12: TMEM lane q
 constexpr int kEpi = 256;         // epilogue threads (two warps per TMEM lane quadrant)
 constexpr int kThreadsTC = kEpi0 + kEpi;
 constexpr int kWin = 32;          // epilogue window (columns) of the rho kernel
+constexpr int kVTblR = 28;        // atom images of a batch whose slot-pair table the rho kernel keeps in shared memory
 
 // ------------------------------------------------------------------ shared batch metadata
 // An atom image of the batch in shared memory: the first 16 bytes and dh/dl as in Slot, so
@@ -177,6 +178,25 @@ __device__ __forceinline__ void geom_async(const Plan &P, const SInfo *sis, cons
     cp_async_commit();
 }
 
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
+
+// The density kernel's batch metadata (atom images, point offsets, padded K offsets and, for at
+// most kVTbl images, the slot-pair split-store table) copied asynchronously into one half of
+// the producers' double-buffered arrays; the caller waits with cp_async_wait_all and a barrier.
+__device__ __forceinline__ void geom_async_rho(const Plan &P, const SInfo *sis, const SInfo &si0, const Batch &B,
+                                               PSlot *ps, float *poff, int *koffs, int *tbls, int tid, int nthr)
+{
+    geom_async(P, sis, si0, B, ps, poff, nullptr, tid, nthr);
+    const int ns = B.nslots;
+    for (int s = tid; s < ns; s += nthr) cp_async4(koffs + s, P.koff + B.slot0 + s);
+    if (ns <= kVTblR)
+        for (int e = tid; e < ns * ns; e += nthr) cp_async4(tbls + e, P.tbl2 + B.tbl + e);
+    cp_async_commit();
+}
+
 __device__ __forceinline__ void disp(const PSlot &s, const float *po, float &dx, float &dy, float &dz)
 {
     dx = (s.dh[0] + po[0]) + (s.dl[0] + po[3]);
@@ -204,6 +224,7 @@ __device__ __forceinline__ void load_species(const Plan &P, SpecSh *spec, int ti
         q.lpack = lp;
         q.rcut2 = D.rcut_f * D.rcut_f;
         q.inv_dr = D.inv_dr_f;
+        q.shape = shape_of(D.nrad, lp);
         spec[tid] = q;
     }
 }
@@ -339,7 +360,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     if (p < npb) {
                         float dx, dy, dz;
                         disp(sl, poff + 6 * p, dx, dy, dz);
-                        eval_phi_f32<!S::F16>(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) { col[o * KC] = v; });
+                        eval_phi_any<!S::F16>(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) { col[o * KC] = v; });
                     } else {
                         for (int o = 0; o < sl.norb; ++o) col[o * KC] = 0.f;
                     }
@@ -531,58 +552,117 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 }
 
 // ====================================================================== rho / force
+// Psi_b = Phi_b D_b with M = 128 points, N = the batch's orbitals (unpadded, TMEM columns) and K
+// = the batch's orbitals in the padded K layout (every slot rounded up to 8 columns, see kpad).
+// The density matrix arrives pre-split: a per-call kernel writes its NT terms (scaled for fp16)
+// into a padded store in which every block row starts on 16 bytes, so the B operand of a chunk
+// is assembled from 16-byte asynchronous copies (one per row and core-matrix column) with no
+// arithmetic; the producers' only CUDA-core work is the orbital evaluation of the A operand.
+//
+// Operand layout (K-major, no swizzle): core matrices of 8 rows x 16 bytes stored densely, the
+// 8-row groups of one core-matrix column adjacent (SBO = 128 bytes) and the KCM columns of a
+// chunk LBO = rows x 16 bytes apart, so row r of column j sits at j * LBO + 16 r: producers with
+// consecutive rows write consecutive 16 bytes.
+constexpr int kRProd = 256;          // producer threads (warps 0-7)
+constexpr int kRMma = kRProd;        // the MMA-issue thread (warp 8)
+constexpr int kREpi0 = kRProd + 32;  // first epilogue thread (warp 9)
+constexpr int kREPQ = 3;             // epilogue warps per TMEM lane quadrant
+constexpr int kREpi = 128 * kREPQ;   // epilogue threads
+constexpr int kThreadsR = kREpi0 + kREpi;
+
 template <class S>
-struct RSmem {
-    static constexpr int KC = S::KCM * S::CG;              // orbitals per chunk
-    static constexpr int RING = 64;                        // staging rows (orbital ring, see k_rho_tc)
-    static constexpr int EG = KC >= 32 ? 1 : 32 / KC;      // chunks per orbital evaluation
-    static constexpr int ARR_A = arr_bytes<S>(kMaxBatchPts);
-    static constexpr int ARR_B = arr_bytes<S>(kMaxNb);
-    static constexpr int STAGE = S::NT * (ARR_A + ARR_B);
-    // stages per scheme: with one, the MMAs of a chunk overlap the next chunk's orbital
-    // evaluation and gather tables, which come before the stage is rewritten
-    static constexpr int NSTAGE = S::RSTAGES;
-    static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [RING][128]
-    static constexpr int OFF_PSLOT = OFF_STG + RING * kMaxBatchPts * 4;     // producer PSlot[64]
-    static constexpr int OFF_POFF = OFF_PSLOT + kMaxSlots * (int)sizeof(PSlot);
-    static constexpr int OFF_OMAP = OFF_POFF + kMaxBatchPts * 24;           // oslot[256], oidx[256]
-    static constexpr int OFF_GBASE = OFF_OMAP + 2 * kMaxNb;                 // int [64][KC]: chunk gather bases
-    static constexpr int OFF_GNA = OFF_GBASE + kMaxSlots * KC * 4;          // int [KC]: norb of column's slot
-    static constexpr int OFF_EPSLOT = OFF_GNA + KC * 4;                     // epilogue PSlot[64]
+struct RL {
+    static constexpr int CG = S::CG, NT = S::NT;
+    static constexpr int KCM = 4;                      // core-matrix columns per chunk
+    static constexpr int KC = KCM * CG;                // K columns per chunk (16 tf32, 32 16-bit)
+    static constexpr int NS = NT == 2 ? 2 : 1;         // operand stages
+    static constexpr int ESZ = 16 / CG;                // bytes per element
+    static constexpr int LBO_A = kMaxBatchPts * 16;
+    static constexpr int LBO_B = kMaxNb * 16;
+    static constexpr int PLA = KCM * LBO_A;            // one A term of a chunk
+    static constexpr int PLB = KCM * LBO_B;            // one B term
+    static constexpr int STAGE = NT * (PLA + PLB);
+    static constexpr int OFF_STG = NS * STAGE;                                  // float [kKSeg][kRProd]
+    // producer metadata, double-buffered (the next batch's is copied during this one)
+    static constexpr int OFF_PSLOT = OFF_STG + kKSeg * kRProd * 4;                  // PSlot[2][64]
+    static constexpr int OFF_POFF = OFF_PSLOT + 2 * kMaxSlots * (int)sizeof(PSlot); // float [2][128][6]
+    static constexpr int OFF_KOFF = OFF_POFF + 2 * kMaxBatchPts * 24;               // int [2][64]
+    static constexpr int OFF_TBL = OFF_KOFF + 2 * kMaxSlots * 4;                    // int [2][kVTblR^2]
+    static constexpr int OFF_KSLOT = OFF_TBL + 2 * kVTblR * kVTblR * 4;             // short [kMaxKCols / 8]
+    static constexpr int OFF_EPSLOT = OFF_KSLOT + kMaxKCols / 8 * 2;                // epilogue PSlot[64]
     static constexpr int OFF_EPOFF = OFF_EPSLOT + kMaxSlots * (int)sizeof(PSlot);
-    static constexpr int OFF_WIN = OFF_EPOFF + kMaxBatchPts * 24;           // float [8][kWin][32]
-    static constexpr int OFF_RPART = OFF_WIN + 8 * kWin * 32 * 4;           // float [128]
-    static constexpr int OFF_FACC = OFF_RPART + kMaxBatchPts * 4;           // float [64][3]
-    static constexpr int OFF_BAR = OFF_FACC + kMaxSlots * 3 * 4;             // 16 mbarriers
+    static constexpr int OFF_WIN = OFF_EPOFF + kMaxBatchPts * 24;               // float [12][32][32]
+    static constexpr int OFF_RPART = OFF_WIN + (kREpi / 32) * 32 * 32 * 4;      // float [kREPQ][128]
+    static constexpr int OFF_FACC = OFF_RPART + kREPQ * kMaxBatchPts * 4;       // float [64][3]
+    static constexpr int OFF_BAR = (OFF_FACC + kMaxSlots * 12 + 15) / 16 * 16;  // 16 mbarriers
     static constexpr int OFF_MISC = OFF_BAR + 16 * 8;
     static constexpr int OFF_SPEC = OFF_MISC + 64;
     static constexpr int TOTAL = OFF_SPEC + kMaxSpecies * (int)sizeof(SpecSh);
 };
 
+// shared-memory descriptor with explicit strides (K-major, no swizzle)
+__device__ __forceinline__ uint64_t sdesc2(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+// Split density-matrix store: for every block (rows n_I, columns n_J, padded to kpad(n_J) with
+// zeros) its NT terms at soff[b] in each of NT planes of `plane` elements, in 16-byte pieces of
+// CG consecutive columns ordered piece column by piece column: piece (i, c) of the block (row i,
+// columns c .. c + CG - 1) sits at soff[b] + (c / CG) n_I CG + i CG, so the rows of one piece
+// column are adjacent.  sym: the block-symmetric part (DM + DM^T_block) / 2 (derivatives use
+// it).  For fp16 the values are scaled by scale_for(max |DM|), read from amax.
+template <class S>
+__global__ void k_dm_split(Plan P, const int *__restrict__ soff, const double *__restrict__ DM, void *out,
+                           int64_t plane, int sym, const float *amax)
+{
+    constexpr int CG = S::CG, ESZ = 16 / CG;
+    float sc = 1.f;
+    if constexpr (S::HALF) sc = scale_for(amax[0]);
+    unsigned char *o8 = reinterpret_cast<unsigned char *>(out);
+    for (int64_t b = blockIdx.x; b < P.nblocks; b += gridDim.x) {
+        const int64_t off = P.blk_off[b], poff = P.blk_off[P.partner[b]];
+        const int rows = P.blk_rows[b];
+        const int cols = (int)((P.blk_off[b + 1] - off) / rows);
+        const int pc = kpad(cols), npc = pc / CG;
+        for (int e = threadIdx.x; e < rows * npc; e += blockDim.x) {
+            const int i = e / npc, c0 = (e - i * npc) * CG;
+            float x[CG];
+#pragma unroll
+            for (int q = 0; q < CG; ++q) {
+                const int c = c0 + q;
+                double v = 0.0;
+                if (c < cols) v = sym ? 0.5 * (DM[off + i * cols + c] + DM[poff + c * rows + i]) : DM[off + i * cols + c];
+                x[q] = d2f(v) * sc;
+            }
+            unsigned char *dst[S::NT];
+#pragma unroll
+            for (int t = 0; t < S::NT; ++t) dst[t] = o8 + ((int64_t)t * plane + soff[b] + c0 * rows + i * CG) * ESZ;
+            split_store<S>(x, dst);
+        }
+    }
+}
+
 template <class S, bool RHO, bool FORCE, bool STRAIN>
-__global__ void __launch_bounds__(kThreadsTC, 1)
+__global__ void __launch_bounds__(kThreadsR, 1)
     k_rho_tc(Plan P, SInfo si0, const SInfo *__restrict__ sis)
 {
-    using L = RSmem<S>;
-    constexpr int KC = L::KC, RING = L::RING, EG = L::EG, NS = L::NSTAGE;
-    constexpr int SBO = S::KCM * kLBO;
+    using L = RL<S>;
+    constexpr int CG = L::CG, KCM = L::KCM, KC = L::KC, NS = L::NS, NT = S::NT;
     extern __shared__ __align__(1024) unsigned char sm[];
     float *stg = reinterpret_cast<float *>(sm + L::OFF_STG);
-    PSlot *ps = reinterpret_cast<PSlot *>(sm + L::OFF_PSLOT);
-    float *poff = reinterpret_cast<float *>(sm + L::OFF_POFF);
-    unsigned char *oslot = sm + L::OFF_OMAP, *oidx = oslot + kMaxNb;
-    int *gbase = reinterpret_cast<int *>(sm + L::OFF_GBASE);
-    int *gna = reinterpret_cast<int *>(sm + L::OFF_GNA);
-    // slot-pair table of a batch with at most kVTbl atom images, in the tail of the gather
-    // bases (which then use at most kVTbl * KC entries)
-    static_assert(kVTbl * KC + kVTbl * kVTbl <= kMaxSlots * KC, "slot-pair table placement");
-    int *rtbl = gbase + kMaxSlots * KC - kVTbl * kVTbl;
+    PSlot *psb = reinterpret_cast<PSlot *>(sm + L::OFF_PSLOT);
+    float *poffb = reinterpret_cast<float *>(sm + L::OFF_POFF);
+    int *koffb = reinterpret_cast<int *>(sm + L::OFF_KOFF);
+    int *tblb = reinterpret_cast<int *>(sm + L::OFF_TBL);
+    short *kslot = reinterpret_cast<short *>(sm + L::OFF_KSLOT);
     PSlot *eps = reinterpret_cast<PSlot *>(sm + L::OFF_EPSLOT);
     float *epoff = reinterpret_cast<float *>(sm + L::OFF_EPOFF);
     float *win = reinterpret_cast<float *>(sm + L::OFF_WIN);
     float *rpart = reinterpret_cast<float *>(sm + L::OFF_RPART);
-    SpecSh *spec = reinterpret_cast<SpecSh *>(sm + L::OFF_SPEC);
     float *facc = reinterpret_cast<float *>(sm + L::OFF_FACC);
+    SpecSh *spec = reinterpret_cast<SpecSh *>(sm + L::OFF_SPEC);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::OFF_BAR);
     uint64_t *empty = bars, *accfull = bars + 2, *accempty = bars + 4, *fin = bars + 6, *full = bars + 8;
     uint32_t *tmem_base = reinterpret_cast<uint32_t *>(sm + L::OFF_MISC);
@@ -596,8 +676,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         mbar_init(&empty[1], 1);
         mbar_init(&accfull[0], 1);
         mbar_init(&accfull[1], 1);
-        mbar_init(&accempty[0], kEpi);
-        mbar_init(&accempty[1], kEpi);
+        mbar_init(&accempty[0], kREpi);
+        mbar_init(&accempty[1], kREpi);
         mbar_init(fin, 1);
         mbar_init(&full[0], 1);
         mbar_init(&full[1], 1);
@@ -612,184 +692,149 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_base;
 
-    if (tid < kProd) {
-        // ------------------------------------------------------------ producers + MMA issue
+    if (tid < kRProd) {
+        // ------------------------------------------------------------ producers
         const int pt = tid;
         int g = 0;
         bool ok = true;
-        // Orbital ring: when every slot fits (EG KC + norb - 1 <= RING rows), the orbitals of a
-        // slot are evaluated once, every EG chunks for the slots that start in those chunks, into
-        // staging rows (orbital index) mod RING; later chunks read the rows carried over.
-        // Otherwise each chunk evaluates every slot overlapping it and keeps its own columns.
-        int maxnorb = 0;
-        for (int i = 0; i < P.nspecies; ++i) maxnorb = max(maxnorb, P.sp[i].norb);
-        const bool ring = EG * KC + maxnorb - 1 <= RING;
         SInfoCache sic(si0);
         CtaRange cr(P);
-        for (int bi = 0; ok && cr.next(bi);) {
+        int bi = 0, cur = 0;
+        bool have = cr.next(bi);
+        if (have)
+            geom_async_rho(P, sis, si0, P.batches[bi], psb, poffb, koffb, tblb, pt, kRProd);
+        for (; ok && have; have = cr.next(bi), cur ^= 1) {
             const Batch B = P.batches[bi];
             int n1, n2, n3;
             unpack(B.dims, n1, n2, n3);
             const int ns = B.nslots, nb = B.nb, npb = n1 * n2 * n3;
-            const int npad = (nb + 15) & ~15;
+            const PSlot *ps = psb + cur * kMaxSlots;
+            const float *poff = poffb + cur * kMaxBatchPts * 6;
+            const int *koffs = koffb + cur * kMaxSlots;
+            const int *tbls = tblb + cur * kVTblR * kVTblR;
+            // this batch's metadata has arrived and every producer is done with the previous
+            // batch (whose half of the buffers the next batch's copy overwrites)
+            cp_async_wait_all();
+            named_sync(1, kRProd);
+            {
+                CtaRange peek = cr;
+                int bn = 0;
+                if (peek.next(bn))
+                    geom_async_rho(P, sis, si0, P.batches[bn], psb + (cur ^ 1) * kMaxSlots,
+                                   poffb + (cur ^ 1) * kMaxBatchPts * 6, koffb + (cur ^ 1) * kMaxSlots,
+                                   tblb + (cur ^ 1) * kVTblR * kVTblR, pt, kRProd);
+            }
             if (nb == 0) continue;  // the epilogue writes rho = 0 there
             const SInfo SI = sic.get(B, sis);
-            const float *__restrict__ DM = SI.DM32;
-            const int *__restrict__ tbl = P.tbl + B.tbl;
-            float sA = 1.f, sD = 1.f;   // fp16 operands: A = phi sA, B = D sD (undone in the epilogue)
-            if constexpr (S::HALF) {
-                sA = scale_for(SI.phimax);
-                sD = scale_for(SI.amax[1]);
-            }
-            named_sync(1, kProd);
-            load_geom(P, SI, B, ps, poff, pt, kProd);
-            // the batch's slot-pair table in shared memory (gather tables read it per chunk)
-            const bool tsm = ns <= kVTbl;
-            if (tsm)
-                for (int e = pt; e < ns * ns; e += kProd) rtbl[e] = __ldg(tbl + e);
-            named_sync(1, kProd);
-            for (int s = pt; s < ns; s += kProd)
-                for (int o = 0; o < ps[s].norb; ++o) {
-                    oslot[ps[s].off + o] = (unsigned char)s;
-                    oidx[ps[s].off + o] = (unsigned char)o;
+            const bool tsm = ns <= kVTblR;
+            const int ktot = (koffs[ns - 1] + kpad(ps[ns - 1].norb) + KC - 1) / KC * KC;
+            // slot of each 8-column group of the padded K axis (-1: a gap): the last slot
+            // starting at or before the group, if the group lies within its padded width
+            for (int k8 = pt; k8 < ktot / 8; k8 += kRProd) {
+                int lo = 0, hi = ns - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (koffs[mid] <= 8 * k8) lo = mid;
+                    else hi = mid - 1;
                 }
-            named_sync(1, kProd);
-            const int nch = (nb + KC - 1) / KC;
+                kslot[k8] = (short)(8 * k8 < koffs[lo] + kpad(ps[lo].norb) ? lo : -1);
+            }
+            named_sync(1, kRProd);
+            float sA = 1.f;   // fp16: A = phi sA (the density matrix was scaled when it was split)
+            if constexpr (S::HALF) sA = scale_for(SI.phimax);
+            const unsigned char *dms = reinterpret_cast<const unsigned char *>(SI.DMS);
+            const int nch = ktot / KC;
             for (int ch = 0; ch < nch && ok; ++ch, ++g) {
                 const int stage = g % NS;
-                const int k0 = ch * KC, k1 = min(k0 + KC, nb);
-                const int s_lo = oslot[k0], s_hi = oslot[k1 - 1];
-                // staging row of chunk column k: rbase + k
-                const int rbase = ring ? (k0 & (RING - 1)) : 0;
-                // phase 1: orbital values at all points -> staging rows
-                if (ring) {
-                    // at the first chunk of each group: the slots starting in the group's chunks
-                    const int e1 = min(k0 + EG * KC, nb);
-                    const int s_first = ps[s_lo].off >= k0 ? s_lo : s_lo + 1;
-                    const int nsc = ch % EG == 0 ? oslot[e1 - 1] - s_first + 1 : 0;
-                    for (int w = pt; w < kMaxBatchPts * nsc; w += kProd) {
-                        const int p = w % kMaxBatchPts, s = s_first + w / kMaxBatchPts;
-                        const PSlot sl = ps[s];
-                        float *col = stg + p;
-                        if (p < npb) {
-                            float dx, dy, dz;
-                            disp(sl, poff + 6 * p, dx, dy, dz);
-                            eval_phi_f32<true>(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) {
-                                col[((sl.off + o) & (RING - 1)) * kMaxBatchPts] = v;
-                            });
-                        } else {
-                            for (int o = 0; o < sl.norb; ++o) col[((sl.off + o) & (RING - 1)) * kMaxBatchPts] = 0.f;
-                        }
-                    }
-                } else {
-                    const int nsc = s_hi - s_lo + 1;
-                    for (int w = pt; w < kMaxBatchPts * nsc; w += kProd) {
-                        const int p = w % kMaxBatchPts, s = s_lo + w / kMaxBatchPts;
-                        const PSlot sl = ps[s];
-                        float *col = stg + p;
-                        const int base_k = sl.off - k0;
-                        if (p < npb) {
-                            float dx, dy, dz;
-                            disp(sl, poff + 6 * p, dx, dy, dz);
-                            eval_phi_f32<true>(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) {
-                                const int k = base_k + o;
-                                if (k >= 0 && k < KC) col[k * kMaxBatchPts] = v;
-                            });
-                        } else {
-                            for (int o = 0; o < sl.norb; ++o) {
-                                const int k = base_k + o;
-                                if (k >= 0 && k < KC) col[k * kMaxBatchPts] = 0.f;
-                            }
-                        }
-                    }
-                }
-                // columns past the last orbital of the batch (last chunk only)
-                for (int w = pt; w < (KC - (k1 - k0)) * kMaxBatchPts; w += kProd)
-                    stg[(rbase + k1 - k0) * kMaxBatchPts + w] = 0.f;
-                // gather tables of the chunk: element (nu, k) of B is DM32[gbase[b][k] + o_nu * gna[k]]
-                // with b the slot of nu (gbase = -1: no block, or k past the last orbital)
-                for (int w = pt; w < ns * KC; w += kProd) {
-                    const int k = w % KC, b = w / KC;
-                    const int mu = k0 + k;
-                    int v = -1;
-                    if (mu < nb) {
-                        const int a = oslot[mu];
-                        const int e = tsm ? rtbl[b * ns + a] : __ldg(tbl + b * ns + a);
-                        if (e >= 0) v = (e >> 1) + oidx[mu];
-                    }
-                    gbase[w] = v;
-                }
-                for (int k = pt; k < KC; k += kProd) gna[k] = (k0 + k < nb) ? ps[oslot[k0 + k]].norb : 0;
-                if (g >= NS) ok = role_wait(&empty[stage], ((g / NS) - 1) & 1, P, pt, pflag, 1, kProd);
-                else named_sync(1, kProd);
+                const int k0 = ch * KC;
+                if (g >= NS) ok = role_wait(&empty[stage], ((g / NS) - 1) & 1, P, pt, pflag, 1, kRProd);
                 if (!ok) break;
-                unsigned char *base = sm + stage * L::STAGE;
-                // phase 2a: A = Phi (rows = points, K = orbitals of the chunk)
-                for (int w = pt; w < kMaxBatchPts * S::KCM; w += kProd) {
-                    const int p = w % kMaxBatchPts, kc = w / kMaxBatchPts;
-                    unsigned char *da[S::NT];
-#pragma unroll
-                    for (int t = 0; t < S::NT; ++t) da[t] = base + t * L::ARR_A + cm_off<S>(p, kc);
-                    float x[S::CG];
-#pragma unroll
-                    for (int i = 0; i < S::CG; ++i) x[i] = stg[(rbase + kc * S::CG + i) * kMaxBatchPts + p];
-                    if constexpr (S::HALF)
-#pragma unroll
-                        for (int i = 0; i < S::CG; ++i) x[i] *= sA;
-                    split_store<S>(x, da);
-                }
-                // phase 2b: B = D rows nu (N), K = orbitals mu of the chunk: D(b_nu, a_mu)[o_nu][o_mu]
-                // read in FP32 through the chunk tables; GB tasks per thread, loads issued first
-                // (five 4-wide tasks cover a 220-column chunk in one round without spills)
-                constexpr int GB = S::CG == 4 ? 5 : 4;
-                for (int w0 = pt; w0 < npad * S::KCM; w0 += kProd * GB) {
-                    float x[GB][S::CG];
-#pragma unroll
-                    for (int gq = 0; gq < GB; ++gq) {
-                        const int w = w0 + gq * kProd;
-                        const int kc = w % S::KCM, nu = w / S::KCM;
-                        const bool rv = w < npad * S::KCM && nu < nb;
-                        const int b = rv ? oslot[nu] : 0, ob = rv ? oidx[nu] : 0;
-                        const int *gb = gbase + b * KC + kc * S::CG;
-                        const int *gn = gna + kc * S::CG;
-#pragma unroll
-                        for (int i = 0; i < S::CG; ++i) {
-                            const int bs = gb[i];
-                            x[gq][i] = (rv && bs >= 0) ? __ldg(DM + bs + ob * gn[i]) : 0.f;
-                        }
-                    }
-#pragma unroll
-                    for (int gq = 0; gq < GB; ++gq) {
-                        const int w = w0 + gq * kProd;
-                        if (w >= npad * S::KCM) break;
-                        const int kc = w % S::KCM, nu = w / S::KCM;
-                        unsigned char *db[S::NT];
-#pragma unroll
-                        for (int t = 0; t < S::NT; ++t)
-                            db[t] = base + S::NT * L::ARR_A + t * L::ARR_B + cm_off<S>(nu, kc);
-                        if constexpr (S::HALF)
-#pragma unroll
-                            for (int i = 0; i < S::CG; ++i) x[gq][i] *= sD;
-                        split_store<S>(x[gq], db);
+                unsigned char *st0 = sm + stage * L::STAGE;
+                // B: per (term t, core-matrix column j of the chunk, slot b) the rows of slot b;
+                // in the split store the n_b rows of one 16-byte column of block (b, a) are
+                // adjacent, as they are in shared memory (zeros where the column is a gap or the
+                // pair has no block)
+                for (int w = pt; w < NT * KCM * ns; w += kRProd) {
+                    const int t = w / (KCM * ns), r = w - t * KCM * ns, j = r / ns, b = r - j * ns;
+                    const int k = k0 + j * CG, a = kslot[k >> 3];
+                    const int nbo = ps[b].norb;
+                    unsigned char *dst = st0 + NT * L::PLA + t * L::PLB + j * L::LBO_B + ps[b].off * 16;
+                    int e = -1;
+                    if (a >= 0) e = tsm ? tbls[b * ns + a] : __ldg(P.tbl2 + B.tbl + b * ns + a);
+                    if (e >= 0) {
+                        const int64_t el = (int64_t)t * SI.dms_plane + e + ((k - koffs[a]) / CG) * nbo * CG;
+                        const unsigned char *src = dms + el * L::ESZ;
+                        for (int row = 0; row < nbo; ++row) cp_async16(dst + 16 * row, src + 16 * row);
+                    } else {
+                        for (int row = 0; row < nbo; ++row)
+                            *reinterpret_cast<uint4 *>(dst + 16 * row) = make_uint4(0, 0, 0, 0);
                     }
                 }
+                cp_async_commit();
+                // A: per (point, 8-column group of the chunk): the group's slot evaluated at the
+                // point, its columns within the group's 16-column segment split into the operand;
+                // groups that continue the previous group's slot are covered by that task, gaps
+                // are zeroed.  Groups of the first halves of segments come first.
+                for (int w = pt; w < (KC / 8) * kMaxBatchPts; w += kRProd) {
+                    const int p = w % kMaxBatchPts, u = w / kMaxBatchPts;
+                    constexpr int NG = KC / 8;
+                    const int gq = u < (NG + 1) / 2 ? 2 * u : 2 * (u - (NG + 1) / 2) + 1;
+                    const int g8 = (k0 >> 3) + gq;
+                    const int s = kslot[g8];
+                    if (s < 0) {
+#pragma unroll
+                        for (int t = 0; t < NT; ++t)
+#pragma unroll
+                            for (int q = 0; q < 8 / CG; ++q)
+                                *reinterpret_cast<uint4 *>(st0 + t * L::PLA + ((gq * 8) / CG + q) * L::LBO_A + p * 16) =
+                                    make_uint4(0, 0, 0, 0);
+                        continue;
+                    }
+                    if ((gq & 1) && kslot[g8 - 1] == s) continue;   // covered by the group before
+                    if (p >= npb) continue;                          // rows past the batch: unused
+                    const int seg0 = k0 + (gq >> 1) * 16;            // the task's 16-column segment
+                    const PSlot sl = ps[s];
+                    const int ko = koffs[s];
+                    const int clo = max(ko, seg0), chi = min(ko + kpad(sl.norb), seg0 + 16);
+                    const int cval = min(chi, ko + sl.norb);         // columns past it are padding
+                    float dx, dy, dz;
+                    disp(sl, poff + 6 * p, dx, dy, dz);
+                    eval_phi_any<true>(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) {
+                        const int c = ko + o;
+                        if (c >= clo && c < chi) stg[(c - seg0) * kRProd + pt] = v;
+                    });
+                    for (int c = clo; c < chi; c += CG) {
+                        float x[CG];
+#pragma unroll
+                        for (int i = 0; i < CG; ++i) x[i] = (c + i < cval) ? stg[(c + i - seg0) * kRProd + pt] * sA : 0.f;
+                        unsigned char *da[NT];
+#pragma unroll
+                        for (int t = 0; t < NT; ++t) da[t] = st0 + t * L::PLA + ((c - k0) / CG) * L::LBO_A + p * 16;
+                        split_store<S>(x, da);
+                    }
+                }
+                cp_async_wait_all();
                 fence_async_smem();
-                named_sync(1, kProd);
+                named_sync(1, kRProd);
                 if (pt == 0) mbar_arrive(&full[stage]);   // chunk g is in shared memory
             }
         }
-    } else if (tid < kEpi0) {
+        cp_async_wait_all();   // no copy may be in flight when the CTA exits
+    } else if (tid < kREpi0) {
         // ------------------------------------------------------------ MMA issue (one thread)
-        if (tid == kMma) {
+        if (tid == kRMma) {
             int g = 0, it = 0;
             bool ok = true;
             CtaRange cr(P);
             for (int bi = 0; ok && cr.next(bi);) {
-                const int nb = P.batches[bi].nb;
+                const Batch B = P.batches[bi];
+                const int nb = B.nb;
                 if (nb == 0) continue;
                 const int npad = (nb + 15) & ~15;
                 const int buf = it & 1;
-                const int nch = (nb + KC - 1) / KC;
+                const int last = B.slot0 + B.nslots - 1;
+                const int ktot = (__ldg(P.koff + last) + kpad(P.slots[last].norb) + KC - 1) / KC * KC;
+                const int nch = ktot / KC;
                 const uint32_t id = idesc<S>(128, npad);
                 for (int ch = 0; ch < nch && ok; ++ch, ++g) {
                     const int stage = g % NS;
@@ -801,13 +846,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a0 = su32(sm + stage * L::STAGE), b0 = a0 + S::NT * L::ARR_A;
+                    const uint32_t a0 = su32(sm + stage * L::STAGE), b0 = a0 + NT * L::PLA;
 #pragma unroll
-                    for (int ks = 0; ks < S::KCM / 2; ++ks) {
+                    for (int ks = 0; ks < KCM / 2; ++ks) {
 #pragma unroll
                         for (int q = 0; q < S::NPROD; ++q) {
-                            const uint64_t da = sdesc(a0 + term(S::PA, q) * L::ARR_A + ks * 2 * kLBO, SBO);
-                            const uint64_t db = sdesc(b0 + term(S::PB, q) * L::ARR_B + ks * 2 * kLBO, SBO);
+                            const uint64_t da = sdesc2(a0 + term(S::PA, q) * L::PLA + ks * 2 * L::LBO_A, L::LBO_A, 128);
+                            const uint64_t db = sdesc2(b0 + term(S::PB, q) * L::PLB + ks * 2 * L::LBO_B, L::LBO_B, 128);
                             const uint32_t acc = (ch == 0 && ks == 0 && q == 0) ? 0u : 1u;
                             umma<S::F16>(tmem + buf * 256, da, db, id, acc);
                         }
@@ -822,11 +867,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         }
     } else {
         // ------------------------------------------------------------ epilogue: rho and force
-        // warp (q, hh): TMEM lane quadrant q (points 32q..32q+31), atom images s with s % 2 == hh
-        const int et = tid - kEpi0, ew = et >> 5, lane = et & 31;
-        const int q = ew & 3, hh = ew >> 2;
+        // warp (q, hh): TMEM lane quadrant q = warp % 4 (points 32q..32q+31), atom images s with
+        // s % kREPQ == hh
+        const int et = tid - kREpi0, ew = et >> 5, lane = et & 31;
+        const int q = warp & 3, hh = ew >> 2;
         const int p = q * 32 + lane;  // TMEM lane = point of the batch
-        float *w = win + ew * kWin * 32;
+        float *w = win + ew * 32 * 32;
         int it = 0;
         // strain derivative (single-structure launches): [0..8] Sum V grad_a phi . Psi d_b,
         // [9] Sum V rho, over this thread's points and atom images
@@ -847,11 +893,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 if (RHO && hh == 0 && p < npb) SI.rho[grid_index(SI, B, p, n2, n3)] = 0.0;
                 continue;
             }
-            named_sync(2, kEpi);
-            load_geom(P, SI, B, eps, epoff, et, kEpi);
+            named_sync(2, kREpi);
+            load_geom(P, SI, B, eps, epoff, et, kREpi);
             if (FORCE)
-                for (int e = et; e < 3 * ns; e += kEpi) facc[e] = 0.f;
-            if (!role_wait(&accfull[buf], (it >> 1) & 1, P, et, eflag, 2, kEpi)) break;
+                for (int e = et; e < 3 * ns; e += kREpi) facc[e] = 0.f;
+            if (!role_wait(&accfull[buf], (it >> 1) & 1, P, et, eflag, 2, kREpi)) break;
             tc_fence_after();
             const bool pv = p < npb;
             const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256);
@@ -871,45 +917,35 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             float st[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) st[k] = 0.f;
-            int w0 = -1000, wn = 0;
-            for (int s = hh; s < ns; s += 2) {
+            for (int s = hh; s < ns; s += kREPQ) {
                 const PSlot sl = eps[s];
                 float fx = 0.f, fy = 0.f, fz = 0.f;
                 float dx = 0.f, dy = 0.f, dz = 0.f;
                 if (pv) disp(sl, po, dx, dy, dz);
-                // a point outside the image's sphere adds nothing: skip its evaluation (the
-                // window loads below stay warp-uniform)
+                // a point outside the image's sphere adds nothing (the window loads below stay
+                // warp-uniform)
                 const bool in = pv && dx * dx + dy * dy + dz * dz < spec[sl.species].rcut2;
-                // orbitals [oa, ob) of the slot whose columns fit the window (all of them unless
-                // the slot has more than 17 orbitals)
+                // orbitals [oa, ob) of the slot whose columns fit one 32-column window (all of
+                // them unless the slot has more than 17 orbitals)
                 for (int oa = 0; oa < sl.norb;) {
-                    const int ob = min(sl.norb, ((sl.off + oa) & ~15) + kWin - sl.off);
-                    if (sl.off + oa < w0 || sl.off + ob > w0 + wn) {
-                        w0 = (sl.off + oa) & ~15;
-                        wn = ((sl.off + ob - w0) + 15) & ~15;
-                        for (int c = 0; c < wn; c += 16) {
-                            float v[16];
-                            tmem_ld16(trow + (uint32_t)(w0 + c), v);
+                    const int ob = min(sl.norb, ((sl.off + oa) & ~15) + 32 - sl.off);
+                    const int w0 = (sl.off + oa) & ~15;
+                    const int wn = ((sl.off + ob - w0) + 15) & ~15;
+                    for (int c = 0; c < wn; c += 16) {
+                        uint32_t v[16];
+                        tmem_ld16_async(trow + (uint32_t)(w0 + c), v);
+                        tmem_wait_ld();
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) w[(c + j) * 32 + lane] = v[j];
-                        }
+                        for (int j = 0; j < 16; ++j) w[(c + j) * 32 + lane] = __uint_as_float(v[j]);
                     }
+                    __syncwarp();
                     const int cb = sl.off - w0;   // window column of orbital o: cb + o
-                    if (in) {
-                        if (FORCE)
-                            eval_phigrad_f32(spec[sl.species], P.coef32, dx, dy, dz,
-                                             [&](int o, float v, float gx, float gy, float gz) {
-                                                 if (o >= oa && o < ob) {
-                                                     const float y = w[(cb + o) * 32 + lane];
-                                                     racc += v * y;
-                                                     fx += gx * y; fy += gy * y; fz += gz * y;
-                                                 }
-                                             });
-                        else
-                            eval_phi_f32(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) {
-                                if (o >= oa && o < ob) racc += v * w[(cb + o) * 32 + lane];
-                            });
-                    }
+                    if (in)
+                        eval_rho_grad_any<FORCE>(
+                            spec[sl.species], P.coef32, dx, dy, dz,
+                            [&](int o) { return (o >= oa && o < ob) ? w[(cb + o) * 32 + lane] : 0.f; }, racc, fx, fy,
+                            fz);
+                    __syncwarp();
                     oa = ob;
                 }
                 if (strain) {
@@ -926,8 +962,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         fz += __shfl_xor_sync(0xffffffffu, fz, m);
                     }
                     if (lane == 0) {
-                        // the four lane quadrants of a slot meet here: FP32 shared-memory adds
-                        // (native), FP64 from the per-batch sum on
+                        // the four lane quadrants of a slot meet here: FP32 shared-memory adds,
+                        // FP64 from the per-batch sum on
                         atomicAdd(&facc[3 * s + 0], fx);
                         atomicAdd(&facc[3 * s + 1], fy);
                         atomicAdd(&facc[3 * s + 2], fz);
@@ -937,11 +973,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             tc_fence_before();
             mbar_arrive(&accempty[buf]);
             racc *= u;
-            if (RHO && hh == 1) rpart[p] = racc;
-            named_sync(2, kEpi);
-            if (RHO && hh == 0 && pv) SI.rho[gi] = f2d(racc + rpart[p]);
+            if (RHO) rpart[hh * kMaxBatchPts + p] = racc;
+            named_sync(2, kREpi);
+            if (RHO && hh == 0 && pv) {
+                float rs = 0.f;
+#pragma unroll
+                for (int k = 0; k < kREPQ; ++k) rs += rpart[k * kMaxBatchPts + p];
+                SI.rho[gi] = f2d(rs);
+            }
             if (FORCE && SI.F)
-                for (int e = et; e < 3 * ns; e += kEpi)
+                for (int e = et; e < 3 * ns; e += kREpi)
                     red_add_f64(&SI.F[3 * eps[e / 3].atom + e % 3], 2.0 * SI.dV * f2d(facc[e]));
             if (strain && pv) {
 #pragma unroll
@@ -1002,12 +1043,22 @@ cudaError_t vlocal_launch(const Plan &P, const SInfo &si0, const SInfo *sis, cud
 template <class S, bool R, bool Fo, bool St>
 cudaError_t rho_launch3(const Plan &P, const SInfo &si0, const SInfo *sis, cudaStream_t s, int nsm)
 {
-    constexpr int smem = RSmem<S>::TOTAL;
+    constexpr int smem = RL<S>::TOTAL;
     static_assert(smem <= 232448, "rho shared memory");
     cudaError_t e = set_smem(k_rho_tc<S, R, Fo, St>, smem);
     if (e != cudaSuccess) return e;
     const int grid = P.rng ? P.npart : std::min(nsm, P.nbatches);
-    k_rho_tc<S, R, Fo, St><<<grid, kThreadsTC, smem, s>>>(P, si0, sis);
+    k_rho_tc<S, R, Fo, St><<<grid, kThreadsR, smem, s>>>(P, si0, sis);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t dm_split_launch(const Plan &P, const int *soff, const double *DM, void *out, int64_t plane, bool sym,
+                            const float *amax, cudaStream_t s)
+{
+    const int grid = (int)std::min<int64_t>(P.nblocks, 8192);
+    if (grid < 1) return cudaSuccess;
+    k_dm_split<S><<<grid, 128, 0, s>>>(P, soff, DM, out, plane, sym ? 1 : 0, amax);
     return cudaGetLastError();
 }
 
@@ -1034,6 +1085,18 @@ cudaError_t launch_vlocal_tc(const Plan &P, gint_prec prec, const SInfo &si0, co
     case GINT_BF16X3: return vlocal_launch<BF16x3W>(P, si0, sis, s, nsm, max_nb);
     case GINT_BF16X6: return vlocal_launch<BF16x6W>(P, si0, sis, s, nsm, max_nb);
     case GINT_FP16X3: return vlocal_launch<FP16x3W>(P, si0, sis, s, nsm, max_nb);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_dm_split(const Plan &P, gint_prec prec, const int *soff, const double *DM, void *out, int64_t plane,
+                            bool sym, const float *amax, cudaStream_t s)
+{
+    switch (prec) {
+    case GINT_TF32X3: return dm_split_launch<TF32x3W>(P, soff, DM, out, plane, sym, amax, s);
+    case GINT_BF16X3: return dm_split_launch<BF16x3W>(P, soff, DM, out, plane, sym, amax, s);
+    case GINT_BF16X6: return dm_split_launch<BF16x6W>(P, soff, DM, out, plane, sym, amax, s);
+    case GINT_FP16X3: return dm_split_launch<FP16x3W>(P, soff, DM, out, plane, sym, amax, s);
     default: return cudaErrorInvalidValue;
     }
 }

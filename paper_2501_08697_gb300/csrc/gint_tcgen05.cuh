@@ -43,10 +43,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
                      : "=r"(ok)
                      : "r"(a), "r"(parity)
                      : "memory");
-        if (ok) return true;
+        if (ok) return true;   // (try_wait itself suspends the thread for a while before failing)
         if (clock64() - t0 > budget) return false;
-        __nanosleep(128);   // back off: a spinning warp takes issue slots from the working ones
     }
+}
+
+// the mbarrier's current phase also waits for `bytes` more bytes of asynchronous copies
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+
+// bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16) that completes the
+// transaction bytes on `bar`
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     su32(dst)),
+                 "l"(src), "r"(bytes), "r"(su32(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t *bar)
@@ -101,6 +116,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float *v)
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+// 16 TMEM columns of the warp's 32 lanes; complete after tmem_wait_ld()
+__device__ __forceinline__ void tmem_ld16_async(uint32_t addr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(addr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_st16(uint32_t addr, const float *v)
 {

@@ -432,8 +432,9 @@ gint_status build_geometry(gint_handle h, const double *tau, bool update_only)
     const int *dims[2] = {h->opt.batch, h->opt.batch_rho};
     for (int w = 0; w < 2; ++w) {
         for (int i = 0; i < 3; ++i) sets[w].dims[i] = dims[w][i];
-        // vlocal batches stay within 192 orbitals so two accumulators fit in tensor memory
-        sets[w].limit_nb = (w == 0) ? 192 : kMaxNb;
+        // vlocal batches of up to 64 points stay within 192 orbitals (two accumulators fit in
+        // tensor memory); larger ones use the full 256 with one accumulator
+        sets[w].limit_nb = (w == 0 && dims[w][0] * dims[w][1] * dims[w][2] <= 64) ? 192 : kMaxNb;
         gint_status st = build_batches(h, tau, G, bg, rc, packed, offsets, canon, w == 1 ? &soff : nullptr, sets[w]);
         if (st != GINT_OK) return st;
         if (sets[w].max_k + 32 > kMaxKCols) {

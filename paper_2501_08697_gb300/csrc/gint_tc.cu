@@ -563,10 +563,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 // 8-row groups of one core-matrix column adjacent (SBO = 128 bytes) and the KCM columns of a
 // chunk LBO = rows x 16 bytes apart, so row r of column j sits at j * LBO + 16 r: producers with
 // consecutive rows write consecutive 16 bytes.
-constexpr int kRProd = 256;          // producer threads (warps 0-7)
-constexpr int kRMma = kRProd;        // the MMA-issue thread (warp 8)
-constexpr int kREpi0 = kRProd + 32;  // first epilogue thread (warp 9)
-constexpr int kREPQ = 3;             // epilogue warps per TMEM lane quadrant
+constexpr int kRHalf = 256;          // producer warps 0-7 write the A operand
+constexpr int kRBThr = 128;          // producer warps 8-11 copy the B operand
+constexpr int kRProd = kRHalf + kRBThr;
+constexpr int kRMma = kRProd;        // the MMA-issue thread (warp 12)
+constexpr int kREpi0 = kRProd + 32;  // first epilogue thread (warp 13)
+constexpr int kREPQ = 2;             // epilogue warps per TMEM lane quadrant
 constexpr int kREpi = 128 * kREPQ;   // epilogue threads
 constexpr int kThreadsR = kREpi0 + kREpi;
 
@@ -582,16 +584,15 @@ struct RL {
     static constexpr int PLA = KCM * LBO_A;            // one A term of a chunk
     static constexpr int PLB = KCM * LBO_B;            // one B term
     static constexpr int STAGE = NT * (PLA + PLB);
-    static constexpr int OFF_STG = NS * STAGE;                                  // float [kKSeg][kRProd]
     // producer metadata, double-buffered (the next batch's is copied during this one)
-    static constexpr int OFF_PSLOT = OFF_STG + kKSeg * kRProd * 4;                  // PSlot[2][64]
+    static constexpr int OFF_PSLOT = NS * STAGE;                                    // PSlot[2][64]
     static constexpr int OFF_POFF = OFF_PSLOT + 2 * kMaxSlots * (int)sizeof(PSlot); // float [2][128][6]
     static constexpr int OFF_KOFF = OFF_POFF + 2 * kMaxBatchPts * 24;               // int [2][64]
     static constexpr int OFF_TBL = OFF_KOFF + 2 * kMaxSlots * 4;                    // int [2][kVTblR^2]
     static constexpr int OFF_KSLOT = OFF_TBL + 2 * kVTblR * kVTblR * 4;             // short [kMaxKCols / 8]
     static constexpr int OFF_EPSLOT = OFF_KSLOT + kMaxKCols / 8 * 2;                // epilogue PSlot[64]
     static constexpr int OFF_EPOFF = OFF_EPSLOT + kMaxSlots * (int)sizeof(PSlot);
-    static constexpr int OFF_WIN = OFF_EPOFF + kMaxBatchPts * 24;               // float [12][32][32]
+    static constexpr int OFF_WIN = OFF_EPOFF + kMaxBatchPts * 24;               // float [epilogue warps][32][32]
     static constexpr int OFF_RPART = OFF_WIN + (kREpi / 32) * 32 * 32 * 4;      // float [kREPQ][128]
     static constexpr int OFF_FACC = OFF_RPART + kREPQ * kMaxBatchPts * 4;       // float [64][3]
     static constexpr int OFF_BAR = (OFF_FACC + kMaxSlots * 12 + 15) / 16 * 16;  // 16 mbarriers
@@ -651,7 +652,6 @@ __global__ void __launch_bounds__(kThreadsR, 1)
     using L = RL<S>;
     constexpr int CG = L::CG, KCM = L::KCM, KC = L::KC, NS = L::NS, NT = S::NT;
     extern __shared__ __align__(1024) unsigned char sm[];
-    float *stg = reinterpret_cast<float *>(sm + L::OFF_STG);
     PSlot *psb = reinterpret_cast<PSlot *>(sm + L::OFF_PSLOT);
     float *poffb = reinterpret_cast<float *>(sm + L::OFF_POFF);
     int *koffb = reinterpret_cast<int *>(sm + L::OFF_KOFF);
@@ -668,6 +668,7 @@ __global__ void __launch_bounds__(kThreadsR, 1)
     uint32_t *tmem_base = reinterpret_cast<uint32_t *>(sm + L::OFF_MISC);
     volatile int *pflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 4);
     volatile int *eflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 8);
+    volatile int *bflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 12);
 
     const int tid = threadIdx.x, warp = tid >> 5;
     load_species(P, spec, tid);
@@ -679,8 +680,8 @@ __global__ void __launch_bounds__(kThreadsR, 1)
         mbar_init(&accempty[0], kREpi);
         mbar_init(&accempty[1], kREpi);
         mbar_init(fin, 1);
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
+        mbar_init(&full[0], 2);   // one arrival from each producer group
+        mbar_init(&full[1], 2);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_base)),
@@ -715,7 +716,7 @@ __global__ void __launch_bounds__(kThreadsR, 1)
             // this batch's metadata has arrived and every producer is done with the previous
             // batch (whose half of the buffers the next batch's copy overwrites)
             cp_async_wait_all();
-            named_sync(1, kRProd);
+            named_sync(4, kRProd);
             {
                 CtaRange peek = cr;
                 int bn = 0;
@@ -739,84 +740,161 @@ __global__ void __launch_bounds__(kThreadsR, 1)
                 }
                 kslot[k8] = (short)(8 * k8 < koffs[lo] + kpad(ps[lo].norb) ? lo : -1);
             }
-            named_sync(1, kRProd);
+            named_sync(4, kRProd);
             float sA = 1.f;   // fp16: A = phi sA (the density matrix was scaled when it was split)
             if constexpr (S::HALF) sA = scale_for(SI.phimax);
             const unsigned char *dms = reinterpret_cast<const unsigned char *>(SI.DMS);
             const int nch = ktot / KC;
+            // warps 0-7 write the A operand, warps 8-11 copy the B operand; each group waits for
+            // the stage on its own and arrives on the stage's full barrier
+            const bool agrp = pt < kRHalf;
+            const int gt = agrp ? pt : pt - kRHalf;
+            const int gbar = agrp ? 1 : 3, gthr = agrp ? kRHalf : kRBThr;
+            volatile int *gflag = agrp ? pflag : bflag;
+            const int p = gt % kMaxBatchPts;   // the A thread's point (the same in every unit)
+            float po[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) po[c] = poff[6 * (p < npb ? p : 0) + c];
+            constexpr int NG = KC / 8;
+            // A unit (thread, i): point p, 8-column group gq of the chunk.  Groups of the first
+            // halves of 16-column segments come first; a thread's units lie in one segment.
+            auto unit_group = [&](int i) {
+                const int u = (gt + i * kRHalf) / kMaxBatchPts;
+                return u < (NG + 1) / 2 ? 2 * u : 2 * (u - (NG + 1) / 2) + 1;
+            };
+            // A task classes: a slot whose (padded) columns start at its group and fit the
+            // segment, with a compiled evaluator, keeps its values in registers across the wait
+            // for the stage: xe for a task starting at the segment (first group), xo for one
+            // starting at its second group.  Other tasks are evaluated after the wait.
+            auto task_of = [&](int i, int k0, int &gq, int &sg, int &seg0, bool &reg) {
+                gq = unit_group(i);
+                const int g8 = (k0 >> 3) + gq;
+                sg = kslot[g8];
+                seg0 = k0 + (gq >> 1) * 16;
+                reg = false;
+                if (sg < 0) return;
+                if ((gq & 1) && kslot[g8 - 1] == sg) {
+                    sg = -2;   // covered by the task of the group before
+                    return;
+                }
+                const int kw = kpad(ps[sg].norb);
+                reg = spec[ps[sg].species].shape != kShapeGeneric && koffs[sg] == seg0 + 8 * (gq & 1) &&
+                      kw <= 16 - 8 * (gq & 1);
+            };
             for (int ch = 0; ch < nch && ok; ++ch, ++g) {
                 const int stage = g % NS;
                 const int k0 = ch * KC;
-                if (g >= NS) ok = role_wait(&empty[stage], ((g / NS) - 1) & 1, P, pt, pflag, 1, kRProd);
+                float xe[16], xo[8];
+                if (agrp && p < npb) {
+                    // A, first half (before the stage is free): register tasks evaluated
+                    for (int i = 0; i * kRHalf + gt < NG * kMaxBatchPts; ++i) {
+                        int gq, sg, seg0;
+                        bool reg;
+                        task_of(i, k0, gq, sg, seg0, reg);
+                        if (!reg) continue;
+                        const PSlot sl = ps[sg];
+                        const SpecSh &sp = spec[sl.species];
+                        float dx, dy, dz;
+                        disp(sl, po, dx, dy, dz);
+                        if (gq & 1) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) xo[q] = 0.f;
+                            if (sp.shape == kShapeSP) eval_phi_shape<ShapeSP>(sp, P.coef32, dx, dy, dz, [&](int o, float v) { xo[o] = v; });
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) xe[q] = 0.f;
+                            if (sp.shape == kShapeSPD) eval_phi_shape<ShapeSPD>(sp, P.coef32, dx, dy, dz, [&](int o, float v) { xe[o] = v; });
+                            else eval_phi_shape<ShapeSP>(sp, P.coef32, dx, dy, dz, [&](int o, float v) { xe[o] = v; });
+                        }
+                    }
+                }
+                if (g >= NS) ok = role_wait(&empty[stage], ((g / NS) - 1) & 1, P, gt, gflag, gbar, gthr);
                 if (!ok) break;
                 unsigned char *st0 = sm + stage * L::STAGE;
-                // B: per (term t, core-matrix column j of the chunk, slot b) the rows of slot b;
-                // in the split store the n_b rows of one 16-byte column of block (b, a) are
-                // adjacent, as they are in shared memory (zeros where the column is a gap or the
-                // pair has no block)
-                for (int w = pt; w < NT * KCM * ns; w += kRProd) {
-                    const int t = w / (KCM * ns), r = w - t * KCM * ns, j = r / ns, b = r - j * ns;
-                    const int k = k0 + j * CG, a = kslot[k >> 3];
-                    const int nbo = ps[b].norb;
-                    unsigned char *dst = st0 + NT * L::PLA + t * L::PLB + j * L::LBO_B + ps[b].off * 16;
-                    int e = -1;
-                    if (a >= 0) e = tsm ? tbls[b * ns + a] : __ldg(P.tbl2 + B.tbl + b * ns + a);
-                    if (e >= 0) {
-                        const int64_t el = (int64_t)t * SI.dms_plane + e + ((k - koffs[a]) / CG) * nbo * CG;
-                        const unsigned char *src = dms + el * L::ESZ;
-                        for (int row = 0; row < nbo; ++row) cp_async16(dst + 16 * row, src + 16 * row);
-                    } else {
-                        for (int row = 0; row < nbo; ++row)
-                            *reinterpret_cast<uint4 *>(dst + 16 * row) = make_uint4(0, 0, 0, 0);
+                if (!agrp) {
+                    // B: per (term t, core-matrix column j of the chunk, slot b) the rows of slot
+                    // b; in the split store the n_b rows of one 16-byte column of block (b, a) are
+                    // adjacent, as they are in shared memory (zeros where the column is a gap or
+                    // the pair has no block).  One task per thread: the 16-byte copies of a warp
+                    // spread over 32 tasks take the fewest copy instructions.
+                    for (int w = gt; w < NT * KCM * ns; w += kRBThr) {
+                        const int t = w / (KCM * ns), r = w - t * KCM * ns, j = r / ns, b = r - j * ns;
+                        const int k = k0 + j * CG, a = kslot[k >> 3];
+                        const int nbo = ps[b].norb;
+                        unsigned char *dst = st0 + NT * L::PLA + t * L::PLB + j * L::LBO_B + ps[b].off * 16;
+                        int e = -1;
+                        if (a >= 0) e = tsm ? tbls[b * ns + a] : __ldg(P.tbl2 + B.tbl + b * ns + a);
+                        if (e >= 0) {
+                            const int64_t el = (int64_t)t * SI.dms_plane + e + ((k - koffs[a]) / CG) * nbo * CG;
+                            const unsigned char *src = dms + el * L::ESZ;
+                            for (int row = 0; row < nbo; ++row) cp_async16(dst + 16 * row, src + 16 * row);
+                        } else {
+                            for (int row = 0; row < nbo; ++row)
+                                *reinterpret_cast<uint4 *>(dst + 16 * row) = make_uint4(0, 0, 0, 0);
+                        }
+                    }
+                    cp_async_commit();
+                    cp_async_wait_all();
+                } else {
+                    // A, second half: each task's columns split into the operand row p (register
+                    // tasks from their registers, the others evaluated now into a per-thread
+                    // array); gaps zeroed.  Rows past the batch stay unwritten (their accumulator
+                    // rows are not read).
+                    for (int i = 0; i * kRHalf + gt < NG * kMaxBatchPts; ++i) {
+                        int gq, sg, seg0;
+                        bool reg;
+                        task_of(i, k0, gq, sg, seg0, reg);
+                        if (sg == -1) {
+#pragma unroll
+                            for (int t = 0; t < NT; ++t)
+#pragma unroll
+                                for (int q = 0; q < 8 / CG; ++q)
+                                    *reinterpret_cast<uint4 *>(st0 + t * L::PLA + ((gq * 8) / CG + q) * L::LBO_A + p * 16) =
+                                        make_uint4(0, 0, 0, 0);
+                            continue;
+                        }
+                        if (sg < 0 || p >= npb) continue;
+                        unsigned char *row = st0 + p * 16;
+                        auto put = [&](int c, const float *x) {   // CG values of column c on
+                            float y[CG];
+#pragma unroll
+                            for (int q = 0; q < CG; ++q) y[q] = x[q] * sA;
+                            unsigned char *da[NT];
+#pragma unroll
+                            for (int t = 0; t < NT; ++t) da[t] = row + t * L::PLA + ((c - k0) / CG) * L::LBO_A;
+                            split_store<S>(y, da);
+                        };
+                        if (reg) {
+                            if (gq & 1) {
+#pragma unroll
+                                for (int c = 0; c < 8; c += CG) put(seg0 + 8 + c, xo + c);
+                            } else {
+                                const int kw = kpad(ps[sg].norb);
+#pragma unroll
+                                for (int c = 0; c < 16; c += CG)
+                                    if (c < kw) put(seg0 + c, xe + c);
+                            }
+                            continue;
+                        }
+                        // other tasks: every orbital evaluated, the segment's columns kept
+                        const PSlot sl = ps[sg];
+                        const int ko = koffs[sg];
+                        const int clo = max(ko, seg0), chi = min(ko + kpad(sl.norb), seg0 + 16);
+                        float xl[16];
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) xl[q] = 0.f;
+                        float dx, dy, dz;
+                        disp(sl, po, dx, dy, dz);
+                        eval_phi_f32<false>(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) {
+                            const int c = ko + o;
+                            if (c >= clo && c < chi) xl[c - seg0] = v;
+                        });
+                        for (int c = clo; c < chi; c += CG) put(c, xl + (c - seg0));
                     }
                 }
-                cp_async_commit();
-                // A: per (point, 8-column group of the chunk): the group's slot evaluated at the
-                // point, its columns within the group's 16-column segment split into the operand;
-                // groups that continue the previous group's slot are covered by that task, gaps
-                // are zeroed.  Groups of the first halves of segments come first.
-                for (int w = pt; w < (KC / 8) * kMaxBatchPts; w += kRProd) {
-                    const int p = w % kMaxBatchPts, u = w / kMaxBatchPts;
-                    constexpr int NG = KC / 8;
-                    const int gq = u < (NG + 1) / 2 ? 2 * u : 2 * (u - (NG + 1) / 2) + 1;
-                    const int g8 = (k0 >> 3) + gq;
-                    const int s = kslot[g8];
-                    if (s < 0) {
-#pragma unroll
-                        for (int t = 0; t < NT; ++t)
-#pragma unroll
-                            for (int q = 0; q < 8 / CG; ++q)
-                                *reinterpret_cast<uint4 *>(st0 + t * L::PLA + ((gq * 8) / CG + q) * L::LBO_A + p * 16) =
-                                    make_uint4(0, 0, 0, 0);
-                        continue;
-                    }
-                    if ((gq & 1) && kslot[g8 - 1] == s) continue;   // covered by the group before
-                    if (p >= npb) continue;                          // rows past the batch: unused
-                    const int seg0 = k0 + (gq >> 1) * 16;            // the task's 16-column segment
-                    const PSlot sl = ps[s];
-                    const int ko = koffs[s];
-                    const int clo = max(ko, seg0), chi = min(ko + kpad(sl.norb), seg0 + 16);
-                    const int cval = min(chi, ko + sl.norb);         // columns past it are padding
-                    float dx, dy, dz;
-                    disp(sl, poff + 6 * p, dx, dy, dz);
-                    eval_phi_any<true>(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) {
-                        const int c = ko + o;
-                        if (c >= clo && c < chi) stg[(c - seg0) * kRProd + pt] = v;
-                    });
-                    for (int c = clo; c < chi; c += CG) {
-                        float x[CG];
-#pragma unroll
-                        for (int i = 0; i < CG; ++i) x[i] = (c + i < cval) ? stg[(c + i - seg0) * kRProd + pt] * sA : 0.f;
-                        unsigned char *da[NT];
-#pragma unroll
-                        for (int t = 0; t < NT; ++t) da[t] = st0 + t * L::PLA + ((c - k0) / CG) * L::LBO_A + p * 16;
-                        split_store<S>(x, da);
-                    }
-                }
-                cp_async_wait_all();
                 fence_async_smem();
-                named_sync(1, kRProd);
-                if (pt == 0) mbar_arrive(&full[stage]);   // chunk g is in shared memory
+                named_sync(gbar, gthr);
+                if (gt == 0) mbar_arrive(&full[stage]);   // this group's half of chunk g is in place
             }
         }
         cp_async_wait_all();   // no copy may be in flight when the CTA exits
@@ -867,8 +945,8 @@ __global__ void __launch_bounds__(kThreadsR, 1)
         }
     } else {
         // ------------------------------------------------------------ epilogue: rho and force
-        // warp (q, hh): TMEM lane quadrant q = warp % 4 (points 32q..32q+31), atom images s with
-        // s % kREPQ == hh
+        // warp (q, hh): TMEM lane quadrant q = warp % 4 (points 32q..32q+31), the hh-th of the
+        // quadrant's kREPQ warps
         const int et = tid - kREpi0, ew = et >> 5, lane = et & 31;
         const int q = warp & 3, hh = ew >> 2;
         const int p = q * 32 + lane;  // TMEM lane = point of the batch
@@ -917,37 +995,10 @@ __global__ void __launch_bounds__(kThreadsR, 1)
             float st[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) st[k] = 0.f;
-            for (int s = hh; s < ns; s += kREPQ) {
-                const PSlot sl = eps[s];
-                float fx = 0.f, fy = 0.f, fz = 0.f;
-                float dx = 0.f, dy = 0.f, dz = 0.f;
-                if (pv) disp(sl, po, dx, dy, dz);
-                // a point outside the image's sphere adds nothing (the window loads below stay
-                // warp-uniform)
-                const bool in = pv && dx * dx + dy * dy + dz * dz < spec[sl.species].rcut2;
-                // orbitals [oa, ob) of the slot whose columns fit one 32-column window (all of
-                // them unless the slot has more than 17 orbitals)
-                for (int oa = 0; oa < sl.norb;) {
-                    const int ob = min(sl.norb, ((sl.off + oa) & ~15) + 32 - sl.off);
-                    const int w0 = (sl.off + oa) & ~15;
-                    const int wn = ((sl.off + ob - w0) + 15) & ~15;
-                    for (int c = 0; c < wn; c += 16) {
-                        uint32_t v[16];
-                        tmem_ld16_async(trow + (uint32_t)(w0 + c), v);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) w[(c + j) * 32 + lane] = __uint_as_float(v[j]);
-                    }
-                    __syncwarp();
-                    const int cb = sl.off - w0;   // window column of orbital o: cb + o
-                    if (in)
-                        eval_rho_grad_any<FORCE>(
-                            spec[sl.species], P.coef32, dx, dy, dz,
-                            [&](int o) { return (o >= oa && o < ob) ? w[(cb + o) * 32 + lane] : 0.f; }, racc, fx, fy,
-                            fz);
-                    __syncwarp();
-                    oa = ob;
-                }
+            // this warp's atom images: a contiguous range; two consecutive images of one species
+            // whose columns fit one 32-column window are evaluated together (two independent
+            // chains for the scheduler), the others one by one
+            auto slot_done = [&](int s, float fx, float fy, float fz, float dx, float dy, float dz) {
                 if (strain) {
                     st[0] += fx * dx; st[1] += fx * dy; st[2] += fx * dz;
                     st[3] += fy * dx; st[4] += fy * dy; st[5] += fy * dz;
@@ -969,6 +1020,80 @@ __global__ void __launch_bounds__(kThreadsR, 1)
                         atomicAdd(&facc[3 * s + 2], fz);
                     }
                 }
+            };
+            auto load_window = [&](int w0, int wn) {
+                for (int c = 0; c < wn; c += 16) {
+                    uint32_t v[16];
+                    tmem_ld16_async(trow + (uint32_t)(w0 + c), v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) w[(c + j) * 32 + lane] = __uint_as_float(v[j]);
+                }
+                __syncwarp();
+            };
+            const int s_end = (ns * (hh + 1)) / kREPQ;
+            for (int s = (ns * hh) / kREPQ; s < s_end;) {
+                const PSlot sa = eps[s];
+                const int w0 = sa.off & ~15;
+                const bool pair = s + 1 < s_end && eps[s + 1].species == sa.species &&
+                                  eps[s + 1].off + eps[s + 1].norb <= w0 + 32 && spec[sa.species].shape != kShapeGeneric;
+                if (pair) {
+                    const PSlot sb = eps[s + 1];
+                    const SpecSh &sp = spec[sa.species];
+                    float ax = 0.f, ay = 0.f, az = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+                    if (pv) {
+                        disp(sa, po, ax, ay, az);
+                        disp(sb, po, bx, by, bz);
+                    }
+                    const bool ina = pv && ax * ax + ay * ay + az * az < sp.rcut2;
+                    const bool inb = pv && bx * bx + by * by + bz * bz < sp.rcut2;
+                    load_window(w0, ((sb.off + sb.norb - w0) + 15) & ~15);
+                    float fax = 0.f, fay = 0.f, faz = 0.f, fbx = 0.f, fby = 0.f, fbz = 0.f;
+                    if (__any_sync(0xffffffffu, ina || inb)) {
+                        // both images evaluated unconditionally (finite outside the sphere: the
+                        // interval index is clamped) and masked, so the two chains interleave;
+                        // displacements below 1e-12 take the generic centre limits
+                        const int ca = sa.off - w0, cb2 = sb.off - w0;
+                        float ra = 0.f, rb = 0.f;
+                        const float a2 = ina ? ax : 1.f, ay2 = ina ? ay : 0.f, az2 = ina ? az : 0.f;
+                        const float b2 = inb ? bx : 1.f, by2 = inb ? by : 0.f, bz2 = inb ? bz : 0.f;
+                        eval_rho_grad_any<FORCE>(sp, P.coef32, a2, ay2, az2, [&](int o) { return w[(ca + o) * 32 + lane]; },
+                                                 ra, fax, fay, faz);
+                        eval_rho_grad_any<FORCE>(sp, P.coef32, b2, by2, bz2, [&](int o) { return w[(cb2 + o) * 32 + lane]; },
+                                                 rb, fbx, fby, fbz);
+                        if (!ina) ra = fax = fay = faz = 0.f;
+                        if (!inb) rb = fbx = fby = fbz = 0.f;
+                        racc += ra + rb;
+                    }
+                    __syncwarp();
+                    slot_done(s, fax, fay, faz, ax, ay, az);
+                    slot_done(s + 1, fbx, fby, fbz, bx, by, bz);
+                    s += 2;
+                    continue;
+                }
+                float fx = 0.f, fy = 0.f, fz = 0.f;
+                float dx = 0.f, dy = 0.f, dz = 0.f;
+                if (pv) disp(sa, po, dx, dy, dz);
+                // a point outside the image's sphere adds nothing (the window loads stay
+                // warp-uniform)
+                const bool in = pv && dx * dx + dy * dy + dz * dz < spec[sa.species].rcut2;
+                // orbitals [oa, ob) of the slot whose columns fit one 32-column window (all of
+                // them unless the slot has more than 17 orbitals)
+                for (int oa = 0; oa < sa.norb;) {
+                    const int ob = min(sa.norb, ((sa.off + oa) & ~15) + 32 - sa.off);
+                    const int v0 = (sa.off + oa) & ~15;
+                    load_window(v0, ((sa.off + ob - v0) + 15) & ~15);
+                    const int cb = sa.off - v0;   // window column of orbital o: cb + o
+                    if (in)
+                        eval_rho_grad_any<FORCE>(
+                            spec[sa.species], P.coef32, dx, dy, dz,
+                            [&](int o) { return (o >= oa && o < ob) ? w[(cb + o) * 32 + lane] : 0.f; }, racc, fx, fy,
+                            fz);
+                    __syncwarp();
+                    oa = ob;
+                }
+                slot_done(s, fx, fy, fz, dx, dy, dz);
+                ++s;
             }
             tc_fence_before();
             mbar_arrive(&accempty[buf]);

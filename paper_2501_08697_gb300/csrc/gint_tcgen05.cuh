@@ -32,6 +32,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(su32(bar)) : "memory");
 }
 
+constexpr uint32_t kWaitHintNs = 200000;   // longest single suspension of a waiting thread (0.2 ms)
+
 // bounded wait on the phase with the given parity; false if the budget ran out
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long budget)
 {
@@ -39,11 +41,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
     const long long t0 = clock64();
     while (true) {
         uint32_t ok;
-        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        // the thread is suspended until the phase completes or the hint (nanoseconds) runs out,
+        // so a waiting warp takes no issue slots from the working ones
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
                      : "=r"(ok)
-                     : "r"(a), "r"(parity)
+                     : "r"(a), "r"(parity), "r"(kWaitHintNs)
                      : "memory");
-        if (ok) return true;   // (try_wait itself suspends the thread for a while before failing)
+        if (ok) return true;
         if (clock64() - t0 > budget) return false;
     }
 }

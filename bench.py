@@ -3,7 +3,10 @@
 One step = the per-SCF-iteration grid work on one structure: V_mu,nu(R) (gint_vlocal), the
 backward pass rho(r) + Pulay force (gint_rho_force) and the FP64 checks Sum rho dV
 (gint_charge) and Tr(rho_mu,nu V_mu,nu) (gint_block_dot).  The geometry set-up (block list,
-batch lists) is done once per structure and is outside the timed region.
+batch lists) is done once per structure and is outside the timed region.  The headline runs the
+FP16x3 split; the line also carries every other precision's time and error against the FP64
+oracle (on a seeded sample of blocks, grid points and atoms), the multi-structure job and the
+CPU oracle on the other configurations.
 
 Default workload: the 512-atom Si precision case (4x4x4 diamond supercell, 6656 orbitals,
 grid 192^3 = 7,077,888 points), synthetic seeded inputs.  Metric: grid points per second.
@@ -68,7 +71,7 @@ def _traffic(kernel, workload, prec):
 def _tensor_peak(prec, peaks, sustained=True):
     """Dense peak (TFLOP/s) for the contraction dtype: measured bf16 x nominal dtype ratio."""
     bf16 = peaks.get("bf16_tflops_sustained" if sustained else "bf16_tflops", 1700.0)
-    ratio = {"tf32x3": 1.1 / 2.25, "bf16x3": 1.0, "bf16x6": 1.0, "fp32": 1.1 / 2.25}.get(prec, 1.0)
+    ratio = {"tf32x3": 1.1 / 2.25, "bf16x3": 1.0, "bf16x6": 1.0, "fp16x3": 1.0, "fp32": 1.1 / 2.25}.get(prec, 1.0)
     return bf16 * ratio
 
 
@@ -156,6 +159,36 @@ def build_inputs(name):
     return st, V
 
 
+# vlocal batch shape per precision: FP16x3's 16-deep MMA steps keep 128-point batches inside the
+# 1e-6 accumulation-error budget, the other tensor-core schemes stay at 64 points
+VBATCH = {"fp16x3": (4, 4, 8)}
+PRECS = ("fp16x3", "tf32x3", "bf16x6", "bf16x3", "fp32")
+
+
+def vbatch(prec):
+    return VBATCH.get(prec, (4, 4, 4))
+
+
+def oracle_samples(st, Vn, DMn, keys, offs, n_blocks=4096, n_pts=100000, n_atoms=64, seed=2501):
+    """FP64 oracle values on a seeded sample of the workload: n_blocks blocks drawn from the whole
+    pair list (each summed over its first atom's sphere), n_pts grid points of rho and the force
+    on n_atoms atoms (each summed over its own sphere)."""
+    from oracle import Oracle
+    o = Oracle.from_structure(st)
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(len(keys), min(n_blocks, len(keys)), replace=False))
+    idx = np.concatenate([np.arange(offs[b], offs[b + 1]) for b in sel])
+    pts = np.sort(rng.choice(st.npts, min(n_pts, st.npts), replace=False))
+    atoms = np.sort(rng.choice(st.natoms, min(n_atoms, st.natoms), replace=False))
+    t0 = time.perf_counter()
+    ref = dict(idx=idx, H=o.vlocal_blocks(Vn, sel), pts=pts, rho=o.rho(DMn, pts), atoms=atoms,
+               F=-o.dLdtau_atoms(Vn, DMn, atoms))
+    ref["oracle_s"] = time.perf_counter() - t0
+    ref["desc"] = (f"{len(sel)} seeded blocks of the pair list, {len(pts)} seeded grid points, "
+                   f"force on {len(atoms)} seeded atoms")
+    return ref
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2501_08697_gb300 import gint as G
@@ -164,8 +197,10 @@ def run_ours(args, rank, world):
     dev = torch.device(f"cuda:{int(os.environ.get('LOCAL_RANK', 0))}")
     torch.cuda.set_device(dev)
     st, Vn = build_inputs(args.workload)
+    prec = args.prec
+    batch = tuple(args.batch) if args.batch else vbatch(prec)
     t0 = time.time()
-    h = G.setup_structure(st, batch=tuple(args.batch), batch_rho=tuple(args.batch_rho))
+    h = G.setup_structure(st, batch=batch, batch_rho=tuple(args.batch_rho))
     setup_s = time.time() - t0
     keys, offs = h.layout()
     DMn = S.density_matrix(keys, st.norb_atom, seed=st.seed)
@@ -179,23 +214,23 @@ def run_ours(args, rank, world):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(prec, ev=None):
+    def step(hh, p, ev=None):
         if ev:
             ev[0].record(stream)
-        G.gint_vlocal(h, V, H, prec)
+        G.gint_vlocal(hh, V, H, p)
         if ev:
             ev[1].record(stream)
-        G.gint_rho_force(h, V, DM, rho, F, prec)
+        G.gint_rho_force(hh, V, DM, rho, F, p)
         if ev:
             ev[2].record(stream)
-        G.gint_charge(h, rho, chk[0:1])
-        G.gint_block_dot(h, DM, H, chk[1:2])
+        G.gint_charge(hh, rho, chk[0:1])
+        G.gint_block_dot(hh, DM, H, chk[1:2])
         if ev:
             ev[3].record(stream)
 
-    def timed(prec, steps, warmup, all_ranks=True):
+    def timed(hh, p, steps, warmup, all_ranks=True):
         for _ in range(warmup):
-            step(prec)
+            step(hh, p)
         torch.cuda.synchronize()
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
         if all_ranks:
@@ -203,7 +238,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         for i in range(steps):
             flush.fill_(float(i))                       # evict L2 (512 MiB write) outside the events
-            step(prec, evs[i])
+            step(hh, p, evs[i])
         torch.cuda.synchronize()
         tot = sum(e[0].elapsed_time(e[3]) for e in evs) / 1e3
         tv = sum(e[0].elapsed_time(e[1]) for e in evs) / steps / 1e3
@@ -211,29 +246,67 @@ def run_ours(args, rank, world):
         tc = sum(e[2].elapsed_time(e[3]) for e in evs) / steps / 1e3
         return tot, tv, tr, tc
 
-    prec = args.prec
     with ClockSampler(dev.index) as clk:
-        tot, tv, tr, tc = timed(prec, args.steps, args.warmup)
+        tot, tv, tr, tc = timed(h, prec, args.steps, args.warmup)
     clocks = clk.summary()
-    G.gint_get_status(h)
+    assert G.gint_get_status(h) == 0
     tmax = max_over_ranks(tot, world, dev)
     npts = info["npts"]
     value = world * npts * args.steps / tmax
     ms = tmax / args.steps * 1e3
+    extras = rank == 0 and world == 1 and not args.quick
+
+    # errors of each precision against the FP64 oracle (seeded sample) and the FP64 GPU path
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    ref = oracle_samples(st, Vn, DMn, keys, offs) if extras else None
+
+    def errors(p_):
+        Hn, rn, Fn = H.cpu().numpy(), rho.cpu().numpy(), F.cpu().numpy().reshape(-1, 3)
+        return {"H": rel(Hn[ref["idx"]], ref["H"]), "rho": rel(rn[ref["pts"]], ref["rho"]),
+                "F": rel(Fn[ref["atoms"]], ref["F"])}
+
+    err_oracle = None
+    if extras:
+        step(h, prec)
+        torch.cuda.synchronize()
+        err_oracle = errors(prec)
 
     # the FP64 GPU path on the same step, for the split-vs-FP64 comparison
     fp64 = None
+    err = None
     if not args.skip_fp64 and rank == 0:
-        f_tot, f_tv, f_tr, _ = timed("fp64", 1, 1, all_ranks=False)   # rank 0 alone
+        f_tot, f_tv, f_tr, _ = timed(h, "fp64", 1, 1, all_ranks=False)   # rank 0 alone
         fp64 = {"pts_per_s": npts / f_tot, "ms_per_step": f_tot * 1e3, "vlocal_ms": f_tv * 1e3,
-                "rho_force_ms": f_tr * 1e3}
+                "rho_force_ms": f_tr * 1e3,
+                # algorithmic FP64 FLOP/s of the step's two contractions against the FP64 pipe
+                # (2 DFMA per clock per SM sub-partition pair: 2 x 2 x 152 x 2.07 GHz = 1.26 TFLOP/s)
+                "alg_tflops": 2 * info["flops_useful"] / f_tot / 1e12}
+        fp64["frac_of_fp64_pipe"] = fp64["alg_tflops"] / (2 * 2 * 152 * 2.070e9 / 1e12)
+        if extras:
+            fp64["err_vs_oracle"] = errors("fp64")
         H64, rho64, F64 = H.clone(), rho.clone(), F.clone()
-        step(prec)
+        step(h, prec)
         torch.cuda.synchronize()
-        rel = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
-        err = {"H": rel(H, H64), "rho": rel(rho, rho64), "F": rel(F, F64)}
-    else:
-        err = None
+        relt = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+        err = {"H": relt(H, H64), "rho": relt(rho, rho64), "F": relt(F, F64)}
+
+    # the other precisions on the same workload (each with its own vlocal batch shape)
+    per_prec = {}
+    if extras:
+        for p_ in PRECS:
+            if p_ == prec:
+                per_prec[p_] = {"pts_per_s": npts / (tot / args.steps), "vlocal_ms": tv * 1e3, "rho_force_ms": tr * 1e3,
+                                "batch_vlocal": list(batch), "err_vs_oracle": err_oracle}
+                continue
+            h2 = G.setup_structure(st, batch=vbatch(p_), batch_rho=tuple(args.batch_rho))
+            n = 3 if p_ != "fp32" else 1
+            t2, v2, r2, _ = timed(h2, p_, n, 2 if p_ != "fp32" else 1, all_ranks=False)
+            assert G.gint_get_status(h2) == 0
+            step(h2, p_)
+            torch.cuda.synchronize()
+            per_prec[p_] = {"pts_per_s": npts * n / t2, "vlocal_ms": v2 * 1e3, "rho_force_ms": r2 * 1e3,
+                            "batch_vlocal": list(vbatch(p_)), "err_vs_oracle": errors(p_)}
+            h2.close()
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     pin = lambda n: torch.empty(n, dtype=torch.float64).pin_memory()
@@ -254,34 +327,43 @@ def run_ours(args, rank, world):
     peaks, src = _peaks()
     dominant = ("rho_force", tr) if tr >= tv else ("vlocal", tv)
     alg_flops = info["flops_useful"]                       # 2 n(r)^2 summed over the grid
-    exec_flops = {"tf32x3": 3, "bf16x3": 3, "bf16x6": 6}.get(prec, 1) * (
+    exec_flops = {"tf32x3": 3, "bf16x3": 3, "bf16x6": 6, "fp16x3": 3}.get(prec, 1) * (
         info["flops_dense"] if dominant[0] == "vlocal" else info["flops_dense_rho"])
     tp = _tensor_peak(prec, peaks, sustained=True)
     achieved = alg_flops / dominant[1] / 1e12
     roofline = {"bound": "tensor", "kernel": dominant[0], "achieved": achieved, "peak": tp, "unit": "TFLOP/s",
                 "frac": achieved / tp, "traffic": _traffic(dominant[0], args.workload, prec),
                 "peak_source": f"{src} bf16 sustained x nominal {prec} ratio",
-                "executed_tflops": exec_flops / dominant[1] / 1e12}
+                "executed_tflops": exec_flops / dominant[1] / 1e12,
+                "other_kernel": {"kernel": "vlocal" if dominant[0] == "rho_force" else "rho_force",
+                                 "achieved": alg_flops / (tv if dominant[0] == "rho_force" else tr) / 1e12}}
     out = {
         "metric": METRIC, "value": value, "unit": "grid points/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": prec, "data": "synthetic (seeded Si diamond 4x4x4, plane-wave V, random DM)",
         "config": {"workload": workload_name(args.workload, st),
-                   "prec": prec, "batch_vlocal": list(args.batch), "batch_rho": list(args.batch_rho),
+                   "prec": prec, "batch_vlocal": list(batch), "batch_rho": list(args.batch_rho),
                    "step": "vlocal + rho_force + charge + trace", "l2": "flushed between steps (512 MiB write)",
                    "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
                    "nbatches": info["nbatches"], "nbatches_rho": info["nbatches_rho"]},
         "kernel_ms": {"vlocal": tv * 1e3, "rho_force": tr * 1e3, "checks": tc * 1e3},
         "roofline": roofline,
         "e2e": e2e,
-        "gpu_launches": args.steps * 8,
+        "gpu_launches": args.steps * 10,
         "clocks": clocks,
         "fp64_gpu": fp64,
         "err_vs_fp64_gpu": err,
+        "err_vs_oracle": err_oracle,
+        "oracle_sample": ref["desc"] if ref else None,
         "speedup_vs_fp64_gpu": (value / world / fp64["pts_per_s"]) if fp64 else None,
+        "precisions": per_prec or None,
     }
+    if extras and not args.skip_batching:
+        out["batching"] = run_batching(args, rank, world, quiet=True)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, st, Vn, keys, offs, DMn)
+        if extras:
+            out["cpu_baseline_configs"] = cpu_baseline_configs(args)
     h.close()
     return out
 
@@ -319,7 +401,34 @@ def cpu_baseline(args, st, Vn, keys=None, offs=None, DMn=None, budget_pts=None):
                       f"{dt:.1f} s"}
 
 
-def run_batching(args, rank, world):
+def cpu_baseline_configs(args):
+    """The FP64 CPU oracle (as it stands) on the other configurations: the forward pass (vlocal +
+    rho) of the 8-atom Si cell (48^3) in full, and of the 64-atom Si cell (96^3) and the 64-water
+    box (128^3) on their first 1e5 grid points (a slab of i-planes; whole-grid time = slab time
+    x points / 1e5, as the cost per point is uniform to first order)."""
+    from oracle import Oracle
+    from paper_2501_08697_gb300 import synth as S
+    out = {}
+    for name, n in (("si8", None), ("si64", 100000), ("water64", 100000)):
+        st = S.workload(name)
+        Vn = S.local_potential(st)
+        o = Oracle.from_structure(st)
+        k2, _ = o.pairs()
+        DMn = S.density_matrix(k2, st.norb_atom, seed=st.seed)
+        pts = None if n is None else np.arange(n, dtype=np.int64)
+        t0 = time.perf_counter()
+        o.vlocal(Vn, pts)
+        o.rho(DMn, pts)
+        dt = time.perf_counter() - t0
+        np_ = st.npts if n is None else n
+        out[name] = {"value": np_ / dt, "unit": "grid points/s", "cores": Oracle.threads(),
+                     "sample": "whole grid" if n is None else f"first {n} of {st.npts} grid points",
+                     "forward_s": dt if n is None else dt * st.npts / n,
+                     "forward_s_kind": "measured" if n is None else "extrapolated from the slab"}
+    return out
+
+
+def run_batching(args, rank, world, quiet=False):
     """The multi-structure case: 32 structures of uneven size (Si 8/16/64/216 atoms x 4 strains,
     water boxes of 8..32 molecules), forward (vlocal) + adjoint (rho) in one graph-replayed job
     with autotuned batch shapes, against sequential per-structure launches."""
@@ -376,6 +485,12 @@ def run_batching(args, rank, world):
         t_job = max_over_ranks(timed(job.launch), world, dev)
     t_seq = max_over_ranks(timed(seq), world, dev)
     value = world * npts * args.steps / t_job
+    if quiet:
+        return {"workload": f"batching: {len(sts)} structures, {npts} grid points", "prec": prec,
+                "pts_per_s": value, "ms_per_job": t_job / args.steps * 1e3,
+                "sequential_pts_per_s": npts * args.steps / t_seq, "speedup_vs_sequential": t_seq / t_job,
+                "autotuned": {k: {"batch": v[0], "batch_rho": v[1], "vlocal_ms": v[2], "rho_ms": v[3]}
+                              for k, v in shapes.items()}}
     return {"metric": METRIC + " [batched]", "value": value, "unit": "grid points/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_job / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
@@ -551,12 +666,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="si512")
-    ap.add_argument("--prec", default="tf32x3")
-    ap.add_argument("--batch", type=int, nargs=3, default=[4, 4, 4])
+    ap.add_argument("--prec", default="fp16x3")
+    ap.add_argument("--batch", type=int, nargs=3, default=None, help="vlocal batch (default: per precision)")
     ap.add_argument("--batch-rho", type=int, nargs=3, default=[4, 4, 8])
     ap.add_argument("--cpu-points", type=int, default=100000)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-batching", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="headline line only (no per-precision, oracle or batching extras)")
     ap.add_argument("--dm-structure", default="si512", help="structure of --workload dm (si8, si64, si512)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -287,8 +287,9 @@ gint_status gint_batch_launch(gint_batch b, void *stream);
 gint_status gint_batch_destroy(gint_batch b);
 
 /* Choose batch shapes for one structure by timing candidates on the current device: vlocal
- * shapes of at most 64 points (the tensor-core accumulation error grows with the points per
- * batch) and rho shapes of 128 points (one M = 128 tile).  Inputs as for gint_setup; writes
+ * shapes of at most 64 points (the tensor-core accumulation error grows with the MMA steps per
+ * batch; for GINT_FP16X3, whose steps are 16 points deep, up to 128) and rho shapes of 128
+ * points (one M = 128 tile).  Inputs as for gint_setup; writes
  * the fastest shapes into *best (and their times in ms, if the pointers are non-NULL).
  * Allocates and frees its own device buffers. */
 gint_status gint_autotune(const double cell[9], int natoms, const int *species, const double *tau,

@@ -25,6 +25,7 @@ SInfo sinfo_for(const gint_handle_s *h, const double *V, double *H, const void *
     si.dV = h->info.dV;
     si.phimax = h->phimax;
     si.amax = h->d_amax;
+    for (int i = 0; i < 9; ++i) si.hstep[i] = (float)h->plan.h[i];
     return si;
 }
 }

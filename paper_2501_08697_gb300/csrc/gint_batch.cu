@@ -36,8 +36,9 @@ struct gint_batch_s {
     Plan plan[3];                    // combined plans: [0] vlocal (batches <= 192 orbitals),
                                      // [1] rho, [2] vlocal of structures with larger batches
     int max_nb_v[3] = {0, 0, 0};
-    void *d_mem[21] = {nullptr};    // [3w..3w+2] batches, slots, tables; [9] splines; [12+w] CTA ranges;
-                                     // [15+2w], [16+2w] padded K offsets and split-store tables
+    void *d_mem[22] = {nullptr};    // [3w..3w+2] batches, slots, tables; [9] splines; [12+w] CTA ranges;
+                                     // [15+2w], [16+2w] padded K offsets and split-store tables;
+                                     // [21] |phi| envelopes
     SInfo *d_sinfo = nullptr;
     int *d_status = nullptr;
     float *d_amax = nullptr;         // [2 * nstruct]: max |V| and max |DM| of each entry (fp16 path)
@@ -157,6 +158,7 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
     // merged species and spline records
     Plan base = hs[0]->plan;
     std::vector<float4> coef;
+    std::vector<float> env;
     std::vector<std::pair<int, int>> uniq;  // (handle, species) of each merged species
     std::vector<std::vector<int>> remap(nstruct);
     int nsp = 0;
@@ -178,6 +180,9 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
                 coef.insert(coef.end(), hs[i]->coef32_host.begin() + d.coef_off,
                             hs[i]->coef32_host.begin() + d.coef_off + n);
                 d.coef_off = off;
+                const int eoff = (int)env.size();
+                env.insert(env.end(), hs[i]->env_host.begin() + d.env_off, hs[i]->env_host.begin() + d.env_off + d.nint);
+                d.env_off = eoff;
                 base.sp[nsp] = d;
                 uniq.push_back({i, s});
                 found = nsp++;
@@ -269,7 +274,8 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
         si[i] = sinfo_for(hs[i], V[i], H[i], with_rho ? b->dms[i] : nullptr, with_rho ? rho[i] : nullptr, nullptr);
         si[i].amax = b->d_amax + 2 * i;
     }
-    if ((e = upload_vec(&b->d_mem[9], coef)) != cudaSuccess || (e = upload_vec((void **)&b->d_sinfo, si)) != cudaSuccess ||
+    if ((e = upload_vec(&b->d_mem[9], coef)) != cudaSuccess || (e = upload_vec(&b->d_mem[21], env)) != cudaSuccess ||
+        (e = upload_vec((void **)&b->d_sinfo, si)) != cudaSuccess ||
         (e = cudaMalloc((void **)&b->d_status, sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(b->d_status, 0, sizeof(int))) != cudaSuccess) {
         free_batch(b);
@@ -277,6 +283,7 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
     }
     for (int w = 0; w < 3; ++w) {
         b->plan[w].coef32 = (const float4 *)b->d_mem[9];
+        b->plan[w].env = (const float *)b->d_mem[21];
         b->plan[w].status = b->d_status;
     }
     // capture the launch sequence once
@@ -363,8 +370,12 @@ extern "C" gint_status gint_autotune(const double cell[9], int natoms, const int
         set_error("gint_autotune: need an output and a tensor-core precision");
         return GINT_EINVAL;
     }
-    static const int cand_v[][3] = {{4, 4, 4}, {4, 4, 2}, {2, 4, 4}, {4, 2, 4}, {2, 2, 8}, {8, 4, 2}};
+    // vlocal shapes: at most 64 points, except for FP16x3, whose 16-deep MMA steps keep 128-point
+    // batches inside the accumulation-error budget
+    static const int cand_v32[][3] = {{4, 4, 4}, {4, 4, 2}, {2, 4, 4}, {4, 2, 4}, {2, 2, 8}, {8, 4, 2}};
+    static const int cand_v16[][3] = {{4, 4, 8}, {4, 8, 4}, {8, 4, 4}, {4, 4, 4}, {4, 4, 6}, {2, 8, 8}};
     static const int cand_r[][3] = {{4, 4, 8}, {4, 8, 4}, {8, 4, 4}, {2, 8, 8}, {8, 8, 2}, {8, 2, 8}};
+    const int(*cand_v)[3] = prec == GINT_FP16X3 ? cand_v16 : cand_v32;
     const int nc = 6;
     double bestv = 1e30, bestr = 1e30;
     gint_options o{};

@@ -260,7 +260,41 @@ struct SpecSh {
     int nrad, nint, coef_off, lpack;   // lpack: 2 bits of l per radial
     float rcut2, inv_dr;
     int shape;                         // kShapeSPD / kShapeSP: radial list with a compiled evaluator
+    int env_off;                       // first entry of the species' |phi| envelope (Plan::env)
 };
+
+// 2^k for -126 <= k <= 127, exactly
+__device__ __forceinline__ float pow2i(int k) { return __int_as_float((127 + k) << 23); }
+
+// Exponent k of the power-of-two scale with m 2^k < 2^14 (0 if m is 0 or not finite), kept to
+// |k| <= 100 so that 2^k and 2^-k stay normal.
+__device__ __forceinline__ int scale_exp(float m)
+{
+    if (!(m > 0.f) || !(m < 3.0e38f)) return 0;
+    int e;
+    frexpf(m, &e);   // m < 2^e
+    return max(-100, min(100, 14 - e));
+}
+
+// A bound on |phi| of an atom image (displacement d0 = dh + dl of the batch origin from the
+// image) over the points of a batch whose centre lies at bc from the origin and whose points
+// lie within R of the centre: the species' envelope at the lower bound |d0 + bc| - R of their
+// distance.  Written with rounded intrinsics only (no contraction), so every role of a kernel
+// that evaluates it for the same image and batch gets the same bits.
+__device__ __forceinline__ float phi_bound(const float *__restrict__ env, const SpecSh &S, const float *dh,
+                                           const float *dl, const float *bc, float R)
+{
+    float d2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float x = __fadd_rn(__fadd_rn(dh[c], dl[c]), bc[c]);
+        d2 = __fadd_rn(d2, __fmul_rn(x, x));
+    }
+    const float rmin = fmaxf(__fadd_rn(__fsqrt_rn(d2), -R), 0.f);
+    if (!(__fmul_rn(rmin, rmin) < S.rcut2)) return 0.f;
+    const int i = min((int)__fmul_rn(rmin, S.inv_dr), S.nint - 1);
+    return __ldg(env + S.env_off + i);
+}
 
 // Radial lists with compiled (fully unrolled) evaluators: their radials' spline records are
 // fetched together and the radials are evaluated side by side; other lists take the generic

@@ -23,6 +23,7 @@ constexpr int kMaxBatchDim = 16;   // points per batch along one axis
 struct DevSpecies {
     int nrad, norb, nint;          // nint = ntab - 1 spline intervals
     int coef_off;                  // first interval record of this species (see Plan::coef*)
+    int env_off;                   // first entry of this species in Plan::env
     double rcut, inv_dr;
     float rcut_f, inv_dr_f;
     int l[kMaxRad];
@@ -66,6 +67,7 @@ struct SInfo {
     double dV;
     const float *amax;             // device [2]: max |V(r)| and max |density matrix| of the call,
                                    // written before the kernel by the fp16 path (else unused)
+    float hstep[9];                // grid step vectors a_i / N_i of this structure (FP32)
 };
 
 // Everything a kernel needs, passed by value.
@@ -79,6 +81,7 @@ struct Plan {
     DevSpecies sp[kMaxSpecies];
     const double *coef64;          // [interval record][4]: per species, interval-major, radial-minor
     const float4 *coef32;
+    const float *env;              // per species and interval i: a bound on |phi| at r >= i dr
     const Batch *batches;
     const Slot *slots;
     const int *tbl;                // (block offset << 1 | canonical) or -1 if no block
@@ -151,6 +154,8 @@ struct gint_handle_s {
     gint::BatchSet bs[2];            // [0] vlocal batches, [1] rho/force batches
     bool relist[2] = {false, false}; // a position update changed that decomposition's lists
     std::vector<float4> coef32_host; // spline records, as uploaded
+    std::vector<float> env_host;     // |phi| envelopes, as uploaded
+    void *d_env = nullptr;
     gint_options opt{};
     gint_info_t info{};
     // device memory (owned)

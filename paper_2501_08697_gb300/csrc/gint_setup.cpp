@@ -584,7 +584,7 @@ static void free_dev(gint_handle h)
     void *ptrs[] = {h->d_coef64, h->d_coef32, h->d_partner, h->d_blkoff, h->d_blkrows, h->d_status, h->d_dmsym,
                     h->d_dms, h->d_poff, h->d_red, h->d_hostio, h->bs[0].d_batches, h->bs[0].d_slots, h->bs[0].d_tbl,
                     h->bs[0].d_rng, h->bs[1].d_batches, h->bs[1].d_slots, h->bs[1].d_tbl, h->bs[1].d_rng,
-                    h->bs[0].d_koff, h->bs[0].d_tbl2, h->bs[1].d_koff, h->bs[1].d_tbl2, h->d_soff,
+                    h->bs[0].d_koff, h->bs[0].d_tbl2, h->bs[1].d_koff, h->bs[1].d_tbl2, h->d_soff, h->d_env,
                     h->ks.d_keys, h->ks.d_grp, h->ks.d_pair, h->ks.d_colatom, h->ks.d_orboff, h->ks.d_kvec,
                     h->ks.d_phase, h->d_dm_scratch, h->d_dm_planes, h->d_amax};
     for (void *p : ptrs)
@@ -823,7 +823,29 @@ extern "C" gint_status gint_setup(gint_handle *out, const double cell[9], int na
             fmax = std::max(fmax, std::fabs(coef64[i]) + std::fabs(coef64[i + 1]) + std::fabs(coef64[i + 2]) +
                                       std::fabs(coef64[i + 3]));
         h->phimax = (float)(fmax * 0.64);
+        // per species and interval i: max over intervals j >= i and radials of the interval
+        // bound, times the Y_lm bound (non-increasing in r)
+        for (int s = 0; s < nspecies; ++s) {
+            DevSpecies &D = P.sp[s];
+            D.env_off = (int)h->env_host.size();
+            std::vector<float> env(D.nint);
+            double run = 0.0;
+            for (int i = D.nint - 1; i >= 0; --i) {
+                for (int r = 0; r < D.nrad; ++r) {
+                    const double *c = &coef64[4 * ((size_t)D.coef_off + (size_t)i * D.nrad + r)];
+                    run = std::max(run, std::fabs(c[0]) + std::fabs(c[1]) + std::fabs(c[2]) + std::fabs(c[3]));
+                }
+                env[i] = (float)(run * 0.64 * 1.0001);
+            }
+            h->env_host.insert(h->env_host.end(), env.begin(), env.end());
+        }
     }
+    if ((e = upload(&h->d_env, h->env_host)) != cudaSuccess) {
+        free_dev(h);
+        delete h;
+        return cuda_fail(e, "gint_setup: upload envelopes");
+    }
+    P.env = (const float *)h->d_env;
     if ((st = upload_geometry(h)) != GINT_OK) {
         free_dev(h);
         delete h;

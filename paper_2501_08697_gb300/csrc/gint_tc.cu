@@ -204,6 +204,22 @@ __device__ __forceinline__ void disp(const PSlot &s, const float *po, float &dx,
     dz = (s.dh[2] + po[2]) + (s.dl[2] + po[5]);
 }
 
+// centre of a batch relative to its origin point and the radius of a sphere about it that holds
+// all its points (upper bound), from the grid step vectors
+__device__ __forceinline__ void batch_sphere(const SInfo &SI, int n1, int n2, int n3, float *bc, float &R)
+{
+    const float *h = SI.hstep;
+    const float f[3] = {0.5f * (n1 - 1), 0.5f * (n2 - 1), 0.5f * (n3 - 1)};
+    float r = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) bc[c] = __fadd_rn(__fadd_rn(__fmul_rn(f[0], h[c]), __fmul_rn(f[1], h[3 + c])), __fmul_rn(f[2], h[6 + c]));
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        r = __fadd_rn(r, __fmul_rn(f[i], __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(h[3 * i], h[3 * i]), __fmul_rn(h[3 * i + 1], h[3 * i + 1])),
+                                                           __fmul_rn(h[3 * i + 2], h[3 * i + 2])))));
+    R = __fadd_rn(__fmul_rn(r, 1.0001f), 1e-6f);
+}
+
 __device__ __forceinline__ int64_t grid_index(const SInfo &SI, const Batch &B, int p, int n2, int n3)
 {
     const int c = p % n3, b = (p / n3) % n2, a = p / (n3 * n2);
@@ -225,6 +241,7 @@ __device__ __forceinline__ void load_species(const Plan &P, SpecSh *spec, int ti
         q.rcut2 = D.rcut_f * D.rcut_f;
         q.inv_dr = D.inv_dr_f;
         q.shape = shape_of(D.nrad, lp);
+        q.env_off = D.env_off;
         spec[tid] = q;
     }
 }
@@ -254,7 +271,10 @@ struct VSmem {
     static constexpr int OFF_V = OFF_VD + 2 * kMaxBatchPts * 8;             // float [128]
     static constexpr int OFF_TBL = OFF_V + kMaxBatchPts * 4;                // int [kVTbl^2]
     static constexpr int OFF_INFO = OFF_TBL + kVTbl * kVTbl * 4;            // int [256]: slot | o << 8 | norb << 16
-    static constexpr int OFF_TILE = OFF_INFO + kMaxNb * 4;                  // float [8][32][33]
+    static constexpr int EXPB = S::HALF ? 2 * kMaxNb * 2 : 0;              // (fp16 scaling only)
+    static constexpr int OFF_PEXP = OFF_INFO + kMaxNb * 4;                  // short [2][256]: producers' A, B exponents
+    static constexpr int OFF_EEXP = OFF_PEXP + EXPB;                        // short [2][256]: epilogue's copy
+    static constexpr int OFF_TILE = OFF_EEXP + EXPB;                        // float [8][32][33]
     static constexpr int OFF_BAR = OFF_TILE + 8 * 32 * 33 * 4;              // 16 mbarriers
     static constexpr int OFF_MISC = OFF_BAR + 16 * 8;                       // tmem base, flags
     static constexpr int OFF_SPEC = OFF_MISC + 64;                          // SpecSh[kMaxSpecies]
@@ -276,6 +296,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     float *vs = reinterpret_cast<float *>(sm + L::OFF_V);
     int *tbls = reinterpret_cast<int *>(sm + L::OFF_TBL);
     int *info = reinterpret_cast<int *>(sm + L::OFF_INFO);
+    short *pexp = reinterpret_cast<short *>(sm + L::OFF_PEXP), *eexp = reinterpret_cast<short *>(sm + L::OFF_EEXP);
     float *tiles = reinterpret_cast<float *>(sm + L::OFF_TILE);
     SpecSh *spec = reinterpret_cast<SpecSh *>(sm + L::OFF_SPEC);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::OFF_BAR);
@@ -340,11 +361,23 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 continue;
             }
             const SInfo SI = sic.get(B, sis);
-            float dVf = (float)SI.dV, sA = 1.f;
+            const float dVf = (float)SI.dV;
             if constexpr (S::HALF) {
-                // fp16 operands: A = phi sA, B = V dV phi sB (powers of two, undone in the epilogue)
-                sA = scale_for(SI.phimax);
-                dVf *= scale_for(SI.amax[0] * dVf * SI.phimax);
+                // fp16 operands: row mu of A = phi_mu 2^eA(mu), row nu of B = V dV phi_nu 2^eB(nu),
+                // with exponents per atom image from a bound on its |phi| over this batch, so
+                // that the orbitals of distant images keep their relative accuracy (undone in
+                // the epilogue)
+                float bc[3], R;
+                batch_sphere(SI, n1, n2, n3, bc, R);
+                for (int s = pt; s < ns; s += kProd) {
+                    const PSlot sl = ps[s];
+                    const float m = phi_bound(P.env, spec[sl.species], sl.dh, sl.dl, bc, R);
+                    const short ea = (short)scale_exp(m), eb = (short)scale_exp(SI.amax[0] * dVf * m);
+                    for (int o = 0; o < sl.norb; ++o) {
+                        pexp[sl.off + o] = ea;
+                        pexp[kMaxNb + sl.off + o] = eb;
+                    }
+                }
             }
             for (int p = pt; p < kMaxBatchPts; p += kProd)
                 vs[p] = p < npb ? d2f(vdb[cur * kMaxBatchPts + p]) * dVf : 0.f;
@@ -388,11 +421,19 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     }
                     if (row < nb) {
                         float x[S::CG], y[S::CG];
+                        float sa = 1.f, sb = 1.f;
+                        if constexpr (S::HALF) {
+                            sa = pow2i(pexp[row]);
+                            sb = pow2i(pexp[kMaxNb + row]);
+                        }
 #pragma unroll
                         for (int i = 0; i < S::CG; ++i) {
                             x[i] = stg[row * KC + kc * S::CG + i];
                             y[i] = x[i] * vs[ch * KC + kc * S::CG + i];
-                            if constexpr (S::HALF) x[i] *= sA;
+                            if constexpr (S::HALF) {
+                                x[i] *= sa;
+                                y[i] *= sb;
+                            }
                         }
                         split_store<S>(x, da);
                         split_store<S>(y, db);
@@ -475,20 +516,33 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             if (nb == 0) continue;
             const SInfo SIe = sic.get(B, sis);
             double *H = SIe.H;
-            float u = 1.f;   // undoes the fp16 operand scaling (exact: a power of two)
-            if constexpr (S::HALF) {
-                const float dVf = (float)SIe.dV;
-                u = 1.f / (scale_for(SIe.phimax) * scale_for(SIe.amax[0] * dVf * SIe.phimax));
-            }
             const bool small = ns <= kVTbl;
             const int *tbl = small ? tbls : P.tbl + B.tbl;
             named_sync(2, kEpi);
             if (small)
                 for (int e = et; e < ns * ns; e += kEpi) tbls[e] = P.tbl[B.tbl + e];
+            float bc[3], R;
+            if constexpr (S::HALF) {
+                int n1, n2, n3;
+                unpack(B.dims, n1, n2, n3);
+                batch_sphere(SIe, n1, n2, n3, bc, R);
+            }
             for (int s = et; s < ns; s += kEpi) {
                 const Slot &sl = P.slots[B.slot0 + s];
                 const int no = sl.norb, off = sl.orb_off;
-                for (int o = 0; o < no; ++o) info[off + o] = s | (o << 8) | (no << 16);
+                short ea = 0, eb = 0;
+                if constexpr (S::HALF) {
+                    // the producers' exponents of this image (same inputs, same rounded arithmetic)
+                    const float dh[3] = {sl.dh[0], sl.dh[1], sl.dh[2]}, dl[3] = {sl.dl[0], sl.dl[1], sl.dl[2]};
+                    const float m = phi_bound(P.env, spec[sl.species], dh, dl, bc, R);
+                    ea = (short)scale_exp(m);
+                    eb = (short)scale_exp(SIe.amax[0] * (float)SIe.dV * m);
+                }
+                for (int o = 0; o < no; ++o) {
+                    info[off + o] = s | (o << 8) | (no << 16);
+                    eexp[off + o] = ea;
+                    eexp[kMaxNb + off + o] = eb;
+                }
             }
             if (!role_wait(&accfull[buf], (it / nbuf) & 1, P, et, eflag, 2, kEpi)) break;
             tc_fence_after();
@@ -513,12 +567,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     else
 #pragma unroll
                         for (int j = 16; j < 32; ++j) v[j] = 0.f;
+                    // the fp16 scaling is undone here for the row (this lane's TMEM lane) and in
+                    // the scatter for the column (exact: powers of two)
+                    float urow = 1.f, ucol = 1.f;
+                    if constexpr (S::HALF) urow = pow2i(-eexp[min(row0 + lane, kMaxNb - 1)]);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) tl[j * 33 + lane] = v[j];
+                    for (int j = 0; j < 32; ++j) tl[j * 33 + lane] = v[j] * urow;
                     __syncwarp();
                     const int nu = c0 + lane;
                     const bool cv = nu < nb;
                     const int ci = info[cv ? nu : 0];
+                    if constexpr (S::HALF) ucol = pow2i(-eexp[kMaxNb + (cv ? nu : 0)]);
                     const int b = ci & 255, ob = (ci >> 8) & 255, nbo = ci >> 16;
                     // rows in runs of one atom image (warp-uniform): one block lookup per run,
                     // then consecutive block rows are nbo doubles apart
@@ -532,7 +591,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         const int rlim = min(rend, nu - row0 + 1);  // upper triangle: row <= nu
 #pragma unroll 4
                         for (int r2 = r; r2 < rend; ++r2)
-                            if (blk && r2 < rlim) red_add_f64(base + r2 * nbo, f2d_fast(tl[lane * 33 + r2] * u));
+                            if (blk && r2 < rlim) red_add_f64(base + r2 * nbo, f2d_fast(tl[lane * 33 + r2] * ucol));
                         r = rend;
                     }
                     __syncwarp();

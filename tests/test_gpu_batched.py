@@ -39,7 +39,7 @@ def _buffers(items, dev):
     return H, rho
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x6"])
+@pytest.mark.parametrize("prec", ["tf32x3", "fp16x3", "bf16x6"])
 def test_batch_job_matches_single_structure_calls(mix, prec):
     G, items = mix
     dev = torch.device("cuda")
@@ -88,7 +88,10 @@ def test_batched_fp64_runs_per_structure(mix):
 def test_autotune_returns_valid_shapes(mix):
     G, items = mix
     bv, br, tv, tr = G.gint_autotune(items[0]["st"], "tf32x3")
+    # TF32x3 vlocal batches stay at 64 points or fewer (FP32 accumulation error); FP16x3 may use 128
     assert np.prod(bv) <= 64 and np.prod(br) == 128 and bv[2] % 2 == 0 and br[2] % 2 == 0
+    bv16 = G.gint_autotune(items[0]["st"], "fp16x3")[0]
+    assert np.prod(bv16) <= 128 and bv16[2] % 2 == 0
     assert tv > 0 and tr > 0
     # the chosen shapes give a working handle with oracle-level results
     h = G.setup_structure(items[0]["st"], batch=bv, batch_rho=br)
@@ -106,3 +109,64 @@ def test_batch_create_rejects_bad_input(mix):
     H, rho = _buffers(items[:1], dev)
     with pytest.raises(G.GintError):
         G.Batch([items[0]["h"]], [items[0]["V"]], H, prec="fp64")
+
+
+@pytest.fixture(scope="module")
+def batching_job():
+    """The 32-structure batching set (Si cells of 8/16/64/216 atoms x 4 strains, water boxes of
+    8..32 molecules) in one graph-replayed job, FP16x3, with the shapes the autotuner picks once
+    per structure class (the launch configuration of the benchmark's multi-structure line)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2501_08697_gb300 import gint as G
+    from paper_2501_08697_gb300 import synth as S
+    sts = S.batching_set()
+    prec = "fp16x3"
+    shapes = {}
+    for cls in ("si", "water"):
+        rep = max((st for st in sts if st.name.startswith(cls)), key=lambda st: st.npts)
+        shapes[cls] = G.gint_autotune(rep, prec)[:2]
+    dev = torch.device("cuda")
+    items = []
+    for st in sts:
+        bv, br = shapes["si" if st.name.startswith("si") else "water"]
+        h = G.setup_structure(st, batch=bv, batch_rho=br)
+        keys, offs = h.layout()
+        V = S.local_potential(st)
+        DM = S.density_matrix(keys, st.norb_atom, seed=st.seed)
+        items.append(dict(st=st, h=h, keys=keys, offs=offs, Vn=V, DMn=DM, V=torch.from_numpy(V.reshape(-1)).to(dev),
+                          DM=torch.from_numpy(DM).to(dev)))
+    H, rho = _buffers(items, dev)
+    job = G.Batch([x["h"] for x in items], [x["V"] for x in items], H, [x["DM"] for x in items], rho, prec)
+    job.launch()
+    torch.cuda.synchronize()
+    return G, items, [t.cpu().numpy() for t in H], [t.cpu().numpy() for t in rho], shapes
+
+
+def test_batching_set_against_oracle(batching_job):
+    """Every structure of the 32-structure job against the FP64 oracle: structures of at most
+    250k grid points in full (every block, every point); larger ones on 512 seeded blocks from
+    the whole pair list and 20000 seeded grid points.  Tolerance 1e-6 (relative Frobenius)."""
+    from oracle import Oracle
+    G, items, H, rho, shapes = batching_job
+    print("autotuned shapes (vlocal, rho):", shapes)
+    worst = 0.0
+    for x, Hb, rb in zip(items, H, rho):
+        st = x["st"]
+        o = Oracle.from_structure(st)
+        k2, o2 = o.pairs()
+        assert np.array_equal(k2, x["keys"]) and np.array_equal(o2, x["offs"])
+        if st.npts <= 250000:
+            eH = rel_fro(Hb, o.vlocal(x["Vn"]))
+            er = rel_fro(rb, o.rho(x["DMn"]))
+        else:
+            rng = np.random.default_rng(st.seed + 17)
+            sel = np.sort(rng.choice(len(k2), min(512, len(k2)), replace=False))
+            idx = np.concatenate([np.arange(o2[b], o2[b + 1]) for b in sel])
+            eH = rel_fro(Hb[idx], o.vlocal_blocks(x["Vn"], sel))
+            pts = np.sort(rng.choice(st.npts, 20000, replace=False))
+            er = rel_fro(rb[pts], o.rho(x["DMn"], pts))
+        print(f"{st.name}: {st.npts} points, H {eH:.2e} rho {er:.2e}")
+        worst = max(worst, eH, er)
+        assert eH <= 1e-6 and er <= 1e-6, st.name
+    print(f"worst over the 32 structures: {worst:.2e}")

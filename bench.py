@@ -49,8 +49,8 @@ def _peaks():
 # dram__bytes_write.sum from one ncu capture), keyed by the SHA-256 prefix of the kernel sources
 # the counters were taken on: once a kernel source changes, the bench reports traffic = null.
 NCU_TRAFFIC = {
-    # profiles/dram_traffic_si512_tf32x3.md
-    "85e4dee6b452b285": {"si512/tf32x3/rho_force": 227.46e6, "si512/tf32x3/vlocal": 286.02e6},
+    # profiles/dram_k_vlocal_tc_k_rho_tc_si64_fp16x3.md (Si64 counters x 8)
+    "1063b7b728c94328": {"si512/fp16x3/rho_force": 193.3e6, "si512/fp16x3/vlocal": 279.2e6},
 }
 TC_SOURCES = ("gint_tc.cu", "gint_device.cuh", "gint_tcgen05.cuh")
 

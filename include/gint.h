@@ -248,9 +248,10 @@ gint_status gint_block_dot(gint_handle h, const double *A_dev, const double *B_d
  * site (inside an allocator or memory-pool callback, or after a fixed memory budget has been
  * reached).  The paper has no counterpart; this is a service of the library.  Partial sums
  * live in a static device array of 1024 doubles that every GPU loading the library holds
- * until exit; a store of more than 1024 * 65536 values is rejected with GINT_EINVAL.  The
- * first call on a device looks up the array's address (make it before any stream capture).
- * All calls share the array: calls that overlap on the GPU race.  A, B, out: device memory. */
+ * until exit; a store of more than 1024 * 65536 values is rejected with GINT_EINVAL.  Each
+ * call looks up the array's address in the current context.  Errors: GINT_EINVAL for a null
+ * argument or a device other than the handle's.  All calls share the array: calls that
+ * overlap on the GPU race.  A, B, out: device memory. */
 gint_status gint_block_dot_noalloc(gint_handle h, const double *A_dev, const double *B_dev,
                                    double *out_dev, void *stream);
 

@@ -11,6 +11,23 @@ using namespace gint;
 namespace gint {
 cudaError_t launch_mirror(const Plan &P, double *H, cudaStream_t s);
 
+gint_status check_handle(gint_handle h, const char *who)
+{
+    if (!h) {
+        set_error("%s: null handle", who);
+        return GINT_EINVAL;
+    }
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    if (dev != h->device) {
+        set_error("%s: current device %d differs from the handle's device %d", who, dev, h->device);
+        return GINT_EINVAL;
+    }
+    return GINT_OK;
+}
+
+
 SInfo sinfo_for(const gint_handle_s *h, const double *V, double *H, const void *DMS, double *rho, double *F)
 {
     SInfo si{};
@@ -112,21 +129,6 @@ __global__ void k_dot_final(const double *part, int n, double scale, double *out
     if (threadIdx.x == 0) out[0] = sh[0] * scale;
 }
 
-gint_status check_handle(gint_handle h, const char *who)
-{
-    if (!h) {
-        set_error("%s: null handle", who);
-        return GINT_EINVAL;
-    }
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, who);
-    if (dev != h->device) {
-        set_error("%s: current device %d differs from the handle's device %d", who, dev, h->device);
-        return GINT_EINVAL;
-    }
-    return GINT_OK;
-}
 
 bool valid_prec(gint_prec p) { return p >= GINT_FP64 && p <= GINT_FP16X3; }
 

@@ -212,6 +212,8 @@ inline Plan plan_for(const gint_handle_s *h, int which)
 }
 void set_error(const char *fmt, ...);
 gint_status cuda_fail(cudaError_t e, const char *where);
+// GINT_EINVAL (with the message set) unless h is non-null and its device is the current one
+gint_status check_handle(gint_handle h, const char *who);
 // set-up helpers (gint_setup.cpp)
 gint_status build_geometry(gint_handle h, const double *tau, bool update_only);
 // kernel launchers (gint_simt.cu, gint_tc.cu, gint_api.cu)

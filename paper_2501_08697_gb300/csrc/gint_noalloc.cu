@@ -8,13 +8,11 @@
 // file-scope device array instead, so the call itself allocates nothing.
 //
 // The array is a static __device__ symbol: every GPU that loads the library holds
-// kNoAllocPartials doubles (8 KiB) until the process exits.  Its address on a device is
-// looked up once (cudaGetSymbolAddress, with that device current) by the first call on
-// that device; make that first call before any stream capture.  All calls share the
-// array, so calls that overlap on the GPU (e.g. on two streams) race and give wrong sums.
-// Each call overwrites the partials it uses, so nothing needs clearing between calls.
-#include <mutex>
-
+// kNoAllocPartials doubles (8 KiB) until the process exits.  Its address is looked up on
+// every call (cudaGetSymbolAddress in the current context, which allocates nothing), so no
+// address outlives the context it belongs to.  All calls share the array, so calls that
+// overlap on the GPU (e.g. on two streams) race and give wrong sums.  Each call overwrites
+// the partials it uses, so nothing needs clearing between calls.
 #include "gint_internal.h"
 
 namespace {
@@ -22,12 +20,8 @@ namespace {
 constexpr int kNoAllocPartials = 1024;               // partial sums held by the static array
 constexpr int kNoAllocChunk = 65536;                 // values reduced by one block
 constexpr int kNoAllocThreads = 256;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
-
-std::mutex g_mu;
-double *g_addr[kMaxDevices] = {nullptr};
 
 // block b sums A[i] * B[i] over its contiguous chunk [b * kNoAllocChunk, ...) in a fixed order
 __global__ void k_dot_chunks(const double *__restrict__ A, const double *__restrict__ B, int64_t n, double *part)
@@ -65,7 +59,9 @@ __global__ void k_dot_sum(const double *part, int nblk, double *out)
 extern "C" gint_status gint_block_dot_noalloc(gint_handle h, const double *A_dev, const double *B_dev,
                                               double *out_dev, void *stream)
 {
-    if (!h || !A_dev || !B_dev || !out_dev) {
+    gint_status st = gint::check_handle(h, "gint_block_dot_noalloc");
+    if (st != GINT_OK) return st;
+    if (!A_dev || !B_dev || !out_dev) {
         gint::set_error("gint_block_dot_noalloc: null argument");
         return GINT_EINVAL;
     }
@@ -76,26 +72,12 @@ extern "C" gint_status gint_block_dot_noalloc(gint_handle h, const double *A_dev
                         (long long)n, (long long)kNoAllocPartials * kNoAllocChunk, kNoAllocPartials, kNoAllocChunk);
         return GINT_EINVAL;
     }
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return gint::cuda_fail(e, "gint_block_dot_noalloc");
-    if (dev != h->device || dev < 0 || dev >= kMaxDevices) {
-        gint::set_error("gint_block_dot_noalloc: current device %d is not the handle's device %d", dev, h->device);
-        return GINT_EINVAL;
-    }
-    double *part;
-    {
-        // one-time set-up per device: the symbol's device address (host code cannot use the
-        // symbol's name as a device pointer)
-        std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_addr[dev]) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-            if (e != cudaSuccess) return gint::cuda_fail(e, "gint_block_dot_noalloc: cudaGetSymbolAddress");
-            g_addr[dev] = (double *)p;
-        }
-        part = g_addr[dev];
-    }
+    // the symbol's address in the current context (host code cannot use the symbol's name as a
+    // device pointer)
+    void *part_v = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&part_v, g_noalloc_partials);
+    if (e != cudaSuccess) return gint::cuda_fail(e, "gint_block_dot_noalloc: cudaGetSymbolAddress");
+    double *part = (double *)part_v;
     cudaStream_t s = (cudaStream_t)stream;
     const int nblk = n > 0 ? (int)((n + kNoAllocChunk - 1) / kNoAllocChunk) : 0;
     if (nblk > 0) k_dot_chunks<<<nblk, kNoAllocThreads, 0, s>>>(A_dev, B_dev, n, part);

@@ -320,10 +320,11 @@ __host__ __device__ constexpr int shape_of(int nrad, int lpack)
                                                                                              : kShapeGeneric;
 }
 
-// phi of a compiled radial list (same conventions as eval_phi_f32)
+// phi of a compiled radial list (same conventions as eval_phi_f32), times `scale` (applied to
+// the radial values, before the angular factors)
 template <class SH, typename Emit>
 __device__ __forceinline__ void eval_phi_shape(const SpecSh &S, const float4 *__restrict__ coef, float dx, float dy,
-                                               float dz, Emit &&emit)
+                                               float dz, Emit &&emit, float scale = 1.f)
 {
     const float r2 = dx * dx + dy * dy + dz * dz;
     if (!(r2 < S.rcut2)) {
@@ -335,7 +336,7 @@ __device__ __forceinline__ void eval_phi_shape(const SpecSh &S, const float4 *__
         int o = 0;
 #pragma unroll
         for (int ir = 0; ir < SH::nrad; ++ir) {
-            if (SH::l(ir) == 0) emit(o, __ldg(coef + S.coef_off + ir).x * YC<float>::c0);
+            if (SH::l(ir) == 0) emit(o, scale * __ldg(coef + S.coef_off + ir).x * YC<float>::c0);
             else
 #pragma unroll
                 for (int m = 0; m < 2 * SH::l(ir) + 1; ++m) emit(o + m, 0.f);
@@ -356,7 +357,7 @@ __device__ __forceinline__ void eval_phi_shape(const SpecSh &S, const float4 *__
     int o = 0;
 #pragma unroll
     for (int ir = 0; ir < SH::nrad; ++ir) {
-        const float f = c[ir].x + t * (c[ir].y + t * (c[ir].z + t * c[ir].w));
+        const float f = scale * (c[ir].x + t * (c[ir].y + t * (c[ir].z + t * c[ir].w)));
         if (SH::l(ir) == 0) {
             emit(o, f * YC<float>::c0);
         } else if (SH::l(ir) == 1) {

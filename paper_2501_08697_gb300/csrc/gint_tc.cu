@@ -649,7 +649,8 @@ struct RL {
     static constexpr int OFF_KOFF = OFF_POFF + 2 * kMaxBatchPts * 24;               // int [2][64]
     static constexpr int OFF_TBL = OFF_KOFF + 2 * kMaxSlots * 4;                    // int [2][kVTblR^2]
     static constexpr int OFF_KSLOT = OFF_TBL + 2 * kVTblR * kVTblR * 4;             // short [kMaxKCols / 8]
-    static constexpr int OFF_EPSLOT = OFF_KSLOT + kMaxKCols / 8 * 2;                // epilogue PSlot[64]
+    static constexpr int OFF_KTASK = OFF_KSLOT + kMaxKCols / 8 * 2;                 // short [kMaxKCols / 8]
+    static constexpr int OFF_EPSLOT = OFF_KTASK + kMaxKCols / 8 * 2;                // epilogue PSlot[64]
     static constexpr int OFF_EPOFF = OFF_EPSLOT + kMaxSlots * (int)sizeof(PSlot);
     static constexpr int OFF_WIN = OFF_EPOFF + kMaxBatchPts * 24;               // float [epilogue warps][32][32]
     static constexpr int OFF_RPART = OFF_WIN + (kREpi / 32) * 32 * 32 * 4;      // float [kREPQ][128]
@@ -716,6 +717,7 @@ __global__ void __launch_bounds__(kThreadsR, 1)
     int *koffb = reinterpret_cast<int *>(sm + L::OFF_KOFF);
     int *tblb = reinterpret_cast<int *>(sm + L::OFF_TBL);
     short *kslot = reinterpret_cast<short *>(sm + L::OFF_KSLOT);
+    short *ktask = reinterpret_cast<short *>(sm + L::OFF_KTASK);
     PSlot *eps = reinterpret_cast<PSlot *>(sm + L::OFF_EPSLOT);
     float *epoff = reinterpret_cast<float *>(sm + L::OFF_EPOFF);
     float *win = reinterpret_cast<float *>(sm + L::OFF_WIN);
@@ -724,6 +726,7 @@ __global__ void __launch_bounds__(kThreadsR, 1)
     SpecSh *spec = reinterpret_cast<SpecSh *>(sm + L::OFF_SPEC);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::OFF_BAR);
     uint64_t *empty = bars, *accfull = bars + 2, *accempty = bars + 4, *fin = bars + 6, *full = bars + 8;
+    uint64_t *bfull = bars + 10;   // the B operand's bulk copies of a stage have landed
     uint32_t *tmem_base = reinterpret_cast<uint32_t *>(sm + L::OFF_MISC);
     volatile int *pflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 4);
     volatile int *eflag = reinterpret_cast<volatile int *>(sm + L::OFF_MISC + 8);
@@ -741,6 +744,8 @@ __global__ void __launch_bounds__(kThreadsR, 1)
         mbar_init(fin, 1);
         mbar_init(&full[0], 2);   // one arrival from each producer group
         mbar_init(&full[1], 2);
+        mbar_init(&bfull[0], 1);  // the B group's arrival and its copies' bytes
+        mbar_init(&bfull[1], 1);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_base)),
@@ -756,6 +761,7 @@ __global__ void __launch_bounds__(kThreadsR, 1)
         // ------------------------------------------------------------ producers
         const int pt = tid;
         int g = 0;
+        int bph[2] = {0, 0};   // B group: phases of bfull[s] begun
         bool ok = true;
         SInfoCache sic(si0);
         CtaRange cr(P);
@@ -789,7 +795,11 @@ __global__ void __launch_bounds__(kThreadsR, 1)
             const bool tsm = ns <= kVTblR;
             const int ktot = (koffs[ns - 1] + kpad(ps[ns - 1].norb) + KC - 1) / KC * KC;
             // slot of each 8-column group of the padded K axis (-1: a gap): the last slot
-            // starting at or before the group, if the group lies within its padded width
+            // starting at or before the group, if the group lies within its padded width.
+            // ktask: the A task that starts at the group: -1 none (a gap), -2 the group is the
+            // second half of a 16-column segment whose first half's task covers it, else the slot
+            // | 128 when its values can stay in registers across the stage wait (a compiled
+            // evaluator, its padded columns starting at the group and fitting the segment)
             for (int k8 = pt; k8 < ktot / 8; k8 += kRProd) {
                 int lo = 0, hi = ns - 1;
                 while (lo < hi) {
@@ -797,7 +807,16 @@ __global__ void __launch_bounds__(kThreadsR, 1)
                     if (koffs[mid] <= 8 * k8) lo = mid;
                     else hi = mid - 1;
                 }
-                kslot[k8] = (short)(8 * k8 < koffs[lo] + kpad(ps[lo].norb) ? lo : -1);
+                const int ko = koffs[lo], kw = kpad(ps[lo].norb);
+                const int sg = 8 * k8 < ko + kw ? lo : -1;
+                kslot[k8] = (short)sg;
+                int tk = sg;
+                if (sg >= 0) {
+                    if ((k8 & 1) && ko <= 8 * (k8 - 1)) tk = -2;
+                    else if (spec[ps[sg].species].shape != kShapeGeneric && ko == 8 * k8 && kw <= 16 - 8 * (k8 & 1))
+                        tk = sg | 128;
+                }
+                ktask[k8] = (short)tk;
             }
             named_sync(4, kRProd);
             float sA = 1.f;   // fp16: A = phi sA (the density matrix was scaled when it was split)
@@ -821,24 +840,15 @@ __global__ void __launch_bounds__(kThreadsR, 1)
                 const int u = (gt + i * kRHalf) / kMaxBatchPts;
                 return u < (NG + 1) / 2 ? 2 * u : 2 * (u - (NG + 1) / 2) + 1;
             };
-            // A task classes: a slot whose (padded) columns start at its group and fit the
-            // segment, with a compiled evaluator, keeps its values in registers across the wait
-            // for the stage: xe for a task starting at the segment (first group), xo for one
+            // A task classes (ktask): a register task keeps its values in registers across the
+            // wait for the stage: xe for a task starting at the segment (first group), xo for one
             // starting at its second group.  Other tasks are evaluated after the wait.
             auto task_of = [&](int i, int k0, int &gq, int &sg, int &seg0, bool &reg) {
                 gq = unit_group(i);
-                const int g8 = (k0 >> 3) + gq;
-                sg = kslot[g8];
+                const int v = ktask[(k0 >> 3) + gq];
                 seg0 = k0 + (gq >> 1) * 16;
-                reg = false;
-                if (sg < 0) return;
-                if ((gq & 1) && kslot[g8 - 1] == sg) {
-                    sg = -2;   // covered by the task of the group before
-                    return;
-                }
-                const int kw = kpad(ps[sg].norb);
-                reg = spec[ps[sg].species].shape != kShapeGeneric && koffs[sg] == seg0 + 8 * (gq & 1) &&
-                      kw <= 16 - 8 * (gq & 1);
+                reg = v >= 0 && (v & 128);
+                sg = v < 0 ? v : (v & 127);
             };
             for (int ch = 0; ch < nch && ok; ++ch, ++g) {
                 const int stage = g % NS;
@@ -858,12 +868,12 @@ __global__ void __launch_bounds__(kThreadsR, 1)
                         if (gq & 1) {
 #pragma unroll
                             for (int q = 0; q < 8; ++q) xo[q] = 0.f;
-                            if (sp.shape == kShapeSP) eval_phi_shape<ShapeSP>(sp, P.coef32, dx, dy, dz, [&](int o, float v) { xo[o] = v; });
+                            if (sp.shape == kShapeSP) eval_phi_shape<ShapeSP>(sp, P.coef32, dx, dy, dz, [&](int o, float v) { xo[o] = v; }, sA);
                         } else {
 #pragma unroll
                             for (int q = 0; q < 16; ++q) xe[q] = 0.f;
-                            if (sp.shape == kShapeSPD) eval_phi_shape<ShapeSPD>(sp, P.coef32, dx, dy, dz, [&](int o, float v) { xe[o] = v; });
-                            else eval_phi_shape<ShapeSP>(sp, P.coef32, dx, dy, dz, [&](int o, float v) { xe[o] = v; });
+                            if (sp.shape == kShapeSPD) eval_phi_shape<ShapeSPD>(sp, P.coef32, dx, dy, dz, [&](int o, float v) { xe[o] = v; }, sA);
+                            else eval_phi_shape<ShapeSP>(sp, P.coef32, dx, dy, dz, [&](int o, float v) { xe[o] = v; }, sA);
                         }
                     }
                 }
@@ -873,9 +883,10 @@ __global__ void __launch_bounds__(kThreadsR, 1)
                 if (!agrp) {
                     // B: per (term t, core-matrix column j of the chunk, slot b) the rows of slot
                     // b; in the split store the n_b rows of one 16-byte column of block (b, a) are
-                    // adjacent, as they are in shared memory (zeros where the column is a gap or
-                    // the pair has no block).  One task per thread: the 16-byte copies of a warp
-                    // spread over 32 tasks take the fewest copy instructions.
+                    // adjacent, as they are in shared memory, so each is one bulk (TMA) copy of
+                    // 16 n_b bytes that completes its bytes on bfull[stage]; zeros where the
+                    // column is a gap or the pair has no block.  The copies bypass the load/store
+                    // pipeline the orbital evaluations use.
                     for (int w = gt; w < NT * KCM * ns; w += kRBThr) {
                         const int t = w / (KCM * ns), r = w - t * KCM * ns, j = r / ns, b = r - j * ns;
                         const int k = k0 + j * CG, a = kslot[k >> 3];
@@ -886,14 +897,14 @@ __global__ void __launch_bounds__(kThreadsR, 1)
                         if (e >= 0) {
                             const int64_t el = (int64_t)t * SI.dms_plane + e + ((k - koffs[a]) / CG) * nbo * CG;
                             const unsigned char *src = dms + el * L::ESZ;
-                            for (int row = 0; row < nbo; ++row) cp_async16(dst + 16 * row, src + 16 * row);
+                            mbar_expect_tx(&bfull[stage], 16u * (uint32_t)nbo);
+                            bulk_g2s(dst, src, 16u * (uint32_t)nbo, &bfull[stage]);
                         } else {
                             for (int row = 0; row < nbo; ++row)
                                 *reinterpret_cast<uint4 *>(dst + 16 * row) = make_uint4(0, 0, 0, 0);
                         }
                     }
-                    cp_async_commit();
-                    cp_async_wait_all();
+                    ++bph[stage];
                 } else {
                     // A, second half: each task's columns split into the operand row p (register
                     // tasks from their registers, the others evaluated now into a per-thread
@@ -914,14 +925,11 @@ __global__ void __launch_bounds__(kThreadsR, 1)
                         }
                         if (sg < 0 || p >= npb) continue;
                         unsigned char *row = st0 + p * 16;
-                        auto put = [&](int c, const float *x) {   // CG values of column c on
-                            float y[CG];
-#pragma unroll
-                            for (int q = 0; q < CG; ++q) y[q] = x[q] * sA;
+                        auto put = [&](int c, const float *x) {   // CG values (already scaled) of column c on
                             unsigned char *da[NT];
 #pragma unroll
                             for (int t = 0; t < NT; ++t) da[t] = row + t * L::PLA + ((c - k0) / CG) * L::LBO_A;
-                            split_store<S>(y, da);
+                            split_store<S>(x, da);
                         };
                         if (reg) {
                             if (gq & 1) {
@@ -946,17 +954,27 @@ __global__ void __launch_bounds__(kThreadsR, 1)
                         disp(sl, po, dx, dy, dz);
                         eval_phi_f32<false>(spec[sl.species], P.coef32, dx, dy, dz, [&](int o, float v) {
                             const int c = ko + o;
-                            if (c >= clo && c < chi) xl[c - seg0] = v;
+                            if (c >= clo && c < chi) xl[c - seg0] = v * sA;
                         });
                         for (int c = clo; c < chi; c += CG) put(c, xl + (c - seg0));
                     }
                 }
                 fence_async_smem();
                 named_sync(gbar, gthr);
-                if (gt == 0) mbar_arrive(&full[stage]);   // this group's half of chunk g is in place
+                if (gt == 0) {
+                    mbar_arrive(&full[stage]);   // this group's half of chunk g is in place
+                    // every B thread has registered its copies' bytes: the phase now completes
+                    // when they have landed
+                    if (!agrp) mbar_arrive(&bfull[stage]);
+                }
             }
         }
         cp_async_wait_all();   // no copy may be in flight when the CTA exits
+        if (pt == kRHalf) {
+            // bulk copies of the last phase of each stage (consumed already unless a role gave up)
+            for (int st = 0; st < NS; ++st)
+                if (bph[st] > 0 && !mbar_wait(&bfull[st], (uint32_t)((bph[st] - 1) & 1), kDrainBudget)) report_timeout(P);
+        }
     } else if (tid < kREpi0) {
         // ------------------------------------------------------------ MMA issue (one thread)
         if (tid == kRMma) {
@@ -975,7 +993,8 @@ __global__ void __launch_bounds__(kThreadsR, 1)
                 const uint32_t id = idesc<S>(128, npad);
                 for (int ch = 0; ch < nch && ok; ++ch, ++g) {
                     const int stage = g % NS;
-                    ok = !aborted(P) && mbar_wait(&full[stage], (g / NS) & 1, P.spin_limit);
+                    ok = !aborted(P) && mbar_wait(&full[stage], (g / NS) & 1, P.spin_limit) &&
+                         mbar_wait(&bfull[stage], (g / NS) & 1, P.spin_limit);
                     if (ok && ch == 0 && it >= 2)   // the epilogue of batch it - 2 is done
                         ok = !aborted(P) && mbar_wait(&accempty[buf], ((it >> 1) - 1) & 1, P.spin_limit);
                     if (!ok) {

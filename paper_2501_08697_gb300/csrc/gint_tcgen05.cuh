@@ -214,34 +214,34 @@ __device__ __forceinline__ void split_store(const float *x, unsigned char *const
         }
         *reinterpret_cast<float4 *>(dst[0]) = hi;
         *reinterpret_cast<float4 *>(dst[1]) = lo;
-    } else if constexpr (S::HALF) {
-        __align__(16) __half t[S::NT][8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            float r = x[i];
-#pragma unroll
-            for (int k = 0; k < S::NT; ++k) {
-                __half b = __float2half_rn(r);
-                t[k][i] = b;
-                r -= __half2float(b);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < S::NT; ++k) *reinterpret_cast<uint4 *>(dst[k]) = *reinterpret_cast<const uint4 *>(t[k]);
     } else {
-        __align__(16) __nv_bfloat16 t[S::NT][8];
+        // two elements per conversion: term k of elements 2i, 2i + 1 is one packed pair (the
+        // lower address holds element 2i); r - term is exact in FP32
+        uint4 t[S::NT];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            float r = x[i];
+        for (int i = 0; i < 4; ++i) {
+            float a = x[2 * i], b = x[2 * i + 1];
 #pragma unroll
             for (int k = 0; k < S::NT; ++k) {
-                __nv_bfloat16 b = __float2bfloat16_rn(r);
-                t[k][i] = b;
-                r -= __bfloat162float(b);
+                uint32_t w;
+                if constexpr (S::HALF) {
+                    const __half2 h = __floats2half2_rn(a, b);
+                    const float2 f = __half22float2(h);
+                    a -= f.x;
+                    b -= f.y;
+                    w = *reinterpret_cast<const uint32_t *>(&h);
+                } else {
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+                    const float2 f = __bfloat1622float2(h);
+                    a -= f.x;
+                    b -= f.y;
+                    w = *reinterpret_cast<const uint32_t *>(&h);
+                }
+                (&t[k].x)[i] = w;
             }
         }
 #pragma unroll
-        for (int k = 0; k < S::NT; ++k) *reinterpret_cast<uint4 *>(dst[k]) = *reinterpret_cast<const uint4 *>(t[k]);
+        for (int k = 0; k < S::NT; ++k) *reinterpret_cast<uint4 *>(dst[k]) = t[k];
     }
 }
 

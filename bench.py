@@ -282,6 +282,10 @@ def run_ours(args, rank, world):
                 # (2 DFMA per clock per SM sub-partition pair: 2 x 2 x 152 x 2.07 GHz = 1.26 TFLOP/s)
                 "alg_tflops": 2 * info["flops_useful"] / f_tot / 1e12}
         fp64["frac_of_fp64_pipe"] = fp64["alg_tflops"] / (2 * 2 * 152 * 2.070e9 / 1e12)
+        # the per-batch contractions as executed (nb x nb per point; vlocal forms the upper
+        # triangle only), against the same pipe
+        fp64["batch_tflops"] = (0.5 * info["flops_dense"] + info["flops_dense_rho"]) / f_tot / 1e12
+        fp64["batch_frac_of_fp64_pipe"] = fp64["batch_tflops"] / (2 * 2 * 152 * 2.070e9 / 1e12)
         if extras:
             fp64["err_vs_oracle"] = errors("fp64")
         H64, rho64, F64 = H.clone(), rho.clone(), F.clone()

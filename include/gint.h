@@ -148,15 +148,18 @@ gint_status gint_destroy(gint_handle h);
 gint_status gint_block_layout(gint_handle h, int64_t *nblocks, int64_t *nvalues,
                               const int32_t **keys, const int64_t **offsets);
 
+/* The handle's description.  After gint_update_positions, the first call counts flops_useful
+ * again for the new positions (a host pass over every grid point of the vlocal batches). */
 gint_status gint_get_info(gint_handle h, gint_info_t *info);
 
 /* Move the atoms (host tau, natoms*3).  The block list (and with it the layout of H and of the
  * density matrix) must stay the same: if some pair enters or leaves the cutoff, nothing changes
  * and GINT_ESTATE is returned (build a new handle).  The batch -> atom-image lists are rebuilt
- * for the new positions; a decomposition whose lists are unchanged keeps its device arrays and
- * receives the new positions only, one whose lists changed is re-uploaded.  Blocking: the call
- * synchronises with the device before replacing arrays.  A multi-structure job
- * (gint_batch_create) copies the lists when it is created: create it again after a move. */
+ * for the new positions on the host (in parallel over host threads); a decomposition whose lists
+ * are unchanged keeps its device arrays and tables and receives the new slot positions only, one
+ * whose lists changed is re-uploaded.  Blocking: the call synchronises with the device before
+ * replacing arrays.  A multi-structure job (gint_batch_create) copies the lists when it is
+ * created: create it again after a move. */
 gint_status gint_update_positions(gint_handle h, const double *tau);
 
 /* H <- V_mu,nu(R) for the potential V (device, npts doubles).  H (device, nvalues doubles)

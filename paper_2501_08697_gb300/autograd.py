@@ -33,7 +33,7 @@ class GintVlocal(torch.autograd.Function):
         tau_h = tau.detach().to("cpu", torch.float64).numpy().reshape(-1).copy()
         _move_to(handle, tau_h)
         Vc = V.detach().contiguous()
-        H = torch.empty(handle.info["nvalues"], dtype=torch.float64, device=V.device)
+        H = torch.empty(handle.nvalues, dtype=torch.float64, device=V.device)
         G.gint_vlocal(handle, Vc, H, prec)
         ctx.save_for_backward(Vc)
         ctx.handle, ctx.prec, ctx.tau_device, ctx.tau_h = handle, prec, tau.device, tau_h

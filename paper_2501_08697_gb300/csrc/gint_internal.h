@@ -153,6 +153,7 @@ struct gint_handle_s {
     std::vector<int> partner;
     gint::BatchSet bs[2];            // [0] vlocal batches, [1] rho/force batches
     bool relist[2] = {false, false}; // a position update changed that decomposition's lists
+    bool flops_stale = false;        // info.flops_useful predates the last position update
     std::vector<float4> coef32_host; // spline records, as uploaded
     std::vector<float> env_host;     // |phi| envelopes, as uploaded
     void *d_env = nullptr;
@@ -215,7 +216,9 @@ gint_status cuda_fail(cudaError_t e, const char *where);
 // GINT_EINVAL (with the message set) unless h is non-null and its device is the current one
 gint_status check_handle(gint_handle h, const char *who);
 // set-up helpers (gint_setup.cpp)
-gint_status build_geometry(gint_handle h, const double *tau, bool update_only);
+// old: the handle whose positions are being updated (its block list must stay the same), or
+// nullptr at set-up
+gint_status build_geometry(gint_handle h, const double *tau, const gint_handle_s *old);
 // kernel launchers (gint_simt.cu, gint_tc.cu, gint_api.cu)
 cudaError_t launch_vlocal_simt(const Plan &p, bool fp64, const double *V, double *H, cudaStream_t s, int nsm);
 cudaError_t launch_rho_force_simt(const Plan &p, bool fp64, const double *V, const double *DM,

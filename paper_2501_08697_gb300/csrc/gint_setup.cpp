@@ -156,58 +156,105 @@ static bool sphere_meets_batch(const BatchGeom &bg, const double *c, double rc, 
 }
 
 // ---------------------------------------------------------------------------------------
+// Host threads for the set-up loops (the lists of different batches are independent).
+static int host_threads()
+{
+    const unsigned n = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(n, 64u));
+}
+
+// f(begin, end, part) over [0, n) split into contiguous parts, one host thread each; parts are
+// numbered in index order so their outputs concatenate to the serial order.
+template <class F>
+static void parallel_parts(int64_t n, int nparts, F &&f)
+{
+    if (nparts <= 1 || n <= 1) {
+        f((int64_t)0, n, 0);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(nparts);
+    for (int t = 0; t < nparts; ++t)
+        th.emplace_back([&f, n, nparts, t] { f(n * t / nparts, n * (t + 1) / nparts, t); });
+    for (auto &x : th) x.join();
+}
+
+// Block key -> block index (open addressing over the packed keys, which are >= 0).
+struct KeyIndex {
+    std::vector<int64_t> key;
+    std::vector<int> val;
+    uint64_t mask = 0;
+    explicit KeyIndex(const std::vector<int64_t> &packed)
+    {
+        size_t cap = 16;
+        while (cap < 2 * packed.size()) cap <<= 1;
+        key.assign(cap, -1);
+        val.assign(cap, -1);
+        mask = cap - 1;
+        for (size_t i = 0; i < packed.size(); ++i) {
+            uint64_t h = slot_of(packed[i]);
+            while (key[h] != -1) h = (h + 1) & mask;
+            key[h] = packed[i];
+            val[h] = (int)i;
+        }
+    }
+    uint64_t slot_of(int64_t k) const { return ((uint64_t)k * 0x9E3779B97F4A7C15ull >> 17) & mask; }
+    int find(int64_t k) const
+    {
+        for (uint64_t h = slot_of(k);; h = (h + 1) & mask) {
+            if (key[h] == k) return val[h];
+            if (key[h] == -1) return -1;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------------------
+// Position of a slot's atom image relative to its batch origin org: d0 = org - (tau_I + n.A),
+// in FP64 and as an FP32 hi + lo pair.
+static inline void slot_position(Slot &S, const double *org, const double *tau, const int *n, const Geo &G)
+{
+    for (int q = 0; q < 3; ++q) {
+        S.d0[q] = org[q] - (tau[3 * S.atom + q] + n[0] * G.A[q] + n[1] * G.A[3 + q] + n[2] * G.A[6 + q]);
+        S.dh[q] = (float)S.d0[q];
+        S.dl[q] = (float)(S.d0[q] - (double)S.dh[q]);
+    }
+}
+
+static inline void batch_origin(const BatchGeom &bg, int i0, int j0, int k0, double *org)
+{
+    for (int c = 0; c < 3; ++c) org[c] = i0 * bg.h[c] + j0 * bg.h[3 + c] + k0 * bg.h[6 + c];
+}
+
+// ---------------------------------------------------------------------------------------
 // Batches of `out.dims` grid points, each with the atom images whose sphere meets it and the
 // slot-pair -> block table; batches over the orbital or image limits are halved recursively.
+// The base batches are processed in parts of consecutive a1 rows, one host thread each, and the
+// parts concatenated in order (the result does not depend on the number of parts).
+// With `old` (a position update): if every batch keeps its atom-image list, *same is set and
+// out.slots receives old's slots at the new positions (nothing else of out is filled).
 static gint_status build_batches(gint_handle h, const double *tau, const Geo &G, const BatchGeom &bg,
-                                 const std::vector<double> &rc, const std::vector<int64_t> &packed,
+                                 const std::vector<double> &rc, const KeyIndex &kidx,
                                  const std::vector<int64_t> &offsets, const std::vector<uint8_t> &canon,
-                                 const std::vector<int> *soff, BatchSet &out)
+                                 const std::vector<int> *soff, const BatchSet *old, bool *same, BatchSet &out)
 {
     const int natoms = h->natoms;
     const int N1 = h->grid[0], N2 = h->grid[1], N3 = h->grid[2];
     const int B1 = out.dims[0], B2 = out.dims[1], B3 = out.dims[2];
     const int nb1 = (N1 + B1 - 1) / B1, nb2 = (N2 + B2 - 1) / B2, nb3 = (N3 + B3 - 1) / B3;
-    const int64_t nbase = (int64_t)nb1 * nb2 * nb3;
-    std::vector<std::vector<RawSlot>> lists(nbase);
-    for (int I = 0; I < natoms; ++I) {
-        const double *t = tau + 3 * I;
-        int lo[3], hi[3];
-        for (int i = 0; i < 3; ++i) {
-            double s = frac_of(G, t, i);
-            lo[i] = (int)std::floor(-s - rc[I] * G.gn[i]) - 1;
-            hi[i] = (int)std::ceil(1.0 - s + rc[I] * G.gn[i]) + 1;
-        }
-        for (int n1 = lo[0]; n1 <= hi[0]; ++n1)
-            for (int n2 = lo[1]; n2 <= hi[1]; ++n2)
-                for (int n3 = lo[2]; n3 <= hi[2]; ++n3) {
-                    double c[3];
-                    for (int x = 0; x < 3; ++x) c[x] = t[x] + n1 * G.A[x] + n2 * G.A[3 + x] + n3 * G.A[6 + x];
-                    int ilo[3], ihi[3];
-                    bool empty = false;
-                    for (int i = 0; i < 3; ++i) {
-                        double s = frac_of(G, c, i) * h->grid[i];
-                        double ext = rc[I] * G.gn[i] * h->grid[i];
-                        ilo[i] = std::max(0, (int)std::floor(s - ext) - 1);
-                        ihi[i] = std::min(h->grid[i] - 1, (int)std::ceil(s + ext) + 1);
-                        if (ilo[i] > ihi[i]) empty = true;
-                    }
-                    if (empty) continue;
-                    for (int b1 = ilo[0] / B1; b1 <= ihi[0] / B1; ++b1)
-                        for (int b2 = ilo[1] / B2; b2 <= ihi[1] / B2; ++b2)
-                            for (int b3 = ilo[2] / B3; b3 <= ihi[2] / B3; ++b3) {
-                                int i0 = b1 * B1, j0 = b2 * B2, k0 = b3 * B3;
-                                int n1p = std::min(B1, N1 - i0), n2p = std::min(B2, N2 - j0), n3p = std::min(B3, N3 - k0);
-                                double lo3[3], hi3[3], ctr[3], rad;
-                                batch_box(bg, i0, j0, k0, n1p, n2p, n3p, lo3, hi3, ctr, &rad);
-                                if (sphere_meets_batch(bg, c, rc[I], lo3, hi3, ctr, rad))
-                                    lists[((int64_t)b1 * nb2 + b2) * nb3 + b3].push_back({I, {n1, n2, n3}});
-                            }
-                }
-    }
-    struct Work {
-        int i0, j0, k0, n1, n2, n3;
-        std::vector<RawSlot> s;
+    const int limit_nb = out.limit_nb;
+    if (same) *same = false;
+    struct Acc {
+        int i0, j0, k0, n1, n2, n3, r0, ns;   // accepted batch; its slots are raw[r0 .. r0 + ns)
     };
+    struct Part {
+        std::vector<Acc> acc;
+        std::vector<RawSlot> raw;
+        BatchSet s;
+        gint_status st = GINT_OK;
+        char err[256] = {0};
+    };
+    const int nparts = std::min(host_threads(), nb1);
+    std::vector<Part> parts(nparts);
     auto orb_count = [&](const std::vector<RawSlot> &s) {
         int n = 0;
         for (auto &x : s) n += h->norb_atom[x.atom];
@@ -223,125 +270,314 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
         if (a.n[1] != b.n[1]) return a.n[1] > b.n[1];
         return a.n[2] > b.n[2];
     };
-    for (int b1 = 0; b1 < nb1; ++b1)
-        for (int b2 = 0; b2 < nb2; ++b2)
-            for (int b3 = 0; b3 < nb3; ++b3) {
-                std::vector<Work> stack;
-                Work w0{b1 * B1, b2 * B2, b3 * B3, std::min(B1, N1 - b1 * B1), std::min(B2, N2 - b2 * B2),
-                        std::min(B3, N3 - b3 * B3), std::move(lists[((int64_t)b1 * nb2 + b2) * nb3 + b3])};
-                stack.push_back(std::move(w0));
-                while (!stack.empty()) {
-                    Work w = std::move(stack.back());
-                    stack.pop_back();
-                    std::sort(w.s.begin(), w.s.end(), slot_less);
-                    int nb = orb_count(w.s);
-                    if (nb > out.limit_nb || (int)w.s.size() > kMaxSlots) {
-                        // halve the longest axis; a3 halves stay even so batch origins stay even
-                        int dims[3] = {w.n1, w.n2, w.n3};
-                        int ax = -1;
-                        for (int a = 0; a < 3; ++a) {
-                            bool can = (a == 2) ? dims[a] >= 4 : dims[a] >= 2;
-                            if (can && (ax < 0 || dims[a] > dims[ax])) ax = a;
+    // phase 1: the accepted batches and their sorted atom-image lists
+    parallel_parts(nb1, nparts, [&](int64_t r0, int64_t r1, int part) {
+        Part &pt = parts[part];
+        auto fail = [&](const char *fmt, int x, int y) {
+            if (pt.st == GINT_OK) {
+                snprintf(pt.err, sizeof(pt.err), fmt, x, y);
+                pt.st = GINT_EINVAL;
+            }
+        };
+        const int rows = (int)(r1 - r0);
+        std::vector<std::vector<RawSlot>> lists((size_t)rows * nb2 * nb3);
+        for (int I = 0; I < natoms; ++I) {
+            const double *t = tau + 3 * I;
+            int lo[3], hi[3];
+            for (int i = 0; i < 3; ++i) {
+                double s = frac_of(G, t, i);
+                lo[i] = (int)std::floor(-s - rc[I] * G.gn[i]) - 1;
+                hi[i] = (int)std::ceil(1.0 - s + rc[I] * G.gn[i]) + 1;
+            }
+            for (int n1 = lo[0]; n1 <= hi[0]; ++n1)
+                for (int n2 = lo[1]; n2 <= hi[1]; ++n2)
+                    for (int n3 = lo[2]; n3 <= hi[2]; ++n3) {
+                        double c[3];
+                        for (int x = 0; x < 3; ++x) c[x] = t[x] + n1 * G.A[x] + n2 * G.A[3 + x] + n3 * G.A[6 + x];
+                        int ilo[3], ihi[3];
+                        bool empty = false;
+                        for (int i = 0; i < 3; ++i) {
+                            double s = frac_of(G, c, i) * h->grid[i];
+                            double ext = rc[I] * G.gn[i] * h->grid[i];
+                            ilo[i] = std::max(0, (int)std::floor(s - ext) - 1);
+                            ihi[i] = std::min(h->grid[i] - 1, (int)std::ceil(s + ext) + 1);
+                            if (ilo[i] > ihi[i]) empty = true;
                         }
-                        if (ax < 0) {
-                            // cannot split further: accept up to the hard kernel limits
-                            if (nb <= kMaxNb && (int)w.s.size() <= kMaxSlots) goto accept;
-                            set_error("gint_setup: a grid batch sees %d orbitals / %d atom images (limits %d / %d)",
-                                      nb, (int)w.s.size(), kMaxNb, kMaxSlots);
-                            return GINT_EINVAL;
-                        }
-                        int cut = dims[ax] / 2;
-                        if (ax == 2 && (cut % 2)) cut += 1;
-                        Work a = w, b = w;
-                        if (ax == 0) { a.n1 = cut; b.i0 += cut; b.n1 -= cut; }
-                        if (ax == 1) { a.n2 = cut; b.j0 += cut; b.n2 -= cut; }
-                        if (ax == 2) { a.n3 = cut; b.k0 += cut; b.n3 -= cut; }
-                        for (Work *x : {&b, &a}) {
-                            double lo3[3], hi3[3], ctr[3], rad;
-                            batch_box(bg, x->i0, x->j0, x->k0, x->n1, x->n2, x->n3, lo3, hi3, ctr, &rad);
-                            std::vector<RawSlot> keep;
-                            for (auto &s : w.s) {
-                                double c[3];
-                                for (int q = 0; q < 3; ++q)
-                                    c[q] = tau[3 * s.atom + q] + s.n[0] * G.A[q] + s.n[1] * G.A[3 + q] + s.n[2] * G.A[6 + q];
-                                if (sphere_meets_batch(bg, c, rc[s.atom], lo3, hi3, ctr, rad)) keep.push_back(s);
-                            }
-                            x->s = std::move(keep);
-                            stack.push_back(std::move(*x));
-                        }
-                        continue;
-                    }
-                accept:
-                    Batch B{};
-                    B.i0 = w.i0; B.j0 = w.j0; B.k0 = w.k0;
-                    B.dims = w.n1 | (w.n2 << 8) | (w.n3 << 16);
-                    B.slot0 = (int)out.slots.size();
-                    B.nslots = (int)w.s.size();
-                    B.nb = nb;
-                    B.tbl = (int)out.tbl.size();
-                    out.flops_dense += 2.0 * (w.n1 * w.n2 * w.n3) * (double)nb * nb;
-                    out.max_nb = std::max(out.max_nb, nb);
-                    out.max_slots = std::max(out.max_slots, (int)w.s.size());
-                    int off = 0, kcur = 0;
-                    double o[3];
-                    for (int c = 0; c < 3; ++c) o[c] = w.i0 * bg.h[c] + w.j0 * bg.h[3 + c] + w.k0 * bg.h[6 + c];
-                    for (auto &s : w.s) {
-                        // padded K column: slots of up to kKSeg columns do not cross a multiple of kKSeg,
-                        // wider ones start on one
-                        const int kw = kpad(h->norb_atom[s.atom]);
-                        if ((kw <= kKSeg && kcur % kKSeg + kw > kKSeg) || (kw > kKSeg && kcur % kKSeg))
-                            kcur = (kcur / kKSeg + 1) * kKSeg;
-                        out.koff.push_back(kcur);
-                        kcur += kw;
-                    }
-                    out.max_k = std::max(out.max_k, kcur);
-                    for (auto &s : w.s) {
-                        Slot S{};
-                        S.atom = s.atom;
-                        S.species = h->species[s.atom];
-                        S.orb_off = off;
-                        S.norb = h->norb_atom[s.atom];
-                        for (int q = 0; q < 3; ++q) {
-                            S.d0[q] = o[q] - (tau[3 * s.atom + q] + s.n[0] * G.A[q] + s.n[1] * G.A[3 + q] + s.n[2] * G.A[6 + q]);
-                            S.dh[q] = (float)S.d0[q];
-                            S.dl[q] = (float)(S.d0[q] - (double)S.dh[q]);
-                        }
-                        off += S.norb;
-                        out.slots.push_back(S);
-                        out.slot_img.insert(out.slot_img.end(), {s.n[0], s.n[1], s.n[2]});
-                    }
-                    for (size_t ia = 0; ia < w.s.size(); ++ia)
-                        for (size_t ib = 0; ib < w.s.size(); ++ib) {
-                            const RawSlot &sa = w.s[ia], &sb = w.s[ib];
-                            int64_t pk = pack_key(sa.atom, sb.atom, sb.n[0] - sa.n[0], sb.n[1] - sa.n[1], sb.n[2] - sa.n[2]);
-                            auto it = std::lower_bound(packed.begin(), packed.end(), pk);
-                            if (it == packed.end() || *it != pk) {
-                                out.tbl.push_back(-1);
-                                if (soff) out.tbl2.push_back(-1);
-                            } else {
-                                int64_t bi = it - packed.begin();
-                                if (ia <= ib && !canon[bi]) {
-                                    set_error("gint_setup: internal error, slot order breaks the canonical-pair rule");
-                                    return GINT_EINVAL;
+                        if (empty) continue;
+                        const int b1lo = std::max<int>(ilo[0] / B1, (int)r0), b1hi = std::min<int>(ihi[0] / B1, (int)r1 - 1);
+                        const int b2lo = ilo[1] / B2, b2hi = ihi[1] / B2, b3lo = ilo[2] / B3, b3hi = ihi[2] / B3;
+                        if (b1lo > b1hi) continue;
+                        if (bg.ortho) {
+                            // the box distance of an orthogonal cell separates by axis: the same
+                            // sum as box_dist2, from per-row / column / layer squared distances
+                            const double rr = rc[I] * rc[I];
+                            auto d2 = [&](int ax, int b, int Bx, int Nx) {
+                                const int i0 = b * Bx, np = std::min(Bx, Nx - i0);
+                                const double o = i0 * bg.h[4 * ax], e = (np - 1) * bg.h[4 * ax];
+                                const double lo = o + std::min(0.0, e), hi = o + std::max(0.0, e);
+                                const double d = c[ax] < lo ? lo - c[ax] : (c[ax] > hi ? c[ax] - hi : 0.0);
+                                return d * d;
+                            };
+                            double dz2[64];
+                            const int n3c = std::min(b3hi - b3lo + 1, 64);
+                            for (int q = 0; q < n3c; ++q) dz2[q] = d2(2, b3lo + q, B3, N3);
+                            for (int b1 = b1lo; b1 <= b1hi; ++b1) {
+                                const double s1 = 0.0 + d2(0, b1, B1, N1);
+                                if (!(s1 < rr)) continue;
+                                for (int b2 = b2lo; b2 <= b2hi; ++b2) {
+                                    const double s12 = s1 + d2(1, b2, B2, N2);
+                                    if (!(s12 < rr)) continue;
+                                    for (int b3 = b3lo; b3 <= b3hi; ++b3) {
+                                        const double dz = b3 - b3lo < 64 ? dz2[b3 - b3lo] : d2(2, b3, B3, N3);
+                                        if (s12 + dz < rr)
+                                            lists[((size_t)(b1 - r0) * nb2 + b2) * nb3 + b3].push_back({I, {n1, n2, n3}});
+                                    }
                                 }
-                                out.tbl.push_back((int)((offsets[bi] << 1) | canon[bi]));
-                                if (soff) out.tbl2.push_back((*soff)[bi]);
                             }
+                            continue;
                         }
-                    out.batches.push_back(B);
+                        for (int b1 = b1lo; b1 <= b1hi; ++b1)
+                            for (int b2 = b2lo; b2 <= b2hi; ++b2)
+                                for (int b3 = b3lo; b3 <= b3hi; ++b3) {
+                                    int i0 = b1 * B1, j0 = b2 * B2, k0 = b3 * B3;
+                                    int n1p = std::min(B1, N1 - i0), n2p = std::min(B2, N2 - j0), n3p = std::min(B3, N3 - k0);
+                                    double lo3[3], hi3[3], ctr[3], rad;
+                                    batch_box(bg, i0, j0, k0, n1p, n2p, n3p, lo3, hi3, ctr, &rad);
+                                    if (sphere_meets_batch(bg, c, rc[I], lo3, hi3, ctr, rad))
+                                        lists[((size_t)(b1 - r0) * nb2 + b2) * nb3 + b3].push_back({I, {n1, n2, n3}});
+                                }
+                    }
+        }
+        struct Work {
+            int i0, j0, k0, n1, n2, n3;
+            std::vector<RawSlot> s;
+        };
+        for (int b1 = (int)r0; b1 < (int)r1 && pt.st == GINT_OK; ++b1)
+            for (int b2 = 0; b2 < nb2; ++b2)
+                for (int b3 = 0; b3 < nb3; ++b3) {
+                    std::vector<Work> stack;
+                    Work w0{b1 * B1, b2 * B2, b3 * B3, std::min(B1, N1 - b1 * B1), std::min(B2, N2 - b2 * B2),
+                            std::min(B3, N3 - b3 * B3), std::move(lists[((size_t)(b1 - r0) * nb2 + b2) * nb3 + b3])};
+                    stack.push_back(std::move(w0));
+                    while (!stack.empty() && pt.st == GINT_OK) {
+                        Work w = std::move(stack.back());
+                        stack.pop_back();
+                        std::sort(w.s.begin(), w.s.end(), slot_less);
+                        int nb = orb_count(w.s);
+                        if (nb > limit_nb || (int)w.s.size() > kMaxSlots) {
+                            // halve the longest axis; a3 halves stay even so batch origins stay even
+                            int dims[3] = {w.n1, w.n2, w.n3};
+                            int ax = -1;
+                            for (int a = 0; a < 3; ++a) {
+                                bool can = (a == 2) ? dims[a] >= 4 : dims[a] >= 2;
+                                if (can && (ax < 0 || dims[a] > dims[ax])) ax = a;
+                            }
+                            if (ax < 0) {
+                                // cannot split further: accept up to the hard kernel limits
+                                if (nb <= kMaxNb && (int)w.s.size() <= kMaxSlots) goto accept;
+                                fail("gint_setup: a grid batch sees %d orbitals / %d atom images", nb, (int)w.s.size());
+                                break;
+                            }
+                            int cut = dims[ax] / 2;
+                            if (ax == 2 && (cut % 2)) cut += 1;
+                            Work a = w, b = w;
+                            if (ax == 0) { a.n1 = cut; b.i0 += cut; b.n1 -= cut; }
+                            if (ax == 1) { a.n2 = cut; b.j0 += cut; b.n2 -= cut; }
+                            if (ax == 2) { a.n3 = cut; b.k0 += cut; b.n3 -= cut; }
+                            for (Work *x : {&b, &a}) {
+                                double lo3[3], hi3[3], ctr[3], rad;
+                                batch_box(bg, x->i0, x->j0, x->k0, x->n1, x->n2, x->n3, lo3, hi3, ctr, &rad);
+                                std::vector<RawSlot> keep;
+                                for (auto &s : w.s) {
+                                    double c[3];
+                                    for (int q = 0; q < 3; ++q)
+                                        c[q] = tau[3 * s.atom + q] + s.n[0] * G.A[q] + s.n[1] * G.A[3 + q] + s.n[2] * G.A[6 + q];
+                                    if (sphere_meets_batch(bg, c, rc[s.atom], lo3, hi3, ctr, rad)) keep.push_back(s);
+                                }
+                                x->s = std::move(keep);
+                                stack.push_back(std::move(*x));
+                            }
+                            continue;
+                        }
+                    accept:
+                        pt.acc.push_back({w.i0, w.j0, w.k0, w.n1, w.n2, w.n3, (int)pt.raw.size(), (int)w.s.size()});
+                        pt.raw.insert(pt.raw.end(), w.s.begin(), w.s.end());
+                    }
+                }
+    });
+    std::vector<size_t> bat0(nparts + 1, 0);
+    for (int t = 0; t < nparts; ++t) {
+        if (parts[t].st != GINT_OK) {
+            set_error("%s", parts[t].err);
+            return parts[t].st;
+        }
+        bat0[t + 1] = bat0[t] + parts[t].acc.size();
+    }
+    if (bat0[nparts] >= ((size_t)1 << 31)) {
+        set_error("gint_setup: too many batches");
+        return GINT_EINVAL;
+    }
+    // a position update whose lists are all unchanged: the old slots at the new positions
+    if (old && old->batches.size() == bat0[nparts]) {
+        std::vector<int> eq(nparts, 1);
+        parallel_parts(nparts, nparts, [&](int64_t t0, int64_t t1, int) {
+            for (int64_t t = t0; t < t1; ++t) {
+                const Part &pt = parts[t];
+                for (size_t q = 0; q < pt.acc.size() && eq[t]; ++q) {
+                    const Acc &A = pt.acc[q];
+                    const Batch &B = old->batches[bat0[t] + q];
+                    if (B.i0 != A.i0 || B.j0 != A.j0 || B.k0 != A.k0 || B.dims != (A.n1 | (A.n2 << 8) | (A.n3 << 16)) ||
+                        B.nslots != A.ns) {
+                        eq[t] = 0;
+                        break;
+                    }
+                    for (int s = 0; s < A.ns; ++s) {
+                        const RawSlot &r = pt.raw[A.r0 + s];
+                        const int *n = &old->slot_img[3 * ((size_t)B.slot0 + s)];
+                        if (old->slots[B.slot0 + s].atom != r.atom || n[0] != r.n[0] || n[1] != r.n[1] || n[2] != r.n[2]) {
+                            eq[t] = 0;
+                            break;
+                        }
+                    }
                 }
             }
-    if ((int64_t)out.tbl.size() >= ((int64_t)1 << 31) || out.batches.size() >= ((size_t)1 << 31) ||
-        out.slots.size() >= ((size_t)1 << 31)) {
+        });
+        if (std::all_of(eq.begin(), eq.end(), [](int x) { return x != 0; })) {
+            out.slots = old->slots;
+            const size_t nbat = old->batches.size();
+            parallel_parts((int64_t)nbat, host_threads(), [&](int64_t q0, int64_t q1, int) {
+                for (int64_t q = q0; q < q1; ++q) {
+                    const Batch &B = old->batches[q];
+                    double org[3];
+                    batch_origin(bg, B.i0, B.j0, B.k0, org);
+                    for (int s = 0; s < B.nslots; ++s)
+                        slot_position(out.slots[B.slot0 + s], org, tau, &old->slot_img[3 * ((size_t)B.slot0 + s)], G);
+                }
+            });
+            if (same) *same = true;
+            return GINT_OK;
+        }
+    }
+    // phase 2: slot records, padded K offsets and slot-pair block tables of every part
+    parallel_parts(nparts, nparts, [&](int64_t t0, int64_t t1, int) {
+        for (int64_t t = t0; t < t1; ++t) {
+            Part &pt = parts[t];
+            BatchSet &o = pt.s;
+            o.batches.reserve(pt.acc.size());
+            o.slots.reserve(pt.raw.size());
+            o.koff.reserve(pt.raw.size());
+            o.slot_img.reserve(3 * pt.raw.size());
+            for (const Acc &A : pt.acc) {
+                const RawSlot *ws = pt.raw.data() + A.r0;
+                int nb = 0;
+                for (int s = 0; s < A.ns; ++s) nb += h->norb_atom[ws[s].atom];
+                Batch B{};
+                B.i0 = A.i0; B.j0 = A.j0; B.k0 = A.k0;
+                B.dims = A.n1 | (A.n2 << 8) | (A.n3 << 16);
+                B.slot0 = (int)o.slots.size();   // part-local; made global when the parts are joined
+                B.nslots = A.ns;
+                B.nb = nb;
+                B.tbl = (int)o.tbl.size();
+                o.flops_dense += 2.0 * (A.n1 * A.n2 * A.n3) * (double)nb * nb;
+                o.max_nb = std::max(o.max_nb, nb);
+                o.max_slots = std::max(o.max_slots, A.ns);
+                int off = 0, kcur = 0;
+                double org[3];
+                batch_origin(bg, A.i0, A.j0, A.k0, org);
+                for (int s = 0; s < A.ns; ++s) {
+                    // padded K column: slots of up to kKSeg columns do not cross a multiple of kKSeg,
+                    // wider ones start on one
+                    const int kw = kpad(h->norb_atom[ws[s].atom]);
+                    if ((kw <= kKSeg && kcur % kKSeg + kw > kKSeg) || (kw > kKSeg && kcur % kKSeg))
+                        kcur = (kcur / kKSeg + 1) * kKSeg;
+                    o.koff.push_back(kcur);
+                    kcur += kw;
+                }
+                o.max_k = std::max(o.max_k, kcur);
+                for (int s = 0; s < A.ns; ++s) {
+                    Slot S{};
+                    S.atom = ws[s].atom;
+                    S.species = h->species[ws[s].atom];
+                    S.orb_off = off;
+                    S.norb = h->norb_atom[ws[s].atom];
+                    slot_position(S, org, tau, ws[s].n, G);
+                    off += S.norb;
+                    o.slots.push_back(S);
+                    o.slot_img.insert(o.slot_img.end(), {ws[s].n[0], ws[s].n[1], ws[s].n[2]});
+                }
+                for (int ia = 0; ia < A.ns && pt.st == GINT_OK; ++ia)
+                    for (int ib = 0; ib < A.ns; ++ib) {
+                        const RawSlot &sa = ws[ia], &sb = ws[ib];
+                        const int bi = kidx.find(
+                            pack_key(sa.atom, sb.atom, sb.n[0] - sa.n[0], sb.n[1] - sa.n[1], sb.n[2] - sa.n[2]));
+                        if (bi < 0) {
+                            o.tbl.push_back(-1);
+                            if (soff) o.tbl2.push_back(-1);
+                        } else {
+                            if (ia <= ib && !canon[bi]) {
+                                snprintf(pt.err, sizeof(pt.err), "%s",
+                                         "gint_setup: internal error, slot order breaks the canonical-pair rule");
+                                pt.st = GINT_EINVAL;
+                                break;
+                            }
+                            o.tbl.push_back((int)((offsets[bi] << 1) | canon[bi]));
+                            if (soff) o.tbl2.push_back((*soff)[bi]);
+                        }
+                    }
+                o.batches.push_back(B);
+            }
+            std::vector<RawSlot>().swap(pt.raw);
+        }
+    });
+    // join the parts in order
+    std::vector<size_t> sl0(nparts + 1, 0), tb0(nparts + 1, 0);
+    for (int t = 0; t < nparts; ++t) {
+        if (parts[t].st != GINT_OK) {
+            set_error("%s", parts[t].err);
+            return parts[t].st;
+        }
+        sl0[t + 1] = sl0[t] + parts[t].s.slots.size();
+        tb0[t + 1] = tb0[t] + parts[t].s.tbl.size();
+    }
+    if ((int64_t)tb0[nparts] >= ((int64_t)1 << 31) || sl0[nparts] >= ((size_t)1 << 31)) {
         set_error("gint_setup: too many batches / table entries");
         return GINT_EINVAL;
+    }
+    out.batches.resize(bat0[nparts]);
+    out.slots.resize(sl0[nparts]);
+    out.slot_img.resize(3 * sl0[nparts]);
+    out.koff.resize(sl0[nparts]);
+    out.tbl.resize(tb0[nparts]);
+    if (soff) out.tbl2.resize(tb0[nparts]);
+    parallel_parts(nparts, nparts, [&](int64_t t0, int64_t t1, int) {
+        for (int64_t t = t0; t < t1; ++t) {
+            const BatchSet &ps = parts[t].s;
+            for (size_t q = 0; q < ps.batches.size(); ++q) {
+                Batch B = ps.batches[q];
+                B.slot0 += (int)sl0[t];
+                B.tbl += (int)tb0[t];
+                out.batches[bat0[t] + q] = B;
+            }
+            std::copy(ps.slots.begin(), ps.slots.end(), out.slots.begin() + sl0[t]);
+            std::copy(ps.slot_img.begin(), ps.slot_img.end(), out.slot_img.begin() + 3 * sl0[t]);
+            std::copy(ps.koff.begin(), ps.koff.end(), out.koff.begin() + sl0[t]);
+            std::copy(ps.tbl.begin(), ps.tbl.end(), out.tbl.begin() + tb0[t]);
+            if (soff) std::copy(ps.tbl2.begin(), ps.tbl2.end(), out.tbl2.begin() + tb0[t]);
+        }
+    });
+    for (auto &pt : parts) {
+        out.flops_dense += pt.s.flops_dense;
+        out.max_nb = std::max(out.max_nb, pt.s.max_nb);
+        out.max_slots = std::max(out.max_slots, pt.s.max_slots);
+        out.max_k = std::max(out.max_k, pt.s.max_k);
     }
     return GINT_OK;
 }
 
 // ---------------------------------------------------------------------------------------
-gint_status build_geometry(gint_handle h, const double *tau, bool update_only)
+gint_status build_geometry(gint_handle h, const double *tau, const gint_handle_s *old)
 {
+    const bool update_only = old != nullptr;
     const int natoms = h->natoms;
     Geo G = make_geo(h->cell);
     Plan &P = h->plan;
@@ -349,38 +585,52 @@ gint_status build_geometry(gint_handle h, const double *tau, bool update_only)
     std::vector<double> rc(natoms);
     for (int I = 0; I < natoms; ++I) rc[I] = P.sp[h->species[I]].rcut;
 
-    // ---- block list: all (I, J, n) with |tau_J + n.A - tau_I| < rc_I + rc_J
+    // ---- block list: all (I, J, n) with |tau_J + n.A - tau_I| < rc_I + rc_J (rows I in parts,
+    // one host thread each, joined in order)
     std::vector<int32_t> keys;
     std::vector<int64_t> packed;
-    for (int I = 0; I < natoms; ++I) {
-        for (int J = 0; J < natoms; ++J) {
-            double rs = rc[I] + rc[J];
-            double dt[3] = {tau[3 * J] - tau[3 * I], tau[3 * J + 1] - tau[3 * I + 1], tau[3 * J + 2] - tau[3 * I + 2]};
-            int lo[3], hi[3];
-            for (int i = 0; i < 3; ++i) {
-                double s = frac_of(G, dt, i);
-                lo[i] = (int)std::floor(-s - rs * G.gn[i]) - 1;
-                hi[i] = (int)std::ceil(-s + rs * G.gn[i]) + 1;
-            }
-            for (int n1 = lo[0]; n1 <= hi[0]; ++n1)
-                for (int n2 = lo[1]; n2 <= hi[1]; ++n2)
-                    for (int n3 = lo[2]; n3 <= hi[2]; ++n3) {
-                        double v[3];
-                        for (int x = 0; x < 3; ++x) v[x] = dt[x] + n1 * G.A[x] + n2 * G.A[3 + x] + n3 * G.A[6 + x];
-                        if (v[0] * v[0] + v[1] * v[1] + v[2] * v[2] < rs * rs) {
-                            if (std::abs(n1) > 63 || std::abs(n2) > 63 || std::abs(n3) > 63) {
-                                set_error("gint_setup: periodic image index beyond 63 (cell too small for rcut)");
-                                return GINT_EINVAL;
-                            }
-                            keys.insert(keys.end(), {I, J, n1, n2, n3});
-                            packed.push_back(pack_key(I, J, n1, n2, n3));
-                        }
+    {
+        const int nparts = std::min(host_threads(), natoms);
+        std::vector<std::vector<int32_t>> pkeys(nparts);
+        std::vector<std::vector<int64_t>> ppacked(nparts);
+        std::vector<int> bad(nparts, 0);
+        parallel_parts(natoms, nparts, [&](int64_t i0, int64_t i1, int part) {
+            for (int I = (int)i0; I < (int)i1 && !bad[part]; ++I) {
+                for (int J = 0; J < natoms; ++J) {
+                    double rs = rc[I] + rc[J];
+                    double dt[3] = {tau[3 * J] - tau[3 * I], tau[3 * J + 1] - tau[3 * I + 1], tau[3 * J + 2] - tau[3 * I + 2]};
+                    int lo[3], hi[3];
+                    for (int i = 0; i < 3; ++i) {
+                        double s = frac_of(G, dt, i);
+                        lo[i] = (int)std::floor(-s - rs * G.gn[i]) - 1;
+                        hi[i] = (int)std::ceil(-s + rs * G.gn[i]) + 1;
                     }
+                    for (int n1 = lo[0]; n1 <= hi[0]; ++n1)
+                        for (int n2 = lo[1]; n2 <= hi[1]; ++n2)
+                            for (int n3 = lo[2]; n3 <= hi[2]; ++n3) {
+                                double v[3];
+                                for (int x = 0; x < 3; ++x) v[x] = dt[x] + n1 * G.A[x] + n2 * G.A[3 + x] + n3 * G.A[6 + x];
+                                if (v[0] * v[0] + v[1] * v[1] + v[2] * v[2] < rs * rs) {
+                                    if (std::abs(n1) > 63 || std::abs(n2) > 63 || std::abs(n3) > 63) bad[part] = 1;
+                                    pkeys[part].insert(pkeys[part].end(), {I, J, n1, n2, n3});
+                                    ppacked[part].push_back(pack_key(I, J, n1, n2, n3));
+                                }
+                            }
+                }
+            }
+        });
+        for (int t = 0; t < nparts; ++t) {
+            if (bad[t]) {
+                set_error("gint_setup: periodic image index beyond 63 (cell too small for rcut)");
+                return GINT_EINVAL;
+            }
+            keys.insert(keys.end(), pkeys[t].begin(), pkeys[t].end());
+            packed.insert(packed.end(), ppacked[t].begin(), ppacked[t].end());
         }
     }
     const int64_t nblocks = (int64_t)packed.size();
     if (update_only) {
-        if (keys != h->keys) {
+        if (keys != old->keys) {
             set_error("gint_update_positions: block list changed; build a new handle");
             return GINT_ESTATE;
         }
@@ -406,17 +656,18 @@ gint_status build_geometry(gint_handle h, const double *tau, bool update_only)
         set_error("gint_setup: padded block store of %lld values exceeds 2^30", (long long)splane);
         return GINT_EINVAL;
     }
+    const KeyIndex kidx(packed);
     std::vector<int> partner(nblocks);
     std::vector<uint8_t> canon(nblocks);
     for (int64_t b = 0; b < nblocks; ++b) {
         const int32_t *k = &keys[5 * b];
         int64_t pk = pack_key(k[1], k[0], -k[2], -k[3], -k[4]);
-        auto it = std::lower_bound(packed.begin(), packed.end(), pk);
-        if (it == packed.end() || *it != pk) {
+        const int pb = kidx.find(pk);
+        if (pb < 0) {
             set_error("gint_setup: internal error, partner block missing");
             return GINT_EINVAL;
         }
-        partner[b] = (int)(it - packed.begin());
+        partner[b] = pb;
         canon[b] = packed[b] <= pk;
     }
 
@@ -429,54 +680,27 @@ gint_status build_geometry(gint_handle h, const double *tau, bool update_only)
     for (int i = 0; i < 3; ++i)
         for (int c = 0; c < 3; ++c) bg.h[3 * i + c] = h->cell[3 * i + c] / h->grid[i];
     BatchSet sets[2];
+    bool same[2] = {false, false};
     const int *dims[2] = {h->opt.batch, h->opt.batch_rho};
     for (int w = 0; w < 2; ++w) {
         for (int i = 0; i < 3; ++i) sets[w].dims[i] = dims[w][i];
         // vlocal batches of up to 64 points stay within 192 orbitals (two accumulators fit in
         // tensor memory); larger ones use the full 256 with one accumulator
         sets[w].limit_nb = (w == 0 && dims[w][0] * dims[w][1] * dims[w][2] <= 64) ? 192 : kMaxNb;
-        gint_status st = build_batches(h, tau, G, bg, rc, packed, offsets, canon, w == 1 ? &soff : nullptr, sets[w]);
+        gint_status st = build_batches(h, tau, G, bg, rc, kidx, offsets, canon, w == 1 ? &soff : nullptr,
+                                       update_only ? &old->bs[w] : nullptr, &same[w], sets[w]);
         if (st != GINT_OK) return st;
-        if (sets[w].max_k + 32 > kMaxKCols) {
+        if (!same[w] && sets[w].max_k + 32 > kMaxKCols) {
             set_error("gint_setup: a batch's padded orbital columns (%d) exceed %d", sets[w].max_k, kMaxKCols - 32);
             return GINT_EINVAL;
         }
     }
-    // useful flops: 2 n(r)^2 per point, n(r) = orbitals whose sphere contains r (exact count
-    // per point from the vlocal decomposition)
-    double flops_useful = 0.0;
-    for (auto &B : sets[0].batches) {
-        int n1 = B.dims & 255, n2 = (B.dims >> 8) & 255, n3 = (B.dims >> 16) & 255;
-        for (int a = 0; a < n1; ++a)
-            for (int b = 0; b < n2; ++b)
-                for (int c = 0; c < n3; ++c) {
-                    double off[3];
-                    for (int q = 0; q < 3; ++q) off[q] = a * bg.h[q] + b * bg.h[3 + q] + c * bg.h[6 + q];
-                    int n = 0;
-                    for (int s = 0; s < B.nslots; ++s) {
-                        const Slot &S = sets[0].slots[B.slot0 + s];
-                        double d[3] = {S.d0[0] + off[0], S.d0[1] + off[1], S.d0[2] + off[2]};
-                        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                        if (r2 < rc[S.atom] * rc[S.atom]) n += S.norb;
-                    }
-                    flops_useful += 2.0 * n * (double)n;
-                }
-    }
     if (update_only) {
-        // a decomposition whose atom-image lists are unchanged keeps its device arrays and gets
-        // new slot positions only; one whose lists changed is replaced as a whole
+        // a decomposition whose atom-image lists are unchanged gets new slot positions only
+        // (sets[w] holds just the slots); one whose lists changed is replaced as a whole
         for (int w = 0; w < 2; ++w) {
-            const BatchSet &o = h->bs[w], &n = sets[w];
-            bool same = o.batches.size() == n.batches.size() && o.slot_img == n.slot_img && o.tbl == n.tbl &&
-                        o.slots.size() == n.slots.size();
-            for (size_t i = 0; same && i < n.slots.size(); ++i) same = o.slots[i].atom == n.slots[i].atom;
-            if (same) {
-                h->bs[w].slots = std::move(sets[w].slots);
-                h->relist[w] = false;
-            } else {
-                h->bs[w] = std::move(sets[w]);
-                h->relist[w] = true;
-            }
+            h->bs[w] = std::move(sets[w]);
+            h->relist[w] = !same[w];
         }
     } else {
         h->keys = std::move(keys);
@@ -487,29 +711,70 @@ gint_status build_geometry(gint_handle h, const double *tau, bool update_only)
         for (int w = 0; w < 2; ++w) h->bs[w] = std::move(sets[w]);
     }
     h->tau.assign(tau, tau + 3 * natoms);
+    (void)rows;
+    (void)nblocks;
+    (void)N1; (void)N2; (void)N3;
+    h->plan.dV = std::fabs(G.det) / ((double)N1 * N2 * N3);
+    for (int i = 0; i < 3; ++i)
+        for (int c = 0; c < 3; ++c) h->plan.h[3 * i + c] = bg.h[3 * i + c];
+    return GINT_OK;
+}
+
+// useful flops of the handle's vlocal decomposition: 2 n(r)^2 per point, n(r) = orbitals whose
+// sphere contains r (exact count per point); per batch in parallel, summed in batch order
+static double useful_flops(const gint_handle_s *h)
+{
+    const BatchSet &bs = h->bs[0];
+    std::vector<double> fb(bs.batches.size(), 0.0);
+    parallel_parts((int64_t)bs.batches.size(), host_threads(), [&](int64_t q0, int64_t q1, int) {
+        for (int64_t q = q0; q < q1; ++q) {
+            const Batch &B = bs.batches[q];
+            int n1 = B.dims & 255, n2 = (B.dims >> 8) & 255, n3 = (B.dims >> 16) & 255;
+            double f = 0.0;
+            for (int a = 0; a < n1; ++a)
+                for (int b = 0; b < n2; ++b)
+                    for (int c = 0; c < n3; ++c) {
+                        double off[3];
+                        for (int x = 0; x < 3; ++x) off[x] = a * h->plan.h[x] + b * h->plan.h[3 + x] + c * h->plan.h[6 + x];
+                        int n = 0;
+                        for (int s = 0; s < B.nslots; ++s) {
+                            const Slot &S = bs.slots[B.slot0 + s];
+                            const double rc = h->plan.sp[S.species].rcut;
+                            double d[3] = {S.d0[0] + off[0], S.d0[1] + off[1], S.d0[2] + off[2]};
+                            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                            if (r2 < rc * rc) n += S.norb;
+                        }
+                        f += 2.0 * n * (double)n;
+                    }
+            fb[q] = f;
+        }
+    });
+    double t = 0.0;
+    for (double f : fb) t += f;
+    return t;
+}
+
+// the handle's description (all but flops_useful, see useful_flops)
+static void fill_info(gint_handle h)
+{
     gint_info_t &info = h->info;
-    info.npts = (int64_t)N1 * N2 * N3;
+    const int64_t nblocks = (int64_t)h->keys.size() / 5;
+    info.npts = (int64_t)h->grid[0] * h->grid[1] * h->grid[2];
     info.nblocks = nblocks;
     info.nvalues = h->offsets[nblocks];
     info.nbatches = (int64_t)h->bs[0].batches.size();
     info.nslots = (int64_t)h->bs[0].slots.size();
     info.max_orbitals = h->bs[0].max_nb;
     info.max_slots = h->bs[0].max_slots;
-    info.dV = std::fabs(G.det) / (double)info.npts;
-    info.flops_useful = flops_useful;
+    info.dV = h->plan.dV;
     info.flops_dense = h->bs[0].flops_dense;
     info.nbatches_rho = (int64_t)h->bs[1].batches.size();
     info.max_orbitals_rho = h->bs[1].max_nb;
     info.nbasis = 0;
-    for (int I = 0; I < natoms; ++I) info.nbasis += h->norb_atom[I];
+    for (int I = 0; I < h->natoms; ++I) info.nbasis += h->norb_atom[I];
     info.flops_dense_rho = h->bs[1].flops_dense;
-    (void)rows;
     h->plan.nblocks = nblocks;
     h->plan.nvalues = info.nvalues;
-    h->plan.dV = info.dV;
-    for (int i = 0; i < 3; ++i)
-        for (int c = 0; c < 3; ++c) h->plan.h[3 * i + c] = bg.h[3 * i + c];
-    return GINT_OK;
 }
 
 // Estimated cost of one batch in a persistent tensor-core kernel.  The producers evaluate every
@@ -802,11 +1067,13 @@ extern "C" gint_status gint_setup(gint_handle *out, const double cell[9], int na
     h->norb_atom.resize(natoms);
     for (int i = 0; i < natoms; ++i) h->norb_atom[i] = P.sp[species[i]].norb;
 
-    gint_status st = build_geometry(h, tau, false);
+    gint_status st = build_geometry(h, tau, nullptr);
     if (st != GINT_OK) {
         delete h;
         return st;
     }
+    fill_info(h);
+    h->info.flops_useful = useful_flops(h);
     if ((e = upload(&h->d_coef64, coef64)) != cudaSuccess || (e = upload(&h->d_coef32, coef32)) != cudaSuccess) {
         free_dev(h);
         delete h;
@@ -915,6 +1182,10 @@ extern "C" gint_status gint_get_info(gint_handle h, gint_info_t *info)
         set_error("gint_get_info: null argument");
         return GINT_EINVAL;
     }
+    if (h->flops_stale) {
+        h->info.flops_useful = useful_flops(h);
+        h->flops_stale = false;
+    }
     *info = h->info;
     return GINT_OK;
 }
@@ -930,7 +1201,8 @@ extern "C" gint_status gint_update_positions(gint_handle h, const double *tau)
             set_error("gint_update_positions: non-finite position");
             return GINT_EINVAL;
         }
-    // build into a scratch copy so a topology change leaves the handle untouched
+    // build into a scratch handle (compared with this one) so a topology change leaves the
+    // handle untouched
     gint_handle_s tmp;
     tmp.plan = h->plan;
     memcpy(tmp.cell, h->cell, sizeof(tmp.cell));
@@ -939,16 +1211,9 @@ extern "C" gint_status gint_update_positions(gint_handle h, const double *tau)
     tmp.nspecies = h->nspecies;
     tmp.species = h->species;
     tmp.norb_atom = h->norb_atom;
-    tmp.keys = h->keys;
-    tmp.offsets = h->offsets;
-    for (int w = 0; w < 2; ++w) {
-        tmp.bs[w].batches = h->bs[w].batches;
-        tmp.bs[w].slots = h->bs[w].slots;
-        tmp.bs[w].slot_img = h->bs[w].slot_img;
-        tmp.bs[w].tbl = h->bs[w].tbl;
-    }
     tmp.opt = h->opt;
-    gint_status st = build_geometry(&tmp, tau, true);
+    for (int w = 0; w < 2; ++w) tmp.bs[w].limit_nb = h->bs[w].limit_nb;
+    gint_status st = build_geometry(&tmp, tau, h);
     if (st != GINT_OK) return st;
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(e, "gint_update_positions");
@@ -970,8 +1235,9 @@ extern "C" gint_status gint_update_positions(gint_handle h, const double *tau)
         }
     }
     h->tau = std::move(tmp.tau);
-    h->info = tmp.info;
     h->plan.dV = tmp.plan.dV;
+    fill_info(h);
+    h->flops_stale = true;   // recounted when the description is next read
     return upload_geometry(h);
 }
 

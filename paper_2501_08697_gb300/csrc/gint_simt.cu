@@ -20,8 +20,10 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kSubPts = 64;     // points per shared-memory sub-batch (vlocal)
-constexpr int kRhoPts = 32;     // points per sub-batch (rho/force)
+constexpr int kRhoPts = 128;    // most points per sub-batch (rho/force)
 constexpr int kDChunk = 16;     // rows of D staged at a time (rho/force)
+constexpr int kRhoTile = 8192;  // elements of the Phi / Psi tile (points x padded orbitals)
+constexpr int kDRegs = kDChunk * kMaxNb / kThreads;   // staged D values per thread
 
 struct SlotSh {
     int atom, species, orb_off, norb;
@@ -177,9 +179,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char *oidx = oslot + kMaxNb;
     double *fsl = reinterpret_cast<double *>(oidx + kMaxNb);   // [kMaxSlots][3] force partials
     double *rhos = fsl + 3 * kMaxSlots;                         // [kRhoPts]
-    T *Phi = reinterpret_cast<T *>(rhos + kRhoPts);             // [kRhoPts][kMaxNb]
-    T *Psi = Phi + kRhoPts * kMaxNb;                            // [kRhoPts][kMaxNb]
-    T *Ds = Psi + kRhoPts * kMaxNb;                             // [kDChunk][kMaxNb]
+    T *Phi = reinterpret_cast<T *>(rhos + kRhoPts);             // [np_sub][npad]; Psi after the product
+    T *Ds = Phi + kRhoTile;                                     // [2][kDChunk][npad]
 
     const int tid = threadIdx.x;
     // strain derivative: [0..8] Sum V grad_a phi . Psi d_b, [9] Sum V rho (this thread)
@@ -192,6 +193,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         unpack_dims(B.dims, n1, n2, n3);
         const int ns = B.nslots, nb = B.nb, npb = n1 * n2 * n3;
         const int npad = (nb + 7) & ~7;
+        // Psi = Phi D tiling: thread (tp, tc) owns points 4 tp .. 4 tp + 3 and columns
+        // 8 tc .. 8 tc + 7; a sub-batch has as many points as the 256 threads cover, so every
+        // multiply-add of a sub-batch lies inside the padded orbital range
+        const int ncg = npad > 0 ? npad / 8 : 1;
+        const int ngrp = kThreads / ncg;
+        const int nsub = min(kRhoPts, 4 * ngrp);
         __syncthreads();
         for (int s = tid; s < ns; s += kThreads) {
             Slot S = P.slots[B.slot0 + s];
@@ -206,12 +213,36 @@ __global__ void __launch_bounds__(kThreads, 1)
                 oslot[sl[s].orb_off + o] = (unsigned char)s;
                 oidx[sl[s].orb_off + o] = (unsigned char)o;
             }
-        for (int p0 = 0; p0 < npb; p0 += kRhoPts) {
-            const int np = min(kRhoPts, npb - p0);
+        // D rows k0 .. k0 + kDChunk - 1 (all columns; zero outside the batch) into registers
+        T dv[kDRegs];
+        auto gather = [&](int k0) {
+#pragma unroll
+            for (int q = 0; q < kDRegs; ++q) {
+                const int e = tid + q * kThreads;
+                const int kr = e / npad, nu = e - kr * npad;
+                const int mu = k0 + kr;
+                T v = T(0);
+                if (kr < kDChunk && mu < nb && nu < nb) {
+                    const int a = oslot[mu], b = oslot[nu];
+                    const int t = tbl[a * ns + b];
+                    if (t >= 0) v = (T)DM[(t >> 1) + oidx[mu] * sl[b].norb + oidx[nu]];
+                }
+                dv[q] = v;
+            }
+        };
+        auto stage = [&](T *dst) {
+#pragma unroll
+            for (int q = 0; q < kDRegs; ++q) {
+                const int e = tid + q * kThreads;
+                if (e < kDChunk * npad) dst[e] = dv[q];
+            }
+        };
+        for (int p0 = 0; p0 < npb; p0 += nsub) {
+            const int np = min(nsub, npb - p0);
             __syncthreads();
-            for (int w = tid; w < kRhoPts * ns; w += kThreads) {
+            for (int w = tid; w < nsub * ns; w += kThreads) {
                 const int p = w / ns, s = w - p * ns;
-                T *row = Phi + p * kMaxNb + sl[s].orb_off;
+                T *row = Phi + p * npad + sl[s].orb_off;
                 if (p >= np) {
                     for (int o = 0; o < sl[s].norb; ++o) row[o] = T(0);
                     continue;
@@ -232,52 +263,50 @@ __global__ void __launch_bounds__(kThreads, 1)
                     eval_orbitals<float, false>(P, sl[s].species, dx, dy, dz, [&](int o, float v) { row[o] = v; });
                 }
             }
-            for (int w = tid; w < kRhoPts * (npad - nb); w += kThreads) {
+            for (int w = tid; w < nsub * (npad - nb); w += kThreads) {
                 const int p = w / (npad - nb), q = w - p * (npad - nb);
-                Phi[p * kMaxNb + nb + q] = T(0);
+                Phi[p * npad + nb + q] = T(0);
             }
-            if (tid < kRhoPts) rhos[tid] = 0.0;
-            // Psi = Phi D_b: thread (tp, tc) owns points tp*4..+3, columns tc*8..+7
-            const int tp = tid >> 5, tc = tid & 31;
+            for (int p = tid; p < nsub; p += kThreads) rhos[p] = 0.0;
+            const bool gemm = tid < ngrp * ncg && npad > 0;
+            const int tp = tid / ncg, tc = tid - (tid / ncg) * ncg;
             T acc[4][8];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
-            for (int k0 = 0; k0 < npad; k0 += kDChunk) {
+            // the next chunk's D values are loaded while the current chunk is multiplied
+            if (npad > 0) {
+                gather(0);
+                stage(Ds);
+            }
+            for (int k0 = 0, buf = 0; k0 < npad; k0 += kDChunk, buf ^= 1) {
                 __syncthreads();
-                // gather D rows k0 .. k0+kDChunk-1 (all columns), zero outside the batch
-                for (int e = tid; e < kDChunk * npad; e += kThreads) {
-                    const int kr = e / npad, nu = e - kr * npad;
-                    const int mu = k0 + kr;
-                    T v = T(0);
-                    if (mu < nb && nu < nb) {
-                        const int a = oslot[mu], b = oslot[nu];
-                        const int t = tbl[a * ns + b];
-                        if (t >= 0) v = (T)DM[(t >> 1) + oidx[mu] * sl[b].norb + oidx[nu]];
-                    }
-                    Ds[kr * kMaxNb + nu] = v;
-                }
-                __syncthreads();
+                const bool more = k0 + kDChunk < npad;
+                if (more) gather(k0 + kDChunk);
+                const T *D0 = Ds + buf * kDChunk * npad;
                 const int kmax = min(kDChunk, npad - k0);
-                for (int kr = 0; kr < kmax; ++kr) {
-                    T pa[4], db[8];
+                if (gemm && 4 * tp < nsub)
+                    for (int kr = 0; kr < kmax; ++kr) {
+                        T pa[4], db[8];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) pa[i] = Phi[(tp * 4 + i) * kMaxNb + k0 + kr];
+                        for (int i = 0; i < 4; ++i) pa[i] = Phi[(tp * 4 + i) * npad + k0 + kr];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) db[j] = (tc * 8 + j < npad) ? Ds[kr * kMaxNb + tc * 8 + j] : T(0);
+                        for (int j = 0; j < 8; ++j) db[j] = D0[kr * npad + tc * 8 + j];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                        for (int i = 0; i < 4; ++i)
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) acc[i][j] = fma(pa[i], db[j], acc[i][j]);
-                }
+                            for (int j = 0; j < 8; ++j) acc[i][j] = fma(pa[i], db[j], acc[i][j]);
+                    }
+                if (more) stage(Ds + (buf ^ 1) * kDChunk * npad);
             }
             __syncthreads();
+            if (gemm && 4 * tp < nsub)
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (tc * 8 + j < npad) Psi[(tp * 4 + i) * kMaxNb + tc * 8 + j] = acc[i][j];
+                    for (int j = 0; j < 8; ++j) Phi[(tp * 4 + i) * npad + tc * 8 + j] = acc[i][j];
+            const T *Psi = Phi;
             __syncthreads();
             // per (point, slot): rho and force contributions with recomputed (grad) orbitals
             for (int w = tid; w < np * ns; w += kThreads) {
@@ -286,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int c = lp % n3, b = (lp / n3) % n2, a = lp / (n3 * n2);
                 double off[3];
                 point_offset64(P, a, b, c, off);
-                const T *prow = Psi + p * kMaxNb + sl[s].orb_off;
+                const T *prow = Psi + p * npad + sl[s].orb_off;
                 T racc = T(0), gx = T(0), gy = T(0), gz = T(0);
                 T ddx, ddy, ddz;   // displacement r - tau - R of this (point, atom image)
                 if constexpr (sizeof(T) == 8) {
@@ -379,7 +408,7 @@ template <typename T>
 size_t rho_smem()
 {
     return sizeof(SlotSh) * kMaxSlots + sizeof(int) * kMaxSlots * kMaxSlots + 2 * kMaxNb +
-           sizeof(double) * (3 * kMaxSlots + kRhoPts) + sizeof(T) * (2 * kRhoPts + kDChunk) * kMaxNb;
+           sizeof(double) * (3 * kMaxSlots + kRhoPts) + sizeof(T) * (kRhoTile + 2 * kDChunk * kMaxNb);
 }
 
 template <typename K>

@@ -614,9 +614,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 // Psi_b = Phi_b D_b with M = 128 points, N = the batch's orbitals (unpadded, TMEM columns) and K
 // = the batch's orbitals in the padded K layout (every slot rounded up to 8 columns, see kpad).
 // The density matrix arrives pre-split: a per-call kernel writes its NT terms (scaled for fp16)
-// into a padded store in which every block row starts on 16 bytes, so the B operand of a chunk
-// is assembled from 16-byte asynchronous copies (one per row and core-matrix column) with no
-// arithmetic; the producers' only CUDA-core work is the orbital evaluation of the A operand.
+// into a padded store in which the rows of one 16-byte block column are adjacent, so the B
+// operand of a chunk is assembled from bulk copies (one per term, core-matrix column and slot)
+// with no arithmetic; the producers' only CUDA-core work is the orbital evaluation of the A
+// operand.
 //
 // Operand layout (K-major, no swizzle): core matrices of 8 rows x 16 bytes stored densely, the
 // 8-row groups of one core-matrix column adjacent (SBO = 128 bytes) and the KCM columns of a

@@ -148,10 +148,18 @@ class Handle:
     def __init__(self, ptr, natoms):
         self._ptr = C.c_void_p(ptr)
         self.natoms = natoms
-        info = _Info()
-        _check(load().gint_get_info(self._ptr, C.byref(info)))
-        self.info = {k: getattr(info, k) for k, _ in _Info._fields_}
+        self._info = None
         self._layout = None
+        self.nvalues = self.info["nvalues"]   # the block list, hence nvalues, is fixed for the handle
+
+    @property
+    def info(self):
+        """gint_get_info as a dict (read again after a position update)."""
+        if self._info is None:
+            info = _Info()
+            _check(load().gint_get_info(self._ptr, C.byref(info)))
+            self._info = {k: getattr(info, k) for k, _ in _Info._fields_}
+        return self._info
 
     @property
     def ptr(self):
@@ -230,9 +238,7 @@ def gint_update_positions(h: Handle, tau):
     tau = np.ascontiguousarray(tau, np.float64).reshape(-1)
     _check(load().gint_update_positions(h.ptr, tau.ctypes.data_as(C.POINTER(C.c_double))))
     h._layout = None
-    info = _Info()
-    _check(load().gint_get_info(h.ptr, C.byref(info)))
-    h.info = {k: getattr(info, k) for k, _ in _Info._fields_}
+    h._info = None
 
 
 def gint_vlocal(h: Handle, V, H, prec="fp64", stream=None):

@@ -404,3 +404,21 @@ def test_blockwise_forms_match_pointwise_sums(si8_small):
         tau[3, 1] += sgn * h
         Ls.append((DM * Oracle(st.cell, st.species, tau, st.tables, st.grid).vlocal(V)).sum())
     assert (Ls[0] - Ls[1]) / (2 * h) == pytest.approx(ga[3, 1], rel=1e-6, abs=1e-9 * np.abs(ga).max())
+
+
+def test_oracle_reproduces_golden_fixture():
+    """Regression guard: the oracle, pinned by the tests above, still gives the values stored in
+    tests/golden/water1_vacuum.txt (V_mu,nu(R), rho at seeded points, the Pulay force and the
+    charge of one water molecule; written from the oracle by tests/golden/make_golden.py)."""
+    import importlib.util
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    stored = mg.read(os.path.join(here, "water1_vacuum.txt"))
+    now = mg.golden_values()
+    for k, v in stored.items():
+        assert now[k].shape == v.shape, k
+        scale = max(np.abs(v).max(), 1e-300)
+        assert np.abs(now[k] - v).max() <= 1e-12 * scale, k

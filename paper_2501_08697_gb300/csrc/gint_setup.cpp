@@ -12,6 +12,7 @@
 #include <mutex>
 #include <numeric>
 #include <thread>
+#include <unordered_map>
 
 #include "gint_internal.h"
 
@@ -260,6 +261,20 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
         for (auto &x : s) n += h->norb_atom[x.atom];
         return n;
     };
+    // padded K width of a slot list and, with koff, each slot's first padded column: slot widths
+    // rounded up to kpad; slots of up to kKSeg columns do not cross a multiple of kKSeg, wider
+    // ones start on one
+    auto padded_width = [&](const RawSlot *s, int ns, std::vector<int> *koff) {
+        int kcur = 0;
+        for (int i = 0; i < ns; ++i) {
+            const int kw = kpad(h->norb_atom[s[i].atom]);
+            if ((kw <= kKSeg && kcur % kKSeg + kw > kKSeg) || (kw > kKSeg && kcur % kKSeg))
+                kcur = (kcur / kKSeg + 1) * kKSeg;
+            if (koff) koff->push_back(kcur);
+            kcur += kw;
+        }
+        return kcur;
+    };
     // Atom images ordered by atom ascending, then image n descending.  With this order every
     // pair of slots a < b maps to the canonical member of its partner pair {(I,J,R), (J,I,-R)}:
     // I_a < I_b, or I_a == I_b with R = n_b - n_a lexicographically negative.  The tensor-core
@@ -458,86 +473,19 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
             return GINT_OK;
         }
     }
-    // phase 2: slot records, padded K offsets and slot-pair block tables of every part
-    parallel_parts(nparts, nparts, [&](int64_t t0, int64_t t1, int) {
-        for (int64_t t = t0; t < t1; ++t) {
-            Part &pt = parts[t];
-            BatchSet &o = pt.s;
-            o.batches.reserve(pt.acc.size());
-            o.slots.reserve(pt.raw.size());
-            o.koff.reserve(pt.raw.size());
-            o.slot_img.reserve(3 * pt.raw.size());
-            for (const Acc &A : pt.acc) {
-                const RawSlot *ws = pt.raw.data() + A.r0;
-                int nb = 0;
-                for (int s = 0; s < A.ns; ++s) nb += h->norb_atom[ws[s].atom];
-                Batch B{};
-                B.i0 = A.i0; B.j0 = A.j0; B.k0 = A.k0;
-                B.dims = A.n1 | (A.n2 << 8) | (A.n3 << 16);
-                B.slot0 = (int)o.slots.size();   // part-local; made global when the parts are joined
-                B.nslots = A.ns;
-                B.nb = nb;
-                B.tbl = (int)o.tbl.size();
-                o.flops_dense += 2.0 * (A.n1 * A.n2 * A.n3) * (double)nb * nb;
-                o.max_nb = std::max(o.max_nb, nb);
-                o.max_slots = std::max(o.max_slots, A.ns);
-                int off = 0, kcur = 0;
-                double org[3];
-                batch_origin(bg, A.i0, A.j0, A.k0, org);
-                for (int s = 0; s < A.ns; ++s) {
-                    // padded K column: slots of up to kKSeg columns do not cross a multiple of kKSeg,
-                    // wider ones start on one
-                    const int kw = kpad(h->norb_atom[ws[s].atom]);
-                    if ((kw <= kKSeg && kcur % kKSeg + kw > kKSeg) || (kw > kKSeg && kcur % kKSeg))
-                        kcur = (kcur / kKSeg + 1) * kKSeg;
-                    o.koff.push_back(kcur);
-                    kcur += kw;
-                }
-                o.max_k = std::max(o.max_k, kcur);
-                for (int s = 0; s < A.ns; ++s) {
-                    Slot S{};
-                    S.atom = ws[s].atom;
-                    S.species = h->species[ws[s].atom];
-                    S.orb_off = off;
-                    S.norb = h->norb_atom[ws[s].atom];
-                    slot_position(S, org, tau, ws[s].n, G);
-                    off += S.norb;
-                    o.slots.push_back(S);
-                    o.slot_img.insert(o.slot_img.end(), {ws[s].n[0], ws[s].n[1], ws[s].n[2]});
-                }
-                for (int ia = 0; ia < A.ns && pt.st == GINT_OK; ++ia)
-                    for (int ib = 0; ib < A.ns; ++ib) {
-                        const RawSlot &sa = ws[ia], &sb = ws[ib];
-                        const int bi = kidx.find(
-                            pack_key(sa.atom, sb.atom, sb.n[0] - sa.n[0], sb.n[1] - sa.n[1], sb.n[2] - sa.n[2]));
-                        if (bi < 0) {
-                            o.tbl.push_back(-1);
-                            if (soff) o.tbl2.push_back(-1);
-                        } else {
-                            if (ia <= ib && !canon[bi]) {
-                                snprintf(pt.err, sizeof(pt.err), "%s",
-                                         "gint_setup: internal error, slot order breaks the canonical-pair rule");
-                                pt.st = GINT_EINVAL;
-                                break;
-                            }
-                            o.tbl.push_back((int)((offsets[bi] << 1) | canon[bi]));
-                            if (soff) o.tbl2.push_back((*soff)[bi]);
-                        }
-                    }
-                o.batches.push_back(B);
-            }
-            std::vector<RawSlot>().swap(pt.raw);
-        }
-    });
-    // join the parts in order
+    // phase 2: slot records, padded K offsets and slot-pair block tables, written in place (the
+    // parts' offsets are known from phase 1).  A batch whose origin, shape and atom-image list
+    // equal those of a batch of `old` copies its tables and offsets from there and only gets new
+    // slot positions; the others look their blocks up.
     std::vector<size_t> sl0(nparts + 1, 0), tb0(nparts + 1, 0);
     for (int t = 0; t < nparts; ++t) {
-        if (parts[t].st != GINT_OK) {
-            set_error("%s", parts[t].err);
-            return parts[t].st;
+        size_t ns = 0, nt = 0;
+        for (const Acc &A : parts[t].acc) {
+            ns += A.ns;
+            nt += (size_t)A.ns * A.ns;
         }
-        sl0[t + 1] = sl0[t] + parts[t].s.slots.size();
-        tb0[t + 1] = tb0[t] + parts[t].s.tbl.size();
+        sl0[t + 1] = sl0[t] + ns;
+        tb0[t + 1] = tb0[t] + nt;
     }
     if ((int64_t)tb0[nparts] >= ((int64_t)1 << 31) || sl0[nparts] >= ((size_t)1 << 31)) {
         set_error("gint_setup: too many batches / table entries");
@@ -549,23 +497,113 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
     out.koff.resize(sl0[nparts]);
     out.tbl.resize(tb0[nparts]);
     if (soff) out.tbl2.resize(tb0[nparts]);
+    std::unordered_map<int64_t, int> oldpos;   // batch origin (grid index) -> batch of old
+    const bool reuse = old && old->koff.size() == old->slots.size() && (!soff || old->tbl2.size() == old->tbl.size());
+    if (reuse) {
+        oldpos.reserve(old->batches.size() * 2);
+        for (size_t q = 0; q < old->batches.size(); ++q) {
+            const Batch &B = old->batches[q];
+            oldpos.emplace(((int64_t)B.i0 * N2 + B.j0) * N3 + B.k0, (int)q);
+        }
+    }
     parallel_parts(nparts, nparts, [&](int64_t t0, int64_t t1, int) {
         for (int64_t t = t0; t < t1; ++t) {
-            const BatchSet &ps = parts[t].s;
-            for (size_t q = 0; q < ps.batches.size(); ++q) {
-                Batch B = ps.batches[q];
-                B.slot0 += (int)sl0[t];
-                B.tbl += (int)tb0[t];
+            Part &pt = parts[t];
+            BatchSet &o = pt.s;   // per-part statistics only
+            size_t so = sl0[t], to = tb0[t];
+            for (size_t q = 0; q < pt.acc.size() && pt.st == GINT_OK; ++q) {
+                const Acc &A = pt.acc[q];
+                const RawSlot *ws = pt.raw.data() + A.r0;
+                int nb = 0;
+                for (int s = 0; s < A.ns; ++s) nb += h->norb_atom[ws[s].atom];
+                Batch B{};
+                B.i0 = A.i0; B.j0 = A.j0; B.k0 = A.k0;
+                B.dims = A.n1 | (A.n2 << 8) | (A.n3 << 16);
+                B.slot0 = (int)so;
+                B.nslots = A.ns;
+                B.nb = nb;
+                B.tbl = (int)to;
+                o.flops_dense += 2.0 * (A.n1 * A.n2 * A.n3) * (double)nb * nb;
+                o.max_nb = std::max(o.max_nb, nb);
+                o.max_slots = std::max(o.max_slots, A.ns);
+                double org[3];
+                batch_origin(bg, A.i0, A.j0, A.k0, org);
+                const Batch *ob = nullptr;
+                if (reuse) {
+                    auto it = oldpos.find(((int64_t)A.i0 * N2 + A.j0) * N3 + A.k0);
+                    if (it != oldpos.end()) {
+                        const Batch &C = old->batches[it->second];
+                        bool eq = C.dims == B.dims && C.nslots == A.ns;
+                        for (int s = 0; eq && s < A.ns; ++s) {
+                            const int *n = &old->slot_img[3 * ((size_t)C.slot0 + s)];
+                            eq = old->slots[C.slot0 + s].atom == ws[s].atom && n[0] == ws[s].n[0] && n[1] == ws[s].n[1] &&
+                                 n[2] == ws[s].n[2];
+                        }
+                        if (eq) ob = &C;
+                    }
+                }
+                if (ob) {
+                    // unchanged list: the old records at the new positions, the old tables
+                    for (int s = 0; s < A.ns; ++s) {
+                        Slot S = old->slots[ob->slot0 + s];
+                        slot_position(S, org, tau, ws[s].n, G);
+                        out.slots[so + s] = S;
+                        out.koff[so + s] = old->koff[ob->slot0 + s];
+                    }
+                    std::copy_n(old->slot_img.begin() + 3 * (size_t)ob->slot0, 3 * A.ns, out.slot_img.begin() + 3 * so);
+                    std::copy_n(old->tbl.begin() + ob->tbl, (size_t)A.ns * A.ns, out.tbl.begin() + to);
+                    if (soff) std::copy_n(old->tbl2.begin() + ob->tbl, (size_t)A.ns * A.ns, out.tbl2.begin() + to);
+                    o.max_k = std::max(o.max_k, padded_width(ws, A.ns, nullptr));
+                } else {
+                    std::vector<int> ko;
+                    ko.reserve(A.ns);
+                    o.max_k = std::max(o.max_k, padded_width(ws, A.ns, &ko));
+                    int off = 0;
+                    for (int s = 0; s < A.ns; ++s) {
+                        Slot S{};
+                        S.atom = ws[s].atom;
+                        S.species = h->species[ws[s].atom];
+                        S.orb_off = off;
+                        S.norb = h->norb_atom[ws[s].atom];
+                        slot_position(S, org, tau, ws[s].n, G);
+                        off += S.norb;
+                        out.slots[so + s] = S;
+                        out.koff[so + s] = ko[s];
+                        for (int c = 0; c < 3; ++c) out.slot_img[3 * (so + s) + c] = ws[s].n[c];
+                    }
+                    for (int ia = 0; ia < A.ns && pt.st == GINT_OK; ++ia)
+                        for (int ib = 0; ib < A.ns; ++ib) {
+                            const RawSlot &sa = ws[ia], &sb = ws[ib];
+                            const int bi = kidx.find(
+                                pack_key(sa.atom, sb.atom, sb.n[0] - sa.n[0], sb.n[1] - sa.n[1], sb.n[2] - sa.n[2]));
+                            const size_t x = to + (size_t)ia * A.ns + ib;
+                            if (bi < 0) {
+                                out.tbl[x] = -1;
+                                if (soff) out.tbl2[x] = -1;
+                            } else {
+                                if (ia <= ib && !canon[bi]) {
+                                    snprintf(pt.err, sizeof(pt.err), "%s",
+                                             "gint_setup: internal error, slot order breaks the canonical-pair rule");
+                                    pt.st = GINT_EINVAL;
+                                    break;
+                                }
+                                out.tbl[x] = (int)((offsets[bi] << 1) | canon[bi]);
+                                if (soff) out.tbl2[x] = (*soff)[bi];
+                            }
+                        }
+                }
                 out.batches[bat0[t] + q] = B;
+                so += A.ns;
+                to += (size_t)A.ns * A.ns;
             }
-            std::copy(ps.slots.begin(), ps.slots.end(), out.slots.begin() + sl0[t]);
-            std::copy(ps.slot_img.begin(), ps.slot_img.end(), out.slot_img.begin() + 3 * sl0[t]);
-            std::copy(ps.koff.begin(), ps.koff.end(), out.koff.begin() + sl0[t]);
-            std::copy(ps.tbl.begin(), ps.tbl.end(), out.tbl.begin() + tb0[t]);
-            if (soff) std::copy(ps.tbl2.begin(), ps.tbl2.end(), out.tbl2.begin() + tb0[t]);
+            std::vector<RawSlot>().swap(pt.raw);
         }
     });
     for (auto &pt : parts) {
+        if (pt.st != GINT_OK) {
+            set_error("%s", pt.err);
+            return pt.st;
+        }
         out.flops_dense += pt.s.flops_dense;
         out.max_nb = std::max(out.max_nb, pt.s.max_nb);
         out.max_slots = std::max(out.max_slots, pt.s.max_slots);

@@ -35,6 +35,7 @@ SInfo sinfo_for(const gint_handle_s *h, const double *V, double *H, const void *
     si.H = H;
     si.DMS = DMS;
     si.dms_plane = h->dms_plane;
+    si.padn = h->bs[1].padn ? 1 : 0;
     si.rho = rho;
     si.F = F;
     si.poff = h->d_poff;
@@ -187,7 +188,8 @@ gint_status run_rho_force(gint_handle h, const double *V, const double *DM, doub
                      (e = launch_absmax(DM, h->info.nvalues, amax, s)) != cudaSuccess))
             return cuda_fail(e, "gint_rho: range");
         if (h->info.nvalues > 0 &&
-            (e = launch_dm_split(h->plan, prec, (const int *)h->d_soff, DM, h->d_dms, h->dms_plane, grad, amax, s)) !=
+            (e = launch_dm_split(h->plan, prec, (const int *)h->d_soff, DM, h->d_dms, h->dms_plane, h->bs[1].padn, grad,
+                                 amax, s)) !=
                 cudaSuccess)
             return cuda_fail(e, "gint_rho: split");
         SInfo si = sinfo_for(h, V, nullptr, h->d_dms, rho, F);

@@ -101,8 +101,8 @@ gint_status issue(gint_batch b, cudaStream_t s)
             float *am = half ? b->d_amax + 2 * i + 1 : nullptr;
             if (am && (e = launch_absmax(b->DM[i], h->info.nvalues, am, s)) != cudaSuccess)
                 return cuda_fail(e, "gint_batch: density-matrix range");
-            if ((e = launch_dm_split(h->plan, b->prec, (const int *)h->d_soff, b->DM[i], b->dms[i], h->dms_plane, false,
-                                     am, s)) != cudaSuccess)
+            if ((e = launch_dm_split(h->plan, b->prec, (const int *)h->d_soff, b->DM[i], b->dms[i], h->dms_plane,
+                                     h->bs[1].padn, false, am, s)) != cudaSuccess)
                 return cuda_fail(e, "gint_batch: split");
         }
     }

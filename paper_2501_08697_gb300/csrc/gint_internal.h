@@ -55,9 +55,10 @@ constexpr long long kDrainBudget = 4000000000LL;  // final wait for in-flight MM
 struct SInfo {
     const double *V;
     double *H;
-    const void *DMS;               // split density matrix: NT planes of dms_plane elements, each
-                                   //   block n_I x kpad(n_J), row-major, at its split offset
+    const void *DMS;               // split density matrix (k_dm_split): every block's NT terms,
+                                   //   rows and columns padded, at element NT x its split offset
     int64_t dms_plane;
+    int padn;                      // the split store's layout (padded, or row layout) and N columns
     double *rho;
     double *F;
     double *dLde;                  // 9 values: strain derivative (single-structure launches only)
@@ -118,6 +119,8 @@ struct BatchSet {
     std::vector<int> tbl2;           // per slot pair (b, a): offset of block (b, a) in the split
                                      //   density-matrix store, or -1 (rho/force set only)
     int limit_nb = 256;              // batches with more orbitals are split
+    bool padn = false;               // rho/force: N columns at the padded K offsets, padded
+                                     //   density layout (otherwise N = the unpadded orbitals)
     int max_nb = 0, max_slots = 0;
     int max_k = 0;                   // largest padded K of a batch
     double flops_dense = 0.0;
@@ -165,7 +168,8 @@ struct gint_handle_s {
     int *d_status = nullptr;
     double *d_dmsym = nullptr;       // scratch: block-symmetrised density matrix (FP64 kernels)
     void *d_dms = nullptr;           // scratch: split density matrix of the tensor-core kernels
-    int64_t dms_plane = 0;           // elements per plane of it (Sum_b n_I kpad(n_J), rounded to 8)
+    int64_t dms_plane = 0;           // elements per term of it (Sum_b kpad(n_I) kpad(n_J) in the padded
+                                     //   layout, Sum_b n_I kpad(n_J) in the row layout; rounded to 8)
     std::vector<int> soff;           // per block: offset in a plane of the split store
     void *d_soff = nullptr;
     float *d_poff = nullptr;         // point-offset table
@@ -226,8 +230,9 @@ cudaError_t launch_rho_force_simt(const Plan &p, bool fp64, const double *V, con
 cudaError_t launch_vlocal_tc(const Plan &p, gint_prec prec, const SInfo &si0, const SInfo *sis, cudaStream_t s,
                              int nsm, int max_nb);
 // NT terms of the (block-symmetrised if sym) density matrix into the padded split store
-cudaError_t launch_dm_split(const Plan &P, gint_prec prec, const int *soff, const double *DM, void *out, int64_t plane,
-                            bool sym, const float *amax, cudaStream_t s);
+// the handle's split density-matrix store (padded or row layout, see k_dm_split)
+cudaError_t launch_dm_split(const Plan &P, gint_prec prec, const int *soff, const double *DM, void *out,
+                            int64_t plane, bool padn, bool sym, const float *amax, cudaStream_t s);
 cudaError_t launch_absmax(const double *x, int64_t n, float *out, cudaStream_t s);
 cudaError_t launch_rho_force_tc(const Plan &p, gint_prec prec, const SInfo &si0, const SInfo *sis, bool rho,
                                 bool force, cudaStream_t s, int nsm);

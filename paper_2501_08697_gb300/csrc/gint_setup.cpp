@@ -236,14 +236,18 @@ static inline void batch_origin(const BatchGeom &bg, int i0, int j0, int k0, dou
 static gint_status build_batches(gint_handle h, const double *tau, const Geo &G, const BatchGeom &bg,
                                  const std::vector<double> &rc, const KeyIndex &kidx,
                                  const std::vector<int64_t> &offsets, const std::vector<uint8_t> &canon,
-                                 const std::vector<int> *soff, const BatchSet *old, bool *same, BatchSet &out)
+                                 const std::vector<int> *soff, bool padn, bool *pad_fail, const BatchSet *old,
+                                 bool *same, BatchSet &out)
 {
     const int natoms = h->natoms;
     const int N1 = h->grid[0], N2 = h->grid[1], N3 = h->grid[2];
     const int B1 = out.dims[0], B2 = out.dims[1], B3 = out.dims[2];
     const int nb1 = (N1 + B1 - 1) / B1, nb2 = (N2 + B2 - 1) / B2, nb3 = (N3 + B3 - 1) / B3;
     const int limit_nb = out.limit_nb;
+    // padn (rho/force decomposition, padded density layout): the N axis is laid out like the
+    // padded K axis, so the padded width must fit the accumulator's kMaxNb columns too
     if (same) *same = false;
+    if (pad_fail) *pad_fail = false;
     struct Acc {
         int i0, j0, k0, n1, n2, n3, r0, ns;   // accepted batch; its slots are raw[r0 .. r0 + ns)
     };
@@ -252,6 +256,7 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
         std::vector<RawSlot> raw;
         BatchSet s;
         gint_status st = GINT_OK;
+        bool padfail = false;   // failed only because of the padded N width
         char err[256] = {0};
     };
     const int nparts = std::min(host_threads(), nb1);
@@ -263,8 +268,11 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
     };
     // padded K width of a slot list and, with koff, each slot's first padded column: slot widths
     // rounded up to kpad; slots of up to kKSeg columns do not cross a multiple of kKSeg, wider
-    // ones start on one
+    // ones start on one.  In the rho/force decomposition the same offsets are the N columns, so
+    // a list whose segment-aligned width exceeds the accumulator's kMaxNb columns is packed
+    // densely instead (the density kernel then evaluates a straddling slot once per segment).
     auto padded_width = [&](const RawSlot *s, int ns, std::vector<int> *koff) {
+        const size_t k0 = koff ? koff->size() : 0;
         int kcur = 0;
         for (int i = 0; i < ns; ++i) {
             const int kw = kpad(h->norb_atom[s[i].atom]);
@@ -272,6 +280,14 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                 kcur = (kcur / kKSeg + 1) * kKSeg;
             if (koff) koff->push_back(kcur);
             kcur += kw;
+        }
+        if (padn && kcur > kMaxNb) {
+            if (koff) koff->resize(k0);
+            kcur = 0;
+            for (int i = 0; i < ns; ++i) {
+                if (koff) koff->push_back(kcur);
+                kcur += kpad(h->norb_atom[s[i].atom]);
+            }
         }
         return kcur;
     };
@@ -379,7 +395,8 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                         stack.pop_back();
                         std::sort(w.s.begin(), w.s.end(), slot_less);
                         int nb = orb_count(w.s);
-                        if (nb > limit_nb || (int)w.s.size() > kMaxSlots) {
+                        const int pw = padn ? padded_width(w.s.data(), (int)w.s.size(), nullptr) : 0;
+                        if (nb > limit_nb || (int)w.s.size() > kMaxSlots || pw > kMaxNb) {
                             // halve the longest axis; a3 halves stay even so batch origins stay even
                             int dims[3] = {w.n1, w.n2, w.n3};
                             int ax = -1;
@@ -389,7 +406,8 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                             }
                             if (ax < 0) {
                                 // cannot split further: accept up to the hard kernel limits
-                                if (nb <= kMaxNb && (int)w.s.size() <= kMaxSlots) goto accept;
+                                if (nb <= kMaxNb && (int)w.s.size() <= kMaxSlots && pw <= kMaxNb) goto accept;
+                                if (nb <= kMaxNb && (int)w.s.size() <= kMaxSlots) pt.padfail = true;
                                 fail("gint_setup: a grid batch sees %d orbitals / %d atom images", nb, (int)w.s.size());
                                 break;
                             }
@@ -424,6 +442,7 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
     for (int t = 0; t < nparts; ++t) {
         if (parts[t].st != GINT_OK) {
             set_error("%s", parts[t].err);
+            if (pad_fail) *pad_fail = parts[t].padfail;
             return parts[t].st;
         }
         bat0[t + 1] = bat0[t] + parts[t].acc.size();
@@ -683,13 +702,19 @@ gint_status build_geometry(gint_handle h, const double *tau, const gint_handle_s
         set_error("gint_setup: block store of %lld values exceeds 2^30", (long long)offsets[nblocks]);
         return GINT_EINVAL;
     }
-    // offsets of the blocks in the split density-matrix store (rows n_I, columns padded)
-    std::vector<int> soff(nblocks);
-    int64_t splane = 0;
+    // offsets of the blocks in the split density-matrix store, per term.  Padded layout: rows and
+    // columns padded to kpad, a block holds all its terms (element offset NT soff[b]).  Row
+    // layout: rows n_I, columns padded, each term in its own plane of splane elements.
+    std::vector<int> soff_pad(nblocks), soff_row(nblocks);
+    int64_t splane_pad = 0, splane_row = 0;
     for (int64_t b = 0; b < nblocks; ++b) {
-        soff[b] = (int)splane;
-        splane += (int64_t)h->norb_atom[keys[5 * b]] * kpad(h->norb_atom[keys[5 * b + 1]]);
+        const int nI = h->norb_atom[keys[5 * b]], nJ = h->norb_atom[keys[5 * b + 1]];
+        soff_pad[b] = (int)splane_pad;
+        soff_row[b] = (int)splane_row;
+        splane_pad += (int64_t)kpad(nI) * kpad(nJ);
+        splane_row += (int64_t)nI * kpad(nJ);
     }
+    const int64_t splane = splane_pad;   // the larger of the two
     if (splane >= ((int64_t)1 << 30)) {
         set_error("gint_setup: padded block store of %lld values exceeds 2^30", (long long)splane);
         return GINT_EINVAL;
@@ -725,9 +750,26 @@ gint_status build_geometry(gint_handle h, const double *tau, const gint_handle_s
         // vlocal batches of up to 64 points stay within 192 orbitals (two accumulators fit in
         // tensor memory); larger ones use the full 256 with one accumulator
         sets[w].limit_nb = (w == 0 && dims[w][0] * dims[w][1] * dims[w][2] <= 64) ? 192 : kMaxNb;
-        gint_status st = build_batches(h, tau, G, bg, rc, kidx, offsets, canon, w == 1 ? &soff : nullptr,
+        // the rho/force decomposition takes the padded density layout when every batch fits it
+        // (a position update keeps the handle's layout)
+        bool padn = w == 1 && (update_only ? old->bs[1].padn : true), pad_fail = false;
+        gint_status st = build_batches(h, tau, G, bg, rc, kidx, offsets, canon,
+                                       w == 1 ? (padn ? &soff_pad : &soff_row) : nullptr, padn, &pad_fail,
                                        update_only ? &old->bs[w] : nullptr, &same[w], sets[w]);
+        if (st != GINT_OK && pad_fail && update_only) {
+            set_error("gint_update_positions: a batch no longer fits the padded density layout; build a new handle");
+            return GINT_ESTATE;
+        }
+        if (st != GINT_OK && pad_fail) {
+            padn = false;
+            sets[w] = BatchSet{};
+            for (int i = 0; i < 3; ++i) sets[w].dims[i] = dims[w][i];
+            sets[w].limit_nb = kMaxNb;
+            st = build_batches(h, tau, G, bg, rc, kidx, offsets, canon, &soff_row, false, nullptr, nullptr, &same[w],
+                               sets[w]);
+        }
         if (st != GINT_OK) return st;
+        sets[w].padn = padn;
         if (!same[w] && sets[w].max_k + 32 > kMaxKCols) {
             set_error("gint_setup: a batch's padded orbital columns (%d) exceed %d", sets[w].max_k, kMaxKCols - 32);
             return GINT_EINVAL;
@@ -744,8 +786,9 @@ gint_status build_geometry(gint_handle h, const double *tau, const gint_handle_s
         h->keys = std::move(keys);
         h->offsets = std::move(offsets);
         h->partner = std::move(partner);
-        h->soff = std::move(soff);
-        h->dms_plane = (splane + 7) / 8 * 8;
+        const bool pad = sets[1].padn;
+        h->soff = pad ? std::move(soff_pad) : std::move(soff_row);
+        h->dms_plane = ((pad ? splane_pad : splane_row) + 7) / 8 * 8;
         for (int w = 0; w < 2; ++w) h->bs[w] = std::move(sets[w]);
     }
     h->tau.assign(tau, tau + 3 * natoms);

@@ -611,18 +611,19 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 }
 
 // ====================================================================== rho / force
-// Psi_b = Phi_b D_b with M = 128 points, N = the batch's orbitals (unpadded, TMEM columns) and K
-// = the batch's orbitals in the padded K layout (every slot rounded up to 8 columns, see kpad).
-// The density matrix arrives pre-split: a per-call kernel writes its NT terms (scaled for fp16)
-// into a padded store in which the rows of one 16-byte block column are adjacent, so the B
-// operand of a chunk is assembled from bulk copies (one per term, core-matrix column and slot)
-// with no arithmetic; the producers' only CUDA-core work is the orbital evaluation of the A
-// operand.
+// Psi_b = Phi_b D_b with M = 128 points and both N and K = the batch's orbitals in the padded
+// layout (every slot rounded up to 8 columns, see kpad; slot s starts at koff[s]): Psi's TMEM
+// columns and D's rows follow the same padded offsets.  The density matrix arrives pre-split: a
+// per-call kernel writes its NT terms (scaled for fp16) into a padded store in which the units of
+// one 16-byte block column (all rows, all terms) are adjacent, so the B operand of a chunk is
+// assembled from bulk copies (one per core-matrix column and slot) with no arithmetic; the
+// producers' only CUDA-core work is the orbital evaluation of the A operand.
 //
-// Operand layout (K-major, no swizzle): core matrices of 8 rows x 16 bytes stored densely, the
-// 8-row groups of one core-matrix column adjacent (SBO = 128 bytes) and the KCM columns of a
-// chunk LBO = rows x 16 bytes apart, so row r of column j sits at j * LBO + 16 r: producers with
-// consecutive rows write consecutive 16 bytes.
+// Operand layouts (K-major, no swizzle; core matrices of 8 rows x 16 bytes stored densely).
+// A: the 8-row groups of one core-matrix column adjacent (SBO = 128 bytes) and the KCM columns
+// of a chunk LBO = 128 x 16 bytes apart, so row r of column j sits at j * LBO + 16 r: producers
+// with consecutive rows write consecutive 16 bytes.  B: per core-matrix column the 8-row groups
+// of N in order, each with its NT terms side by side (SBO = NT x 128 bytes, term t at + 128 t).
 constexpr int kRHalf = 256;          // producer warps 0-7 write the A operand
 constexpr int kRBThr = 128;          // producer warps 8-11 copy the B operand
 constexpr int kRProd = kRHalf + kRBThr;
@@ -640,10 +641,18 @@ struct RL {
     static constexpr int NS = NT == 2 ? 2 : 1;         // operand stages
     static constexpr int ESZ = 16 / CG;                // bytes per element
     static constexpr int LBO_A = kMaxBatchPts * 16;
-    static constexpr int LBO_B = kMaxNb * 16;
     static constexpr int PLA = KCM * LBO_A;            // one A term of a chunk
-    static constexpr int PLB = KCM * LBO_B;            // one B term
-    static constexpr int STAGE = NT * (PLA + PLB);
+    // B: [core-matrix column j][8-row group of N][term][row][16 bytes]: the terms of an 8-row
+    // group adjacent (a term's 8-row groups SBO_B = NT x 128 bytes apart), columns LBO_B apart
+    static constexpr int SBO_B = NT * 128;
+    static constexpr int LBO_B = (kMaxNb / 8) * SBO_B;
+    static constexpr int PLB = KCM * LBO_B;            // all B terms of a chunk
+    // B, row layout (batches whose padded width exceeds the accumulator): term planes of PLBR
+    // bytes, the N rows of a core-matrix column adjacent (SBO 128), columns LBO_BR apart
+    static constexpr int LBO_BR = kMaxNb * 16;
+    static constexpr int PLBR = KCM * LBO_BR;
+    static_assert(NT * PLBR == PLB, "both B layouts fill the same stage");
+    static constexpr int STAGE = NT * PLA + PLB;
     // producer metadata, double-buffered (the next batch's is copied during this one)
     static constexpr int OFF_PSLOT = NS * STAGE;                                    // PSlot[2][64]
     static constexpr int OFF_POFF = OFF_PSLOT + 2 * kMaxSlots * (int)sizeof(PSlot); // float [2][128][6]
@@ -669,17 +678,23 @@ __device__ __forceinline__ uint64_t sdesc2(uint32_t addr, uint32_t lbo, uint32_t
            (1ull << 46);
 }
 
-// Split density-matrix store: for every block (rows n_I, columns n_J, padded to kpad(n_J) with
-// zeros) its NT terms at soff[b] in each of NT planes of `plane` elements, in 16-byte pieces of
-// CG consecutive columns ordered piece column by piece column: piece (i, c) of the block (row i,
-// columns c .. c + CG - 1) sits at soff[b] + (c / CG) n_I CG + i CG, so the rows of one piece
-// column are adjacent.  sym: the block-symmetric part (DM + DM^T_block) / 2 (derivatives use
-// it).  For fp16 the values are scaled by scale_for(max |DM|), read from amax.
+// Split density-matrix store: every block (rows n_I, columns n_J, both padded to kpad with zeros)
+// holds its NT terms at element NT soff[b] in 16-byte units of CG consecutive columns, ordered
+// [column piece j][8-row group G][term t][row r]: unit (j, G, t, r) holds row 8 G + r, columns
+// j CG .. j CG + CG - 1 of term t.  The units of one column piece (all rows, all terms) are
+// adjacent, exactly as the B operand of the density kernel wants them in shared memory.
+// sym: the block-symmetric part (DM + DM^T_block) / 2 (derivatives use it).  For fp16 the values
+// are scaled by scale_for(max |DM|), read from amax.
+//
+// Row layout (padn == 0, decompositions whose padded width would exceed the accumulator): rows
+// n_I, columns padded to kpad, term t in its own plane of `plane` elements; piece (i, c) (row i,
+// columns c .. c + CG - 1) at soff[b] + (c / CG) n_I CG + i CG, so the rows of one piece are
+// adjacent.
 template <class S>
 __global__ void k_dm_split(Plan P, const int *__restrict__ soff, const double *__restrict__ DM, void *out,
-                           int64_t plane, int sym, const float *amax)
+                           int64_t plane, int padn, int sym, const float *amax)
 {
-    constexpr int CG = S::CG, ESZ = 16 / CG;
+    constexpr int CG = S::CG, ESZ = 16 / CG, NT = S::NT;
     float sc = 1.f;
     if constexpr (S::HALF) sc = scale_for(amax[0]);
     unsigned char *o8 = reinterpret_cast<unsigned char *>(out);
@@ -687,20 +702,24 @@ __global__ void k_dm_split(Plan P, const int *__restrict__ soff, const double *_
         const int64_t off = P.blk_off[b], poff = P.blk_off[P.partner[b]];
         const int rows = P.blk_rows[b];
         const int cols = (int)((P.blk_off[b + 1] - off) / rows);
-        const int pc = kpad(cols), npc = pc / CG;
-        for (int e = threadIdx.x; e < rows * npc; e += blockDim.x) {
-            const int i = e / npc, c0 = (e - i * npc) * CG;
+        const int pr = padn ? kpad(rows) : rows, ng = pr / 8, npc = kpad(cols) / CG;
+        unsigned char *base = o8 + (int64_t)(padn ? NT : 1) * soff[b] * ESZ;
+        for (int e = threadIdx.x; e < pr * npc; e += blockDim.x) {
+            const int j = e / pr, i = e - j * pr, c0 = j * CG;
             float x[CG];
 #pragma unroll
             for (int q = 0; q < CG; ++q) {
                 const int c = c0 + q;
                 double v = 0.0;
-                if (c < cols) v = sym ? 0.5 * (DM[off + i * cols + c] + DM[poff + c * rows + i]) : DM[off + i * cols + c];
+                if (i < rows && c < cols)
+                    v = sym ? 0.5 * (DM[off + i * cols + c] + DM[poff + c * rows + i]) : DM[off + i * cols + c];
                 x[q] = d2f(v) * sc;
             }
-            unsigned char *dst[S::NT];
+            unsigned char *dst[NT];
 #pragma unroll
-            for (int t = 0; t < S::NT; ++t) dst[t] = o8 + ((int64_t)t * plane + soff[b] + c0 * rows + i * CG) * ESZ;
+            for (int t = 0; t < NT; ++t)
+                dst[t] = padn ? base + (((j * ng + (i >> 3)) * NT + t) * 8 + (i & 7)) * 16
+                              : base + ((int64_t)t * plane + (int64_t)c0 * rows + i * CG) * ESZ;
             split_store<S>(x, dst);
         }
     }
@@ -882,29 +901,53 @@ __global__ void __launch_bounds__(kThreadsR, 1)
                 if (!ok) break;
                 unsigned char *st0 = sm + stage * L::STAGE;
                 if (!agrp) {
-                    // B: per (term t, core-matrix column j of the chunk, slot b) the rows of slot
-                    // b; in the split store the n_b rows of one 16-byte column of block (b, a) are
-                    // adjacent, as they are in shared memory, so each is one bulk (TMA) copy of
-                    // 16 n_b bytes that completes its bytes on bfull[stage]; zeros where the
-                    // column is a gap or the pair has no block.  The copies bypass the load/store
-                    // pipeline the orbital evaluations use.
-                    for (int w = gt; w < NT * KCM * ns; w += kRBThr) {
-                        const int t = w / (KCM * ns), r = w - t * KCM * ns, j = r / ns, b = r - j * ns;
+                    // B: per (core-matrix column j of the chunk, slot b) the padded rows of slot b
+                    // (N rows koff_b ..), all terms: in the split store these units of block (b, a)
+                    // are adjacent, as they are in shared memory, so each is one bulk (TMA) copy
+                    // of NT x 16 kpad(n_b) bytes that completes its bytes on bfull[stage]; zeros
+                    // where the column is a gap or the pair has no block.  The copies bypass the
+                    // load/store pipeline the orbital evaluations use.
+                    uint32_t tx = 0;   // bytes of this thread's copies
+                    if (!SI.padn) {
+                        // row layout: per (term t, column j, slot b) the n_b rows, 16 n_b bytes
+                        for (int w = gt; w < NT * KCM * ns; w += kRBThr) {
+                            const int t = w / (KCM * ns), r = w - t * KCM * ns, j = r / ns, b = r - j * ns;
+                            const int k = k0 + j * CG, a = kslot[k >> 3];
+                            const int nbo = ps[b].norb;
+                            unsigned char *dst = st0 + NT * L::PLA + t * L::PLBR + j * L::LBO_BR + ps[b].off * 16;
+                            int e = -1;
+                            if (a >= 0) e = tsm ? tbls[b * ns + a] : __ldg(P.tbl2 + B.tbl + b * ns + a);
+                            if (e >= 0) {
+                                const int64_t el = (int64_t)t * SI.dms_plane + e + ((k - koffs[a]) / CG) * nbo * CG;
+                                bulk_g2s(dst, dms + el * L::ESZ, 16u * (uint32_t)nbo, &bfull[stage]);
+                                tx += 16u * (uint32_t)nbo;
+                            } else {
+                                for (int row = 0; row < nbo; ++row)
+                                    *reinterpret_cast<uint4 *>(dst + 16 * row) = make_uint4(0, 0, 0, 0);
+                            }
+                        }
+                    }
+                    for (int w = gt; SI.padn && w < KCM * ns; w += kRBThr) {
+                        const int j = w / ns, b = w - j * ns;
                         const int k = k0 + j * CG, a = kslot[k >> 3];
-                        const int nbo = ps[b].norb;
-                        unsigned char *dst = st0 + NT * L::PLA + t * L::PLB + j * L::LBO_B + ps[b].off * 16;
+                        const int ng = kpad(ps[b].norb) / 8;
+                        const uint32_t bytes = (uint32_t)(ng * L::SBO_B);
+                        unsigned char *dst = st0 + NT * L::PLA + j * L::LBO_B + (koffs[b] / 8) * L::SBO_B;
                         int e = -1;
                         if (a >= 0) e = tsm ? tbls[b * ns + a] : __ldg(P.tbl2 + B.tbl + b * ns + a);
                         if (e >= 0) {
-                            const int64_t el = (int64_t)t * SI.dms_plane + e + ((k - koffs[a]) / CG) * nbo * CG;
-                            const unsigned char *src = dms + el * L::ESZ;
-                            mbar_expect_tx(&bfull[stage], 16u * (uint32_t)nbo);
-                            bulk_g2s(dst, src, 16u * (uint32_t)nbo, &bfull[stage]);
+                            const int64_t unit = (int64_t)NT * e / CG + (int64_t)((k - koffs[a]) / CG) * ng * NT * 8;
+                            bulk_g2s(dst, dms + unit * 16, bytes, &bfull[stage]);
+                            tx += bytes;
                         } else {
-                            for (int row = 0; row < nbo; ++row)
-                                *reinterpret_cast<uint4 *>(dst + 16 * row) = make_uint4(0, 0, 0, 0);
+                            for (uint32_t q = 0; q < bytes; q += 16)
+                                *reinterpret_cast<uint4 *>(dst + q) = make_uint4(0, 0, 0, 0);
                         }
                     }
+                    // one transaction count per warp (an expect before the copies' completions is
+                    // not needed: the phase cannot complete before this group's arrival below)
+                    tx = __reduce_add_sync(0xffffffffu, tx);
+                    if ((gt & 31) == 0 && tx) mbar_expect_tx(&bfull[stage], tx);
                     ++bph[stage];
                 } else {
                     // A, second half: each task's columns split into the operand row p (register
@@ -982,14 +1025,18 @@ __global__ void __launch_bounds__(kThreadsR, 1)
             int g = 0, it = 0;
             bool ok = true;
             CtaRange cr(P);
+            SInfoCache sic(si0);
             for (int bi = 0; ok && cr.next(bi);) {
                 const Batch B = P.batches[bi];
                 const int nb = B.nb;
                 if (nb == 0) continue;
-                const int npad = (nb + 15) & ~15;
+                const bool padn = sic.get(B, sis).padn != 0;
                 const int buf = it & 1;
                 const int last = B.slot0 + B.nslots - 1;
-                const int ktot = (__ldg(P.koff + last) + kpad(P.slots[last].norb) + KC - 1) / KC * KC;
+                const int kend = __ldg(P.koff + last) + kpad(P.slots[last].norb);   // padded orbitals
+                // N: the orbitals at their padded columns (padded layout) or unpadded
+                const int npad = padn ? (kend + 15) & ~15 : (nb + 15) & ~15;
+                const int ktot = (kend + KC - 1) / KC * KC;
                 const int nch = ktot / KC;
                 const uint32_t id = idesc<S>(128, npad);
                 for (int ch = 0; ch < nch && ok; ++ch, ++g) {
@@ -1009,7 +1056,9 @@ __global__ void __launch_bounds__(kThreadsR, 1)
 #pragma unroll
                         for (int q = 0; q < S::NPROD; ++q) {
                             const uint64_t da = sdesc2(a0 + term(S::PA, q) * L::PLA + ks * 2 * L::LBO_A, L::LBO_A, 128);
-                            const uint64_t db = sdesc2(b0 + term(S::PB, q) * L::PLB + ks * 2 * L::LBO_B, L::LBO_B, 128);
+                            const uint64_t db =
+                                padn ? sdesc2(b0 + term(S::PB, q) * 128 + ks * 2 * L::LBO_B, L::LBO_B, L::SBO_B)
+                                     : sdesc2(b0 + term(S::PB, q) * L::PLBR + ks * 2 * L::LBO_BR, L::LBO_BR, 128);
                             const uint32_t acc = (ch == 0 && ks == 0 && q == 0) ? 0u : 1u;
                             umma<S::F16>(tmem + buf * 256, da, db, id, acc);
                         }
@@ -1052,6 +1101,8 @@ __global__ void __launch_bounds__(kThreadsR, 1)
             }
             named_sync(2, kREpi);
             load_geom(P, SI, B, eps, epoff, et, kREpi);
+            if (SI.padn)
+                for (int s = et; s < ns; s += kREpi) eps[s].off = __ldg(P.koff + B.slot0 + s);   // padded N column
             if (FORCE)
                 for (int e = et; e < 3 * ns; e += kREpi) facc[e] = 0.f;
             if (!role_wait(&accfull[buf], (it >> 1) & 1, P, et, eflag, 2, kREpi)) break;
@@ -1257,12 +1308,12 @@ cudaError_t rho_launch3(const Plan &P, const SInfo &si0, const SInfo *sis, cudaS
 }
 
 template <class S>
-cudaError_t dm_split_launch(const Plan &P, const int *soff, const double *DM, void *out, int64_t plane, bool sym,
-                            const float *amax, cudaStream_t s)
+cudaError_t dm_split_launch(const Plan &P, const int *soff, const double *DM, void *out, int64_t plane, bool padn,
+                            bool sym, const float *amax, cudaStream_t s)
 {
     const int grid = (int)std::min<int64_t>(P.nblocks, 8192);
     if (grid < 1) return cudaSuccess;
-    k_dm_split<S><<<grid, 128, 0, s>>>(P, soff, DM, out, plane, sym ? 1 : 0, amax);
+    k_dm_split<S><<<grid, 128, 0, s>>>(P, soff, DM, out, plane, padn ? 1 : 0, sym ? 1 : 0, amax);
     return cudaGetLastError();
 }
 
@@ -1293,14 +1344,14 @@ cudaError_t launch_vlocal_tc(const Plan &P, gint_prec prec, const SInfo &si0, co
     }
 }
 
-cudaError_t launch_dm_split(const Plan &P, gint_prec prec, const int *soff, const double *DM, void *out, int64_t plane,
-                            bool sym, const float *amax, cudaStream_t s)
+cudaError_t launch_dm_split(const Plan &P, gint_prec prec, const int *soff, const double *DM, void *out,
+                            int64_t plane, bool padn, bool sym, const float *amax, cudaStream_t s)
 {
     switch (prec) {
-    case GINT_TF32X3: return dm_split_launch<TF32x3W>(P, soff, DM, out, plane, sym, amax, s);
-    case GINT_BF16X3: return dm_split_launch<BF16x3W>(P, soff, DM, out, plane, sym, amax, s);
-    case GINT_BF16X6: return dm_split_launch<BF16x6W>(P, soff, DM, out, plane, sym, amax, s);
-    case GINT_FP16X3: return dm_split_launch<FP16x3W>(P, soff, DM, out, plane, sym, amax, s);
+    case GINT_TF32X3: return dm_split_launch<TF32x3W>(P, soff, DM, out, plane, padn, sym, amax, s);
+    case GINT_BF16X3: return dm_split_launch<BF16x3W>(P, soff, DM, out, plane, padn, sym, amax, s);
+    case GINT_BF16X6: return dm_split_launch<BF16x6W>(P, soff, DM, out, plane, padn, sym, amax, s);
+    case GINT_FP16X3: return dm_split_launch<FP16x3W>(P, soff, DM, out, plane, padn, sym, amax, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -910,7 +910,7 @@ __global__ void __launch_bounds__(kThreadsR, 1)
                     uint32_t tx = 0;   // bytes of this thread's copies
                     if (!SI.padn) {
                         // row layout: per (term t, column j, slot b) the n_b rows, 16 n_b bytes
-                        for (int w = gt; w < NT * KCM * ns; w += kRBThr) {
+                        for (int w = (gt & 31) * (kRBThr / 32) + (gt >> 5); w < NT * KCM * ns; w += kRBThr) {
                             const int t = w / (KCM * ns), r = w - t * KCM * ns, j = r / ns, b = r - j * ns;
                             const int k = k0 + j * CG, a = kslot[k >> 3];
                             const int nbo = ps[b].norb;
@@ -927,7 +927,10 @@ __global__ void __launch_bounds__(kThreadsR, 1)
                             }
                         }
                     }
-                    for (int w = gt; SI.padn && w < KCM * ns; w += kRBThr) {
+                    // tasks dealt to the B warps in turn (a warp issues its bulk copies one lane
+                    // after another, so the copies of a chunk are spread over all four warps)
+                    const int bt = (gt & 31) * (kRBThr / 32) + (gt >> 5);
+                    for (int w = bt; SI.padn && w < KCM * ns; w += kRBThr) {
                         const int j = w / ns, b = w - j * ns;
                         const int k = k0 + j * CG, a = kslot[k >> 3];
                         const int ng = kpad(ps[b].norb) / 8;

@@ -267,8 +267,7 @@ struct VSmem {
     static constexpr int OFF_STG = NSTAGE * STAGE;                          // float [256][KC]
     static constexpr int OFF_PSLOT = OFF_STG + ROWS * KC * 4;               // PSlot[2][64]
     static constexpr int OFF_POFF = OFF_PSLOT + 2 * kMaxSlots * (int)sizeof(PSlot);  // float [2][128][6]
-    static constexpr int OFF_VD = OFF_POFF + 2 * kMaxBatchPts * 6 * 4;      // double [2][128]
-    static constexpr int OFF_V = OFF_VD + 2 * kMaxBatchPts * 8;             // float [128]
+    static constexpr int OFF_V = OFF_POFF + 2 * kMaxBatchPts * 6 * 4;       // float [128]: V dV of the batch
     static constexpr int OFF_TBL = OFF_V + kMaxBatchPts * 4;                // int [kVTbl^2]
     static constexpr int OFF_INFO = OFF_TBL + kVTbl * kVTbl * 4;            // int [256]: slot | o << 8 | norb << 16
     static constexpr int EXPB = S::HALF ? 2 * kMaxNb * 2 : 0;              // (fp16 scaling only)
@@ -292,7 +291,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     float *stg = reinterpret_cast<float *>(sm + L::OFF_STG);
     PSlot *psb = reinterpret_cast<PSlot *>(sm + L::OFF_PSLOT);
     float *poffb = reinterpret_cast<float *>(sm + L::OFF_POFF);
-    double *vdb = reinterpret_cast<double *>(sm + L::OFF_VD);
     float *vs = reinterpret_cast<float *>(sm + L::OFF_V);
     int *tbls = reinterpret_cast<int *>(sm + L::OFF_TBL);
     int *info = reinterpret_cast<int *>(sm + L::OFF_INFO);
@@ -340,7 +338,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         CtaRange cr(P);
         int bi = 0, cur = 0;
         bool have = cr.next(bi);
-        if (have) geom_async(P, sis, si0, P.batches[bi], psb, poffb, vdb, pt, kProd);
+        if (have) geom_async(P, sis, si0, P.batches[bi], psb, poffb, nullptr, pt, kProd);
         for (; ok && have; have = cr.next(bi), cur ^= 1) {
             const Batch B = P.batches[bi];
             int n1, n2, n3;
@@ -357,7 +355,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             named_sync(1, kProd);   // this batch's geometry is in buffer cur; buffer cur ^ 1 is free
             if (nb == 0) {          // no orbital reaches this batch: nothing to add
                 if (more) geom_async(P, sis, si0, Bn, psb + (cur ^ 1) * kMaxSlots, poffb + (cur ^ 1) * kMaxBatchPts * 6,
-                                     vdb + (cur ^ 1) * kMaxBatchPts, pt, kProd);
+                                     nullptr, pt, kProd);
                 continue;
             }
             const SInfo SI = sic.get(B, sis);
@@ -379,8 +377,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     }
                 }
             }
+            // V dV of the batch's points (read here; the stages take the shared memory a
+            // prefetched copy would need)
             for (int p = pt; p < kMaxBatchPts; p += kProd)
-                vs[p] = p < npb ? d2f(vdb[cur * kMaxBatchPts + p]) * dVf : 0.f;
+                vs[p] = p < npb ? d2f(__ldg(SI.V + grid_index(SI, B, p, n2, n3))) * dVf : 0.f;
             const int nch = (npb + KC - 1) / KC;
             for (int ch = 0; ch < nch && ok; ++ch, ++g) {
                 const int stage = g % NS;
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 }
                 if (ch == 0 && more)
                     geom_async(P, sis, si0, Bn, psb + (cur ^ 1) * kMaxSlots, poffb + (cur ^ 1) * kMaxBatchPts * 6,
-                               vdb + (cur ^ 1) * kMaxBatchPts, pt, kProd);
+                               nullptr, pt, kProd);
                 if (g >= NS) ok = role_wait(&empty[stage], ((g / NS) - 1) & 1, P, pt, pflag, 1, kProd);
                 else named_sync(1, kProd);
                 if (!ok) break;

@@ -176,7 +176,7 @@ struct BF16x6W {  // hi + mid + lo BF16 terms, the six products of total order <
 struct FP16x3W {  // hi + lo fp16 terms (11-bit significands, as TF32), the three products
     static constexpr int CG = 8, NT = 2, NPROD = 3, KCM = 4;
     static constexpr int RSTAGES = 2;
-    static constexpr int VSTAGES = 1;
+    static constexpr int VSTAGES = 2;
     static constexpr bool F16 = true, HALF = true;
     static constexpr uint32_t FMT = 0, PA = 0x100, PB = 0x010;
 };

@@ -247,10 +247,27 @@ __device__ __forceinline__ void load_species(const Plan &P, SpecSh *spec, int ti
 }
 
 // ====================================================================== vlocal
-// With nbuf = 2 (every batch <= 192 orbitals) TMEM accumulator buffer b occupies columns
-// [256 b, 256 b + 256): tile 0 (rows 0..127, N = npad <= 192) at +0 and tile 1 (rows 128..,
-// N = npad - 128 <= 64) at +192.  With nbuf = 1 (some batch has up to 256 orbitals) one
-// accumulator holds tile 0 at columns [0, 256) and tile 1 at [256, 384).
+// TMEM accumulators: a batch takes tile 0 (rows 0..127, N = npad columns) and, with more than
+// 128 orbitals, tile 1 (rows 128.., N = npad - 128: only the columns of the upper triangle)
+// right after it.  Consecutive batches of a CTA take consecutive column ranges of the 512-column
+// memory (a ring), starting again from column 0 when a batch would not fit: two batches are in
+// flight whenever their widths add up to 512 or less, and the MMA waits for the epilogue of the
+// previous batch only when the ring wraps onto it.
+struct TmemRing {
+    int s = 0, w = 0;   // base column and width of the previous batch
+    // base column of the next batch (npad orbitals, nb > 128 with tile 1); overlap: it wraps
+    // onto the previous batch's columns
+    __device__ __forceinline__ int next(int npad, int nb, bool &overlap)
+    {
+        const int W = npad + (nb > 128 ? npad - 128 : 0);
+        int b = s + w;
+        if (b + W > kTmemCols) b = 0;
+        overlap = b == 0 && w > 0 && s < W;
+        s = b;
+        w = W;
+        return b;
+    }
+};
 // The vlocal epilogue keeps the batch's slot-pair table in shared memory when the batch has
 // at most kVTbl atom images (nearly all batches), otherwise it reads it from global memory.
 constexpr int kVTbl = 28;
@@ -282,7 +299,7 @@ struct VSmem {
 
 template <class S>
 __global__ void __launch_bounds__(kThreadsTC, 1)
-    k_vlocal_tc(Plan P, SInfo si0, const SInfo *__restrict__ sis, int nbuf)
+    k_vlocal_tc(Plan P, SInfo si0, const SInfo *__restrict__ sis)
 {
     using L = VSmem<S>;
     constexpr int KC = L::KC, NS = L::NSTAGE;
@@ -325,7 +342,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_base;
-    const int tile1 = nbuf == 2 ? 192 : 256;   // TMEM column of tile 1 within an accumulator
 
     if (tid < kProd) {
         // ------------------------------------------------------------ producers
@@ -457,6 +473,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             int g = 0, it = 0;
             bool ok = true;
             CtaRange cr(P);
+            TmemRing ring;
             for (int bi = 0; ok && cr.next(bi);) {
                 const Batch B = P.batches[bi];
                 int n1, n2, n3;
@@ -464,13 +481,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 const int nb = B.nb, npb = n1 * n2 * n3;
                 if (nb == 0) continue;
                 const int npad = (nb + 15) & ~15;
-                const int buf = nbuf == 2 ? (it & 1) : 0;
+                const int buf = it & 1;
+                bool wrap;
+                const int base = ring.next(npad, nb, wrap);
                 const int nch = (npb + KC - 1) / KC;
                 for (int ch = 0; ch < nch && ok; ++ch, ++g) {
                     const int stage = g % NS;
                     ok = !aborted(P) && mbar_wait(&full[stage], (g / NS) & 1, P.spin_limit);
-                    if (ok && ch == 0 && it >= nbuf)   // the epilogue of batch it - nbuf is done
-                        ok = !aborted(P) && mbar_wait(&accempty[buf], ((it / nbuf) - 1) & 1, P.spin_limit);
+                    if (ok && ch == 0 && it >= 2)   // the epilogue of batch it - 2 is done
+                        ok = !aborted(P) && mbar_wait(&accempty[buf], ((it >> 1) - 1) & 1, P.spin_limit);
+                    if (ok && ch == 0 && wrap)      // and of batch it - 1, whose columns this one reuses
+                        ok = !aborted(P) && mbar_wait(&accempty[buf ^ 1], ((it - 1) >> 1) & 1, P.spin_limit);
                     if (!ok) {
                         report_timeout(P);
                         break;
@@ -488,7 +509,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                                 const uint64_t da = sdesc(a0 + term(S::PA, q) * L::ARR + rowoff + ks * 2 * kLBO, SBO);
                                 const uint64_t db = sdesc(b0 + term(S::PB, q) * L::ARR + rowoff + ks * 2 * kLBO, SBO);
                                 const uint32_t acc = (ch == 0 && ks == 0 && q == 0) ? 0u : 1u;
-                                umma<S::F16>(tmem + buf * 256 + t * tile1, da, db, id, acc);
+                                umma<S::F16>(tmem + base + t * npad, da, db, id, acc);
                             }
                         }
                     }
@@ -508,19 +529,27 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         int it = 0;
         SInfoCache sic(si0);
         CtaRange cr(P);
+        TmemRing ring;
         for (int bi = 0; cr.next(bi);) {
             const Batch B = P.batches[bi];
             const int ns = B.nslots, nb = B.nb;
             const int npad = (nb + 15) & ~15;
-            const int buf = nbuf == 2 ? (it & 1) : 0;
+            const int buf = it & 1;
             if (nb == 0) continue;
+            bool wrap;
+            const int base = ring.next(npad, nb, wrap);
             const SInfo SIe = sic.get(B, sis);
             double *H = SIe.H;
             const bool small = ns <= kVTbl;
             const int *tbl = small ? tbls : P.tbl + B.tbl;
             named_sync(2, kEpi);
             if (small)
-                for (int e = et; e < ns * ns; e += kEpi) tbls[e] = P.tbl[B.tbl + e];
+                for (int e = et; e < ns * ns; e += kEpi) {
+                    // the scatter adds only for pairs a <= b (the upper triangle): the rest of
+                    // each table row is not fetched
+                    const int a = e / ns;
+                    tbls[e] = e - a * ns >= a ? __ldg(P.tbl + B.tbl + e) : -1;
+                }
             float bc[3], R;
             if constexpr (S::HALF) {
                 int n1, n2, n3;
@@ -544,7 +573,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                     eexp[kMaxNb + off + o] = eb;
                 }
             }
-            if (!role_wait(&accfull[buf], (it / nbuf) & 1, P, et, eflag, 2, kEpi)) break;
+            if (!role_wait(&accfull[buf], (it >> 1) & 1, P, et, eflag, 2, kEpi)) break;
             tc_fence_after();
             // Scatter of the upper triangle.  The atom images of a batch are ordered so that
             // every slot pair a <= b is the canonical member of its partner pair; element
@@ -560,7 +589,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 for (int c0 = t * 128 + hh * 32; c0 < npad; c0 += 64) {
                     if (nrows <= 0 || c0 + 32 <= row0) continue;   // wholly below the diagonal
                     float v[32];
-                    const uint32_t col = (uint32_t)(buf * 256 + t * tile1 + c0 - t * 128);
+                    const uint32_t col = (uint32_t)(base + t * npad + c0 - t * 128);
                     const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + col;
                     tmem_ld16(taddr, v);
                     if (c0 + 16 < npad) tmem_ld16(taddr + 16, v + 16);
@@ -1294,7 +1323,8 @@ cudaError_t vlocal_launch(const Plan &P, const SInfo &si0, const SInfo *sis, cud
     cudaError_t e = set_smem(k_vlocal_tc<S>, smem);
     if (e != cudaSuccess) return e;
     const int grid = P.rng ? P.npart : std::min(nsm, P.nbatches);
-    k_vlocal_tc<S><<<grid, kThreadsTC, smem, s>>>(P, si0, sis, max_nb <= 192 ? 2 : 1);
+    (void)max_nb;
+    k_vlocal_tc<S><<<grid, kThreadsTC, smem, s>>>(P, si0, sis);
     return cudaGetLastError();
 }
 

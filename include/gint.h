@@ -155,9 +155,13 @@ gint_status gint_get_info(gint_handle h, gint_info_t *info);
 /* Move the atoms (host tau, natoms*3).  The block list (and with it the layout of H and of the
  * density matrix) must stay the same: if some pair enters or leaves the cutoff, nothing changes
  * and GINT_ESTATE is returned (build a new handle).  The batch -> atom-image lists are rebuilt
- * for the new positions on the host (in parallel over host threads); a decomposition whose lists
- * are unchanged keeps its device arrays and tables and receives the new slot positions only, one
- * whose lists changed is re-uploaded.  Blocking: the call synchronises with the device before
+ * for the new positions on the host (in parallel over host threads); a batch that keeps its
+ * list keeps its slot-pair tables, one whose list changed takes the entries of the atom images
+ * it kept from its old table and looks the others up.  A decomposition whose lists are all
+ * unchanged keeps its device arrays and tables and receives the new slot positions only, one
+ * whose lists changed is re-uploaded.  The result equals a handle set up at the new positions.
+ * The handle keeps the host arrays an update replaced, as storage for the next one (host memory
+ * about twice the lists').  Blocking: the call synchronises with the device before
  * replacing arrays.  A multi-structure job (gint_batch_create) copies the lists when it is
  * created: create it again after a move. */
 gint_status gint_update_positions(gint_handle h, const double *tau);

@@ -1,7 +1,9 @@
 // Internal data structures shared by the host set-up and the CUDA kernels of libgint.
 #pragma once
 #include <cstdint>
+#include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -109,18 +111,73 @@ constexpr int kKSeg = 16;
 constexpr int kMaxKCols = 4096;        // padded K columns of one batch
 __host__ __device__ constexpr int kpad(int norb) { return (norb + kKPad - 1) / kKPad * kKPad; }
 
+// Allocator whose resize leaves new elements of trivial types uninitialised: the set-up writes
+// every element of its large per-batch arrays itself, so a zero fill would only cost time.
+template <class T>
+struct DefaultInit : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = DefaultInit<U>;
+    };
+    DefaultInit() = default;
+    template <class U>
+    DefaultInit(const DefaultInit<U> &) {}
+    template <class U, class... A>
+    void construct(U *p, A &&...a)
+    {
+        if constexpr (sizeof...(A) == 0)
+            ::new ((void *)p) U;
+        else
+            ::new ((void *)p) U(std::forward<A>(a)...);
+    }
+};
+template <class T>
+using hvec = std::vector<T, DefaultInit<T>>;
+
+// Block key -> block index: open addressing over the packed keys (I, J, n), which are >= 0.
+struct KeyIndex {
+    std::vector<int64_t> key;
+    std::vector<int> val;
+    uint64_t mask = 0;
+    KeyIndex() = default;
+    explicit KeyIndex(const std::vector<int64_t> &packed)
+    {
+        size_t cap = 16;
+        while (cap < 2 * packed.size()) cap <<= 1;
+        key.assign(cap, -1);
+        val.assign(cap, -1);
+        mask = cap - 1;
+        for (size_t i = 0; i < packed.size(); ++i) {
+            uint64_t h = slot_of(packed[i]);
+            while (key[h] != -1) h = (h + 1) & mask;
+            key[h] = packed[i];
+            val[h] = (int)i;
+        }
+    }
+    uint64_t slot_of(int64_t k) const { return ((uint64_t)k * 0x9E3779B97F4A7C15ull >> 17) & mask; }
+    int find(int64_t k) const
+    {
+        for (uint64_t h = slot_of(k);; h = (h + 1) & mask) {
+            if (key[h] == k) return val[h];
+            if (key[h] == -1) return -1;
+        }
+    }
+};
+
 struct BatchSet {
     int dims[3] = {0, 0, 0};
-    std::vector<Batch> batches;
-    std::vector<Slot> slots;
-    std::vector<int> slot_img;       // 3 per slot: image n of the slot's atom
-    std::vector<int> tbl;
-    std::vector<int> koff;           // per slot: first column in the padded K layout
-    std::vector<int> tbl2;           // per slot pair (b, a): offset of block (b, a) in the split
+    hvec<Batch> batches;
+    hvec<Slot> slots;
+    hvec<int> slot_img;              // 3 per slot: image n of the slot's atom
+    hvec<int> tbl;
+    hvec<int> koff;                  // per slot: first column in the padded K layout
+    hvec<int> tbl2;                  // per slot pair (b, a): offset of block (b, a) in the split
                                      //   density-matrix store, or -1 (rho/force set only)
     int limit_nb = 256;              // batches with more orbitals are split
     bool padn = false;               // rho/force: N columns at the padded K offsets, padded
                                      //   density layout (otherwise N = the unpadded orbitals)
+    bool shared = false;             // rho/force: the lists, tables and offsets are copies of the
+                                     //   vlocal ones (same batch shape; only tbl2 is its own)
     int max_nb = 0, max_slots = 0;
     int max_k = 0;                   // largest padded K of a batch
     double flops_dense = 0.0;
@@ -154,7 +211,11 @@ struct gint_handle_s {
     std::vector<int32_t> keys;       // 5 per block
     std::vector<int64_t> offsets;    // nblocks + 1
     std::vector<int> partner;
+    std::vector<uint8_t> canon;      // per block: the canonical member of its partner pair
+    gint::KeyIndex kidx;             // block key -> block index
     gint::BatchSet bs[2];            // [0] vlocal batches, [1] rho/force batches
+    gint::BatchSet spare[2];         // host arrays of the lists a position update replaced, kept
+                                     //   (allocated and touched) for the next update to write into
     bool relist[2] = {false, false}; // a position update changed that decomposition's lists
     bool flops_stale = false;        // info.flops_useful predates the last position update
     std::vector<float4> coef32_host; // spline records, as uploaded

@@ -180,35 +180,6 @@ static void parallel_parts(int64_t n, int nparts, F &&f)
     for (auto &x : th) x.join();
 }
 
-// Block key -> block index (open addressing over the packed keys, which are >= 0).
-struct KeyIndex {
-    std::vector<int64_t> key;
-    std::vector<int> val;
-    uint64_t mask = 0;
-    explicit KeyIndex(const std::vector<int64_t> &packed)
-    {
-        size_t cap = 16;
-        while (cap < 2 * packed.size()) cap <<= 1;
-        key.assign(cap, -1);
-        val.assign(cap, -1);
-        mask = cap - 1;
-        for (size_t i = 0; i < packed.size(); ++i) {
-            uint64_t h = slot_of(packed[i]);
-            while (key[h] != -1) h = (h + 1) & mask;
-            key[h] = packed[i];
-            val[h] = (int)i;
-        }
-    }
-    uint64_t slot_of(int64_t k) const { return ((uint64_t)k * 0x9E3779B97F4A7C15ull >> 17) & mask; }
-    int find(int64_t k) const
-    {
-        for (uint64_t h = slot_of(k);; h = (h + 1) & mask) {
-            if (key[h] == k) return val[h];
-            if (key[h] == -1) return -1;
-        }
-    }
-};
-
 // ---------------------------------------------------------------------------------------
 // Position of a slot's atom image relative to its batch origin org: d0 = org - (tau_I + n.A),
 // in FP64 and as an FP32 hi + lo pair.
@@ -233,10 +204,40 @@ static inline void batch_origin(const BatchGeom &bg, int i0, int j0, int k0, dou
 // parts concatenated in order (the result does not depend on the number of parts).
 // With `old` (a position update): if every batch keeps its atom-image list, *same is set and
 // out.slots receives old's slots at the new positions (nothing else of out is filled).
+// Accepted batches of one host thread's rows of top-level cells, in order, with their sorted
+// atom-image lists.
+struct BatchAcc {
+    int i0, j0, k0, n1, n2, n3, r0, ns;   // accepted batch; its slots are raw[r0 .. r0 + ns)
+};
+struct BatchPart {
+    std::vector<BatchAcc> acc;
+    std::vector<RawSlot> raw;
+    BatchSet s;
+    gint_status st = GINT_OK;
+    bool padfail = false;   // failed only because of the padded N width
+    char err[256] = {0};
+};
+
+// The rho/force decomposition takes the vlocal lists when both use the same batch shape and
+// limits and every vlocal batch fits the rho/force layout (its padded width, with the padded
+// density layout): the vlocal build then also writes the rho/force slot-pair offsets.
+struct ShareReq {
+    const std::vector<int> *soff = nullptr;   // rho/force split-store offsets (null: no sharing)
+    bool allow = false;                       // the lists may be shared (a position update keeps
+                                              //   separate lists once the handle has them)
+    bool padn = false;                        // rho/force layout is the padded one
+    const BatchSet *old = nullptr;            // the handle's rho/force set, if it shared (update)
+    hvec<int> *tbl2 = nullptr;                // out: rho/force slot-pair offsets
+    bool ok = false;                          // out: the lists are shared
+    std::vector<BatchPart> parts;             // out: the vlocal batches and lists, which seed the
+                                              //   rho/force build when they are not shared
+};
+
 static gint_status build_batches(gint_handle h, const double *tau, const Geo &G, const BatchGeom &bg,
                                  const std::vector<double> &rc, const KeyIndex &kidx,
                                  const std::vector<int64_t> &offsets, const std::vector<uint8_t> &canon,
-                                 const std::vector<int> *soff, bool padn, bool *pad_fail, const BatchSet *old,
+                                 const std::vector<int> &partner, const std::vector<int> *soff, ShareReq *share,
+                                 const std::vector<BatchPart> *seed, bool padn, bool *pad_fail, const BatchSet *old,
                                  bool *same, BatchSet &out)
 {
     const int natoms = h->natoms;
@@ -248,19 +249,11 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
     // padded K axis, so the padded width must fit the accumulator's kMaxNb columns too
     if (same) *same = false;
     if (pad_fail) *pad_fail = false;
-    struct Acc {
-        int i0, j0, k0, n1, n2, n3, r0, ns;   // accepted batch; its slots are raw[r0 .. r0 + ns)
-    };
-    struct Part {
-        std::vector<Acc> acc;
-        std::vector<RawSlot> raw;
-        BatchSet s;
-        gint_status st = GINT_OK;
-        bool padfail = false;   // failed only because of the padded N width
-        char err[256] = {0};
-    };
+    using Acc = BatchAcc;
+    using Part = BatchPart;
     const int nparts = std::min(host_threads(), nb1);
     std::vector<Part> parts(nparts);
+    if (seed && (int)seed->size() != nparts) seed = nullptr;
     auto orb_count = [&](const std::vector<RawSlot> &s) {
         int n = 0;
         for (auto &x : s) n += h->norb_atom[x.atom];
@@ -310,8 +303,82 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                 pt.st = GINT_EINVAL;
             }
         };
+        struct Work {
+            int i0, j0, k0, n1, n2, n3;
+            std::vector<RawSlot> s;
+        };
+        // accepts w0, or splits it (halving the longest axis) until every piece fits the limits
+        auto run = [&](Work &&w0) {
+            std::vector<Work> stack;
+            stack.push_back(std::move(w0));
+            while (!stack.empty() && pt.st == GINT_OK) {
+                Work w = std::move(stack.back());
+                stack.pop_back();
+                std::sort(w.s.begin(), w.s.end(), slot_less);
+                int nb = orb_count(w.s);
+                const int pw = padn ? padded_width(w.s.data(), (int)w.s.size(), nullptr) : 0;
+                if (nb > limit_nb || (int)w.s.size() > kMaxSlots || pw > kMaxNb) {
+                    // halve the longest axis; a3 halves stay even so batch origins stay even
+                    int dims[3] = {w.n1, w.n2, w.n3};
+                    int ax = -1;
+                    for (int a = 0; a < 3; ++a) {
+                        bool can = (a == 2) ? dims[a] >= 4 : dims[a] >= 2;
+                        if (can && (ax < 0 || dims[a] > dims[ax])) ax = a;
+                    }
+                    if (ax < 0) {
+                        // cannot split further: accept up to the hard kernel limits
+                        if (nb <= kMaxNb && (int)w.s.size() <= kMaxSlots && pw <= kMaxNb) goto accept;
+                        if (nb <= kMaxNb && (int)w.s.size() <= kMaxSlots) pt.padfail = true;
+                        fail("gint_setup: a grid batch sees %d orbitals / %d atom images", nb, (int)w.s.size());
+                        break;
+                    }
+                    int cut = dims[ax] / 2;
+                    if (ax == 2 && (cut % 2)) cut += 1;
+                    Work a = w, b = w;
+                    if (ax == 0) { a.n1 = cut; b.i0 += cut; b.n1 -= cut; }
+                    if (ax == 1) { a.n2 = cut; b.j0 += cut; b.n2 -= cut; }
+                    if (ax == 2) { a.n3 = cut; b.k0 += cut; b.n3 -= cut; }
+                    for (Work *x : {&b, &a}) {
+                        double lo3[3], hi3[3], ctr[3], rad;
+                        batch_box(bg, x->i0, x->j0, x->k0, x->n1, x->n2, x->n3, lo3, hi3, ctr, &rad);
+                        std::vector<RawSlot> keep;
+                        for (auto &s : w.s) {
+                            double c[3];
+                            for (int q = 0; q < 3; ++q)
+                                c[q] = tau[3 * s.atom + q] + s.n[0] * G.A[q] + s.n[1] * G.A[3 + q] + s.n[2] * G.A[6 + q];
+                            if (sphere_meets_batch(bg, c, rc[s.atom], lo3, hi3, ctr, rad)) keep.push_back(s);
+                        }
+                        x->s = std::move(keep);
+                        stack.push_back(std::move(*x));
+                    }
+                    continue;
+                }
+            accept:
+                pt.acc.push_back({w.i0, w.j0, w.k0, w.n1, w.n2, w.n3, (int)pt.raw.size(), (int)w.s.size()});
+                pt.raw.insert(pt.raw.end(), w.s.begin(), w.s.end());
+            }
+        };
+        if (seed) {
+            // the vlocal batches of these rows (same shape and limits): this decomposition
+            // splits them further where a batch exceeds the padded layout's width
+            const Part &sp = (*seed)[part];
+            pt.raw.reserve(sp.raw.size());
+            pt.acc.reserve(sp.acc.size());
+            for (const Acc &A : sp.acc) {
+                if (pt.st != GINT_OK) break;
+                const RawSlot *l = sp.raw.data() + A.r0;
+                if (!padn || padded_width(l, A.ns, nullptr) <= kMaxNb) {
+                    pt.acc.push_back({A.i0, A.j0, A.k0, A.n1, A.n2, A.n3, (int)pt.raw.size(), A.ns});
+                    pt.raw.insert(pt.raw.end(), l, l + A.ns);
+                } else {
+                    run(Work{A.i0, A.j0, A.k0, A.n1, A.n2, A.n3, std::vector<RawSlot>(l, l + A.ns)});
+                }
+            }
+            return;
+        }
         const int rows = (int)(r1 - r0);
         std::vector<std::vector<RawSlot>> lists((size_t)rows * nb2 * nb3);
+        for (auto &l : lists) l.reserve(32);
         for (int I = 0; I < natoms; ++I) {
             const double *t = tau + 3 * I;
             int lo[3], hi[3];
@@ -379,63 +446,29 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                                 }
                     }
         }
-        struct Work {
-            int i0, j0, k0, n1, n2, n3;
-            std::vector<RawSlot> s;
-        };
+        {
+            size_t nraw = 0;
+            for (const auto &l : lists) nraw += l.size();
+            pt.raw.reserve(nraw);
+            pt.acc.reserve(lists.size());
+        }
         for (int b1 = (int)r0; b1 < (int)r1 && pt.st == GINT_OK; ++b1)
             for (int b2 = 0; b2 < nb2; ++b2)
                 for (int b3 = 0; b3 < nb3; ++b3) {
-                    std::vector<Work> stack;
-                    Work w0{b1 * B1, b2 * B2, b3 * B3, std::min(B1, N1 - b1 * B1), std::min(B2, N2 - b2 * B2),
-                            std::min(B3, N3 - b3 * B3), std::move(lists[((size_t)(b1 - r0) * nb2 + b2) * nb3 + b3])};
-                    stack.push_back(std::move(w0));
-                    while (!stack.empty() && pt.st == GINT_OK) {
-                        Work w = std::move(stack.back());
-                        stack.pop_back();
-                        std::sort(w.s.begin(), w.s.end(), slot_less);
-                        int nb = orb_count(w.s);
-                        const int pw = padn ? padded_width(w.s.data(), (int)w.s.size(), nullptr) : 0;
-                        if (nb > limit_nb || (int)w.s.size() > kMaxSlots || pw > kMaxNb) {
-                            // halve the longest axis; a3 halves stay even so batch origins stay even
-                            int dims[3] = {w.n1, w.n2, w.n3};
-                            int ax = -1;
-                            for (int a = 0; a < 3; ++a) {
-                                bool can = (a == 2) ? dims[a] >= 4 : dims[a] >= 2;
-                                if (can && (ax < 0 || dims[a] > dims[ax])) ax = a;
-                            }
-                            if (ax < 0) {
-                                // cannot split further: accept up to the hard kernel limits
-                                if (nb <= kMaxNb && (int)w.s.size() <= kMaxSlots && pw <= kMaxNb) goto accept;
-                                if (nb <= kMaxNb && (int)w.s.size() <= kMaxSlots) pt.padfail = true;
-                                fail("gint_setup: a grid batch sees %d orbitals / %d atom images", nb, (int)w.s.size());
-                                break;
-                            }
-                            int cut = dims[ax] / 2;
-                            if (ax == 2 && (cut % 2)) cut += 1;
-                            Work a = w, b = w;
-                            if (ax == 0) { a.n1 = cut; b.i0 += cut; b.n1 -= cut; }
-                            if (ax == 1) { a.n2 = cut; b.j0 += cut; b.n2 -= cut; }
-                            if (ax == 2) { a.n3 = cut; b.k0 += cut; b.n3 -= cut; }
-                            for (Work *x : {&b, &a}) {
-                                double lo3[3], hi3[3], ctr[3], rad;
-                                batch_box(bg, x->i0, x->j0, x->k0, x->n1, x->n2, x->n3, lo3, hi3, ctr, &rad);
-                                std::vector<RawSlot> keep;
-                                for (auto &s : w.s) {
-                                    double c[3];
-                                    for (int q = 0; q < 3; ++q)
-                                        c[q] = tau[3 * s.atom + q] + s.n[0] * G.A[q] + s.n[1] * G.A[3 + q] + s.n[2] * G.A[6 + q];
-                                    if (sphere_meets_batch(bg, c, rc[s.atom], lo3, hi3, ctr, rad)) keep.push_back(s);
-                                }
-                                x->s = std::move(keep);
-                                stack.push_back(std::move(*x));
-                            }
+                    std::vector<RawSlot> &l0 = lists[((size_t)(b1 - r0) * nb2 + b2) * nb3 + b3];
+                    const int n01 = std::min(B1, N1 - b1 * B1), n02 = std::min(B2, N2 - b2 * B2),
+                              n03 = std::min(B3, N3 - b3 * B3);
+                    {
+                        // the common case, a cell that needs no split, without the work stack
+                        std::sort(l0.begin(), l0.end(), slot_less);
+                        const int pw = padn ? padded_width(l0.data(), (int)l0.size(), nullptr) : 0;
+                        if (orb_count(l0) <= limit_nb && (int)l0.size() <= kMaxSlots && pw <= kMaxNb) {
+                            pt.acc.push_back({b1 * B1, b2 * B2, b3 * B3, n01, n02, n03, (int)pt.raw.size(), (int)l0.size()});
+                            pt.raw.insert(pt.raw.end(), l0.begin(), l0.end());
                             continue;
                         }
-                    accept:
-                        pt.acc.push_back({w.i0, w.j0, w.k0, w.n1, w.n2, w.n3, (int)pt.raw.size(), (int)w.s.size()});
-                        pt.raw.insert(pt.raw.end(), w.s.begin(), w.s.end());
                     }
+                    run(Work{b1 * B1, b2 * B2, b3 * B3, n01, n02, n03, std::move(l0)});
                 }
     });
     std::vector<size_t> bat0(nparts + 1, 0);
@@ -450,6 +483,19 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
     if (bat0[nparts] >= ((size_t)1 << 31)) {
         set_error("gint_setup: too many batches");
         return GINT_EINVAL;
+    }
+    if (share && share->soff) {
+        std::vector<int> fits(nparts, 1);
+        if (share->padn && share->allow)
+            parallel_parts(nparts, nparts, [&](int64_t t0, int64_t t1, int) {
+                for (int64_t t = t0; t < t1; ++t)
+                    for (const Acc &A : parts[t].acc)
+                        if (padded_width(parts[t].raw.data() + A.r0, A.ns, nullptr) > kMaxNb) {
+                            fits[t] = 0;
+                            break;
+                        }
+            });
+        share->ok = share->allow && std::all_of(fits.begin(), fits.end(), [](int x) { return x != 0; });
     }
     // a position update whose lists are all unchanged: the old slots at the new positions
     if (old && old->batches.size() == bat0[nparts]) {
@@ -477,18 +523,9 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
             }
         });
         if (std::all_of(eq.begin(), eq.end(), [](int x) { return x != 0; })) {
-            out.slots = old->slots;
-            const size_t nbat = old->batches.size();
-            parallel_parts((int64_t)nbat, host_threads(), [&](int64_t q0, int64_t q1, int) {
-                for (int64_t q = q0; q < q1; ++q) {
-                    const Batch &B = old->batches[q];
-                    double org[3];
-                    batch_origin(bg, B.i0, B.j0, B.k0, org);
-                    for (int s = 0; s < B.nslots; ++s)
-                        slot_position(out.slots[B.slot0 + s], org, tau, &old->slot_img[3 * ((size_t)B.slot0 + s)], G);
-                }
-            });
+            // the caller writes the new slot positions into the handle's records
             if (same) *same = true;
+            if (share && share->soff) share->parts = std::move(parts);
             return GINT_OK;
         }
     }
@@ -515,14 +552,24 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
     out.slot_img.resize(3 * sl0[nparts]);
     out.koff.resize(sl0[nparts]);
     out.tbl.resize(tb0[nparts]);
-    if (soff) out.tbl2.resize(tb0[nparts]);
-    std::unordered_map<int64_t, int> oldpos;   // batch origin (grid index) -> batch of old
-    const bool reuse = old && old->koff.size() == old->slots.size() && (!soff || old->tbl2.size() == old->tbl.size());
+    // slot-pair offsets into the split store: this set's own (rho/force), or the rho/force set's
+    // when it shares these lists (written next to the vlocal tables)
+    const std::vector<int> *sf = soff ? soff : (share && share->ok ? share->soff : nullptr);
+    hvec<int> *t2v = soff ? &out.tbl2 : (sf ? share->tbl2 : nullptr);
+    if (t2v) t2v->resize(tb0[nparts]);
+    int *const t2 = t2v ? t2v->data() : nullptr;
+    const hvec<int> *old_t2 = !old ? nullptr : soff ? &old->tbl2 : (sf && share->old ? &share->old->tbl2 : nullptr);
+    // batches of old by top-level cell: the batches a cell was split into are consecutive
+    // (cell -> first such batch, or -1)
+    const bool reuse =
+        old && old->koff.size() == old->slots.size() && (!sf || (old_t2 && old_t2->size() == old->tbl.size()));
+    std::vector<int> oldcell;
+    auto cell_of = [&](int i0, int j0, int k0) { return ((int64_t)(i0 / B1) * nb2 + j0 / B2) * nb3 + k0 / B3; };
     if (reuse) {
-        oldpos.reserve(old->batches.size() * 2);
-        for (size_t q = 0; q < old->batches.size(); ++q) {
+        oldcell.assign((size_t)nb1 * nb2 * nb3, -1);
+        for (size_t q = old->batches.size(); q-- > 0;) {
             const Batch &B = old->batches[q];
-            oldpos.emplace(((int64_t)B.i0 * N2 + B.j0) * N3 + B.k0, (int)q);
+            oldcell[cell_of(B.i0, B.j0, B.k0)] = (int)q;
         }
     }
     parallel_parts(nparts, nparts, [&](int64_t t0, int64_t t1, int) {
@@ -547,11 +594,17 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                 o.max_slots = std::max(o.max_slots, A.ns);
                 double org[3];
                 batch_origin(bg, A.i0, A.j0, A.k0, org);
-                const Batch *ob = nullptr;
+                const Batch *ob = nullptr, *near = nullptr;   // old batch at this origin: same list / other
                 if (reuse) {
-                    auto it = oldpos.find(((int64_t)A.i0 * N2 + A.j0) * N3 + A.k0);
-                    if (it != oldpos.end()) {
-                        const Batch &C = old->batches[it->second];
+                    const int64_t cell = cell_of(A.i0, A.j0, A.k0);
+                    int q0 = oldcell[cell];
+                    while (q0 >= 0 && q0 < (int)old->batches.size() &&
+                           cell_of(old->batches[q0].i0, old->batches[q0].j0, old->batches[q0].k0) == cell &&
+                           (old->batches[q0].i0 != A.i0 || old->batches[q0].j0 != A.j0 || old->batches[q0].k0 != A.k0))
+                        ++q0;
+                    if (q0 >= 0 && q0 < (int)old->batches.size() && old->batches[q0].i0 == A.i0 &&
+                        old->batches[q0].j0 == A.j0 && old->batches[q0].k0 == A.k0) {
+                        const Batch &C = old->batches[q0];
                         bool eq = C.dims == B.dims && C.nslots == A.ns;
                         for (int s = 0; eq && s < A.ns; ++s) {
                             const int *n = &old->slot_img[3 * ((size_t)C.slot0 + s)];
@@ -559,6 +612,7 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                                  n[2] == ws[s].n[2];
                         }
                         if (eq) ob = &C;
+                        else near = &C;
                     }
                 }
                 if (ob) {
@@ -571,7 +625,7 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                     }
                     std::copy_n(old->slot_img.begin() + 3 * (size_t)ob->slot0, 3 * A.ns, out.slot_img.begin() + 3 * so);
                     std::copy_n(old->tbl.begin() + ob->tbl, (size_t)A.ns * A.ns, out.tbl.begin() + to);
-                    if (soff) std::copy_n(old->tbl2.begin() + ob->tbl, (size_t)A.ns * A.ns, out.tbl2.begin() + to);
+                    if (t2) std::copy_n(old_t2->begin() + ob->tbl, (size_t)A.ns * A.ns, t2 + to);
                     o.max_k = std::max(o.max_k, padded_width(ws, A.ns, nullptr));
                 } else {
                     std::vector<int> ko;
@@ -590,24 +644,59 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                         out.koff[so + s] = ko[s];
                         for (int c = 0; c < 3; ++c) out.slot_img[3 * (so + s) + c] = ws[s].n[c];
                     }
+                    // om[s]: the slot of the old batch at this origin with the same atom image, or
+                    // -1 (both lists are in slot order); a pair of such slots takes the old entries
+                    int om[kMaxSlots];
+                    for (int s = 0; s < A.ns; ++s) om[s] = -1;
+                    if (near)
+                        for (int s = 0, j = 0; s < A.ns && j < near->nslots;) {
+                            const size_t g = (size_t)near->slot0 + j;
+                            const RawSlot r{old->slots[g].atom,
+                                            {old->slot_img[3 * g], old->slot_img[3 * g + 1], old->slot_img[3 * g + 2]}};
+                            if (slot_less(ws[s], r)) {
+                                ++s;
+                            } else if (slot_less(r, ws[s])) {
+                                ++j;
+                            } else {
+                                om[s++] = j++;
+                            }
+                        }
+                    // one look-up per unordered slot pair: block (I_b, I_a, n_a - n_b) of the pair
+                    // (b, a) is the partner of block (I_a, I_b, n_b - n_a)
                     for (int ia = 0; ia < A.ns && pt.st == GINT_OK; ++ia)
-                        for (int ib = 0; ib < A.ns; ++ib) {
+                        for (int ib = ia; ib < A.ns; ++ib) {
+                            const size_t x = to + (size_t)ia * A.ns + ib, xt = to + (size_t)ib * A.ns + ia;
+                            if (om[ia] >= 0 && om[ib] >= 0) {
+                                const size_t ox = (size_t)near->tbl + (size_t)om[ia] * near->nslots + om[ib],
+                                             oxt = (size_t)near->tbl + (size_t)om[ib] * near->nslots + om[ia];
+                                out.tbl[x] = old->tbl[ox];
+                                out.tbl[xt] = old->tbl[oxt];
+                                if (t2) {
+                                    t2[x] = (*old_t2)[ox];
+                                    t2[xt] = (*old_t2)[oxt];
+                                }
+                                continue;
+                            }
                             const RawSlot &sa = ws[ia], &sb = ws[ib];
                             const int bi = kidx.find(
                                 pack_key(sa.atom, sb.atom, sb.n[0] - sa.n[0], sb.n[1] - sa.n[1], sb.n[2] - sa.n[2]));
-                            const size_t x = to + (size_t)ia * A.ns + ib;
                             if (bi < 0) {
-                                out.tbl[x] = -1;
-                                if (soff) out.tbl2[x] = -1;
-                            } else {
-                                if (ia <= ib && !canon[bi]) {
-                                    snprintf(pt.err, sizeof(pt.err), "%s",
-                                             "gint_setup: internal error, slot order breaks the canonical-pair rule");
-                                    pt.st = GINT_EINVAL;
-                                    break;
-                                }
-                                out.tbl[x] = (int)((offsets[bi] << 1) | canon[bi]);
-                                if (soff) out.tbl2[x] = (*soff)[bi];
+                                out.tbl[x] = out.tbl[xt] = -1;
+                                if (t2) t2[x] = t2[xt] = -1;
+                                continue;
+                            }
+                            if (!canon[bi]) {
+                                snprintf(pt.err, sizeof(pt.err), "%s",
+                                         "gint_setup: internal error, slot order breaks the canonical-pair rule");
+                                pt.st = GINT_EINVAL;
+                                break;
+                            }
+                            const int bt = partner[bi];
+                            out.tbl[x] = (int)((offsets[bi] << 1) | canon[bi]);
+                            out.tbl[xt] = (int)((offsets[bt] << 1) | canon[bt]);
+                            if (t2) {
+                                t2[x] = (*sf)[bi];
+                                t2[xt] = (*sf)[bt];
                             }
                         }
                 }
@@ -615,7 +704,7 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                 so += A.ns;
                 to += (size_t)A.ns * A.ns;
             }
-            std::vector<RawSlot>().swap(pt.raw);
+            if (!(share && share->soff)) std::vector<RawSlot>().swap(pt.raw);
         }
     });
     for (auto &pt : parts) {
@@ -628,7 +717,58 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
         out.max_slots = std::max(out.max_slots, pt.s.max_slots);
         out.max_k = std::max(out.max_k, pt.s.max_k);
     }
+    if (share && share->soff) share->parts = std::move(parts);
     return GINT_OK;
+}
+
+static BatchGeom batch_geom(const gint_handle_s *h)
+{
+    BatchGeom bg;
+    bg.ortho = true;
+    for (int i = 0; i < 3; ++i)
+        for (int c = 0; c < 3; ++c)
+            if (i != c && h->cell[3 * i + c] != 0.0) bg.ortho = false;
+    for (int i = 0; i < 3; ++i)
+        for (int c = 0; c < 3; ++c) bg.h[3 * i + c] = h->cell[3 * i + c] / h->grid[i];
+    return bg;
+}
+
+template <class V>
+static void par_copy(V &dst, const V &src)
+{
+    dst.resize(src.size());
+    parallel_parts((int64_t)src.size(), src.size() < ((size_t)1 << 16) ? 1 : host_threads(),
+                   [&](int64_t a, int64_t b, int) { std::copy(src.begin() + a, src.begin() + b, dst.begin() + a); });
+}
+
+// Moves the host arrays of src into dst, emptied but keeping their capacity.
+static void take_storage(BatchSet &dst, BatchSet &src)
+{
+    dst.batches = std::move(src.batches);
+    dst.slots = std::move(src.slots);
+    dst.slot_img = std::move(src.slot_img);
+    dst.tbl = std::move(src.tbl);
+    dst.koff = std::move(src.koff);
+    dst.tbl2 = std::move(src.tbl2);
+    for (auto *v : {&dst.slot_img, &dst.tbl, &dst.koff, &dst.tbl2}) v->clear();
+    dst.batches.clear();
+    dst.slots.clear();
+}
+
+// New positions of the slots of a decomposition whose atom-image lists are unchanged, in place.
+static void place_slots(const gint_handle_s *h, BatchSet &bs, const double *tau)
+{
+    const Geo G = make_geo(h->cell);
+    const BatchGeom bg = batch_geom(h);
+    parallel_parts((int64_t)bs.batches.size(), host_threads(), [&](int64_t q0, int64_t q1, int) {
+        for (int64_t q = q0; q < q1; ++q) {
+            const Batch &B = bs.batches[q];
+            double org[3];
+            batch_origin(bg, B.i0, B.j0, B.k0, org);
+            for (int s = 0; s < B.nslots; ++s)
+                slot_position(bs.slots[B.slot0 + s], org, tau, &bs.slot_img[3 * ((size_t)B.slot0 + s)], G);
+        }
+    });
 }
 
 // ---------------------------------------------------------------------------------------
@@ -643,10 +783,14 @@ gint_status build_geometry(gint_handle h, const double *tau, const gint_handle_s
     for (int I = 0; I < natoms; ++I) rc[I] = P.sp[h->species[I]].rcut;
 
     // ---- block list: all (I, J, n) with |tau_J + n.A - tau_I| < rc_I + rc_J (rows I in parts,
-    // one host thread each, joined in order)
+    // one host thread each, joined in order).  |v| < r bounds the fractional coordinate
+    // g_i.v = s_i + n_i of v by r |g_i|, which gives each image index's range.
     std::vector<int32_t> keys;
     std::vector<int64_t> packed;
     {
+        std::vector<double> fr(3 * (size_t)natoms);
+        for (int I = 0; I < natoms; ++I)
+            for (int i = 0; i < 3; ++i) fr[3 * I + i] = frac_of(G, tau + 3 * I, i);
         const int nparts = std::min(host_threads(), natoms);
         std::vector<std::vector<int32_t>> pkeys(nparts);
         std::vector<std::vector<int64_t>> ppacked(nparts);
@@ -654,25 +798,28 @@ gint_status build_geometry(gint_handle h, const double *tau, const gint_handle_s
         parallel_parts(natoms, nparts, [&](int64_t i0, int64_t i1, int part) {
             for (int I = (int)i0; I < (int)i1 && !bad[part]; ++I) {
                 for (int J = 0; J < natoms; ++J) {
-                    double rs = rc[I] + rc[J];
-                    double dt[3] = {tau[3 * J] - tau[3 * I], tau[3 * J + 1] - tau[3 * I + 1], tau[3 * J + 2] - tau[3 * I + 2]};
+                    const double rs = rc[I] + rc[J], rr = rs * rs;
+                    const double dt[3] = {tau[3 * J] - tau[3 * I], tau[3 * J + 1] - tau[3 * I + 1],
+                                          tau[3 * J + 2] - tau[3 * I + 2]};
                     int lo[3], hi[3];
                     for (int i = 0; i < 3; ++i) {
-                        double s = frac_of(G, dt, i);
-                        lo[i] = (int)std::floor(-s - rs * G.gn[i]) - 1;
-                        hi[i] = (int)std::ceil(-s + rs * G.gn[i]) + 1;
+                        const double s = fr[3 * J + i] - fr[3 * I + i], x = rs * G.gn[i];
+                        lo[i] = (int)std::floor(-s - x);
+                        hi[i] = (int)std::ceil(-s + x);
                     }
                     for (int n1 = lo[0]; n1 <= hi[0]; ++n1)
-                        for (int n2 = lo[1]; n2 <= hi[1]; ++n2)
+                        for (int n2 = lo[1]; n2 <= hi[1]; ++n2) {
+                            double v12[3];
+                            for (int x = 0; x < 3; ++x) v12[x] = dt[x] + n1 * G.A[x] + n2 * G.A[3 + x];
                             for (int n3 = lo[2]; n3 <= hi[2]; ++n3) {
-                                double v[3];
-                                for (int x = 0; x < 3; ++x) v[x] = dt[x] + n1 * G.A[x] + n2 * G.A[3 + x] + n3 * G.A[6 + x];
-                                if (v[0] * v[0] + v[1] * v[1] + v[2] * v[2] < rs * rs) {
+                                const double v[3] = {v12[0] + n3 * G.A[6], v12[1] + n3 * G.A[7], v12[2] + n3 * G.A[8]};
+                                if (v[0] * v[0] + v[1] * v[1] + v[2] * v[2] < rr) {
                                     if (std::abs(n1) > 63 || std::abs(n2) > 63 || std::abs(n3) > 63) bad[part] = 1;
                                     pkeys[part].insert(pkeys[part].end(), {I, J, n1, n2, n3});
-                                    ppacked[part].push_back(pack_key(I, J, n1, n2, n3));
+                                    if (!update_only) ppacked[part].push_back(pack_key(I, J, n1, n2, n3));
                                 }
                             }
+                        }
                 }
             }
         });
@@ -681,81 +828,131 @@ gint_status build_geometry(gint_handle h, const double *tau, const gint_handle_s
                 set_error("gint_setup: periodic image index beyond 63 (cell too small for rcut)");
                 return GINT_EINVAL;
             }
-            keys.insert(keys.end(), pkeys[t].begin(), pkeys[t].end());
-            packed.insert(packed.end(), ppacked[t].begin(), ppacked[t].end());
+        }
+        if (update_only) {
+            // the block list must be the handle's, in the same order
+            bool eq = true;
+            size_t at = 0;
+            for (int t = 0; t < nparts && eq; ++t) {
+                eq = at + pkeys[t].size() <= old->keys.size() &&
+                     std::equal(pkeys[t].begin(), pkeys[t].end(), old->keys.begin() + at);
+                at += pkeys[t].size();
+            }
+            if (!eq || at != old->keys.size()) {
+                set_error("gint_update_positions: block list changed; build a new handle");
+                return GINT_ESTATE;
+            }
+        } else {
+            for (int t = 0; t < nparts; ++t) {
+                keys.insert(keys.end(), pkeys[t].begin(), pkeys[t].end());
+                packed.insert(packed.end(), ppacked[t].begin(), ppacked[t].end());
+            }
         }
     }
-    const int64_t nblocks = (int64_t)packed.size();
-    if (update_only) {
-        if (keys != old->keys) {
-            set_error("gint_update_positions: block list changed; build a new handle");
-            return GINT_ESTATE;
-        }
-    }
-    std::vector<int64_t> offsets(nblocks + 1, 0);
-    std::vector<int> rows(nblocks);
-    for (int64_t b = 0; b < nblocks; ++b) {
-        rows[b] = h->norb_atom[keys[5 * b]];
-        offsets[b + 1] = offsets[b] + (int64_t)h->norb_atom[keys[5 * b]] * h->norb_atom[keys[5 * b + 1]];
-    }
-    if (offsets[nblocks] >= ((int64_t)1 << 30)) {
-        set_error("gint_setup: block store of %lld values exceeds 2^30", (long long)offsets[nblocks]);
-        return GINT_EINVAL;
-    }
-    // offsets of the blocks in the split density-matrix store, per term.  Padded layout: rows and
-    // columns padded to kpad, a block holds all its terms (element offset NT soff[b]).  Row
-    // layout: rows n_I, columns padded, each term in its own plane of splane elements.
-    std::vector<int> soff_pad(nblocks), soff_row(nblocks);
+    // Block offsets, split-store offsets, key index and partner blocks depend on the block list
+    // only: a position update (same list) takes the handle's.
+    std::vector<int64_t> offsets;
+    std::vector<int> soff_pad, soff_row, partner;
+    std::vector<uint8_t> canon;
+    KeyIndex kidx_new;
     int64_t splane_pad = 0, splane_row = 0;
-    for (int64_t b = 0; b < nblocks; ++b) {
-        const int nI = h->norb_atom[keys[5 * b]], nJ = h->norb_atom[keys[5 * b + 1]];
-        soff_pad[b] = (int)splane_pad;
-        soff_row[b] = (int)splane_row;
-        splane_pad += (int64_t)kpad(nI) * kpad(nJ);
-        splane_row += (int64_t)nI * kpad(nJ);
-    }
-    const int64_t splane = splane_pad;   // the larger of the two
-    if (splane >= ((int64_t)1 << 30)) {
-        set_error("gint_setup: padded block store of %lld values exceeds 2^30", (long long)splane);
-        return GINT_EINVAL;
-    }
-    const KeyIndex kidx(packed);
-    std::vector<int> partner(nblocks);
-    std::vector<uint8_t> canon(nblocks);
-    for (int64_t b = 0; b < nblocks; ++b) {
-        const int32_t *k = &keys[5 * b];
-        int64_t pk = pack_key(k[1], k[0], -k[2], -k[3], -k[4]);
-        const int pb = kidx.find(pk);
-        if (pb < 0) {
-            set_error("gint_setup: internal error, partner block missing");
+    if (!update_only) {
+        const int64_t nblocks = (int64_t)packed.size();
+        offsets.assign(nblocks + 1, 0);
+        for (int64_t b = 0; b < nblocks; ++b)
+            offsets[b + 1] = offsets[b] + (int64_t)h->norb_atom[keys[5 * b]] * h->norb_atom[keys[5 * b + 1]];
+        if (offsets[nblocks] >= ((int64_t)1 << 30)) {
+            set_error("gint_setup: block store of %lld values exceeds 2^30", (long long)offsets[nblocks]);
             return GINT_EINVAL;
         }
-        partner[b] = pb;
-        canon[b] = packed[b] <= pk;
+        // offsets of the blocks in the split density-matrix store, per term.  Padded layout: rows
+        // and columns padded to kpad, a block holds all its terms (element offset NT soff[b]).
+        // Row layout: rows n_I, columns padded, each term in its own plane of splane elements.
+        soff_pad.resize(nblocks);
+        soff_row.resize(nblocks);
+        for (int64_t b = 0; b < nblocks; ++b) {
+            const int nI = h->norb_atom[keys[5 * b]], nJ = h->norb_atom[keys[5 * b + 1]];
+            soff_pad[b] = (int)splane_pad;
+            soff_row[b] = (int)splane_row;
+            splane_pad += (int64_t)kpad(nI) * kpad(nJ);
+            splane_row += (int64_t)nI * kpad(nJ);
+        }
+        if (splane_pad >= ((int64_t)1 << 30)) {   // the larger of the two
+            set_error("gint_setup: padded block store of %lld values exceeds 2^30", (long long)splane_pad);
+            return GINT_EINVAL;
+        }
+        kidx_new = KeyIndex(packed);
+        partner.resize(nblocks);
+        canon.resize(nblocks);
+        for (int64_t b = 0; b < nblocks; ++b) {
+            const int32_t *k = &keys[5 * b];
+            int64_t pk = pack_key(k[1], k[0], -k[2], -k[3], -k[4]);
+            const int pb = kidx_new.find(pk);
+            if (pb < 0) {
+                set_error("gint_setup: internal error, partner block missing");
+                return GINT_EINVAL;
+            }
+            partner[b] = pb;
+            canon[b] = packed[b] <= pk;
+        }
     }
+    const KeyIndex &kidx = update_only ? old->kidx : kidx_new;
+    const std::vector<int64_t> &offs = update_only ? old->offsets : offsets;
+    const std::vector<uint8_t> &can = update_only ? old->canon : canon;
+    const std::vector<int> &part = update_only ? old->partner : partner;
 
     // ---- batches and their atom-image slots, once per decomposition
-    BatchGeom bg;
-    bg.ortho = true;
-    for (int i = 0; i < 3; ++i)
-        for (int c = 0; c < 3; ++c)
-            if (i != c && h->cell[3 * i + c] != 0.0) bg.ortho = false;
-    for (int i = 0; i < 3; ++i)
-        for (int c = 0; c < 3; ++c) bg.h[3 * i + c] = h->cell[3 * i + c] / h->grid[i];
+    const BatchGeom bg = batch_geom(h);
     BatchSet sets[2];
     bool same[2] = {false, false};
     const int *dims[2] = {h->opt.batch, h->opt.batch_rho};
     for (int w = 0; w < 2; ++w) {
+        // a position update writes into the storage the caller left in h->bs (earlier lists)
+        if (update_only) take_storage(sets[w], h->bs[w]);
         for (int i = 0; i < 3; ++i) sets[w].dims[i] = dims[w][i];
         // vlocal batches of up to 64 points stay within 192 orbitals (two accumulators fit in
         // tensor memory); larger ones use the full 256 with one accumulator
         sets[w].limit_nb = (w == 0 && dims[w][0] * dims[w][1] * dims[w][2] <= 64) ? 192 : kMaxNb;
-        // the rho/force decomposition takes the padded density layout when every batch fits it
-        // (a position update keeps the handle's layout)
-        bool padn = w == 1 && (update_only ? old->bs[1].padn : true), pad_fail = false;
-        gint_status st = build_batches(h, tau, G, bg, rc, kidx, offsets, canon,
-                                       w == 1 ? (padn ? &soff_pad : &soff_row) : nullptr, padn, &pad_fail,
-                                       update_only ? &old->bs[w] : nullptr, &same[w], sets[w]);
+    }
+    // the rho/force decomposition takes the padded density layout when every batch fits it (a
+    // position update keeps the handle's layout and its split-store offsets)
+    const bool padn1 = update_only ? old->bs[1].padn : true;
+    ShareReq share;
+    if (std::equal(dims[0], dims[0] + 3, dims[1]) && sets[0].limit_nb == sets[1].limit_nb) {
+        share.soff = update_only ? &old->soff : &soff_pad;
+        share.allow = !update_only || old->bs[1].shared;
+        share.padn = padn1;
+        share.old = update_only && old->bs[1].shared ? &old->bs[1] : nullptr;
+        share.tbl2 = &sets[1].tbl2;
+    }
+    for (int w = 0; w < 2; ++w) {
+        if (w == 1 && share.ok) {
+            // the vlocal lists, tables and offsets; the slot-pair offsets are written already
+            if (same[0]) {
+                same[1] = true;
+            } else {
+                BatchSet &d = sets[1];
+                const BatchSet &v = sets[0];
+                par_copy(d.batches, v.batches);
+                par_copy(d.slots, v.slots);
+                par_copy(d.slot_img, v.slot_img);
+                par_copy(d.tbl, v.tbl);
+                par_copy(d.koff, v.koff);
+                d.max_nb = v.max_nb;
+                d.max_slots = v.max_slots;
+                d.max_k = v.max_k;
+                d.flops_dense = v.flops_dense;
+            }
+            sets[1].padn = padn1;
+            sets[1].shared = true;
+            continue;
+        }
+        bool padn = w == 1 && padn1, pad_fail = false;
+        const std::vector<int> *soff = w == 0 ? nullptr : update_only ? &old->soff : padn ? &soff_pad : &soff_row;
+        // a rho/force build of the vlocal batch shape starts from the vlocal batches
+        const std::vector<BatchPart> *seed = w == 1 && share.soff && !share.parts.empty() ? &share.parts : nullptr;
+        gint_status st = build_batches(h, tau, G, bg, rc, kidx, offs, can, part, soff, w == 0 ? &share : nullptr, seed,
+                                       padn, &pad_fail, update_only ? &old->bs[w] : nullptr, &same[w], sets[w]);
         if (st != GINT_OK && pad_fail && update_only) {
             set_error("gint_update_positions: a batch no longer fits the padded density layout; build a new handle");
             return GINT_ESTATE;
@@ -765,19 +962,20 @@ gint_status build_geometry(gint_handle h, const double *tau, const gint_handle_s
             sets[w] = BatchSet{};
             for (int i = 0; i < 3; ++i) sets[w].dims[i] = dims[w][i];
             sets[w].limit_nb = kMaxNb;
-            st = build_batches(h, tau, G, bg, rc, kidx, offsets, canon, &soff_row, false, nullptr, nullptr, &same[w],
-                               sets[w]);
+            st = build_batches(h, tau, G, bg, rc, kidx, offs, can, part, &soff_row, nullptr, seed, false, nullptr,
+                               nullptr, &same[w], sets[w]);
         }
         if (st != GINT_OK) return st;
         sets[w].padn = padn;
+        sets[w].shared = false;
         if (!same[w] && sets[w].max_k + 32 > kMaxKCols) {
             set_error("gint_setup: a batch's padded orbital columns (%d) exceed %d", sets[w].max_k, kMaxKCols - 32);
             return GINT_EINVAL;
         }
     }
     if (update_only) {
-        // a decomposition whose atom-image lists are unchanged gets new slot positions only
-        // (sets[w] holds just the slots); one whose lists changed is replaced as a whole
+        // a decomposition whose atom-image lists are unchanged gets new slot positions only, in
+        // place (sets[w] holds the unused storage); one whose lists changed is replaced as a whole
         for (int w = 0; w < 2; ++w) {
             h->bs[w] = std::move(sets[w]);
             h->relist[w] = !same[w];
@@ -786,15 +984,14 @@ gint_status build_geometry(gint_handle h, const double *tau, const gint_handle_s
         h->keys = std::move(keys);
         h->offsets = std::move(offsets);
         h->partner = std::move(partner);
+        h->canon = std::move(canon);
+        h->kidx = std::move(kidx_new);
         const bool pad = sets[1].padn;
         h->soff = pad ? std::move(soff_pad) : std::move(soff_row);
         h->dms_plane = ((pad ? splane_pad : splane_row) + 7) / 8 * 8;
         for (int w = 0; w < 2; ++w) h->bs[w] = std::move(sets[w]);
     }
     h->tau.assign(tau, tau + 3 * natoms);
-    (void)rows;
-    (void)nblocks;
-    (void)N1; (void)N2; (void)N3;
     h->plan.dV = std::fabs(G.det) / ((double)N1 * N2 * N3);
     for (int i = 0; i < 3; ++i)
         for (int c = 0; c < 3; ++c) h->plan.h[3 * i + c] = bg.h[3 * i + c];
@@ -915,9 +1112,10 @@ std::vector<int2> segment_ranges(const Batch *b, const std::vector<int> &seg, in
 // ---------------------------------------------------------------------------------------
 using namespace gint;
 
-template <class T>
-static cudaError_t upload(void **dst, const std::vector<T> &v)
+template <class Vec>
+static cudaError_t upload(void **dst, const Vec &v)
 {
+    using T = typename Vec::value_type;
     size_t bytes = std::max<size_t>(sizeof(T), v.size() * sizeof(T));
     cudaError_t e = cudaMalloc(dst, bytes);
     if (e != cudaSuccess) return e;
@@ -1283,7 +1481,7 @@ extern "C" gint_status gint_update_positions(gint_handle h, const double *tau)
             return GINT_EINVAL;
         }
     // build into a scratch handle (compared with this one) so a topology change leaves the
-    // handle untouched
+    // handle untouched; the lists are written into the storage the previous update replaced
     gint_handle_s tmp;
     tmp.plan = h->plan;
     memcpy(tmp.cell, h->cell, sizeof(tmp.cell));
@@ -1293,17 +1491,25 @@ extern "C" gint_status gint_update_positions(gint_handle h, const double *tau)
     tmp.species = h->species;
     tmp.norb_atom = h->norb_atom;
     tmp.opt = h->opt;
-    for (int w = 0; w < 2; ++w) tmp.bs[w].limit_nb = h->bs[w].limit_nb;
+    for (int w = 0; w < 2; ++w) {
+        take_storage(tmp.bs[w], h->spare[w]);
+        tmp.bs[w].limit_nb = h->bs[w].limit_nb;
+    }
     gint_status st = build_geometry(&tmp, tau, h);
-    if (st != GINT_OK) return st;
+    if (st != GINT_OK) {
+        for (int w = 0; w < 2; ++w) take_storage(h->spare[w], tmp.bs[w]);
+        return st;
+    }
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(e, "gint_update_positions");
     for (int w = 0; w < 2; ++w) {
         h->relist[w] = tmp.relist[w];
+        BatchSet &o = h->bs[w];
         if (tmp.relist[w]) {
-            // the new lists, with the old device arrays (freed and replaced by upload_geometry)
-            BatchSet &o = h->bs[w];
+            // the new lists, with the old device arrays (freed and replaced by upload_geometry);
+            // the old host arrays become the storage of the next update
             void *dev[6] = {o.d_batches, o.d_slots, o.d_tbl, o.d_rng, o.d_koff, o.d_tbl2};
+            take_storage(h->spare[w], o);
             o = std::move(tmp.bs[w]);
             o.d_batches = dev[0];
             o.d_slots = dev[1];
@@ -1312,7 +1518,8 @@ extern "C" gint_status gint_update_positions(gint_handle h, const double *tau)
             o.d_koff = dev[4];
             o.d_tbl2 = dev[5];
         } else {
-            h->bs[w].slots = std::move(tmp.bs[w].slots);
+            take_storage(h->spare[w], tmp.bs[w]);
+            place_slots(h, o, tau);
         }
     }
     h->tau = std::move(tmp.tau);

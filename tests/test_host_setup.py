@@ -1,0 +1,131 @@
+"""Host logic of the set-up and of position updates, on the CPU: gint_setup.cpp is compiled with
+host-memory stand-ins for the CUDA runtime calls it makes (tests/host/cuda_stub.cpp), and a
+handle moved with gint_update_positions must hold exactly the batches, atom-image slots, slot-pair
+tables and padded offsets of a handle set up at the new positions (Sec. IV.B: the batch lists
+follow from strict locality, so they are a function of the positions alone).  Covered: unchanged
+lists (new positions only), changed lists (per-batch reuse, partial reuse of a batch's old
+table), a refused update (block list changed: the handle stays as it was), rho/force lists shared
+with the vlocal lists when both use the same batch shape, and the row-layout fallback."""
+import ctypes as C
+import os
+import shutil
+import subprocess
+from contextlib import contextmanager
+
+import numpy as np
+import pytest
+
+from tests._cases import structure
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2501_08697_gb300", "csrc")
+HOST = os.path.join(ROOT, "tests", "host")
+
+
+def _cuda_include():
+    for d in (os.environ.get("CUDA_HOME"), "/usr/local/cuda"):
+        if d and os.path.exists(os.path.join(d, "include", "cuda_runtime.h")):
+            return os.path.join(d, "include")
+    return None
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    inc = _cuda_include()
+    if shutil.which("g++") is None or inc is None:
+        pytest.skip("needs g++ and the CUDA headers")
+    out = tmp_path_factory.mktemp("hostsetup")
+    so = str(out / "libgint_host.so")
+    srcs = [os.path.join(CSRC, "gint_setup.cpp"), os.path.join(HOST, "cuda_stub.cpp"), os.path.join(HOST, "inspect.cpp")]
+    # -Bsymbolic: the set-up code calls these stand-ins even where the process has loaded the CUDA
+    # runtime already (through torch)
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-Wl,-Bsymbolic", "-I", inc, "-I", CSRC,
+                           "-I", os.path.join(ROOT, "include"), *srcs, "-o", so, "-lpthread"])
+    from paper_2501_08697_gb300 import gint as G
+    L = C.CDLL(so)
+    P, vp, i32, d = C.POINTER, C.c_void_p, C.c_int, C.c_double
+    L.gint_setup.argtypes = [P(vp), P(d), i32, P(i32), P(d), i32, P(G._Species), P(i32), P(G._Options)]
+    L.gint_get_info.argtypes = [vp, P(G._Info)]
+    L.gint_update_positions.argtypes = [vp, P(d)]
+    L.gint_destroy.argtypes = [vp]
+    L.gint_block_layout.argtypes = [vp, P(C.c_int64), P(C.c_int64), P(P(C.c_int32)), P(P(C.c_int64))]
+    L.gint_last_error.restype = C.c_char_p
+    L.inspect_compare.argtypes = [vp, vp]
+    L.inspect_summary.argtypes = [vp, i32, P(C.c_longlong)]
+    for n in ("gint_setup", "gint_get_info", "gint_update_positions", "gint_destroy", "gint_block_layout",
+              "inspect_compare"):
+        getattr(L, n).restype = C.c_int
+    return L
+
+
+@contextmanager
+def host_lib(L):
+    """gint.py's marshalling over the host build (the module's library is put back after)."""
+    from paper_2501_08697_gb300 import gint as G
+    keep = G._lib
+    G._lib = L
+    try:
+        yield G
+    finally:
+        G._lib = keep
+
+
+def _summary(L, h, w):
+    out = (C.c_longlong * 6)()
+    L.inspect_summary(h._ptr, w, out)
+    return dict(zip(("batches", "slots", "entries", "padn", "shared", "max_k"), list(out)))
+
+
+CASES = [("si8", (4, 4, 8)), ("si64", (4, 4, 8)), ("si64", (4, 4, 4)), ("water8", (4, 4, 8)),
+         ("si16_strained", (4, 4, 4)), ("si8_2d", (4, 4, 8)), ("h64_dense", (4, 4, 8))]
+
+
+@pytest.mark.parametrize("name,batch", CASES)
+def test_update_equals_fresh_setup(lib, name, batch):
+    st = structure(name)
+    rng = np.random.default_rng(2501)
+    with host_lib(lib) as G:
+        h = G.setup_structure(st, batch=batch, batch_rho=(4, 4, 8))
+        cur, moved = st.tau, 0
+        for sigma in (0.0, 1e-6, 0.01, 0.05, 0.05, 0.01):
+            tau = st.tau + rng.normal(0.0, sigma, st.tau.shape)
+            fresh = G.setup_structure(st, batch=batch, batch_rho=(4, 4, 8), tau=tau)
+            if np.array_equal(fresh.layout()[0], h.layout()[0]):
+                G.gint_update_positions(h, tau)
+                assert lib.inspect_compare(h._ptr, fresh._ptr) == 0, (name, sigma)
+                cur, moved = tau, moved + 1
+            else:
+                # the block list changed: refused, and the handle keeps its lists
+                with pytest.raises(G.GintError) as e:
+                    G.gint_update_positions(h, tau)
+                assert e.value.code == G.GINT_ESTATE
+                before = G.setup_structure(st, batch=batch, batch_rho=(4, 4, 8), tau=cur)
+                assert lib.inspect_compare(h._ptr, before._ptr) == 0, (name, sigma)
+                before.close()
+            fresh.close()
+        assert moved >= 2
+        h.close()
+
+
+def test_rho_lists_shared_with_vlocal(lib):
+    """Same batch shape: the rho/force set is the vlocal set (and its own slot-pair offsets) when
+    every vlocal batch fits the padded layout; another shape or a wider batch builds its own."""
+    with host_lib(lib) as G:
+        for name in ("si8", "si64"):       # an ideal crystal, and one with displaced atoms
+            h = G.setup_structure(structure(name), batch=(4, 4, 8), batch_rho=(4, 4, 8))
+            v, r = _summary(lib, h, 0), _summary(lib, h, 1)
+            if name == "si8" or v["max_k"] <= 256:
+                assert r["shared"] == 1 and r["padn"] == 1
+                assert (v["batches"], v["slots"], v["entries"]) == (r["batches"], r["slots"], r["entries"])
+            else:
+                assert r["shared"] == 0 and r["batches"] >= v["batches"]
+            h.close()
+        st = structure("si64")
+        h = G.setup_structure(st, batch=(4, 4, 4), batch_rho=(4, 4, 8))
+        assert _summary(lib, h, 1)["shared"] == 0
+        # the comparison sees a change of positions alone
+        tau = st.tau + np.random.default_rng(3).normal(0.0, 1e-3, st.tau.shape)
+        g = G.setup_structure(st, batch=(4, 4, 4), batch_rho=(4, 4, 8), tau=tau)
+        assert lib.inspect_compare(h._ptr, g._ptr) != 0
+        g.close()
+        h.close()

@@ -36,9 +36,9 @@ struct gint_batch_s {
     Plan plan[3];                    // combined plans: [0] vlocal (batches <= 192 orbitals),
                                      // [1] rho, [2] vlocal of structures with larger batches
     int max_nb_v[3] = {0, 0, 0};
-    void *d_mem[22] = {nullptr};    // [3w..3w+2] batches, slots, tables; [9] splines; [12+w] CTA ranges;
+    void *d_mem[25] = {nullptr};    // [3w..3w+2] batches, slots, tables; [9] splines; [12+w] CTA ranges;
                                      // [15+2w], [16+2w] padded K offsets and split-store tables;
-                                     // [21] |phi| envelopes
+                                     // [21] |phi| envelopes; [22+w] tensor-core slot records
     SInfo *d_sinfo = nullptr;
     int *d_status = nullptr;
     float *d_amax = nullptr;         // [2 * nstruct]: max |V| and max |DM| of each entry (fp16 path)
@@ -195,6 +195,7 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
     for (int w = 0; w < 3; ++w) {
         std::vector<Batch> bat;
         std::vector<Slot> sl;
+        std::vector<TSlot> tsl;
         std::vector<int> tbl, koff, tbl2;
         std::vector<int> seg{0};
         const int src = w == 1 ? 1 : 0;
@@ -212,6 +213,16 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
             for (Slot S : bs.slots) {
                 S.species = remap[i][S.species];
                 sl.push_back(S);
+                TSlot T;
+                T.atom = S.atom;
+                T.species = S.species;
+                T.orb_off = S.orb_off;
+                T.norb = S.norb;
+                for (int c = 0; c < 3; ++c) {
+                    T.dh[c] = S.dh[c];
+                    T.dl[c] = S.dl[c];
+                }
+                tsl.push_back(T);
             }
             tbl.insert(tbl.end(), bs.tbl.begin(), bs.tbl.end());
             koff.insert(koff.end(), bs.koff.begin(), bs.koff.end());
@@ -221,6 +232,7 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
         }
         if ((e = upload_vec(&b->d_mem[3 * w + 0], bat)) != cudaSuccess ||
             (e = upload_vec(&b->d_mem[3 * w + 1], sl)) != cudaSuccess ||
+            (e = upload_vec(&b->d_mem[22 + w], tsl)) != cudaSuccess ||
             (e = upload_vec(&b->d_mem[3 * w + 2], tbl)) != cudaSuccess ||
             (e = upload_vec(&b->d_mem[15 + 2 * w], koff)) != cudaSuccess ||
             (e = upload_vec(&b->d_mem[16 + 2 * w], tbl2)) != cudaSuccess) {
@@ -240,6 +252,7 @@ extern "C" gint_status gint_batch_create(gint_batch *out, int nstruct, const gin
         p.nseg = (int)seg.size() - 1;
         p.batches = (const Batch *)b->d_mem[3 * w + 0];
         p.slots = (const Slot *)b->d_mem[3 * w + 1];
+        p.tslots = (const TSlot *)b->d_mem[22 + w];
         p.tbl = (const int *)b->d_mem[3 * w + 2];
         p.koff = (const int *)b->d_mem[15 + 2 * w];
         p.tbl2 = (const int *)b->d_mem[16 + 2 * w];

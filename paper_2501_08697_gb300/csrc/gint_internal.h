@@ -37,7 +37,8 @@ struct Batch {
     int i0, j0, k0;
     int dims;                      // n1 | n2 << 8 | n3 << 16 | structure id << 24
     int slot0, nslots, nb;
-    int tbl;                       // first entry of this batch's nslots x nslots pair table
+    int tbl;                       // first entry of this batch's nslots x nslots pair tables
+                                   //   (BatchSet::tbl in tbl_index order, tbl2 row-major)
 };
 
 // An atom image seen by a batch.  d0 = (grid point (i0,j0,k0)) - (tau_I + R_a), Cartesian,
@@ -45,6 +46,13 @@ struct Batch {
 struct Slot {
     int atom, species, orb_off, norb;
     double d0[3];
+    float dh[3], dl[3];
+};
+
+// The fields of a Slot that the tensor-core kernels read, as a 40-byte record of its own array
+// (a batch's records then span 5/8 of the memory sectors of its Slot records).
+struct TSlot {
+    int atom, species, orb_off, norb;
     float dh[3], dl[3];
 };
 
@@ -87,6 +95,7 @@ struct Plan {
     const float *env;              // per species and interval i: a bound on |phi| at r >= i dr
     const Batch *batches;
     const Slot *slots;
+    const TSlot *tslots;           // the same atom images, the tensor-core kernels' fields
     const int *tbl;                // (block offset << 1 | canonical) or -1 if no block
     const int *koff;               // per slot: padded K column (density kernel)
     const int *tbl2;               // per slot pair: split density-matrix block offset or -1
@@ -164,12 +173,21 @@ struct KeyIndex {
     }
 };
 
+// Entry of slot pair (a, b) in a batch's ns x ns slot-pair table (Batch::tbl): the upper
+// triangle a <= b first, row by row, then the strictly lower triangle row by row, so that the
+// tensor-core scatter, which reads only pairs a <= b, reads one contiguous range.
+__host__ __device__ inline int tbl_index(int a, int b, int ns)
+{
+    return a <= b ? a * ns - a * (a - 1) / 2 + (b - a) : ns * (ns + 1) / 2 + a * (a - 1) / 2 + b;
+}
+
 struct BatchSet {
     int dims[3] = {0, 0, 0};
     hvec<Batch> batches;
     hvec<Slot> slots;
     hvec<int> slot_img;              // 3 per slot: image n of the slot's atom
-    hvec<int> tbl;
+    hvec<int> tbl;                   // per slot pair (a, b), at tbl_index(a, b, ns): block
+                                     //   offset << 1 | canonical, or -1
     hvec<int> koff;                  // per slot: first column in the padded K layout
     hvec<int> tbl2;                  // per slot pair (b, a): offset of block (b, a) in the split
                                      //   density-matrix store, or -1 (rho/force set only)
@@ -184,6 +202,7 @@ struct BatchSet {
     std::vector<int2> rng;           // cost-balanced CTA ranges of the persistent kernels
     void *d_batches = nullptr, *d_slots = nullptr, *d_tbl = nullptr, *d_rng = nullptr;
     void *d_koff = nullptr, *d_tbl2 = nullptr;
+    void *d_tslots = nullptr;
 };
 
 // Split batches [0, n) into at most nparts contiguous ranges of about equal estimated cost
@@ -267,6 +286,7 @@ inline Plan plan_for(const gint_handle_s *h, int which)
     const BatchSet &b = h->bs[which];
     p.batches = (const Batch *)b.d_batches;
     p.slots = (const Slot *)b.d_slots;
+    p.tslots = (const TSlot *)b.d_tslots;
     p.tbl = (const int *)b.d_tbl;
     p.koff = (const int *)b.d_koff;
     p.tbl2 = (const int *)b.d_tbl2;

@@ -665,15 +665,17 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                     // (b, a) is the partner of block (I_a, I_b, n_b - n_a)
                     for (int ia = 0; ia < A.ns && pt.st == GINT_OK; ++ia)
                         for (int ib = ia; ib < A.ns; ++ib) {
-                            const size_t x = to + (size_t)ia * A.ns + ib, xt = to + (size_t)ib * A.ns + ia;
+                            // x, xt: entries of (a, b) and (b, a) in the vlocal table layout
+                            // (tbl_index), y, yt: in the row-major split-store table
+                            const size_t x = to + tbl_index(ia, ib, A.ns), xt = to + tbl_index(ib, ia, A.ns);
+                            const size_t y = to + (size_t)ia * A.ns + ib, yt = to + (size_t)ib * A.ns + ia;
                             if (om[ia] >= 0 && om[ib] >= 0) {
-                                const size_t ox = (size_t)near->tbl + (size_t)om[ia] * near->nslots + om[ib],
-                                             oxt = (size_t)near->tbl + (size_t)om[ib] * near->nslots + om[ia];
-                                out.tbl[x] = old->tbl[ox];
-                                out.tbl[xt] = old->tbl[oxt];
+                                const int na = near->nslots, a0 = om[ia], b0 = om[ib];
+                                out.tbl[x] = old->tbl[(size_t)near->tbl + tbl_index(a0, b0, na)];
+                                out.tbl[xt] = old->tbl[(size_t)near->tbl + tbl_index(b0, a0, na)];
                                 if (t2) {
-                                    t2[x] = (*old_t2)[ox];
-                                    t2[xt] = (*old_t2)[oxt];
+                                    t2[y] = (*old_t2)[(size_t)near->tbl + (size_t)a0 * na + b0];
+                                    t2[yt] = (*old_t2)[(size_t)near->tbl + (size_t)b0 * na + a0];
                                 }
                                 continue;
                             }
@@ -682,7 +684,7 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                                 pack_key(sa.atom, sb.atom, sb.n[0] - sa.n[0], sb.n[1] - sa.n[1], sb.n[2] - sa.n[2]));
                             if (bi < 0) {
                                 out.tbl[x] = out.tbl[xt] = -1;
-                                if (t2) t2[x] = t2[xt] = -1;
+                                if (t2) t2[y] = t2[yt] = -1;
                                 continue;
                             }
                             if (!canon[bi]) {
@@ -695,8 +697,8 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
                             out.tbl[x] = (int)((offsets[bi] << 1) | canon[bi]);
                             out.tbl[xt] = (int)((offsets[bt] << 1) | canon[bt]);
                             if (t2) {
-                                t2[x] = (*sf)[bi];
-                                t2[xt] = (*sf)[bt];
+                                t2[y] = (*sf)[bi];
+                                t2[yt] = (*sf)[bt];
                             }
                         }
                 }
@@ -1128,7 +1130,8 @@ static void free_dev(gint_handle h)
     void *ptrs[] = {h->d_coef64, h->d_coef32, h->d_partner, h->d_blkoff, h->d_blkrows, h->d_status, h->d_dmsym,
                     h->d_dms, h->d_poff, h->d_red, h->d_hostio, h->bs[0].d_batches, h->bs[0].d_slots, h->bs[0].d_tbl,
                     h->bs[0].d_rng, h->bs[1].d_batches, h->bs[1].d_slots, h->bs[1].d_tbl, h->bs[1].d_rng,
-                    h->bs[0].d_koff, h->bs[0].d_tbl2, h->bs[1].d_koff, h->bs[1].d_tbl2, h->d_soff, h->d_env,
+                    h->bs[0].d_koff, h->bs[0].d_tbl2, h->bs[1].d_koff, h->bs[1].d_tbl2, h->bs[0].d_tslots,
+                    h->bs[1].d_tslots, h->d_soff, h->d_env,
                     h->ks.d_keys, h->ks.d_grp, h->ks.d_pair, h->ks.d_colatom, h->ks.d_orboff, h->ks.d_kvec,
                     h->ks.d_phase, h->d_dm_scratch, h->d_dm_planes, h->d_amax};
     for (void *p : ptrs)
@@ -1138,6 +1141,28 @@ static void free_dev(gint_handle h)
     if (h->io_stream) cudaStreamDestroy(h->io_stream);
 }
 
+// the tensor-core kernels' records of a slot array (the FP64 kernels read the Slot records)
+static std::vector<TSlot> tslots_of(const hvec<Slot> &slots)
+{
+    std::vector<TSlot> t(slots.size());
+    parallel_parts((int64_t)slots.size(), slots.size() < ((size_t)1 << 16) ? 1 : host_threads(),
+                   [&](int64_t a, int64_t b, int) {
+                       for (int64_t i = a; i < b; ++i) {
+                           const Slot &S = slots[i];
+                           TSlot &T = t[i];
+                           T.atom = S.atom;
+                           T.species = S.species;
+                           T.orb_off = S.orb_off;
+                           T.norb = S.norb;
+                           for (int c = 0; c < 3; ++c) {
+                               T.dh[c] = S.dh[c];
+                               T.dl[c] = S.dl[c];
+                           }
+                       }
+                   });
+    return t;
+}
+
 // device arrays of one batch decomposition (replacing any earlier ones)
 static gint_status upload_batchset(gint_handle h, int w)
 {
@@ -1145,7 +1170,7 @@ static gint_status upload_batchset(gint_handle h, int w)
     BatchSet &b = h->bs[w];
     // kernels still queued may read the old arrays
     if (b.d_batches && (e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "synchronise");
-    for (void **p : {&b.d_batches, &b.d_slots, &b.d_tbl, &b.d_rng, &b.d_koff, &b.d_tbl2})
+    for (void **p : {&b.d_batches, &b.d_slots, &b.d_tbl, &b.d_rng, &b.d_koff, &b.d_tbl2, &b.d_tslots})
         if (*p) {
             cudaFree(*p);
             *p = nullptr;
@@ -1155,6 +1180,10 @@ static gint_status upload_batchset(gint_handle h, int w)
     if ((e = upload(&b.d_tbl, b.tbl)) != cudaSuccess) return cuda_fail(e, "upload tables");
     if ((e = upload(&b.d_koff, b.koff)) != cudaSuccess) return cuda_fail(e, "upload K offsets");
     if ((e = upload(&b.d_tbl2, b.tbl2)) != cudaSuccess) return cuda_fail(e, "upload split tables");
+    {
+        const std::vector<TSlot> ts = tslots_of(b.slots);
+        if ((e = upload(&b.d_tslots, ts)) != cudaSuccess) return cuda_fail(e, "upload slots");
+    }
     const int nb = (int)b.batches.size();
     b.rng = segment_ranges(b.batches.data(), {0, nb}, std::max(1, std::min(h->nsm, nb)), w);
     if ((e = upload(&b.d_rng, b.rng)) != cudaSuccess) return cuda_fail(e, "upload CTA ranges");
@@ -1185,6 +1214,9 @@ static gint_status upload_geometry(gint_handle h)
             }
             if (b.slots.empty()) continue;
             e = cudaMemcpy(b.d_slots, b.slots.data(), b.slots.size() * sizeof(Slot), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(e, "update slots");
+            const std::vector<TSlot> ts = tslots_of(b.slots);
+            e = cudaMemcpy(b.d_tslots, ts.data(), ts.size() * sizeof(TSlot), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) return cuda_fail(e, "update slots");
         }
     }
@@ -1508,7 +1540,7 @@ extern "C" gint_status gint_update_positions(gint_handle h, const double *tau)
         if (tmp.relist[w]) {
             // the new lists, with the old device arrays (freed and replaced by upload_geometry);
             // the old host arrays become the storage of the next update
-            void *dev[6] = {o.d_batches, o.d_slots, o.d_tbl, o.d_rng, o.d_koff, o.d_tbl2};
+            void *dev[7] = {o.d_batches, o.d_slots, o.d_tbl, o.d_rng, o.d_koff, o.d_tbl2, o.d_tslots};
             take_storage(h->spare[w], o);
             o = std::move(tmp.bs[w]);
             o.d_batches = dev[0];
@@ -1517,6 +1549,7 @@ extern "C" gint_status gint_update_positions(gint_handle h, const double *tau)
             o.d_rng = dev[3];
             o.d_koff = dev[4];
             o.d_tbl2 = dev[5];
+            o.d_tslots = dev[6];
         } else {
             take_storage(h->spare[w], tmp.bs[w]);
             place_slots(h, o, tau);

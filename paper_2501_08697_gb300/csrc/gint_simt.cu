@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_vlocal_simt(Plan P, const doubl
             Slot S = P.slots[B.slot0 + s];
             sl[s] = {S.atom, S.species, S.orb_off, S.norb, {S.d0[0], S.d0[1], S.d0[2]}};
         }
-        for (int e = tid; e < ns * ns; e += kThreads) tbl[e] = P.tbl[B.tbl + e];
+        for (int e = tid; e < ns * ns; e += kThreads) tbl[e] = P.tbl[B.tbl + tbl_index(e / ns, e % ns, ns)];
         __syncthreads();
         for (int s = tid; s < ns; s += kThreads)
             for (int o = 0; o < sl[s].norb; ++o) {
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             Slot S = P.slots[B.slot0 + s];
             sl[s] = {S.atom, S.species, S.orb_off, S.norb, {S.d0[0], S.d0[1], S.d0[2]}};
         }
-        for (int e = tid; e < ns * ns; e += kThreads) tbl[e] = P.tbl[B.tbl + e];
+        for (int e = tid; e < ns * ns; e += kThreads) tbl[e] = P.tbl[B.tbl + tbl_index(e / ns, e % ns, ns)];
         if (FORCE)
             for (int e = tid; e < 3 * ns; e += kThreads) fsl[e] = 0.0;
         __syncthreads();

@@ -50,7 +50,7 @@ struct PSlot {
     float dh[3], dl[3];
 };
 static_assert(sizeof(PSlot) == 40, "PSlot layout");
-static_assert(offsetof(Slot, dh) == 40 && sizeof(Slot) == 64, "Slot layout");
+static_assert(offsetof(TSlot, dh) == 16 && sizeof(TSlot) == 40, "TSlot layout: copied into PSlot as is");
 
 __device__ __forceinline__ void unpack(int dims, int &n1, int &n2, int &n3)
 {
@@ -115,7 +115,7 @@ __device__ __forceinline__ void load_geom(const Plan &P, const SInfo &SI, const 
                                           int tid, int nthr)
 {
     for (int s = tid; s < B.nslots; s += nthr) {
-        const Slot &S = P.slots[B.slot0 + s];
+        const TSlot &S = P.tslots[B.slot0 + s];
         PSlot q;
         q.species = S.species;
         q.off = S.orb_off;
@@ -156,10 +156,9 @@ __device__ __forceinline__ void geom_async(const Plan &P, const SInfo *sis, cons
     }
     for (int w = tid; w < B.nslots * 5; w += nthr) {
         const int s = w / 5, part = w - 5 * s;
-        const char *src = reinterpret_cast<const char *>(P.slots + B.slot0 + s);
+        const char *src = reinterpret_cast<const char *>(P.tslots + B.slot0 + s);
         char *dst = reinterpret_cast<char *>(ps + s);
-        if (part < 2) cp_async8(dst + 8 * part, src + 8 * part);           // atom .. norb
-        else cp_async8(dst + 8 * part, src + 24 + 8 * part);               // dh, dl
+        cp_async8(dst + 8 * part, src + 8 * part);
     }
     int n1, n2, n3;
     n1 = B.dims & 255;
@@ -541,14 +540,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             const SInfo SIe = sic.get(B, sis);
             double *H = SIe.H;
             const bool small = ns <= kVTbl;
-            const int *tbl = small ? tbls : P.tbl + B.tbl;
+            const int *tbl = P.tbl + B.tbl;
             named_sync(2, kEpi);
             if (small)
                 for (int e = et; e < ns * ns; e += kEpi) {
-                    // the scatter adds only for pairs a <= b (the upper triangle): the rest of
-                    // each table row is not fetched
-                    const int a = e / ns;
-                    tbls[e] = e - a * ns >= a ? __ldg(P.tbl + B.tbl + e) : -1;
+                    // the scatter adds only for pairs a <= b: the upper triangle, which leads the
+                    // table, is fetched, and the rest of the copy (row-major) is -1
+                    const int a = e / ns, b = e - a * ns;
+                    tbls[e] = b >= a ? __ldg(tbl + tbl_index(a, b, ns)) : -1;
                 }
             float bc[3], R;
             if constexpr (S::HALF) {
@@ -557,7 +556,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 batch_sphere(SIe, n1, n2, n3, bc, R);
             }
             for (int s = et; s < ns; s += kEpi) {
-                const Slot &sl = P.slots[B.slot0 + s];
+                const TSlot &sl = P.tslots[B.slot0 + s];
                 const int no = sl.norb, off = sl.orb_off;
                 short ea = 0, eb = 0;
                 if constexpr (S::HALF) {
@@ -614,7 +613,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                         const int ri = info[row0 + r];
                         const int oa = (ri >> 8) & 255;
                         const int rend = min(nrows, r + (ri >> 16) - oa);
-                        const int e = tbl[(ri & 255) * ns + b];
+                        const int a = ri & 255;
+                        const int e = small ? tbls[a * ns + b] : a <= b ? __ldg(tbl + tbl_index(a, b, ns)) : -1;
                         const bool blk = cv && e >= 0;
                         double *base = H + (e >> 1) + (oa - r) * nbo + ob;
                         const int rlim = min(rend, nu - row0 + 1);  // upper triangle: row <= nu
@@ -1065,7 +1065,7 @@ __global__ void __launch_bounds__(kThreadsR, 1)
                 const bool padn = sic.get(B, sis).padn != 0;
                 const int buf = it & 1;
                 const int last = B.slot0 + B.nslots - 1;
-                const int kend = __ldg(P.koff + last) + kpad(P.slots[last].norb);   // padded orbitals
+                const int kend = __ldg(P.koff + last) + kpad(P.tslots[last].norb);   // padded orbitals
                 // N: the orbitals at their padded columns (padded layout) or unpadded
                 const int npad = padn ? (kend + 15) & ~15 : (nb + 15) & ~15;
                 const int ktot = (kend + KC - 1) / KC * KC;

@@ -1,6 +1,8 @@
 // Test-only views of a handle's host arrays: compare two handles (a position update against a
 // fresh set-up at the same positions), and read a decomposition's summary.
+#include <array>
 #include <cmath>
+#include <map>
 #include <cstdio>
 #include <cstring>
 
@@ -62,4 +64,42 @@ extern "C" void inspect_summary(gint_handle a, int w, long long *out)
     out[3] = x.padn;
     out[4] = x.shared;
     out[5] = x.max_k;
+}
+
+// Every slot-pair entry against the block list, looked up here through an ordered map of the
+// block keys: tbl at tbl_index(a, b, ns) holds offset << 1 | canonical of block
+// (I_a, I_b, n_b - n_a), or -1 if there is none, and the rho/force tbl2 (row-major) its
+// split-store offset.  Returns the number of wrong entries.
+extern "C" long long inspect_check_tables(gint_handle h)
+{
+    std::map<std::array<int, 5>, int> blk;
+    const int64_t nblocks = (int64_t)h->keys.size() / 5;
+    for (int64_t b = 0; b < nblocks; ++b) {
+        const int32_t *k = &h->keys[5 * b];
+        blk[{k[0], k[1], k[2], k[3], k[4]}] = (int)b;
+    }
+    long long bad = 0;
+    for (int w = 0; w < 2; ++w) {
+        const BatchSet &s = h->bs[w];
+        for (const Batch &B : s.batches) {
+            const int ns = B.nslots;
+            for (int a = 0; a < ns; ++a)
+                for (int b = 0; b < ns; ++b) {
+                    const size_t sa = (size_t)B.slot0 + a, sb = (size_t)B.slot0 + b;
+                    const int *na = &s.slot_img[3 * sa], *nb = &s.slot_img[3 * sb];
+                    auto it = blk.find({s.slots[sa].atom, s.slots[sb].atom, nb[0] - na[0], nb[1] - na[1], nb[2] - na[2]});
+                    const int bi = it == blk.end() ? -1 : it->second;
+                    int want = -1;
+                    if (bi >= 0) {
+                        const int32_t *k = &h->keys[5 * bi];
+                        auto pt = blk.find({k[1], k[0], -k[2], -k[3], -k[4]});
+                        const bool canon = pt != blk.end() && bi <= pt->second;
+                        want = (int)((h->offsets[bi] << 1) | (canon ? 1 : 0));
+                    }
+                    if (s.tbl[(size_t)B.tbl + tbl_index(a, b, ns)] != want) ++bad;
+                    if (w == 1 && s.tbl2[(size_t)B.tbl + (size_t)a * ns + b] != (bi < 0 ? -1 : h->soff[bi])) ++bad;
+                }
+        }
+    }
+    return bad;
 }

@@ -52,6 +52,8 @@ def lib(tmp_path_factory):
     L.gint_last_error.restype = C.c_char_p
     L.inspect_compare.argtypes = [vp, vp]
     L.inspect_summary.argtypes = [vp, i32, P(C.c_longlong)]
+    L.inspect_check_tables.argtypes = [vp]
+    L.inspect_check_tables.restype = C.c_longlong
     for n in ("gint_setup", "gint_get_info", "gint_update_positions", "gint_destroy", "gint_block_layout",
               "inspect_compare"):
         getattr(L, n).restype = C.c_int
@@ -86,6 +88,7 @@ def test_update_equals_fresh_setup(lib, name, batch):
     rng = np.random.default_rng(2501)
     with host_lib(lib) as G:
         h = G.setup_structure(st, batch=batch, batch_rho=(4, 4, 8))
+        assert lib.inspect_check_tables(h._ptr) == 0
         cur, moved = st.tau, 0
         for sigma in (0.0, 1e-6, 0.01, 0.05, 0.05, 0.01):
             tau = st.tau + rng.normal(0.0, sigma, st.tau.shape)
@@ -104,6 +107,7 @@ def test_update_equals_fresh_setup(lib, name, batch):
                 before.close()
             fresh.close()
         assert moved >= 2
+        assert lib.inspect_check_tables(h._ptr) == 0
         h.close()
 
 

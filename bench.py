@@ -312,6 +312,26 @@ def run_ours(args, rank, world):
                             "batch_vlocal": list(vbatch(p_)), "err_vs_oracle": errors(p_)}
             h2.close()
 
+    # position updates (host lists and tables, re-upload of what changed): seeded N(0, 0.05 bohr)
+    # moves of every atom, alternating between two moved geometries, on a handle of its own
+    upd = None
+    if extras:
+        h3 = G.setup_structure(st, batch=batch, batch_rho=tuple(args.batch_rho))
+        rng = np.random.default_rng(2501)
+        taus = [st.tau + rng.normal(0.0, 0.05, st.tau.shape) for _ in range(2)]
+        ts, refused = [], 0
+        for i in range(8):
+            t0 = time.perf_counter()
+            try:
+                G.gint_update_positions(h3, taus[i % 2])
+            except G.GintError:
+                refused += 1
+                continue
+            ts.append(time.perf_counter() - t0)
+        h3.close()
+        upd = {"sigma_bohr": 0.05, "median_ms": 1e3 * statistics.median(ts) if ts else None,
+               "first_ms": 1e3 * ts[0] if ts else None, "updates": len(ts), "refused": refused}
+
     # end to end through the C ABI with host buffers (copies inside the timed region)
     pin = lambda n: torch.empty(n, dtype=torch.float64).pin_memory()
     Vh, DMh = pin(npts), pin(info["nvalues"])
@@ -348,7 +368,8 @@ def run_ours(args, rank, world):
         "config": {"workload": workload_name(args.workload, st),
                    "prec": prec, "batch_vlocal": list(batch), "batch_rho": list(args.batch_rho),
                    "step": "vlocal + rho_force + charge + trace", "l2": "flushed between steps (512 MiB write)",
-                   "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 2),
+                   "parallelism": f"replicas x{world}", "setup_s": round(setup_s, 3),
+                   "position_update": upd,
                    "nbatches": info["nbatches"], "nbatches_rho": info["nbatches_rho"]},
         "kernel_ms": {"vlocal": tv * 1e3, "rho_force": tr * 1e3, "checks": tc * 1e3},
         "roofline": roofline,

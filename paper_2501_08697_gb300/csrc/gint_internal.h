@@ -235,6 +235,7 @@ struct gint_handle_s {
     gint::BatchSet bs[2];            // [0] vlocal batches, [1] rho/force batches
     gint::BatchSet spare[2];         // host arrays of the lists a position update replaced, kept
                                      //   (allocated and touched) for the next update to write into
+    gint::hvec<gint::TSlot> tslot_stage;  // host staging of the tensor-core slot records (upload)
     bool relist[2] = {false, false}; // a position update changed that decomposition's lists
     bool flops_stale = false;        // info.flops_useful predates the last position update
     std::vector<float4> coef32_host; // spline records, as uploaded

@@ -204,6 +204,19 @@ static inline void batch_origin(const BatchGeom &bg, int i0, int j0, int k0, dou
 // parts concatenated in order (the result does not depend on the number of parts).
 // With `old` (a position update): if every batch keeps its atom-image list, *same is set and
 // out.slots receives old's slots at the new positions (nothing else of out is filled).
+// Resizes a host array to n elements without initialising them; storage that must grow gets
+// an eighth more, so that the next position updates (lists of about the same size, written
+// into the storage this one replaces) need no new memory.
+template <class V>
+static void fit(V &v, size_t n)
+{
+    if (v.capacity() < n) {
+        v.clear();
+        v.reserve(n + n / 8);
+    }
+    v.resize(n);
+}
+
 // Accepted batches of one host thread's rows of top-level cells, in order, with their sorted
 // atom-image lists.
 struct BatchAcc {
@@ -547,16 +560,16 @@ static gint_status build_batches(gint_handle h, const double *tau, const Geo &G,
         set_error("gint_setup: too many batches / table entries");
         return GINT_EINVAL;
     }
-    out.batches.resize(bat0[nparts]);
-    out.slots.resize(sl0[nparts]);
-    out.slot_img.resize(3 * sl0[nparts]);
-    out.koff.resize(sl0[nparts]);
-    out.tbl.resize(tb0[nparts]);
+    fit(out.batches, bat0[nparts]);
+    fit(out.slots, sl0[nparts]);
+    fit(out.slot_img, 3 * sl0[nparts]);
+    fit(out.koff, sl0[nparts]);
+    fit(out.tbl, tb0[nparts]);
     // slot-pair offsets into the split store: this set's own (rho/force), or the rho/force set's
     // when it shares these lists (written next to the vlocal tables)
     const std::vector<int> *sf = soff ? soff : (share && share->ok ? share->soff : nullptr);
     hvec<int> *t2v = soff ? &out.tbl2 : (sf ? share->tbl2 : nullptr);
-    if (t2v) t2v->resize(tb0[nparts]);
+    if (t2v) fit(*t2v, tb0[nparts]);
     int *const t2 = t2v ? t2v->data() : nullptr;
     const hvec<int> *old_t2 = !old ? nullptr : soff ? &old->tbl2 : (sf && share->old ? &share->old->tbl2 : nullptr);
     // batches of old by top-level cell: the batches a cell was split into are consecutive
@@ -738,7 +751,7 @@ static BatchGeom batch_geom(const gint_handle_s *h)
 template <class V>
 static void par_copy(V &dst, const V &src)
 {
-    dst.resize(src.size());
+    fit(dst, src.size());
     parallel_parts((int64_t)src.size(), src.size() < ((size_t)1 << 16) ? 1 : host_threads(),
                    [&](int64_t a, int64_t b, int) { std::copy(src.begin() + a, src.begin() + b, dst.begin() + a); });
 }
@@ -1141,10 +1154,12 @@ static void free_dev(gint_handle h)
     if (h->io_stream) cudaStreamDestroy(h->io_stream);
 }
 
-// the tensor-core kernels' records of a slot array (the FP64 kernels read the Slot records)
-static std::vector<TSlot> tslots_of(const hvec<Slot> &slots)
+// the tensor-core kernels' records of a slot array (the FP64 kernels read the Slot records),
+// written into the handle's staging array
+static const hvec<TSlot> &tslots_of(gint_handle h, const hvec<Slot> &slots)
 {
-    std::vector<TSlot> t(slots.size());
+    hvec<TSlot> &t = h->tslot_stage;
+    fit(t, slots.size());
     parallel_parts((int64_t)slots.size(), slots.size() < ((size_t)1 << 16) ? 1 : host_threads(),
                    [&](int64_t a, int64_t b, int) {
                        for (int64_t i = a; i < b; ++i) {
@@ -1181,8 +1196,7 @@ static gint_status upload_batchset(gint_handle h, int w)
     if ((e = upload(&b.d_koff, b.koff)) != cudaSuccess) return cuda_fail(e, "upload K offsets");
     if ((e = upload(&b.d_tbl2, b.tbl2)) != cudaSuccess) return cuda_fail(e, "upload split tables");
     {
-        const std::vector<TSlot> ts = tslots_of(b.slots);
-        if ((e = upload(&b.d_tslots, ts)) != cudaSuccess) return cuda_fail(e, "upload slots");
+        if ((e = upload(&b.d_tslots, tslots_of(h, b.slots))) != cudaSuccess) return cuda_fail(e, "upload slots");
     }
     const int nb = (int)b.batches.size();
     b.rng = segment_ranges(b.batches.data(), {0, nb}, std::max(1, std::min(h->nsm, nb)), w);
@@ -1215,7 +1229,7 @@ static gint_status upload_geometry(gint_handle h)
             if (b.slots.empty()) continue;
             e = cudaMemcpy(b.d_slots, b.slots.data(), b.slots.size() * sizeof(Slot), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) return cuda_fail(e, "update slots");
-            const std::vector<TSlot> ts = tslots_of(b.slots);
+            const hvec<TSlot> &ts = tslots_of(h, b.slots);
             e = cudaMemcpy(b.d_tslots, ts.data(), ts.size() * sizeof(TSlot), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) return cuda_fail(e, "update slots");
         }

@@ -103,3 +103,34 @@ extern "C" long long inspect_check_tables(gint_handle h)
     }
     return bad;
 }
+
+namespace gint {
+std::vector<int2> segment_ranges(const Batch *b, const std::vector<int> &seg, int npart, int kind);
+}
+
+// Batches of decomposition w: out[4 i .. 4 i + 3] = points, orbitals, slots, first slot.
+extern "C" long long inspect_batches(gint_handle h, int w, int *out, long long cap)
+{
+    const BatchSet &s = h->bs[w];
+    const long long n = (long long)s.batches.size();
+    for (long long i = 0; i < n && 4 * i + 3 < cap; ++i) {
+        const Batch &B = s.batches[i];
+        out[4 * i] = (B.dims & 255) * ((B.dims >> 8) & 255) * ((B.dims >> 16) & 255);
+        out[4 * i + 1] = B.nb;
+        out[4 * i + 2] = B.nslots;
+        out[4 * i + 3] = B.slot0;
+    }
+    return n;
+}
+
+// The persistent kernels' CTA ranges for the batches of decomposition w cut into the segments
+// seg[0..nseg]: out[2 (g npart + c)] = first, last + 1 of CTA c in segment g.
+extern "C" void inspect_segment_ranges(gint_handle h, int w, const int *seg, int nseg, int npart, int *out)
+{
+    const std::vector<int> sv(seg, seg + nseg + 1);
+    const std::vector<int2> r = segment_ranges(h->bs[w].batches.data(), sv, npart, w);
+    for (size_t i = 0; i < r.size(); ++i) {
+        out[2 * i] = r[i].x;
+        out[2 * i + 1] = r[i].y;
+    }
+}

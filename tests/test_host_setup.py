@@ -5,7 +5,8 @@ tables and padded offsets of a handle set up at the new positions (Sec. IV.B: th
 follow from strict locality, so they are a function of the positions alone).  Covered: unchanged
 lists (new positions only), changed lists (per-batch reuse, partial reuse of a batch's old
 table), a refused update (block list changed: the handle stays as it was), rho/force lists shared
-with the vlocal lists when both use the same batch shape, and the row-layout fallback."""
+with the vlocal lists when both use the same batch shape, and the row-layout fallback; and the
+cost-balanced CTA ranges of the persistent kernels."""
 import ctypes as C
 import os
 import shutil
@@ -132,4 +133,50 @@ def test_rho_lists_shared_with_vlocal(lib):
         g = G.setup_structure(st, batch=(4, 4, 4), batch_rho=(4, 4, 8), tau=tau)
         assert lib.inspect_compare(h._ptr, g._ptr) != 0
         g.close()
+        h.close()
+
+
+def test_cta_ranges_cover_and_balance(lib):
+    """The persistent kernels' CTA ranges (segment_ranges): within each segment of the batch list
+    the non-empty ranges tile it in order, one per CTA, with min(CTAs, batches) of them; each
+    range's estimated cost is within one batch's cost of the segment's mean per range; and the
+    CTAs that get work rotate from one segment to the next, so short segments land on different
+    CTAs."""
+    lib.inspect_batches.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_longlong]
+    lib.inspect_batches.restype = C.c_longlong
+    lib.inspect_segment_ranges.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+    npart = 152
+    with host_lib(lib) as G:
+        h = G.setup_structure(structure("si64"), batch=(4, 4, 8), batch_rho=(4, 4, 8))
+        for w in (0, 1):
+            n = lib.inspect_batches(h._ptr, w, None, 0)
+            buf = np.zeros(4 * n, np.int32)
+            lib.inspect_batches(h._ptr, w, buf.ctypes.data, 4 * n)
+            pts, nb = buf.reshape(n, 4)[:, 0].astype(float), buf.reshape(n, 4)[:, 1].astype(float)
+            # the cost model of the partition (relative cycles per batch, one form per kernel)
+            cost = (2000.0 + 2.6 * pts * nb + 0.65 * nb * nb) if w == 0 else (4000.0 + 4.0 * pts * nb + nb * nb)
+            for seg in ([0, n], [0, n // 3, n // 3 + 5, n], [0, 7, 20, 30, n]):
+                nseg = len(seg) - 1
+                out = np.zeros(2 * nseg * npart, np.int32)
+                sa = np.array(seg, np.int32)
+                lib.inspect_segment_ranges(h._ptr, w, sa.ctypes.data, nseg, npart, out.ctypes.data)
+                r = out.reshape(nseg, npart, 2)
+                used = []
+                for g in range(nseg):
+                    lo, hi = seg[g], seg[g + 1]
+                    ranges = sorted((int(a), int(b), c) for c, (a, b) in enumerate(r[g]) if b > a)
+                    assert len(ranges) == min(npart, hi - lo)
+                    assert ranges[0][0] == lo and ranges[-1][1] == hi
+                    assert all(ranges[i][1] == ranges[i + 1][0] for i in range(len(ranges) - 1))
+                    # ranges are dealt to CTAs in order, starting where the last segment stopped
+                    ctas = [c for _, _, c in ranges]
+                    assert ctas == [(ctas[0] + i) % npart for i in range(len(ctas))]
+                    if used:
+                        assert ctas[0] == (used[-1][-1] + 1) % npart
+                    used.append(ctas)
+                    if hi - lo >= 4 * npart:
+                        mean = cost[lo:hi].sum() / len(ranges)
+                        cmax = cost[lo:hi].max()
+                        for a, b, _ in ranges:
+                            assert abs(cost[a:b].sum() - mean) <= cmax * (1 + 1e-9), (w, g, a, b)
         h.close()

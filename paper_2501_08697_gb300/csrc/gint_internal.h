@@ -203,6 +203,8 @@ struct BatchSet {
     void *d_batches = nullptr, *d_slots = nullptr, *d_tbl = nullptr, *d_rng = nullptr;
     void *d_koff = nullptr, *d_tbl2 = nullptr;
     void *d_tslots = nullptr;
+    size_t d_cap[7] = {0, 0, 0, 0, 0, 0, 0};   // bytes allocated for d_batches, d_slots, d_tbl, d_rng,
+                                             //   d_koff, d_tbl2, d_tslots
 };
 
 // Split batches [0, n) into at most nparts contiguous ranges of about equal estimated cost

@@ -1138,6 +1138,25 @@ static cudaError_t upload(void **dst, const Vec &v)
     return e;
 }
 
+// Copies v into the device array *dst of *cap bytes; an array v does not fit is replaced by one
+// with an eighth of headroom, so that position updates (lists of about the same size) reuse it.
+template <class Vec>
+static cudaError_t upload_fit(void **dst, size_t *cap, const Vec &v)
+{
+    using T = typename Vec::value_type;
+    const size_t bytes = v.size() * sizeof(T);
+    if (!*dst || *cap < bytes) {
+        if (*dst) cudaFree(*dst);
+        *dst = nullptr;
+        *cap = 0;
+        const size_t want = std::max<size_t>(sizeof(T), bytes + bytes / 8);
+        cudaError_t e = cudaMalloc(dst, want);
+        if (e != cudaSuccess) return e;
+        *cap = want;
+    }
+    return bytes ? cudaMemcpy(*dst, v.data(), bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+}
+
 static void free_dev(gint_handle h)
 {
     void *ptrs[] = {h->d_coef64, h->d_coef32, h->d_partner, h->d_blkoff, h->d_blkrows, h->d_status, h->d_dmsym,
@@ -1183,24 +1202,18 @@ static gint_status upload_batchset(gint_handle h, int w)
 {
     cudaError_t e;
     BatchSet &b = h->bs[w];
-    // kernels still queued may read the old arrays
+    // kernels still queued may read the arrays being replaced or overwritten
     if (b.d_batches && (e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "synchronise");
-    for (void **p : {&b.d_batches, &b.d_slots, &b.d_tbl, &b.d_rng, &b.d_koff, &b.d_tbl2, &b.d_tslots})
-        if (*p) {
-            cudaFree(*p);
-            *p = nullptr;
-        }
-    if ((e = upload(&b.d_batches, b.batches)) != cudaSuccess) return cuda_fail(e, "upload batches");
-    if ((e = upload(&b.d_slots, b.slots)) != cudaSuccess) return cuda_fail(e, "upload slots");
-    if ((e = upload(&b.d_tbl, b.tbl)) != cudaSuccess) return cuda_fail(e, "upload tables");
-    if ((e = upload(&b.d_koff, b.koff)) != cudaSuccess) return cuda_fail(e, "upload K offsets");
-    if ((e = upload(&b.d_tbl2, b.tbl2)) != cudaSuccess) return cuda_fail(e, "upload split tables");
-    {
-        if ((e = upload(&b.d_tslots, tslots_of(h, b.slots))) != cudaSuccess) return cuda_fail(e, "upload slots");
-    }
+    size_t *c = b.d_cap;
+    if ((e = upload_fit(&b.d_batches, &c[0], b.batches)) != cudaSuccess) return cuda_fail(e, "upload batches");
+    if ((e = upload_fit(&b.d_slots, &c[1], b.slots)) != cudaSuccess) return cuda_fail(e, "upload slots");
+    if ((e = upload_fit(&b.d_tbl, &c[2], b.tbl)) != cudaSuccess) return cuda_fail(e, "upload tables");
+    if ((e = upload_fit(&b.d_koff, &c[4], b.koff)) != cudaSuccess) return cuda_fail(e, "upload K offsets");
+    if ((e = upload_fit(&b.d_tbl2, &c[5], b.tbl2)) != cudaSuccess) return cuda_fail(e, "upload split tables");
+    if ((e = upload_fit(&b.d_tslots, &c[6], tslots_of(h, b.slots))) != cudaSuccess) return cuda_fail(e, "upload slots");
     const int nb = (int)b.batches.size();
     b.rng = segment_ranges(b.batches.data(), {0, nb}, std::max(1, std::min(h->nsm, nb)), w);
-    if ((e = upload(&b.d_rng, b.rng)) != cudaSuccess) return cuda_fail(e, "upload CTA ranges");
+    if ((e = upload_fit(&b.d_rng, &c[3], b.rng)) != cudaSuccess) return cuda_fail(e, "upload CTA ranges");
     return GINT_OK;
 }
 
@@ -1552,11 +1565,15 @@ extern "C" gint_status gint_update_positions(gint_handle h, const double *tau)
         h->relist[w] = tmp.relist[w];
         BatchSet &o = h->bs[w];
         if (tmp.relist[w]) {
-            // the new lists, with the old device arrays (freed and replaced by upload_geometry);
+            // the new lists, with the old device arrays (refilled, or replaced where too small, by
+            // upload_geometry);
             // the old host arrays become the storage of the next update
             void *dev[7] = {o.d_batches, o.d_slots, o.d_tbl, o.d_rng, o.d_koff, o.d_tbl2, o.d_tslots};
+            size_t cap[7];
+            memcpy(cap, o.d_cap, sizeof(cap));
             take_storage(h->spare[w], o);
             o = std::move(tmp.bs[w]);
+            memcpy(o.d_cap, cap, sizeof(cap));
             o.d_batches = dev[0];
             o.d_slots = dev[1];
             o.d_tbl = dev[2];

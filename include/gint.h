@@ -159,7 +159,8 @@ gint_status gint_get_info(gint_handle h, gint_info_t *info);
  * list keeps its slot-pair tables, one whose list changed takes the entries of the atom images
  * it kept from its old table and looks the others up.  A decomposition whose lists are all
  * unchanged keeps its device arrays and tables and receives the new slot positions only, one
- * whose lists changed is re-uploaded.  The result equals a handle set up at the new positions.
+ * whose lists changed is copied into its device arrays again (an array too small for the new
+ * lists is replaced by a larger one).  The result equals a handle set up at the new positions.
  * The handle keeps the host arrays an update replaced, as storage for the next one (host memory
  * about twice the lists').  Blocking: the call synchronises with the device before
  * replacing arrays.  A multi-structure job (gint_batch_create) copies the lists when it is
